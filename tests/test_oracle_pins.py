@@ -1,0 +1,298 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mechanics,
+independent of the oracle's own formulas (closed forms, energy derivatives,
+conservation laws, exact symmetries, brute force, Green-Kubo)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02990_gb300 import inputs
+
+RC = 2.0 ** (1.0 / 6.0)
+
+
+def bulk(N, **kw):
+    return oracle.Bulk(n=N, L=tuple(inputs.bulk_box(N)), **kw)
+
+
+# ---------------------------------------------------------------- Eq. 6 ----
+def test_wca_closed_forms():
+    # phi(sigma) = eps (the shift is +eps), F(sigma) = 24 eps/sigma.
+    phi1, f1 = oracle.wca(1.0)
+    assert phi1 == pytest.approx(1.0, abs=1e-15)
+    assert f1 * 1.0 == pytest.approx(24.0, abs=1e-13)
+    # Continuity at r_c: phi -> 0 and F -> 0 from below; zero beyond.
+    phic, fc = oracle.wca(RC * RC * (1 - 1e-12))
+    assert abs(phic) < 1e-10 and abs(fc) < 1e-9
+    assert oracle.wca(RC * RC * 1.0001) == (0.0, 0.0)
+    # Minimum of the LJ part sits at r_c: phi(r_c) - 1 = -eps.
+    # F = -dphi/dr by central differences at several r.
+    for r in (0.9, 0.97, 1.05, 1.1):
+        h = 1e-6
+        dphi = (oracle.wca((r + h) ** 2)[0] - oracle.wca((r - h) ** 2)[0]) / (2 * h)
+        assert oracle.wca(r * r)[1] * r == pytest.approx(-dphi, rel=1e-7)
+
+
+# ------------------------------------------------ forces, images, virial ----
+@pytest.mark.parametrize("N", [108, 256])
+def test_cells_equal_brute_force_with_le_offsets(N):
+    b = bulk(N)
+    st = inputs.jittered_states(N, 3, seed=11, amp=0.12)
+    rng = np.random.default_rng(5)
+    for k in range(3):
+        delta = rng.uniform(-0.5, 0.5) * b.L[0]
+        Fc, Wc, Uc = oracle.forces(b, st[k], delta, brute=False)
+        Fb, Wb, Ub = oracle.forces(b, st[k], delta, brute=True)
+        assert np.abs(Fc - Fb).max() <= 1e-12 * np.abs(Fb).max()
+        assert np.allclose(Wc, Wb, rtol=1e-12, atol=1e-12)
+        assert Uc == pytest.approx(Ub, rel=1e-12)
+        assert Uc > 0  # jitter of 0.12 creates overlaps
+
+
+def test_two_atoms_across_the_le_boundary():
+    """Atom j sits near the bottom face; its image above is shifted by +delta
+    in x.  The only interacting image is at (x_j + delta, y_j + Ly)."""
+    b = bulk(256)
+    L = b.L[0]
+    delta = 0.3 * L
+    # a 2-atom system in the box of the N=256 state point
+    b2 = oracle.Bulk(n=2, L=b.L, use_cells=False)
+    s = np.zeros((6, 2))
+    xi, yi = 0.1, 0.5 * L - 0.1
+    xj, yj = xi - delta + 0.5, -0.5 * L + 0.3
+    s[0] = [xi, xj]; s[1] = [yi, yj]; s[2] = [0.0, 0.05]
+    F, W, U = oracle.forces(b2, s, delta)
+    d = np.array([xi - (xj + delta), yi - (yj + L), 0.0 - 0.05])  # (-0.5, -0.4, -0.05)
+    r2 = d @ d
+    phi, for_ = oracle.wca(r2)
+    assert r2 < RC * RC
+    assert np.allclose(F[:, 0], for_ * d, rtol=1e-13)
+    assert np.allclose(F[:, 1], -for_ * d, rtol=1e-13)
+    assert U == pytest.approx(phi, rel=1e-14)
+    assert W[3] == pytest.approx(for_ * d[0] * d[1], rel=1e-13)
+    # with delta = 0 the same pair is out of range
+    F0, _, U0 = oracle.forces(b2, s, 0.0)
+    assert U0 == 0.0
+
+
+def test_newton_third_law_and_cluster_virial():
+    b = bulk(256)
+    st = inputs.jittered_states(256, 1, seed=3, amp=0.12)[0]
+    F, W, U = oracle.forces(b, st, 0.37 * b.L[0])
+    assert np.abs(F.sum(axis=1)).max() < 1e-10 * np.abs(F).max()
+    # Isolated cluster in a big box: W_ab = sum_i r_i,a F_i,b exactly.
+    rng = np.random.default_rng(2)
+    n = 40
+    pos = rng.uniform(-1.6, 1.6, size=(3, n))
+    big = oracle.Bulk(n=n, L=(50.0, 50.0, 50.0), use_cells=False)
+    s = np.zeros((6, n)); s[:3] = pos
+    Fc, Wc, _ = oracle.forces(big, s)
+    idx = {0: (0, 0), 1: (1, 1), 2: (2, 2), 3: (0, 1), 4: (0, 2), 5: (1, 2)}
+    for k, (a, c) in idx.items():
+        assert Wc[k] == pytest.approx(np.sum(pos[a] * Fc[c]), rel=1e-10, abs=1e-9)
+
+
+def test_virial_is_minus_strain_derivative_of_energy():
+    """Shear strain eps: x -> x + eps*y with Lees-Edwards offset eps*Ly gives
+    dU/deps = -W_xy; isotropic scaling gives dU/dlambda = -(Wxx+Wyy+Wzz).
+    This pins the virial's sign, its 1/2 and the LE image convention."""
+    N = 256
+    b = bulk(N)
+    st = inputs.jittered_states(N, 1, seed=8, amp=0.12)[0]
+    _, W, _ = oracle.forces(b, st, 0.0)
+
+    def U_shear(e):
+        s = st.copy()
+        s[0] = s[0] + e * s[1]
+        return oracle.forces(b, s, e * b.L[1])[2]
+
+    h = 1e-6
+    dU = (U_shear(h) - U_shear(-h)) / (2 * h)
+    assert dU == pytest.approx(-W[3], rel=1e-6)
+
+    def U_scale(lam):
+        bl = oracle.Bulk(n=N, L=tuple(np.asarray(b.L) * lam))
+        s = st.copy(); s[:3] *= lam
+        return oracle.forces(bl, s, 0.0)[2]
+
+    dUl = (U_scale(1 + h) - U_scale(1 - h)) / (2 * h)
+    assert dUl == pytest.approx(-(W[0] + W[1] + W[2]), rel=1e-6)
+
+
+# ----------------------------------------------------------- integrator ----
+def _eq_state(N=256, seed=7, n_eq=3000):
+    b = bulk(N)
+    ms, al = oracle.mother(b, inputs.initial_state(N, seed), n_eq, 1, 10)
+    return b, ms[0], al[0]
+
+
+def test_nve_energy_error_is_second_order():
+    b, st, _ = _eq_state()
+    dev = []
+    for dt in (0.0025, 0.00125):
+        bb = oracle.Bulk(n=b.n, L=b.L, dt=dt, tau_T=1e12)
+        _, _, _, obs = oracle.trajectory(bb, st, int(round(1.0 / dt)), alpha=0.0)
+        E = 0.5 * obs[:, 0] + obs[:, 1]
+        dev.append(np.abs(E - E[0]).max())
+        assert abs(E[-1] - E[0]) < 5e-4 * b.n  # no drift beyond the fluctuation
+    assert 2.8 < dev[0] / dev[1] < 5.5
+
+
+def test_nvt_extended_energy_is_conserved():
+    b, st, a0 = _eq_state()
+    dev = []
+    for dt in (0.0025, 0.00125):
+        bb = oracle.Bulk(n=b.n, L=b.L, dt=dt)
+        _, _, _, obs = oracle.trajectory(bb, st, int(round(1.0 / dt)), alpha=a0)
+        dev.append(np.abs(obs[:, 7] - obs[0, 7]).max())
+    assert dev[0] < 0.05 and 2.5 < dev[0] / dev[1] < 6.0
+
+
+def test_sheared_energy_balance_pins_the_sign_of_pxy():
+    """dH_ext/dt = -gamma V P_xy for SLLOD + Nose-Hoover (Eq. 5); with the
+    opposite sign the balance fails by orders of magnitude."""
+    b, st, a0 = _eq_state()
+    g = 0.5
+    dev = []
+    for dt in (0.0025, 0.00125):
+        bb = oracle.Bulk(n=b.n, L=b.L, dt=dt)
+        _, _, _, obs = oracle.trajectory(bb, st, int(round(1.0 / dt)), gamma=g, alpha=a0)
+        H, P = obs[:, 7], obs[:, 4]
+        I = np.concatenate([[0.0], np.cumsum(0.5 * dt * (P[1:] + P[:-1]))])
+        good = H + g * bb.V * I
+        bad = H - g * bb.V * I
+        dev.append(np.abs(good - good[0]).max())
+        assert np.abs(bad - bad[0]).max() > 100 * dev[-1]
+    assert 2.5 < dev[0] / dev[1] < 6.0
+
+
+def test_time_reversal_at_zero_field():
+    """Mapping 1 (p -> -p, alpha -> -alpha) reverses the zero-field dynamics:
+    n steps forward, map, n steps, map back = the start (Eq. 3, 5)."""
+    b, st, a0 = _eq_state()
+    s1, a1, _, _ = oracle.trajectory(b, st, 300, alpha=a0)
+    r, ar = oracle.apply_mapping(b, 1, s1, a1)
+    s2, a2, _, _ = oracle.trajectory(b, r, 300, alpha=ar)
+    back, ab = oracle.apply_mapping(b, 1, s2, a2)
+    d = back[:3] - st[:3]
+    d -= np.asarray(b.L)[:, None] * np.rint(d / np.asarray(b.L)[:, None])
+    assert np.abs(d).max() < 1e-9
+    assert np.abs(back[3:] - st[3:]).max() < 1e-9
+    assert ab == pytest.approx(a0, abs=1e-9)
+
+
+def test_total_momentum_stays_zero_under_shear():
+    b, st, a0 = _eq_state()
+    s1, _, _, _ = oracle.trajectory(b, st, 400, gamma=0.3, alpha=a0)
+    assert np.abs(st[3:].sum(axis=1)).max() < 1e-10
+    assert np.abs(s1[3:].sum(axis=1)).max() < 1e-9
+
+
+# -------------------------------------------------------------- Eq. 3 ----
+def test_mappings_cancel_omega_and_pxy_exactly():
+    b = bulk(256)
+    st = inputs.jittered_states(256, 4, seed=21, amp=0.1)
+    for k in range(4):
+        P = [oracle.pressure(b, oracle.apply_mapping(b, m, st[k])[0])[0][3] for m in range(4)]
+        kin = [np.sum(oracle.apply_mapping(b, m, st[k])[0][3] *
+                      oracle.apply_mapping(b, m, st[k])[0][4]) for m in range(4)]
+        # kinetic parts negate bitwise, configurational parts up to summation order
+        assert kin[0] == kin[1] == -kin[2] == -kin[3]
+        assert abs(sum(P)) <= 1e-12 * sum(abs(p) for p in P)
+        assert P[0] == pytest.approx(P[1], rel=1e-14)
+        assert P[2] == pytest.approx(-P[0], rel=1e-10)
+    # m3 = m1 o m2, and alpha flips for the time-reversing mappings only
+    s = st[0]
+    a = 0.123
+    m2, a2 = oracle.apply_mapping(b, 2, s, a)
+    m12, a12 = oracle.apply_mapping(b, 1, m2, a2)
+    m3, a3 = oracle.apply_mapping(b, 3, s, a)
+    assert np.array_equal(m12, m3) and a12 == a3 == -a and a2 == a
+    assert oracle.apply_mapping(b, 3, s, a, reset_alpha=True)[1] == 0.0
+
+
+def test_daughter_omega_definition():
+    b = bulk(256)
+    st = inputs.jittered_states(256, 1, seed=4, amp=0.1)[0]
+    g = 1e-3
+    B, om, _, _ = oracle.daughter(b, st, 0.0, 0, g, 5)
+    P = oracle.pressure(b, st)[0][3]
+    assert B[0] == pytest.approx(P, rel=1e-14)
+    assert om == pytest.approx(-g * b.V * P / b.T, rel=1e-14)
+
+
+# -------------------------------------------------------- Eq. 1, 2, 4 ----
+def test_reduce_closed_forms():
+    # Two groups of four; B linear in t -> trapezoid is exact.
+    S, ds = 11, 0.1
+    t = np.arange(S) * ds
+    Om = np.array([1.0, 1.0, -1.0, -1.0, 2.0, 2.0, -2.0, -2.0])
+    B = np.stack([(1 + k) * t for k in range(8)])
+    r = oracle.responses(B, Om, 4, ds)
+    corr = (Om[:, None] * B).mean(axis=0)
+    assert np.allclose(r["corr"], corr)
+    slope = np.mean(Om * (1 + np.arange(8)))
+    assert np.allclose(r["ttcf"], slope * t ** 2 / 2, atol=1e-14)
+    assert np.allclose(r["dav"], 4.5 * t)
+    assert r["omega_mean"] == 0.0
+    # Eq. 4 correction with nonzero <Omega>: subtracts <Omega><B(s)>.
+    Om2 = Om + 0.5
+    r2 = oracle.responses(B, Om2, 4, ds, corrected=True)
+    expect = np.mean(Om2 * (1 + np.arange(8))) * t ** 2 / 2 - 0.5 * 4.5 * t ** 2 / 2
+    assert np.allclose(r2["ttcf"], expect, atol=1e-13)
+
+
+def test_dav_standard_error_is_zero_at_t0(eq_mothers_256):
+    b, ms, al = eq_mothers_256
+    B, Om = oracle.daughters(b, ms[:8], al[:8], 1e-3, 40)
+    r = oracle.responses(B, Om, 4, b.dt)
+    assert abs(r["dav"][0]) < 1e-16 and r["dav_se"][0] < 1e-16
+    assert abs(Om.sum()) <= 1e-12 * np.abs(Om).sum()
+    # grows from zero during the transient (Fig. 8)
+    assert 0 < r["dav_se"][10] < r["dav_se"][20] < r["dav_se"][40]
+
+
+def test_ttcf_reduces_to_green_kubo_at_weak_field(eq_mothers_256):
+    """Eq. 1 with Eq. 7 at gamma -> 0 is the Green-Kubo integral of Eq. 8
+    evaluated on zero-field trajectories from the same mapped states."""
+    b, ms, al = eq_mothers_256
+    n = 120
+    g = 1e-8
+    B, Om = oracle.daughters(b, ms[:16], al[:16], g, n)
+    eta = oracle.viscosity(oracle.responses(B, Om, 4, b.dt), g)["eta_ttcf"]
+    B0, _ = oracle.daughters(b, ms[:16], al[:16], 0.0, n)
+    acf = (B0[:, :1] * B0).mean(axis=0)
+    gk = b.V / b.T * np.concatenate([[0.0], np.cumsum(0.5 * b.dt * (acf[1:] + acf[:-1]))])
+    assert np.allclose(eta[1:], gk[1:], rtol=1e-5, atol=1e-7 * np.abs(gk).max())
+
+
+def test_ttcf_agrees_with_direct_average_at_high_shear(eq_mothers_256):
+    """At strong field the direct average is precise and TTCF must agree
+    with it (Example 1, Fig. 3; Example 2 at gamma = 1e-1)."""
+    b, ms, al = eq_mothers_256
+    g, n = 1.0, 200
+    B, Om = oracle.daughters(b, ms, al, g, n)
+    G = ms.shape[0]
+    Bg = B.reshape(G, 4, -1)
+    Og = Om.reshape(G, 4)
+    Y = np.einsum("gm,gms->gs", Og, Bg) / 4
+    J = Bg.mean(axis=1)[:, :1] + np.concatenate(
+        [np.zeros((G, 1)), np.cumsum(0.5 * b.dt * (Y[:, 1:] + Y[:, :-1]), axis=1)], axis=1)
+    Dg = Bg.mean(axis=1)
+    for s in (100, 200):
+        diff = J[:, s] - Dg[:, s]
+        se = diff.std(ddof=1) / np.sqrt(G)
+        assert abs(diff.mean()) < 2.0 * se, (s, diff.mean(), se)
+    r = oracle.responses(B, Om, 4, b.dt)
+    assert r["dav"][-1] < -5 * r["dav_se"][-1]  # a real, negative P_xy response
+
+
+def test_mapping_keeps_positions_in_the_half_open_box():
+    """x -> -x sends an atom on the face x = -L/2 to +L/2, which is the same
+    periodic point; the mapped state stays in [-L/2, L/2)."""
+    b = bulk(256)
+    st = inputs.initial_state(256, 3)
+    st[0, 0] = -0.5 * b.L[0]
+    for m in (2, 3):
+        out, _ = oracle.apply_mapping(b, m, st)
+        assert out[0, 0] == -0.5 * b.L[0]
+        assert np.all(out[0] >= -0.5 * b.L[0]) and np.all(out[0] < 0.5 * b.L[0])
