@@ -1,0 +1,231 @@
+/*
+ * ttcf.h -- C ABI of the GB300 TTCF daughter-ensemble engine.
+ *
+ * The engine computes the transient-time correlation function (TTCF)
+ * response of a sheared bulk WCA fluid (arXiv:2312.02990, Example 1):
+ *
+ *   <B(t)> = <B(0)> + int_0^t <Omega(0) B(s)> ds                      (Eq. 1)
+ *   <Omega(0) B(s)> = (1/N) sum_i Omega(0)_i B(s)_i                   (Eq. 2)
+ *
+ * over daughter trajectories that start from the four phase-space mappings
+ * (Eq. 3) of equilibrium mother states, follow the thermostatted SLLOD
+ * equations of motion (Eq. 5) with the WCA pair potential (Eq. 6) under
+ * Lees-Edwards sliding-brick boundaries, and measure B = P_xy with the
+ * dissipation function Omega = -gamma V P_xy / (k_B T) (Eq. 7; the sign
+ * follows from Omega = beta dH^ad/dt of the Mathematical Framework with the
+ * standard pressure tensor).  The viscosity is eta = -<P_xy>/gamma (Eq. 8).
+ *
+ * Conventions shared by every call:
+ *  - Reduced units: sigma = epsilon = m = k_B = 1.
+ *  - A phase point is a C-contiguous float64 array [6][N]: rows x, y, z,
+ *    px, py, pz.  Positions lie in the centred box [-L/2, L/2).  Momenta
+ *    are peculiar (thermal) momenta; the streaming profile gamma*y of the
+ *    daughter is carried by the equations of motion, never added to p.
+ *  - The caller owns every array passed in or out.  Inputs are copied
+ *    during the call.  The library owns all device memory it allocates,
+ *    through the allocator given in ttcf_config (torch's caching allocator
+ *    when created from Python) or cudaMalloc/cudaFree.
+ *  - Every call returns a ttcf_status; no exception crosses the ABI and the
+ *    process never aborts.  After an error, ttcf_last_error() holds a
+ *    one-line description.
+ *  - Work is queued on ttcf_config.stream; calls that return results to
+ *    host memory synchronise that stream before returning.
+ */
+#ifndef TTCF_H
+#define TTCF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttcf_ctx ttcf_ctx;
+
+typedef enum {
+    TTCF_OK = 0,
+    TTCF_E_INVALID = 1,  /* bad argument or configuration                  */
+    TTCF_E_CUDA = 2,     /* a CUDA runtime call failed                       */
+    TTCF_E_OOM = 3,      /* device or host allocation failed                 */
+    TTCF_E_NUMERIC = 4,  /* >= 1 daughter stopped: NaN/Inf, lost atom,
+                            neighbour-list overflow; its group is excluded    */
+    TTCF_E_TIMEOUT = 5,  /* ttcf_run exceeded timeout_s and was aborted      */
+    TTCF_E_STATE = 6     /* call out of order (e.g. response before run)     */
+} ttcf_status;
+
+enum { TTCF_BULK_WCA = 0 };
+
+/* Arithmetic of the daughter integrator.
+ *  TTCF_FP64:  every per-atom quantity in IEEE double (slow on GB300).
+ *  TTCF_MIXED: FP32 pair forces and virial; positions and momenta kept as
+ *              unevaluated float pairs (about 48 significand bits) updated
+ *              on the FP32 pipe; alpha, the Lees-Edwards offset, Omega(0),
+ *              B(0) and every accumulation in IEEE double.                  */
+enum { TTCF_FP64 = 0, TTCF_MIXED = 1 };
+
+/* Per-daughter flags reported by ttcf_group_status (bitwise OR per group). */
+enum {
+    TTCF_D_OK = 0,
+    TTCF_D_NONFINITE = 1,      /* NaN or Inf in a reduced sum                 */
+    TTCF_D_NBR_OVERFLOW = 2,   /* an atom had more Verlet neighbours than fit */
+    TTCF_D_FAST_ATOM = 4,      /* an atom moved more than skin/2 in one step  */
+    TTCF_D_ABORTED = 8         /* stopped by the host (timeout)               */
+};
+
+typedef void *(*ttcf_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*ttcf_free_fn)(void *ptr, void *stream, void *user);
+
+/* Plain-old-data configuration; copied by ttcf_create. */
+typedef struct {
+    int system;             /* TTCF_BULK_WCA                                 */
+    int precision;          /* TTCF_FP64 or TTCF_MIXED                       */
+    double dt;              /* time step h (Example 1: 0.0025)               */
+    double T;               /* thermostat k_B T (Example 1: 0.722)           */
+    double tau_T;           /* Nose-Hoover time: Q = g T tau_T^2             */
+    int dof_mode;           /* 0: g = 3N as printed in Eq. 5; 1: g = 3N - 3  */
+    int n_steps;            /* daughter length in steps                      */
+    int sample_every;       /* B(s) recorded every sample_every steps;
+                               n_steps must be a multiple of it              */
+    unsigned mapping_mask;  /* bit m selects mapping m of Eq. 3 (0xF = all)  */
+    int reset_alpha;        /* 0: daughters inherit the mother's alpha,
+                               negated by the time-reversing mappings 1, 3;
+                               1: alpha = 0 at switch-on                     */
+    int keep_state;         /* 1: keep every daughter's phase point on the
+                               device after ttcf_run (ttcf_get_state)        */
+    double skin;            /* Verlet skin (sigma); <= 0 selects autotuned   */
+    int block_threads;      /* threads per daughter CTA; 0 = autotuned       */
+    void *stream;           /* cudaStream_t; NULL = legacy default stream    */
+    ttcf_alloc_fn dev_alloc;/* NULL: cudaMalloc                              */
+    ttcf_free_fn dev_free;  /* NULL: cudaFree                                */
+    void *alloc_user;       /* passed to dev_alloc / dev_free                */
+    double timeout_s;       /* ttcf_run wall-clock limit; <= 0: none         */
+} ttcf_config;
+
+/* Fill *cfg with the Example 1 defaults: MIXED, dt 0.0025, T 0.722,
+ * tau_T 0.25, g = 3N, 1000 steps, sample_every 1, all four mappings,
+ * alpha carried, autotuned skin and block size.                           */
+void ttcf_config_default(ttcf_config *cfg);
+
+/* Create a context.  *out receives an owned handle (ttcf_destroy frees it).
+ * Errors: TTCF_E_INVALID (bad field), TTCF_E_CUDA (no device).             */
+ttcf_status ttcf_create(const ttcf_config *cfg, ttcf_ctx **out);
+
+/* Append one batch of daughters (Figure 1, Algorithm 2 "apply mapping",
+ * "switch on ext. field"): for each of the n_mothers mother states g, one
+ * daughter per mapping selected in mapping_mask, daughter index within the
+ * batch d = g*M + k (k-th selected mapping, M = popcount(mask)).  Groups
+ * stay contiguous so that <Omega(0)> = 0 holds per group (Eq. 3).
+ *
+ *  n_atoms       N of this batch (bulk WCA, 4 <= N <= 4096)
+ *  box           [3] edge lengths Lx, Ly, Lz (each > 2 * (r_c + skin))
+ *  mother_soa    [n_mothers][6][N] float64 phase points
+ *  mother_alpha  [n_mothers] Nose-Hoover multipliers, or NULL for zeros
+ *  shear_rates   [n_mothers] field gamma of each group (same for its M
+ *                daughters); gamma = 0 is allowed (Omega = 0)
+ *  ptr_is_device 1 if the three arrays are device pointers, else host
+ *  batch_id      receives the batch index used by ttcf_response etc.
+ *
+ * Runs the spawn kernel: copies and maps the states and computes, in
+ * IEEE double, B(0) = P_xy(0) and Omega(0) of every daughter.  Must be
+ * called before the first ttcf_run.  Errors: TTCF_E_INVALID, TTCF_E_OOM,
+ * TTCF_E_CUDA, TTCF_E_STATE (after ttcf_run).                              */
+ttcf_status ttcf_spawn_daughters(ttcf_ctx *ctx, int n_atoms, const double box[3],
+                                 int n_mothers, const double *mother_soa,
+                                 const double *mother_alpha, const double *shear_rates,
+                                 int ptr_is_device, int *batch_id);
+
+/* Advance every daughter of every batch by n_steps steps (SLLOD + Nose-
+ * Hoover, Eq. 5; pair forces, Eq. 6) in one persistent launch per size
+ * class, recording B(s) on device.  May be called in chunks; chunks give
+ * bitwise the same result as one call.  n_steps = 0 or more than remain:
+ * runs the rest.  Returns after the stream is synchronised.
+ * Errors: TTCF_E_STATE (nothing spawned), TTCF_E_NUMERIC (some daughters
+ * failed; see ttcf_group_status), TTCF_E_TIMEOUT, TTCF_E_CUDA.             */
+ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps);
+
+/* Ensemble responses of one batch (Eq. 1, 2; Eq. 4 if corrected != 0),
+ * reduced on the device in a fixed order in IEEE double, over the groups
+ * whose daughters all finished.  Each output is [S] with S = n_steps /
+ * sample_every + 1 samples at t = s * sample_every * dt; any output pointer
+ * may be NULL.  Standard errors are taken over mother groups.
+ *  t        sample times
+ *  dav      direct average <B(t)>, dav_se its standard error
+ *  corr     <Omega(0) B(s)>, corr_se
+ *  ttcf     <B(0)> + trapezoid integral of corr, ttcf_se
+ * capacity is the length of each caller array; *n_samples receives S.
+ * Errors: TTCF_E_STATE (run not finished), TTCF_E_INVALID (capacity < S).  */
+ttcf_status ttcf_response(ttcf_ctx *ctx, int batch_id, int corrected, double *t,
+                          double *dav, double *dav_se, double *corr, double *corr_se,
+                          double *ttcf, double *ttcf_se, int capacity, int *n_samples);
+
+/* Shear viscosity of a batch whose groups share one shear rate gamma
+ * (Eq. 8 with the standard pressure tensor): eta(t) = -<P_xy(t)>/gamma
+ * from the TTCF and the direct averages, with standard errors.  Arrays as
+ * in ttcf_response.  Errors: as ttcf_response; TTCF_E_INVALID if gamma
+ * differs between groups or is 0.                                          */
+ttcf_status ttcf_viscosity(ttcf_ctx *ctx, int batch_id, double *t, double *eta_ttcf,
+                           double *eta_ttcf_se, double *eta_dav, double *eta_dav_se,
+                           int capacity, int *n_samples);
+
+/* Raw per-daughter outputs of a batch: B [D][S] and Omega [D] (host
+ * arrays, D = n_mothers * M).  capacity_B is the element count of B.      */
+ttcf_status ttcf_daughter_series(ttcf_ctx *ctx, int batch_id, double *B, double *Omega,
+                                 size_t capacity_B);
+
+/* Per-group status flags (TTCF_D_*, OR over the group's daughters) [G].   */
+ttcf_status ttcf_group_status(ttcf_ctx *ctx, int batch_id, int *status, int capacity);
+
+/* Phase point [6][N], alpha and Lees-Edwards offset of daughter d of a
+ * batch after the last ttcf_run; requires keep_state = 1.  Positions are
+ * wrapped into the box.                                                    */
+ttcf_status ttcf_get_state(ttcf_ctx *ctx, int batch_id, int daughter, double *soa,
+                           double *alpha, double *delta);
+
+/* Work counters of the last ttcf_run: device time of the persistent
+ * launch(es) measured with CUDA events on the context's stream (ms), the
+ * spawn and reduce times (ms), the number of interacting ordered pairs
+ * (r < r_c) summed over all atoms and steps, the number of Verlet-list
+ * rebuilds, atom-steps, and kernel launches issued.                        */
+typedef struct {
+    double ms_run, ms_spawn, ms_reduce;
+    double pairs_interacting;   /* ordered pairs (i,j), r_ij < r_c, summed  */
+    double rebuilds;            /* neighbour-list builds, summed over daughters */
+    double atom_steps;          /* sum over daughters of N * steps run       */
+    int launches;               /* kernels launched by the last ttcf_run     */
+    int block_threads;          /* block size used (largest class)          */
+    double skin;                /* Verlet skin used                          */
+} ttcf_stats;
+ttcf_status ttcf_get_stats(ttcf_ctx *ctx, ttcf_stats *out);
+
+/* Equilibrium mother states on the GPU (Algorithm 2, mother part): from
+ * each of n_init initial phase points [n_init][6][N] (host), run n_eq
+ * zero-field Nose-Hoover steps, then store n_states phase points `spacing`
+ * steps apart.  out_soa [n_init][n_states][6][N] and out_alpha
+ * [n_init][n_states] are host arrays.  Uses the context's precision and
+ * kernels with gamma = 0.  Independent of any spawned batch.               */
+ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_init,
+                                const double *init_soa, int n_eq, int n_states, int spacing,
+                                double *out_soa, double *out_alpha);
+
+/* Pair forces of n_states phase points [n_states][6][N] (host; rows 0-2
+ * used) at Lees-Edwards offset delta, with the context's precision and the
+ * same device code the daughters use: F [n_states][3][N] and virial
+ * W [n_states][6] (xx yy zz xy xz yz, sum over pairs of r_a F_b), U
+ * [n_states] (potential energy).  Host outputs.                            */
+ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
+                        double delta, const double *soa, double *F, double *W, double *U);
+
+/* Release the context and all its device memory.  NULL is ignored.       */
+void ttcf_destroy(ttcf_ctx *ctx);
+
+/* Last error text of ctx (or of the last failed ttcf_create if ctx is
+ * NULL).  Owned by the library; valid until the next call on ctx.         */
+const char *ttcf_last_error(const ttcf_ctx *ctx);
+
+/* Library version string (static storage).                                */
+const char *ttcf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTCF_H */

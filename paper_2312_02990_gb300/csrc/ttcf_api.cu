@@ -1,0 +1,800 @@
+// ttcf_api.cu -- host implementation of the C ABI declared in ttcf.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ttcf_internal.h"
+
+using namespace ttcf;
+
+namespace {
+
+constexpr double RC_WCA = 1.1224620483093730;   // 2^(1/6)
+constexpr double DEFAULT_SKIN = 0.3;
+
+thread_local std::string g_create_error;
+
+struct BatchHost {
+    int N = 0, M = 0, G = 0, S = 0;
+    int maps[4] = {0, 0, 0, 0};
+    double L[3] = {0, 0, 0};
+    double V = 0, Q = 0, gT = 0;
+    int nc[3] = {0, 0, 0}, ncell = 0;     // list cells, width >= r_c + skin
+    int snc[3] = {0, 0, 0}, sncell = 0;   // spawn cells, width >= r_c
+    long long d0 = 0;
+    int apt = 1, threads = 256;
+    std::vector<double> gamma;
+    unsigned long long *mothers = nullptr;
+    double *m_alpha = nullptr, *gamma_d = nullptr, *B = nullptr, *Omega = nullptr;
+    int *status = nullptr;
+    unsigned long long *pairs = nullptr;
+    unsigned int *rebuilds = nullptr;
+    double *scal = nullptr;
+    unsigned long long *state = nullptr;
+    double *feat = nullptr;
+    // reduction
+    bool reduced = false;
+    double *Y = nullptr, *Dg = nullptr, *J = nullptr, *Og = nullptr, *valid = nullptr, *out = nullptr;
+    long long D() const { return (long long)G * M; }
+};
+
+}  // namespace
+
+struct ttcf_ctx {
+    ttcf_config cfg;
+    std::string err;
+    cudaStream_t st = nullptr;
+    int device = 0, nsm = 0, smem_optin = 0;
+    double skin = DEFAULT_SKIN;
+    std::vector<BatchHost> batches;
+    std::vector<void *> allocs;
+    long long total_d = 0;
+    int steps_done = 0;
+    bool ran = false;
+    int *h_abort = nullptr, *d_abort = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ttcf_stats stats;
+    // launch tables, rebuilt when batches change
+    bool tables_ok = false;
+    BatchDev *d_batches = nullptr;
+    int *d_dbatch = nullptr, *d_work = nullptr, *d_queue = nullptr;
+    unsigned short *d_nbr = nullptr;
+    size_t nbr_elems = 0;
+};
+
+namespace {
+
+ttcf_status fail(ttcf_ctx *c, ttcf_status s, const std::string &msg) {
+    if (c) c->err = msg; else g_create_error = msg;
+    return s;
+}
+
+ttcf_status cuda_fail(ttcf_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, TTCF_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call);     \
+    } while (0)
+
+void *dev_alloc_raw(ttcf_ctx *ctx, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (ctx->cfg.dev_alloc) {
+        p = ctx->cfg.dev_alloc(bytes, ctx->cfg.stream, ctx->cfg.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dev_free_raw(ttcf_ctx *ctx, void *p) {
+    if (!p) return;
+    if (ctx->cfg.dev_free) ctx->cfg.dev_free(p, ctx->cfg.stream, ctx->cfg.alloc_user);
+    else cudaFree(p);
+}
+
+// Scoped set of device allocations; `keep` hands them to the context.
+struct Pool {
+    ttcf_ctx *ctx;
+    std::vector<void *> ptrs;
+    bool oom = false;
+    explicit Pool(ttcf_ctx *c) : ctx(c) {}
+    template <class T> T *get(size_t count) {
+        void *p = dev_alloc_raw(ctx, count * sizeof(T));
+        if (!p) { oom = true; return nullptr; }
+        ptrs.push_back(p);
+        return (T *)p;
+    }
+    void keep() { ctx->allocs.insert(ctx->allocs.end(), ptrs.begin(), ptrs.end()); ptrs.clear(); }
+    ~Pool() {
+        if (!ptrs.empty()) cudaStreamSynchronize(ctx->st);
+        for (void *p : ptrs) dev_free_raw(ctx, p);
+    }
+};
+
+int popcount4(unsigned m) { int k = 0; for (int i = 0; i < 4; i++) k += (m >> i) & 1; return k; }
+
+void choose_class(int N, int block_threads, int &apt, int &threads) {
+    if (block_threads > 0) {
+        threads = block_threads;
+        apt = 1;
+        while (apt < 8 && apt * threads < N) apt *= 2;
+        if (threads > max_threads_for_apt(apt)) threads = max_threads_for_apt(apt);
+        while (apt < 8 && apt * threads < N) apt *= 2;
+        return;
+    }
+    if (N <= 256) { apt = 1; threads = std::max(32, (N + 31) / 32 * 32); }
+    else if (N <= 512) { apt = 2; threads = 256; }
+    else if (N <= 1024) { apt = 2; threads = 512; }
+    else if (N <= 2048) { apt = 4; threads = 512; }
+    else { apt = 8; threads = 512; }
+}
+
+// Allocate a batch, copy its mothers and run the spawn kernel.
+ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const double box[3], int G,
+                       const double *soa, const double *alpha, const double *gamma,
+                       int is_dev, const int *maps, int M, int S, double delta0) {
+    const ttcf_config &cf = ctx->cfg;
+    if (N < 4 || N > 4096) return fail(ctx, TTCF_E_INVALID, "n_atoms must be in [4, 4096]");
+    if (G <= 0) return fail(ctx, TTCF_E_INVALID, "n_mothers must be positive");
+    if (!soa) return fail(ctx, TTCF_E_INVALID, "mother_soa is NULL");
+    const double rl = RC_WCA + ctx->skin;
+    for (int k = 0; k < 3; k++) {
+        if (!(box[k] > 0) || !isfinite(box[k])) return fail(ctx, TTCF_E_INVALID, "box edges must be positive");
+        if (box[k] < 3.0 * rl)
+            return fail(ctx, TTCF_E_INVALID, "box edge shorter than 3*(r_c+skin): system too small");
+    }
+    b.N = N; b.G = G; b.M = M; b.S = S;
+    for (int k = 0; k < M; k++) b.maps[k] = maps[k];
+    b.V = box[0] * box[1] * box[2];
+    for (int k = 0; k < 3; k++) {
+        b.L[k] = box[k];
+        b.nc[k] = (int)floor(box[k] / rl);
+        b.snc[k] = (int)floor(box[k] / RC_WCA);
+    }
+    b.ncell = b.nc[0] * b.nc[1] * b.nc[2];
+    b.sncell = b.snc[0] * b.snc[1] * b.snc[2];
+    const double g = cf.dof_mode == 1 ? 3.0 * N - 3.0 : 3.0 * N;
+    b.Q = g * cf.T * cf.tau_T * cf.tau_T;
+    b.gT = g * cf.T;
+    choose_class(N, cf.block_threads, b.apt, b.threads);
+    if (b.apt * b.threads < N) return fail(ctx, TTCF_E_INVALID, "block_threads too small for n_atoms");
+
+    // host copies of gamma (needed for viscosity) and the device arrays
+    b.gamma.resize(G);
+    std::vector<double> alpha_h(G, 0.0);
+    if (is_dev) {
+        if (gamma) CK(cudaMemcpy(b.gamma.data(), gamma, sizeof(double) * G, cudaMemcpyDeviceToHost));
+        else std::fill(b.gamma.begin(), b.gamma.end(), 0.0);
+        if (alpha) CK(cudaMemcpy(alpha_h.data(), alpha, sizeof(double) * G, cudaMemcpyDeviceToHost));
+    } else {
+        for (int k = 0; k < G; k++) b.gamma[k] = gamma ? gamma[k] : 0.0;
+        if (alpha) for (int k = 0; k < G; k++) alpha_h[k] = alpha[k];
+    }
+    for (int k = 0; k < G; k++)
+        if (!isfinite(b.gamma[k]) || !isfinite(alpha_h[k]))
+            return fail(ctx, TTCF_E_INVALID, "non-finite shear rate or alpha");
+    const long long D = b.D();
+    const size_t slots = (size_t)G * 6 * N;
+    b.mothers = pool.get<unsigned long long>(slots);
+    b.m_alpha = pool.get<double>(G);
+    b.gamma_d = pool.get<double>(G);
+    b.B = pool.get<double>((size_t)D * S);
+    b.Omega = pool.get<double>(D);
+    b.status = pool.get<int>(D);
+    b.pairs = pool.get<unsigned long long>(D);
+    b.rebuilds = pool.get<unsigned int>(D);
+    b.scal = pool.get<double>((size_t)D * 4);
+    b.feat = pool.get<double>((size_t)G * 16);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (batch)");
+    cudaStream_t st = ctx->st;
+    CK(cudaMemcpyAsync(b.m_alpha, alpha_h.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b.gamma_d, b.gamma.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(b.B, 0, sizeof(double) * D * S, st));
+    CK(cudaMemsetAsync(b.status, 0, sizeof(int) * D, st));
+    CK(cudaMemsetAsync(b.pairs, 0, sizeof(unsigned long long) * D, st));
+    CK(cudaMemsetAsync(b.rebuilds, 0, sizeof(unsigned int) * D, st));
+    CK(cudaMemsetAsync(b.scal, 0, sizeof(double) * D * 4, st));
+
+    // the FP64 mother states on the device (temporary)
+    Pool tmp(ctx);
+    const double *src = soa;
+    if (!is_dev) {
+        double *s = tmp.get<double>(slots);
+        if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (mother copy)");
+        CK(cudaMemcpyAsync(s, soa, sizeof(double) * slots, cudaMemcpyHostToDevice, st));
+        src = s;
+    }
+    SpawnArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.N = N; sa.M = M; sa.G = G;
+    for (int k = 0; k < 4; k++) sa.maps[k] = b.maps[k];
+    for (int k = 0; k < 3; k++) { sa.nc[k] = b.snc[k]; sa.L[k] = b.L[k]; }
+    sa.ncell = b.sncell;
+    sa.V = b.V; sa.T = cf.T;
+    sa.mixed = cf.precision == TTCF_MIXED;
+    sa.src = src; sa.gamma = b.gamma_d; sa.mothers = b.mothers;
+    sa.B = b.B; sa.S = S; sa.Omega = b.Omega; sa.feat = b.feat; sa.delta = delta0;
+    CK(launch_spawn(sa, st));
+    CK(cudaStreamSynchronize(st));   // before the temporary copy is released
+    return TTCF_OK;
+}
+
+BatchDev to_dev(const BatchHost &b) {
+    BatchDev d;
+    memset(&d, 0, sizeof(d));
+    d.N = b.N; d.M = b.M; d.G = b.G; d.S = b.S;
+    for (int k = 0; k < 4; k++) d.maps[k] = b.maps[k];
+    for (int k = 0; k < 3; k++) { d.nc[k] = b.nc[k]; d.L[k] = b.L[k]; }
+    d.ncell = b.ncell;
+    d.V = b.V; d.Q = b.Q; d.gT = b.gT; d.d0 = b.d0;
+    d.mothers = b.mothers; d.m_alpha = b.m_alpha; d.gamma = b.gamma_d;
+    d.B = b.B; d.Omega = b.Omega; d.status = b.status; d.pairs = b.pairs;
+    d.rebuilds = b.rebuilds; d.scal = b.scal; d.state = b.state;
+    return d;
+}
+
+struct ClassLaunch {
+    int apt, threads, nmax, ncellmax, grid;
+    size_t smem;
+    std::vector<int> work;
+};
+
+// Group the batches' daughters by launch class (apt, threads).
+std::vector<ClassLaunch> plan_classes(ttcf_ctx *ctx, std::vector<BatchHost *> &bs) {
+    std::vector<ClassLaunch> cls;
+    for (BatchHost *b : bs) {
+        ClassLaunch *c = nullptr;
+        for (auto &x : cls) if (x.apt == b->apt && x.threads == b->threads) c = &x;
+        if (!c) { cls.push_back({b->apt, b->threads, 0, 0, 0, 0, {}}); c = &cls.back(); }
+        c->nmax = std::max(c->nmax, b->N);
+        c->ncellmax = std::max(c->ncellmax, b->ncell);
+        for (long long k = 0; k < b->D(); k++) c->work.push_back((int)(b->d0 + k));
+    }
+    const bool mixed = ctx->cfg.precision == TTCF_MIXED;
+    for (auto &c : cls) {
+        c.smem = daughter_smem_bytes(mixed, c.nmax, c.ncellmax);
+        c.grid = 0;
+        if (c.smem > (size_t)ctx->smem_optin) continue;   // rejected by the caller
+        int nb = daughter_occupancy(mixed, c.apt, c.threads, c.smem);
+        if (nb < 1) nb = 1;
+        c.grid = (int)std::min<long long>((long long)c.work.size(), (long long)nb * ctx->nsm);
+        if (c.grid < 1) c.grid = 1;
+    }
+    return cls;
+}
+
+// One persistent launch per class over the given batches (device tables
+// built in `pool`).  `proto` carries the run-wide fields.
+ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &bs,
+                           RunArgs proto, int &launches, cudaEvent_t ev_begin = nullptr,
+                           cudaEvent_t ev_end = nullptr) {
+    const bool mixed = ctx->cfg.precision == TTCF_MIXED;
+    if (bs.empty()) return TTCF_OK;
+    long long dmax = 0;
+    for (BatchHost *b : bs) dmax = std::max(dmax, b->d0 + b->D());
+    std::vector<BatchDev> hb;
+    std::vector<int> dbatch((size_t)dmax, 0);
+    for (size_t k = 0; k < bs.size(); k++) {
+        hb.push_back(to_dev(*bs[k]));
+        for (long long d = 0; d < bs[k]->D(); d++) dbatch[(size_t)(bs[k]->d0 + d)] = (int)k;
+    }
+    std::vector<ClassLaunch> cls = plan_classes(ctx, bs);
+    for (auto &c : cls)
+        if (c.grid == 0)
+            return fail(ctx, TTCF_E_INVALID, "a daughter needs more shared memory than a CTA has "
+                                             "(n_atoms too large for this skin)");
+    BatchDev *d_b = pool.get<BatchDev>(hb.size());
+    int *d_db = pool.get<int>(dbatch.size());
+    int *d_q = pool.get<int>(cls.size());
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (tables)");
+    cudaStream_t st = ctx->st;
+    CK(cudaMemcpyAsync(d_b, hb.data(), sizeof(BatchDev) * hb.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_db, dbatch.data(), sizeof(int) * dbatch.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_q, 0, sizeof(int) * cls.size(), st));
+    std::vector<int *> d_work(cls.size());
+    std::vector<unsigned short *> d_nbr(cls.size());
+    for (size_t k = 0; k < cls.size(); k++) {
+        d_work[k] = pool.get<int>(cls[k].work.size());
+        d_nbr[k] = pool.get<unsigned short>((size_t)cls[k].grid * CAP * cls[k].nmax);
+        if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (work lists)");
+        CK(cudaMemcpyAsync(d_work[k], cls[k].work.data(), sizeof(int) * cls[k].work.size(),
+                           cudaMemcpyHostToDevice, st));
+    }
+    if (ev_begin) CK(cudaEventRecord(ev_begin, st));
+    // classes run concurrently on forked streams joined back into st
+    std::vector<cudaStream_t> side(cls.size(), st);
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+    if (cls.size() > 1) {
+        CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        CK(cudaEventRecord(fork, st));
+        for (size_t k = 1; k < cls.size(); k++) {
+            CK(cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking));
+            CK(cudaStreamWaitEvent(side[k], fork, 0));
+        }
+    }
+    for (size_t k = 0; k < cls.size(); k++) {
+        RunArgs a = proto;
+        a.batches = d_b; a.dbatch = d_db; a.work = d_work[k];
+        a.n_work = (int)cls[k].work.size();
+        a.queue = d_q + k;
+        a.nbr = d_nbr[k]; a.nmax = cls[k].nmax; a.ncellmax = cls[k].ncellmax;
+        CK(launch_daughters(mixed, cls[k].apt, a, cls[k].threads, cls[k].grid, cls[k].smem, side[k]));
+        launches++;
+        ctx->stats.block_threads = std::max(ctx->stats.block_threads, cls[k].threads);
+    }
+    for (size_t k = 1; k < cls.size(); k++) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CK(cudaEventRecord(e, side[k]));
+        CK(cudaStreamWaitEvent(st, e, 0));
+        done.push_back(e);
+    }
+    if (ev_end) CK(cudaEventRecord(ev_end, st));
+    // the side streams and events are released once st has passed them
+    if (!done.empty() || fork) {
+        CK(cudaStreamSynchronize(st));
+        for (auto e : done) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        for (size_t k = 1; k < side.size(); k++) cudaStreamDestroy(side[k]);
+    }
+    return TTCF_OK;
+}
+
+// Wait for the stream with the context's wall-clock limit.
+ttcf_status wait_with_timeout(ttcf_ctx *ctx, cudaEvent_t ev) {
+    const double lim = ctx->cfg.timeout_s;
+    if (lim <= 0) { CK(cudaEventSynchronize(ev)); return TTCF_OK; }
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaSuccess) return TTCF_OK;
+        if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "cudaEventQuery");
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > lim) {
+            *(volatile int *)ctx->h_abort = 1;   // daughters stop within 64 steps
+            CK(cudaEventSynchronize(ev));
+            return fail(ctx, TTCF_E_TIMEOUT, "ttcf_run exceeded timeout_s; daughters aborted");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+ttcf_status reduce_batch(ttcf_ctx *ctx, BatchHost &b) {
+    if (b.reduced) return TTCF_OK;
+    if (!b.out) {
+        Pool p(ctx);
+        b.Y = p.get<double>((size_t)b.G * b.S);
+        b.Dg = p.get<double>((size_t)b.G * b.S);
+        b.J = p.get<double>((size_t)b.G * b.S);
+        b.Og = p.get<double>(b.G);
+        b.valid = p.get<double>(b.G);
+        b.out = p.get<double>((size_t)9 * b.S);
+        if (p.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (reduction)");
+        p.keep();
+    }
+    ReduceArgs r;
+    r.M = b.M; r.G = b.G; r.S = b.S;
+    r.B = b.B; r.Omega = b.Omega; r.status = b.status;
+    r.ds = ctx->cfg.sample_every * ctx->cfg.dt;
+    r.Y = b.Y; r.Dg = b.Dg; r.J = b.J; r.Og = b.Og; r.valid = b.valid; r.out = b.out;
+    CK(launch_reduce(r, ctx->st));
+    b.reduced = true;
+    return TTCF_OK;
+}
+
+BatchHost *get_batch(ttcf_ctx *ctx, int id) {
+    if (!ctx || id < 0 || id >= (int)ctx->batches.size()) return nullptr;
+    return &ctx->batches[id];
+}
+
+}  // namespace
+
+// =================================================================== ABI ==
+extern "C" {
+
+void ttcf_config_default(ttcf_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->system = TTCF_BULK_WCA;
+    c->precision = TTCF_MIXED;
+    c->dt = 0.0025;
+    c->T = 0.722;
+    c->tau_T = 0.25;
+    c->dof_mode = 0;
+    c->n_steps = 1000;
+    c->sample_every = 1;
+    c->mapping_mask = 0xF;
+    c->reset_alpha = 0;
+    c->keep_state = 0;
+    c->skin = 0.0;
+    c->block_threads = 0;
+    c->timeout_s = 0.0;
+}
+
+const char *ttcf_version(void) { return "ttcf-gb300 1.0 (sm_103a)"; }
+
+const char *ttcf_last_error(const ttcf_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+ttcf_status ttcf_create(const ttcf_config *cfg, ttcf_ctx **out) {
+    if (!cfg || !out) return fail(nullptr, TTCF_E_INVALID, "NULL argument");
+    *out = nullptr;
+    const ttcf_config &c = *cfg;
+    if (c.system != TTCF_BULK_WCA) return fail(nullptr, TTCF_E_INVALID, "unknown system");
+    if (c.precision != TTCF_FP64 && c.precision != TTCF_MIXED)
+        return fail(nullptr, TTCF_E_INVALID, "precision must be TTCF_FP64 or TTCF_MIXED");
+    if (!(c.dt > 0) || !(c.T > 0) || !(c.tau_T > 0))
+        return fail(nullptr, TTCF_E_INVALID, "dt, T and tau_T must be positive");
+    if (c.n_steps < 1 || c.sample_every < 1 || c.n_steps % c.sample_every)
+        return fail(nullptr, TTCF_E_INVALID, "n_steps must be a positive multiple of sample_every");
+    if ((c.mapping_mask & 0xF) == 0 || (c.mapping_mask & ~0xFu))
+        return fail(nullptr, TTCF_E_INVALID, "mapping_mask must select mappings 0..3");
+    if (c.block_threads < 0 || c.block_threads % 32 || c.block_threads > 512)
+        return fail(nullptr, TTCF_E_INVALID, "block_threads must be 0 or a multiple of 32 <= 512");
+    if (c.skin > 1.0) return fail(nullptr, TTCF_E_INVALID, "skin must be <= 1");
+    if ((c.dev_alloc == nullptr) != (c.dev_free == nullptr))
+        return fail(nullptr, TTCF_E_INVALID, "dev_alloc and dev_free must be set together");
+    ttcf_ctx *ctx = new (std::nothrow) ttcf_ctx();
+    if (!ctx) return fail(nullptr, TTCF_E_OOM, "host allocation failed");
+    ctx->cfg = c;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->st = (cudaStream_t)c.stream;
+    ctx->skin = c.skin > 0 ? c.skin : DEFAULT_SKIN;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&ctx->h_abort, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) { *ctx->h_abort = 0; e = cudaHostGetDevicePointer((void **)&ctx->d_abort, ctx->h_abort, 0); }
+    for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->ev[k]);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("CUDA initialisation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        ttcf_destroy(ctx);
+        return TTCF_E_CUDA;
+    }
+    *out = ctx;
+    return TTCF_OK;
+}
+
+void ttcf_destroy(ttcf_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->st);
+    for (void *p : ctx->allocs) dev_free_raw(ctx, p);
+    for (int k = 0; k < 4; k++) if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    if (ctx->h_abort) cudaFreeHost(ctx->h_abort);
+    delete ctx;
+}
+
+ttcf_status ttcf_spawn_daughters(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_mothers,
+                                 const double *mother_soa, const double *mother_alpha,
+                                 const double *shear_rates, int ptr_is_device, int *batch_id) {
+    if (!ctx || !box) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (ctx->ran) return fail(ctx, TTCF_E_STATE, "ttcf_spawn_daughters after ttcf_run");
+    int maps[4], M = 0;
+    for (int m = 0; m < 4; m++) if (ctx->cfg.mapping_mask & (1u << m)) maps[M++] = m;
+    const int S = ctx->cfg.n_steps / ctx->cfg.sample_every + 1;
+    BatchHost b;
+    Pool pool(ctx);
+    ttcf_status s = make_batch(ctx, pool, b, n_atoms, box, n_mothers, mother_soa, mother_alpha,
+                               shear_rates, ptr_is_device, maps, M, S, 0.0);
+    if (s != TTCF_OK) return s;
+    if (ctx->total_d + b.D() > 2000000000LL) return fail(ctx, TTCF_E_INVALID, "too many daughters");
+    b.d0 = ctx->total_d;
+    ctx->total_d += b.D();
+    pool.keep();
+    ctx->batches.push_back(b);
+    ctx->tables_ok = false;
+    if (batch_id) *batch_id = (int)ctx->batches.size() - 1;
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
+    if (!ctx) return fail(ctx, TTCF_E_INVALID, "NULL context");
+    if (ctx->batches.empty()) return fail(ctx, TTCF_E_STATE, "ttcf_run before ttcf_spawn_daughters");
+    const ttcf_config &cf = ctx->cfg;
+    const int step0 = ctx->steps_done;
+    if (step0 >= cf.n_steps) return TTCF_OK;
+    const int step1 = (n_steps <= 0 || step0 + n_steps > cf.n_steps) ? cf.n_steps : step0 + n_steps;
+    const bool save = step1 < cf.n_steps || cf.keep_state;
+    if (save) {
+        for (auto &b : ctx->batches) {
+            if (b.state) continue;
+            Pool p(ctx);
+            b.state = p.get<unsigned long long>((size_t)b.D() * 6 * b.N);
+            if (p.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (state)");
+            p.keep();
+        }
+    }
+    if (step0 > 0)
+        for (auto &b : ctx->batches)
+            if (!b.state) return fail(ctx, TTCF_E_STATE, "resume without saved state");
+    ctx->ran = true;
+    *(volatile int *)ctx->h_abort = 0;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+
+    RunArgs a;
+    memset(&a, 0, sizeof(a));
+    a.step0 = step0; a.step1 = step1;
+    a.sample_every = cf.sample_every;
+    a.fresh = step0 == 0;
+    a.save_state = save ? 1 : 0;
+    a.reset_alpha = cf.reset_alpha;
+    a.dt = cf.dt;
+    a.delta0 = 0.0;
+    a.skin = (float)ctx->skin;
+    a.abort_flag = ctx->d_abort;
+
+    std::vector<BatchHost *> bs;
+    for (auto &b : ctx->batches) bs.push_back(&b);
+    Pool pool(ctx);
+    int launches = 0;
+    ttcf_status s = launch_batches(ctx, pool, bs, a, launches, ctx->ev[0], ctx->ev[1]);
+    if (s != TTCF_OK) return s;
+    s = wait_with_timeout(ctx, ctx->ev[1]);
+    if (s != TTCF_OK && s != TTCF_E_TIMEOUT) return s;
+    const bool timed_out = s == TTCF_E_TIMEOUT;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    ctx->stats.ms_run = ms;
+    ctx->stats.skin = ctx->skin;
+    ctx->steps_done = step1;
+
+    // counters and failures
+    bool any_fail = false;
+    for (auto &b : ctx->batches) {
+        std::vector<int> stv(b.D());
+        std::vector<unsigned long long> pr(b.D());
+        std::vector<unsigned int> rb(b.D());
+        CK(cudaMemcpy(stv.data(), b.status, sizeof(int) * b.D(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(pr.data(), b.pairs, sizeof(unsigned long long) * b.D(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(rb.data(), b.rebuilds, sizeof(unsigned int) * b.D(), cudaMemcpyDeviceToHost));
+        for (long long d = 0; d < b.D(); d++) {
+            any_fail |= stv[d] != 0;
+            ctx->stats.pairs_interacting += (double)pr[d];
+            ctx->stats.rebuilds += (double)rb[d];
+        }
+        ctx->stats.atom_steps += (double)b.D() * b.N * (step1 - step0);
+        // counters are per run
+        CK(cudaMemsetAsync(b.pairs, 0, sizeof(unsigned long long) * b.D(), ctx->st));
+        CK(cudaMemsetAsync(b.rebuilds, 0, sizeof(unsigned int) * b.D(), ctx->st));
+    }
+    if (ctx->steps_done >= cf.n_steps) {
+        CK(cudaEventRecord(ctx->ev[2], ctx->st));
+        for (auto &b : ctx->batches) {
+            b.reduced = false;
+            ttcf_status r = reduce_batch(ctx, b);
+            if (r != TTCF_OK) return r;
+            launches += 3;
+        }
+        CK(cudaEventRecord(ctx->ev[3], ctx->st));
+        CK(cudaEventSynchronize(ctx->ev[3]));
+        float msr = 0.f;
+        cudaEventElapsedTime(&msr, ctx->ev[2], ctx->ev[3]);
+        ctx->stats.ms_reduce = msr;
+    }
+    ctx->stats.launches = launches;
+    if (timed_out) return fail(ctx, TTCF_E_TIMEOUT, "ttcf_run exceeded timeout_s; daughters aborted");
+    if (any_fail) return fail(ctx, TTCF_E_NUMERIC, "some daughters failed; see ttcf_group_status");
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_response(ttcf_ctx *ctx, int batch_id, int corrected, double *t, double *dav,
+                          double *dav_se, double *corr, double *corr_se, double *ttcf,
+                          double *ttcf_se, int capacity, int *n_samples) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (!b->reduced) return fail(ctx, TTCF_E_STATE, "run not finished");
+    if (n_samples) *n_samples = b->S;
+    if (capacity < b->S) return fail(ctx, TTCF_E_INVALID, "capacity smaller than the sample count");
+    std::vector<double> h((size_t)9 * b->S);
+    CK(cudaMemcpyAsync(h.data(), b->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const int S = b->S;
+    const double ds = ctx->cfg.sample_every * ctx->cfg.dt;
+    for (int s = 0; s < S; s++) {
+        if (t) t[s] = s * ds;
+        if (corr) corr[s] = corrected ? h[6 * S + s] : h[s];
+        if (corr_se) corr_se[s] = h[S + s];
+        if (dav) dav[s] = h[2 * S + s];
+        if (dav_se) dav_se[s] = h[3 * S + s];
+        if (ttcf) ttcf[s] = corrected ? h[7 * S + s] : h[4 * S + s];
+        if (ttcf_se) ttcf_se[s] = h[5 * S + s];
+    }
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_viscosity(ttcf_ctx *ctx, int batch_id, double *t, double *eta_ttcf,
+                           double *eta_ttcf_se, double *eta_dav, double *eta_dav_se, int capacity,
+                           int *n_samples) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    const double g = b->gamma.empty() ? 0.0 : b->gamma[0];
+    for (double x : b->gamma)
+        if (x != g) return fail(ctx, TTCF_E_INVALID, "shear rate differs between groups");
+    if (g == 0.0) return fail(ctx, TTCF_E_INVALID, "zero shear rate");
+    std::vector<double> tt(b->S), dv(b->S), dse(b->S), tc(b->S), tse(b->S);
+    ttcf_status s = ttcf_response(ctx, batch_id, 0, tt.data(), dv.data(), dse.data(), nullptr,
+                                  nullptr, tc.data(), tse.data(), (int)b->S, n_samples);
+    if (s != TTCF_OK) return s;
+    if (capacity < b->S) return fail(ctx, TTCF_E_INVALID, "capacity smaller than the sample count");
+    for (int k = 0; k < b->S; k++) {
+        if (t) t[k] = tt[k];
+        if (eta_ttcf) eta_ttcf[k] = -tc[k] / g;
+        if (eta_ttcf_se) eta_ttcf_se[k] = tse[k] / fabs(g);
+        if (eta_dav) eta_dav[k] = -dv[k] / g;
+        if (eta_dav_se) eta_dav_se[k] = dse[k] / fabs(g);
+    }
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_daughter_series(ttcf_ctx *ctx, int batch_id, double *B, double *Omega,
+                                 size_t capacity_B) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    const size_t n = (size_t)b->D() * b->S;
+    if (B && capacity_B < n) return fail(ctx, TTCF_E_INVALID, "capacity_B too small");
+    CK(cudaStreamSynchronize(ctx->st));
+    if (B) CK(cudaMemcpy(B, b->B, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (Omega) CK(cudaMemcpy(Omega, b->Omega, sizeof(double) * b->D(), cudaMemcpyDeviceToHost));
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_group_status(ttcf_ctx *ctx, int batch_id, int *status, int capacity) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (!status || capacity < b->G) return fail(ctx, TTCF_E_INVALID, "capacity smaller than n_mothers");
+    std::vector<int> st(b->D());
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(st.data(), b->status, sizeof(int) * b->D(), cudaMemcpyDeviceToHost));
+    for (int g = 0; g < b->G; g++) {
+        int v = 0;
+        for (int k = 0; k < b->M; k++) v |= st[(size_t)g * b->M + k];
+        status[g] = v;
+    }
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_get_state(ttcf_ctx *ctx, int batch_id, int daughter, double *soa, double *alpha,
+                           double *delta) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (!b->state) return fail(ctx, TTCF_E_STATE, "no saved state (set keep_state = 1)");
+    if (daughter < 0 || daughter >= b->D()) return fail(ctx, TTCF_E_INVALID, "bad daughter index");
+    const int N = b->N;
+    std::vector<unsigned long long> sl((size_t)6 * N);
+    double sc[4];
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(sl.data(), b->state + (size_t)daughter * 6 * N, sizeof(unsigned long long) * 6 * N,
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(sc, b->scal + (size_t)daughter * 4, sizeof(sc), cudaMemcpyDeviceToHost));
+    const bool mixed = ctx->cfg.precision == TTCF_MIXED;
+    auto val = [&](size_t k) {
+        if (mixed) { float2 v; memcpy(&v, &sl[k], 8); return (double)v.x + (double)v.y; }
+        double v; memcpy(&v, &sl[k], 8); return v;
+    };
+    const double f = 1.0 + sc[2];
+    const double dl = sc[3];
+    for (int i = 0; i < N; i++) {
+        double x = val(i), y = val(N + i), z = val(2 * N + i);
+        const double ny = rint(y / b->L[1]);
+        y -= ny * b->L[1]; x -= ny * dl;
+        x -= b->L[0] * rint(x / b->L[0]);
+        z -= b->L[2] * rint(z / b->L[2]);
+        if (x >= 0.5 * b->L[0]) x -= b->L[0];
+        if (y >= 0.5 * b->L[1]) y -= b->L[1];
+        if (z >= 0.5 * b->L[2]) z -= b->L[2];
+        if (soa) {
+            soa[i] = x; soa[N + i] = y; soa[2 * N + i] = z;
+            soa[3 * N + i] = f * val(3 * N + i);
+            soa[4 * N + i] = f * val(4 * N + i);
+            soa[5 * N + i] = f * val(5 * N + i);
+        }
+    }
+    if (alpha) *alpha = sc[0];
+    if (delta) *delta = dl;
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_get_stats(ttcf_ctx *ctx, ttcf_stats *out) {
+    if (!ctx || !out) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    *out = ctx->stats;
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_init,
+                                const double *init_soa, int n_eq, int n_states, int spacing,
+                                double *out_soa, double *out_alpha) {
+    if (!ctx || !box || !init_soa || !out_soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (n_eq < 0 || n_states < 1 || spacing < 1) return fail(ctx, TTCF_E_INVALID, "bad sampling schedule");
+    const long long total = (long long)n_eq + (long long)n_states * spacing;
+    if (total > 2000000000LL) return fail(ctx, TTCF_E_INVALID, "trajectory too long");
+    const int maps[1] = {0};
+    BatchHost b;
+    Pool pool(ctx);
+    ttcf_status s = make_batch(ctx, pool, b, n_atoms, box, n_init, init_soa, nullptr, nullptr, 0,
+                               maps, 1, 1, 0.0);
+    if (s != TTCF_OK) return s;
+    b.d0 = 0;
+    const int N = n_atoms;
+    double *snap = pool.get<double>((size_t)n_init * n_states * 6 * N);
+    double *snap_a = pool.get<double>((size_t)n_init * n_states);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (mother snapshots)");
+    RunArgs a;
+    memset(&a, 0, sizeof(a));
+    a.step0 = 0; a.step1 = (int)total;
+    a.sample_every = (int)total + 1;
+    a.fresh = 1; a.dt = ctx->cfg.dt; a.skin = (float)ctx->skin;
+    a.reset_alpha = 1;
+    a.abort_flag = nullptr;
+    a.snap = snap; a.snap_alpha = snap_a;
+    a.snap_first = n_eq + spacing; a.snap_every = spacing; a.n_snap = n_states;
+    std::vector<BatchHost *> bs = {&b};
+    int launches = 0;
+    s = launch_batches(ctx, pool, bs, a, launches);
+    if (s != TTCF_OK) return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<int> stv(b.D());
+    CK(cudaMemcpy(stv.data(), b.status, sizeof(int) * b.D(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out_soa, snap, sizeof(double) * (size_t)n_init * n_states * 6 * N, cudaMemcpyDeviceToHost));
+    if (out_alpha)
+        CK(cudaMemcpy(out_alpha, snap_a, sizeof(double) * (size_t)n_init * n_states, cudaMemcpyDeviceToHost));
+    for (int v : stv)
+        if (v) return fail(ctx, TTCF_E_NUMERIC, "a mother trajectory failed");
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
+                        double delta, const double *soa, double *F, double *W, double *U) {
+    if (!ctx || !box || !soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    const int maps[1] = {0};
+    BatchHost b;
+    Pool pool(ctx);
+    ttcf_status s = make_batch(ctx, pool, b, n_atoms, box, n_states, soa, nullptr, nullptr, 0,
+                               maps, 1, 1, delta);
+    if (s != TTCF_OK) return s;
+    b.d0 = 0;
+    const int N = n_atoms;
+    double *fo = pool.get<double>((size_t)n_states * 3 * N);
+    double *wo = pool.get<double>(n_states);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (forces)");
+    RunArgs a;
+    memset(&a, 0, sizeof(a));
+    a.step0 = 0; a.step1 = 0; a.sample_every = 1; a.fresh = 1;
+    a.dt = ctx->cfg.dt; a.skin = (float)ctx->skin; a.delta0 = delta;
+    a.force_out = fo; a.wxy_out = wo;
+    std::vector<BatchHost *> bs = {&b};
+    int launches = 0;
+    s = launch_batches(ctx, pool, bs, a, launches);
+    if (s != TTCF_OK) return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<double> wxy(n_states), feat((size_t)n_states * 16);
+    if (F) CK(cudaMemcpy(F, fo, sizeof(double) * (size_t)n_states * 3 * N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(wxy.data(), wo, sizeof(double) * n_states, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(feat.data(), b.feat, sizeof(double) * feat.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < n_states; k++) {
+        if (W) {
+            // xy from the kernel under test; the other components from the
+            // double-precision spawn pass (virial part only)
+            for (int c = 0; c < 6; c++) W[6 * k + c] = feat[16 * k + 8 + c] * b.V;
+            W[6 * k + 3] = wxy[k];
+        }
+        if (U) U[k] = feat[16 * k + 6];
+    }
+    return TTCF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,702 @@
+// ttcf_daughter.cu -- the persistent daughter kernel (hot path).
+//
+// One CTA runs one daughter trajectory at a time and pops the next one from
+// an atomic work counter.  A daughter's positions live in shared memory;
+// thread t owns atoms i = t + q*blockDim (q < APT) and keeps their momenta
+// and forces in registers.  One step of the thermostatted SLLOD equations
+// (Eq. 5), split into exactly solvable flows as E D C B A B C D E:
+//   phase A  p *= exp(-alpha h/2) (the end-of-step and start-of-step
+//            halves folded into one factor), p_x -= gamma (h/2) p_y,
+//            p += (h/2) F, drift r += h p + x_hat gamma h (y + h p_y/2)
+//                                                              -> barrier 1
+//   list     Verlet list rebuilt from a Lees-Edwards-aware cell binning
+//            when an atom moved more than (skin - |change of delta|)/2
+//   phase B  WCA pair forces (Eq. 6) and virial W_xy over sorted lists
+//   phase C  p += (h/2) F, p_x -= gamma (h/2) p_y, per-warp partial sums
+//                                                              -> barrier 2
+//   lane 0   in IEEE double: the two Nose-Hoover half-steps of alpha, the
+//            factor exp(-alpha h/2) - 1, the sample B(s) = P_xy(s) of
+//            Eq. 7, the Lees-Edwards offset                    -> barrier 3
+// Lists are sorted by neighbour index and only pairs with r < r_c
+// contribute, so forces are a function of the positions alone; positions
+// are wrapped into the box every WRAP_EVERY steps of absolute time; hence
+// a run split into chunks reproduces one long run bit for bit.
+#include <type_traits>
+
+#include "ttcf_device.cuh"
+#include "ttcf_internal.h"
+
+namespace ttcf {
+
+// ------------------------------------------------ generic state algebra --
+__device__ __forceinline__ df sadd(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ double sadd(double a, double b) { return a + b; }
+__device__ __forceinline__ df smul(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ double smul(double a, double b) { return a * b; }
+__device__ __forceinline__ df smulf(df a, float b) { return df_mul_f(a, b); }
+__device__ __forceinline__ double smulf(double a, double b) { return a * b; }
+__device__ __forceinline__ df sneg(df a) { return df_neg(a); }
+__device__ __forceinline__ double sneg(double a) { return -a; }
+__device__ __forceinline__ float shi(df a) { return a.hi; }
+__device__ __forceinline__ double shi(double a) { return a; }
+__device__ __forceinline__ double sdbl(df a) { return df_to_double(a); }
+__device__ __forceinline__ double sdbl(double a) { return a; }
+template <class S> __device__ __forceinline__ S sfrom(double x);
+template <> __device__ __forceinline__ df sfrom<df>(double x) { return df_from_double(x); }
+template <> __device__ __forceinline__ double sfrom<double>(double x) { return x; }
+
+template <class S> __device__ __forceinline__ S load_slot(const unsigned long long *p);
+template <> __device__ __forceinline__ df load_slot<df>(const unsigned long long *p) {
+    float2 v = *reinterpret_cast<const float2 *>(p);
+    return {v.x, v.y};
+}
+template <> __device__ __forceinline__ double load_slot<double>(const unsigned long long *p) {
+    return *reinterpret_cast<const double *>(p);
+}
+__device__ __forceinline__ void store_slot(unsigned long long *p, df v) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo);
+}
+__device__ __forceinline__ void store_slot(unsigned long long *p, double v) {
+    *reinterpret_cast<double *>(p) = v;
+}
+
+// Per-daughter constants and per-step coefficients, written by thread 0.
+template <class S>
+struct Coef {
+    S e;                   // phase-A momentum factor minus 1
+    S h, hh, gh, chalf;    // h, h/2, gamma h, gamma h/2
+    S L[3];
+    S delta_s;             // Lees-Edwards offset for position wraps
+    double delta_d;        // Lees-Edwards offset (FP64 mode forces)
+    double invL[3];
+    float delta_f;         // Lees-Edwards offset (FP32 forces)
+    float Lf[3], invLf[3];
+    float thr2;            // rebuild threshold, squared; < 0 forces a rebuild
+    float fast2;           // fatal single-step displacement, squared
+    float rl2;             // list radius squared
+    int stop;
+    int snap;              // snapshot index written after this step, or -1
+    double fsnap;          // pending momentum factor for the snapshot
+};
+
+struct Misc {
+    double slot[MAX_WARPS][3];   // per-warp partial sums (df packed or double)
+    int warp_tmp[MAX_WARPS];
+    int flag_rebuild[2];
+    int flag_fast;
+    int flag_ovf;
+    int flag_lost;
+};
+
+// --------------------------------------------------------- reductions --
+__device__ __forceinline__ df shfl_df(df v, int o) {
+    return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ df warp_sum(df v) {
+    for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_df(v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// CTA sums of three per-thread partials in a fixed order (float partials
+// summed as double-float in MIXED mode).  Contains one __syncthreads; the
+// result is valid in thread 0 only.
+template <bool MIXED, class R>
+__device__ __forceinline__ void cta_sum3(R a0, R a1, R a2, Misc *m, double out[3]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    if constexpr (MIXED) {
+        df s0 = warp_sum(df_make(a0)), s1 = warp_sum(df_make(a1)), s2 = warp_sum(df_make(a2));
+        if (lane == 0) {
+            float2 *sl = reinterpret_cast<float2 *>(&m->slot[warp][0]);
+            sl[0] = make_float2(s0.hi, s0.lo);   // slot[warp] holds three float2
+            sl[1] = make_float2(s1.hi, s1.lo);
+            sl[2] = make_float2(s2.hi, s2.lo);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            df t0 = {0.f, 0.f}, t1 = {0.f, 0.f}, t2 = {0.f, 0.f};
+            if (lane < nw) {
+                const float2 *sl = reinterpret_cast<const float2 *>(&m->slot[lane][0]);
+                t0 = {sl[0].x, sl[0].y}; t1 = {sl[1].x, sl[1].y}; t2 = {sl[2].x, sl[2].y};
+            }
+            t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2);
+            if (lane == 0) { out[0] = df_to_double(t0); out[1] = df_to_double(t1); out[2] = df_to_double(t2); }
+        }
+    } else {
+        double s0 = warp_sum((double)a0), s1 = warp_sum((double)a1), s2 = warp_sum((double)a2);
+        if (lane == 0) { m->slot[warp][0] = s0; m->slot[warp][1] = s1; m->slot[warp][2] = s2; }
+        __syncthreads();
+        if (warp == 0) {
+            double t0 = 0, t1 = 0, t2 = 0;
+            if (lane < nw) { t0 = m->slot[lane][0]; t1 = m->slot[lane][1]; t2 = m->slot[lane][2]; }
+            t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2);
+            if (lane == 0) { out[0] = t0; out[1] = t1; out[2] = t2; }
+        }
+    }
+}
+
+// exp(x) - 1 for the small arguments -alpha h/2 (Taylor to x^7 when
+// |x| < 1e-2: truncation below 1e-18 relative), else the library routine.
+__device__ __forceinline__ double expm1_small(double x) {
+    if (fabs(x) < 1e-2) {
+        double t = 1.0 / 5040.0;
+        t = t * x + 1.0 / 720.0;
+        t = t * x + 1.0 / 120.0;
+        t = t * x + 1.0 / 24.0;
+        t = t * x + 1.0 / 6.0;
+        t = t * x + 0.5;
+        t = t * x + 1.0;
+        return t * x;
+    }
+    return expm1(x);
+}
+
+// ------------------------------------------------------- one daughter --
+template <bool MIXED, int APT>
+__device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned char *smem) {
+    using S = typename std::conditional<MIXED, df, double>::type;   // state scalar
+    using R = typename std::conditional<MIXED, float, double>::type; // force arithmetic
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int bi = a.dbatch[d];
+    const BatchDev &b = a.batches[bi];
+    const int N = b.N;
+    const int dl = (int)(d - b.d0);          // daughter index within the batch
+    const int gl = dl / b.M;                 // mother group within the batch
+    const int map = b.maps[dl % b.M];        // mapping of Eq. 3
+    const double gamma = b.gamma[gl];
+    const int nmax = a.nmax, ncm = a.ncellmax;
+    const int *nc = b.nc;
+
+    // shared-memory carve-up (daughter_smem_bytes mirrors this)
+    unsigned char *sp = smem;
+    float4 *pos4 = nullptr, *plo4 = nullptr;
+    double *xd = nullptr, *yd = nullptr, *zd = nullptr;
+    if constexpr (MIXED) {
+        pos4 = (float4 *)sp; sp += (size_t)nmax * 16;
+        plo4 = (float4 *)sp; sp += (size_t)nmax * 16;
+    } else {
+        xd = (double *)sp; sp += (size_t)nmax * 8;
+        yd = (double *)sp; sp += (size_t)nmax * 8;
+        zd = (double *)sp; sp += (size_t)nmax * 8;
+    }
+    float4 *ref4 = (float4 *)sp; sp += (size_t)nmax * 16;
+    int *cnt = (int *)sp; sp += (size_t)ncm * 4;
+    int *start = (int *)sp; sp += (size_t)(ncm + 2) * 4;
+    unsigned short *catom = (unsigned short *)sp; sp += ((size_t)nmax * 2 + 15) / 16 * 16;
+    Coef<S> *cf = (Coef<S> *)sp; sp += (sizeof(Coef<S>) + 15) / 16 * 16;
+    Misc *m = (Misc *)sp;
+
+    unsigned short *nbr = a.nbr + (size_t)blockIdx.x * CAP * nmax;
+
+    // thread 0 keeps the IEEE-double scalars of the daughter in registers
+    double a_end = 0.0, a_cur = 0.0, K2_end = 0.0, e1 = 0.0, delta = 0.0, dsince = 0.0;
+    unsigned int n_rebuild = 0;
+    const double h = a.dt, hh = 0.5 * a.dt, hhQ = hh / b.Q;
+    if (tid == 0) {
+        cf->h = sfrom<S>(h); cf->hh = sfrom<S>(hh);
+        cf->gh = sfrom<S>(gamma * h); cf->chalf = sfrom<S>(gamma * hh);
+        for (int k = 0; k < 3; k++) {
+            cf->L[k] = sfrom<S>(b.L[k]);
+            cf->Lf[k] = (float)b.L[k];
+            cf->invLf[k] = (float)(1.0 / b.L[k]);
+            cf->invL[k] = 1.0 / b.L[k];
+        }
+        const float rl = (float)(1.1224620483093730 + (double)a.skin);
+        cf->rl2 = rl * rl;
+        cf->fast2 = 0.25f * a.skin * a.skin;
+        cf->thr2 = -1.f;
+        cf->stop = 0; cf->snap = -1; cf->fsnap = 1.0;
+        m->flag_rebuild[0] = m->flag_rebuild[1] = 0;
+        m->flag_fast = 0; m->flag_ovf = 0; m->flag_lost = 0;
+        if (a.fresh) {
+            const double sa = (map == 1 || map == 3) ? -1.0 : 1.0;
+            a_end = a.reset_alpha ? 0.0 : sa * b.m_alpha[gl];
+            e1 = 0.0;
+            delta = a.delta0;
+        } else {
+            const double *sc = b.scal + 4 * (size_t)dl;
+            a_end = sc[0]; K2_end = sc[1]; e1 = sc[2]; delta = sc[3];
+        }
+        cf->delta_d = delta; cf->delta_s = sfrom<S>(delta); cf->delta_f = (float)delta;
+    }
+    __syncthreads();
+
+    // ---- load the phase point (mapped mother, or the saved loop state) ----
+    S P[APT][3];
+    R F[APT][3];
+    int ncnt[APT];
+    {
+        const bool flipx = a.fresh && (map == 2 || map == 3);
+        const bool flippx = a.fresh && (map == 1 || map == 2);
+        const bool flippyz = a.fresh && (map == 1 || map == 3);
+        const unsigned long long *src = a.fresh ? b.mothers + (size_t)gl * 6 * N
+                                                : b.state + (size_t)dl * 6 * N;
+        const R Lhx = (R)(0.5 * b.L[0]);
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            ncnt[q] = 0;
+            F[q][0] = F[q][1] = F[q][2] = (R)0;
+            P[q][0] = P[q][1] = P[q][2] = sfrom<S>(0.0);
+            if (i < N) {
+                S x = load_slot<S>(src + i), y = load_slot<S>(src + N + i), z = load_slot<S>(src + 2 * N + i);
+                S px = load_slot<S>(src + 3 * N + i), py = load_slot<S>(src + 4 * N + i), pz = load_slot<S>(src + 5 * N + i);
+                if (flipx) {   // x -> -x; -(-L/2) = +L/2 is the same periodic point
+                    x = sneg(x);
+                    if (shi(x) >= Lhx) x = sadd(x, sneg(cf->L[0]));
+                }
+                if (flippx) px = sneg(px);
+                if (flippyz) { py = sneg(py); pz = sneg(pz); }
+                P[q][0] = px; P[q][1] = py; P[q][2] = pz;
+                if constexpr (MIXED) {
+                    pos4[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
+                    plo4[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
+                } else {
+                    xd[i] = x; yd[i] = y; zd[i] = z;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- geometry helpers ----
+    // minimum-image vector r_i - r_j under Lees-Edwards images (y first)
+    auto pair_vec = [&](int i, int j, R &dx, R &dy, R &dz) {
+        if constexpr (MIXED) {
+            const float4 u = pos4[i], v = pos4[j];
+            dx = u.x - v.x; dy = u.y - v.y; dz = u.z - v.z;
+            const float ny = rint_fma(dy, cf->invLf[1]);
+            dy = __fmaf_rn(-ny, cf->Lf[1], dy);
+            dx = __fmaf_rn(-ny, cf->delta_f, dx);
+            const float nx = rint_fma(dx, cf->invLf[0]);
+            dx = __fmaf_rn(-nx, cf->Lf[0], dx);
+            const float nz = rint_fma(dz, cf->invLf[2]);
+            dz = __fmaf_rn(-nz, cf->Lf[2], dz);
+        } else {
+            dx = xd[i] - xd[j]; dy = yd[i] - yd[j]; dz = zd[i] - zd[j];
+            const double ny = rint(dy * cf->invL[1]);
+            dy -= ny * b.L[1]; dx -= ny * cf->delta_d;
+            dx -= rint(dx * cf->invL[0]) * b.L[0];
+            dz -= rint(dz * cf->invL[2]) * b.L[2];
+        }
+    };
+    // position of atom i mapped into the primary box (for binning only)
+    auto wrapped = [&](int i, float &wx, float &wy, float &wz) {
+        R x, y, z;
+        if constexpr (MIXED) { const float4 v = pos4[i]; x = v.x; y = v.y; z = v.z; }
+        else { x = xd[i]; y = yd[i]; z = zd[i]; }
+        if constexpr (MIXED) {
+            const float ny = rint_fma(y, cf->invLf[1]);
+            y = __fmaf_rn(-ny, cf->Lf[1], y); x = __fmaf_rn(-ny, cf->delta_f, x);
+            x = __fmaf_rn(-rint_fma(x, cf->invLf[0]), cf->Lf[0], x);
+            z = __fmaf_rn(-rint_fma(z, cf->invLf[2]), cf->Lf[2], z);
+        } else {
+            const double ny = rint(y * cf->invL[1]);
+            y -= ny * b.L[1]; x -= ny * cf->delta_d;
+            x -= rint(x * cf->invL[0]) * b.L[0];
+            z -= rint(z * cf->invL[2]) * b.L[2];
+        }
+        wx = (float)x; wy = (float)y; wz = (float)z;
+    };
+    auto cell_of = [&](float w, int k) {
+        int c = (int)floorf((w + 0.5f * cf->Lf[k]) * ((float)nc[k] * cf->invLf[k]));
+        return min(max(c, 0), nc[k] - 1);
+    };
+
+    // ---- Verlet list: cell binning (width >= r_c + skin), sorted lists ----
+    auto build_list = [&]() {
+        const int ncell = b.ncell;
+        for (int c = tid; c < ncell; c += T) cnt[c] = 0;
+        __syncthreads();
+        int mycell[APT], myslot[APT];
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            mycell[q] = 0; myslot[q] = 0;
+            if (i < N) {
+                float wx, wy, wz;
+                wrapped(i, wx, wy, wz);
+                const int c = (cell_of(wz, 2) * nc[1] + cell_of(wy, 1)) * nc[0] + cell_of(wx, 0);
+                mycell[q] = c;
+                myslot[q] = atomicAdd(&cnt[c], 1);
+                if constexpr (MIXED) ref4[i] = pos4[i];
+                else ref4[i] = make_float4((float)xd[i], (float)yd[i], (float)zd[i], 0.f);
+            }
+        }
+        __syncthreads();
+        cta_exclusive_scan(cnt, start, ncell, m->warp_tmp);
+        __syncthreads();
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            if (i < N) catom[start[mycell[q]] + myslot[q]] = (unsigned short)i;
+        }
+        __syncthreads();
+        const float rl = sqrtf(cf->rl2);
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            if (i >= N) continue;
+            float wx, wy, wz;
+            wrapped(i, wx, wy, wz);
+            // a lost (non-finite or runaway) atom ends the daughter; it must
+            // not reach the loops below, whose bounds come from its position
+            if (!(fabsf(wx) <= cf->Lf[0] && fabsf(wy) <= cf->Lf[1] && fabsf(wz) <= cf->Lf[2])) {
+                m->flag_lost = 1;
+                ncnt[q] = 0;
+                continue;
+            }
+            const int cx = cell_of(wx, 0), cy = cell_of(wy, 1), cz = cell_of(wz, 2);
+            unsigned short lst[CAP];
+            int k = 0;
+            bool ovf = false;
+            for (int oy = -1; oy <= 1; oy++) {
+                int yy = cy + oy;
+                const int cross = yy < 0 ? -1 : (yy >= nc[1] ? 1 : 0);
+                yy = (yy + nc[1]) % nc[1];
+                int x0 = cx - 1, x1 = cx + 1;
+                if (cross != 0) {
+                    // the row across the y face is seen shifted by cross*delta
+                    const float xs = wx - (float)cross * cf->delta_f;
+                    const float s = (float)nc[0] * cf->invLf[0];
+                    const float hl = 0.5f * cf->Lf[0];
+                    x0 = (int)floorf((xs - rl + hl) * s);   // |xs| <= 2 L: small ints
+                    x1 = min((int)floorf((xs + rl + hl) * s), x0 + 2);
+                }
+                for (int oz = -1; oz <= 1; oz++) {
+                    const int zz = (cz + oz + nc[2]) % nc[2];
+                    for (int xc = x0; xc <= x1; xc++) {
+                        const int xx = ((xc % nc[0]) + nc[0]) % nc[0];
+                        const int c = (zz * nc[1] + yy) * nc[0] + xx;
+                        const int t1 = start[c + 1];
+                        for (int t = start[c]; t < t1; t++) {
+                            const int j = catom[t];
+                            if (j == i) continue;
+                            R dx, dy, dz;
+                            pair_vec(i, j, dx, dy, dz);
+                            const float r2 = (float)(dx * dx + dy * dy + dz * dz);
+                            if (r2 < cf->rl2) {
+                                if (k == CAP) { ovf = true; continue; }
+                                int pi = k++;
+                                while (pi > 0 && lst[pi - 1] > j) { lst[pi] = lst[pi - 1]; pi--; }
+                                lst[pi] = (unsigned short)j;
+                            }
+                        }
+                    }
+                }
+            }
+            if (ovf) m->flag_ovf = 1;
+            for (int t = 0; t < k; t++) nbr[(size_t)t * nmax + i] = lst[t];
+            ncnt[q] = k;
+        }
+    };
+
+    // ---- WCA forces (Eq. 6) and virial of own atoms ----
+    unsigned int npairs = 0;
+    auto forces = [&]() -> R {
+        const R rc2 = (R)1.2599210498948732;   // r_c^2 = 2^(1/3)
+        R wsum = 0;
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            R fx = 0, fy = 0, fz = 0, w = 0;
+            if (i < N) {
+                const int kk = ncnt[q];
+                for (int t = 0; t < kk; t++) {
+                    const int j = nbr[(size_t)t * nmax + i];
+                    R dx, dy, dz;
+                    pair_vec(i, j, dx, dy, dz);
+                    const R r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < rc2) {
+                        R s;
+                        if constexpr (MIXED) s = rcp_approx(r2); else s = 1.0 / r2;
+                        const R s3 = s * s * s;
+                        const R f = s3 * s * ((R)48 * s3 - (R)24);   // |F|/r
+                        fx += f * dx; fy += f * dy; fz += f * dz;
+                        w += f * dx * dy;
+                        npairs++;
+                    }
+                }
+            }
+            F[q][0] = fx; F[q][1] = fy; F[q][2] = fz;
+            wsum += w;
+        }
+        return wsum;
+    };
+
+    // thread 0: coefficients of the next step from K2_end, a_end, e1, delta
+    auto next_step = [&]() {
+        const double inc = hhQ * (K2_end - b.gT);
+        a_cur = a_end + inc;                       // start-of-step alpha half-step
+        const double e3 = expm1_small(-a_cur * hh);
+        const double ec = e1 + e3 + e1 * e3;       // pending factor times new one
+        e1 = e3;
+        cf->e = sfrom<S>(ec);
+        const double dd = gamma * b.L[1] * h;      // sliding-brick offset advance
+        delta += dd;
+        delta -= b.L[0] * rint(delta * cf->invL[0]);
+        dsince += dd;
+        cf->delta_d = delta; cf->delta_s = sfrom<S>(delta); cf->delta_f = (float)delta;
+        const double thr = 0.5 * ((double)a.skin - fabs(dsince));
+        cf->thr2 = thr > 0.0 ? (float)(thr * thr) : -1.f;
+    };
+
+    // ---- forces and sums of the initial state ----
+    build_list();
+    n_rebuild++;
+    R w0 = forces();
+    if (a.force_out) {
+        double *fo = a.force_out + (size_t)d * 3 * N;
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            if (i < N) { fo[i] = (double)F[q][0]; fo[N + i] = (double)F[q][1]; fo[2 * N + i] = (double)F[q][2]; }
+        }
+    }
+    {
+        R s2 = 0, sxy = 0;
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            if (i < N) {
+                const R px = (R)shi(P[q][0]), py = (R)shi(P[q][1]), pz = (R)shi(P[q][2]);
+                s2 += px * px + py * py + pz * pz;
+                sxy += px * py;
+            }
+        }
+        double sums[3];
+        cta_sum3<MIXED, R>(s2, sxy, w0, m, sums);
+        if (tid == 0) {
+            if (a.wxy_out) a.wxy_out[d] = 0.5 * sums[2];
+            if (a.fresh) K2_end = sums[0];
+            if (m->flag_ovf) cf->stop = TTCF_D_NBR_OVERFLOW;
+            if (m->flag_lost) cf->stop |= TTCF_D_NONFINITE;
+            if (a.step1 > a.step0) next_step();
+        }
+    }
+    __syncthreads();
+
+    // ---- the steps ----
+    const size_t series = (size_t)dl * b.S;
+    for (int s = a.step0 + 1; s <= a.step1; s++) {
+        if (cf->stop) break;
+        const S e = cf->e, chalf = cf->chalf, hS = cf->h, hhS = cf->hh, gh = cf->gh;
+        const bool wrap_now = (s % WRAP_EVERY) == 0;
+        const int fb = s & 1;
+        const float thr2 = cf->thr2, fast2 = cf->fast2;
+        // phase A
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            if (i >= N) continue;
+            S px = P[q][0], py = P[q][1], pz = P[q][2];
+            px = sadd(px, smul(px, e)); py = sadd(py, smul(py, e)); pz = sadd(pz, smul(pz, e));
+            px = sadd(px, sneg(smul(chalf, py)));
+            px = sadd(px, smulf(hhS, F[q][0]));
+            py = sadd(py, smulf(hhS, F[q][1]));
+            pz = sadd(pz, smulf(hhS, F[q][2]));
+            S x, y, z;
+            if constexpr (MIXED) {
+                const float4 hi = pos4[i], lo = plo4[i];
+                x = {hi.x, lo.x}; y = {hi.y, lo.y}; z = {hi.z, lo.z};
+            } else {
+                x = xd[i]; y = yd[i]; z = zd[i];
+            }
+            const S ymid = sadd(y, smul(hhS, py));
+            const S dxs = sadd(smul(hS, px), smul(gh, ymid));
+            const S dys = smul(hS, py), dzs = smul(hS, pz);
+            {
+                const float a0 = (float)shi(dxs), a1 = (float)shi(dys), a2 = (float)shi(dzs);
+                if (a0 * a0 + a1 * a1 + a2 * a2 > fast2) m->flag_fast = 1;
+            }
+            x = sadd(x, dxs); y = sadd(y, dys); z = sadd(z, dzs);
+            if (wrap_now) {   // back into [-L/2, L/2) with the sliding-brick x shift
+                R ny, nx, nz;
+                if constexpr (MIXED) ny = rint_fma(y.hi, cf->invLf[1]);
+                else ny = rint(y * cf->invL[1]);
+                y = sadd(y, sneg(smulf(cf->L[1], ny)));
+                x = sadd(x, sneg(smulf(cf->delta_s, ny)));
+                if constexpr (MIXED) nx = rint_fma(x.hi, cf->invLf[0]);
+                else nx = rint(x * cf->invL[0]);
+                x = sadd(x, sneg(smulf(cf->L[0], nx)));
+                if constexpr (MIXED) nz = rint_fma(z.hi, cf->invLf[2]);
+                else nz = rint(z * cf->invL[2]);
+                z = sadd(z, sneg(smulf(cf->L[2], nz)));
+            }
+            if constexpr (MIXED) {
+                pos4[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
+                plo4[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
+            } else {
+                xd[i] = x; yd[i] = y; zd[i] = z;
+            }
+            const float4 r = ref4[i];
+            const float ex = (float)shi(x) - r.x, ey = (float)shi(y) - r.y, ez = (float)shi(z) - r.z;
+            if (ex * ex + ey * ey + ez * ez > thr2) m->flag_rebuild[fb] = 1;
+            P[q][0] = px; P[q][1] = py; P[q][2] = pz;
+        }
+        __syncthreads();                                        // barrier 1
+        if (m->flag_fast) break;
+        if (wrap_now || m->flag_rebuild[fb] || thr2 < 0.f) {
+            build_list();
+            n_rebuild++;
+            if (tid == 0) dsince = 0.0;
+        }
+        // phase B
+        const R wsum = forces();
+        // phase C
+        R s2 = 0, sxy = 0;
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            if (i >= N) continue;
+            S px = sadd(P[q][0], smulf(hhS, F[q][0]));
+            S py = sadd(P[q][1], smulf(hhS, F[q][1]));
+            S pz = sadd(P[q][2], smulf(hhS, F[q][2]));
+            px = sadd(px, sneg(smul(chalf, py)));
+            P[q][0] = px; P[q][1] = py; P[q][2] = pz;
+            const R hx = (R)shi(px), hy = (R)shi(py), hz = (R)shi(pz);
+            s2 += hx * hx + hy * hy + hz * hz;
+            sxy += hx * hy;
+        }
+        double sums[3];
+        cta_sum3<MIXED, R>(s2, sxy, wsum, m, sums);             // barrier 2
+        if (tid == 0) {
+            // end of step s: pending factor (1+e1) from the scale half-step
+            const double f1 = 1.0 + e1, f1sq = f1 * f1;
+            K2_end = f1sq * sums[0];
+            a_end = a_cur + hhQ * (K2_end - b.gT);              // end-of-step alpha half-step
+            const double pxy = (f1sq * sums[1] + 0.5 * sums[2]) / b.V;
+            if (!isfinite(sums[0] + sums[1] + sums[2])) cf->stop |= TTCF_D_NONFINITE;
+            if (m->flag_ovf) cf->stop |= TTCF_D_NBR_OVERFLOW;
+            if (m->flag_lost) cf->stop |= TTCF_D_NONFINITE;
+            if (s % a.sample_every == 0) b.B[series + s / a.sample_every] = pxy;
+            cf->snap = -1;
+            if (a.snap && s >= a.snap_first && (s - a.snap_first) % a.snap_every == 0) {
+                const int k = (s - a.snap_first) / a.snap_every;
+                if (k < a.n_snap) {
+                    cf->snap = k; cf->fsnap = f1;
+                    a.snap_alpha[(size_t)d * a.n_snap + k] = a_end;
+                }
+            }
+            if (s == a.step1 && a.save_state) {
+                double *sc = b.scal + 4 * (size_t)dl;
+                sc[0] = a_end; sc[1] = K2_end; sc[2] = e1; sc[3] = delta;
+            }
+            if (a.abort_flag && (s & 63) == 0 && *a.abort_flag) cf->stop |= TTCF_D_ABORTED;
+            next_step();
+            m->flag_rebuild[fb ^ 1] = 0;
+        }
+        __syncthreads();                                        // barrier 3
+        if (cf->snap >= 0) {   // mother mode: store the clean phase point
+            double *o = a.snap + ((size_t)d * a.n_snap + cf->snap) * 6 * N;
+            const double fs = cf->fsnap;
+            for (int q = 0; q < APT; q++) {
+                const int i = tid + q * T;
+                if (i >= N) continue;
+                double x, y, z;
+                if constexpr (MIXED) {
+                    const float4 hi = pos4[i], lo = plo4[i];
+                    x = df_to_double({hi.x, lo.x}); y = df_to_double({hi.y, lo.y}); z = df_to_double({hi.z, lo.z});
+                } else { x = xd[i]; y = yd[i]; z = zd[i]; }
+                y -= b.L[1] * rint(y * cf->invL[1]);   // mothers have gamma = 0, delta = 0
+                x -= b.L[0] * rint(x * cf->invL[0]);
+                z -= b.L[2] * rint(z * cf->invL[2]);
+                if (x >= 0.5 * b.L[0]) x -= b.L[0];
+                if (y >= 0.5 * b.L[1]) y -= b.L[1];
+                if (z >= 0.5 * b.L[2]) z -= b.L[2];
+                o[i] = x; o[N + i] = y; o[2 * N + i] = z;
+                o[3 * N + i] = fs * sdbl(P[q][0]);
+                o[4 * N + i] = fs * sdbl(P[q][1]);
+                o[5 * N + i] = fs * sdbl(P[q][2]);
+            }
+        }
+    }
+
+    // ---- end of the chunk ----
+    if (a.save_state && b.state) {
+        unsigned long long *dst = b.state + (size_t)dl * 6 * N;
+        for (int q = 0; q < APT; q++) {
+            const int i = tid + q * T;
+            if (i >= N) continue;
+            S x, y, z;
+            if constexpr (MIXED) {
+                const float4 hi = pos4[i], lo = plo4[i];
+                x = {hi.x, lo.x}; y = {hi.y, lo.y}; z = {hi.z, lo.z};
+            } else { x = xd[i]; y = yd[i]; z = zd[i]; }
+            store_slot(dst + i, x); store_slot(dst + N + i, y); store_slot(dst + 2 * N + i, z);
+            store_slot(dst + 3 * N + i, P[q][0]); store_slot(dst + 4 * N + i, P[q][1]);
+            store_slot(dst + 5 * N + i, P[q][2]);
+        }
+        if (tid == 0 && a.step1 == a.step0) {   // no step ran: state unchanged
+            double *sc = b.scal + 4 * (size_t)dl;
+            sc[0] = a_end; sc[1] = K2_end; sc[2] = e1; sc[3] = delta;
+        }
+    }
+    {
+        unsigned long long np = npairs;
+        for (int o = 16; o > 0; o >>= 1) np += __shfl_down_sync(0xffffffffu, np, o);
+        if ((tid & 31) == 0 && np) atomicAdd(&b.pairs[dl], np);
+    }
+    if (tid == 0) {
+        int st = cf->stop;
+        if (m->flag_fast) st |= TTCF_D_FAST_ATOM;
+        if (m->flag_ovf) st |= TTCF_D_NBR_OVERFLOW;
+        if (m->flag_lost) st |= TTCF_D_NONFINITE;
+        b.status[dl] |= st;
+        b.rebuilds[dl] += n_rebuild;
+    }
+    __syncthreads();
+}
+
+template <bool MIXED, int APT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) daughter_kernel(RunArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int w = s_item;
+        __syncthreads();
+        if (w >= a.n_work) break;
+        run_daughter<MIXED, APT>(a, a.work[w], smem);
+    }
+}
+
+// ------------------------------------------------------------ launchers --
+template <bool MIXED, int APT, int MAXT, int MINB>
+static cudaError_t launch_one(const RunArgs &a, int threads, int grid, size_t smem,
+                              cudaStream_t st) {
+    auto k = daughter_kernel<MIXED, APT, MAXT, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool MIXED, int APT, int MAXT, int MINB>
+static int occupancy_one(int threads, size_t smem) {
+    auto k = daughter_kernel<MIXED, APT, MAXT, MINB>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+#define TTCF_DISPATCH(MIX, FN, ...)                                              \
+    switch (apt) {                                                               \
+    case 1: return FN<MIX, 1, 256, 4>(__VA_ARGS__);                              \
+    case 2: return FN<MIX, 2, 512, 2>(__VA_ARGS__);                              \
+    case 4: return FN<MIX, 4, 512, 1>(__VA_ARGS__);                              \
+    default: return FN<MIX, 8, 512, 1>(__VA_ARGS__);                             \
+    }
+
+cudaError_t launch_daughters(bool mixed, int apt, const RunArgs &a, int threads, int grid,
+                             size_t smem, cudaStream_t st) {
+    if (mixed) { TTCF_DISPATCH(true, launch_one, a, threads, grid, smem, st) }
+    TTCF_DISPATCH(false, launch_one, a, threads, grid, smem, st)
+}
+
+int daughter_occupancy(bool mixed, int apt, int threads, size_t smem) {
+    if (mixed) { TTCF_DISPATCH(true, occupancy_one, threads, smem) }
+    TTCF_DISPATCH(false, occupancy_one, threads, smem)
+}
+
+int max_threads_for_apt(int apt) { return apt == 1 ? 256 : 512; }
+
+}  // namespace ttcf

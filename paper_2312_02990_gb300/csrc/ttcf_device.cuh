@@ -1,0 +1,181 @@
+// ttcf_device.cuh -- device-side building blocks of the TTCF engine.
+//
+// Precision scheme of the MIXED mode (GB300 runs IEEE double at 1/72 of the
+// FP32 rate, and float<->double conversions on the same slow pipe):
+//  * positions and momenta are unevaluated sums hi + lo of two floats
+//    ("double-float", about 48 significand bits), updated with the
+//    error-free transformations TwoSum (Knuth) and FMA-based TwoProduct
+//    (Dekker 1971), all on the FP32 pipe;
+//  * pair forces and the virial are plain FP32, from the hi parts;
+//  * per-daughter scalars (Nose-Hoover alpha, Lees-Edwards offset, the
+//    pressure sample B(s), Omega(0)) are IEEE double, computed by one lane.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttcf {
+
+constexpr int CAP = 32;          // Verlet neighbours kept per atom
+constexpr int WRAP_EVERY = 64;   // positions re-wrapped into the box every 64 steps
+constexpr int MAX_WARPS = 32;
+
+// ----------------------------------------------------------------- df ---
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df df_make(float h) { return {h, 0.0f}; }
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+// Dekker's Fast2Sum, valid for |a| >= |b| (or a == 0).
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+// TwoProduct with FMA; the lo*lo term is below the format's precision.
+__device__ __forceinline__ df df_mul(df a, df b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_from_double(double x) {
+    float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// Round to nearest integer (ties to even) on the FP32 add pipe: valid for
+// |v| < 2^22.  1.5*2^23 has unit spacing, so v + M rounds v once.
+__device__ __forceinline__ float rint_fma(float v, float s) {
+    const float M = 12582912.0f;
+    return __fsub_rn(__fmaf_rn(v, s, M), M);
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ----------------------------------------------------- warp/CTA helpers --
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+__device__ __forceinline__ double warp_incl_scan(double v) {
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of cnt[0..n) into start[0..n], start[n] = total, over the
+// whole CTA (blockDim a multiple of 32, <= 1024).  warp_tmp: 32 ints of
+// shared memory.  Contains two __syncthreads.
+__device__ inline void cta_exclusive_scan(const int *cnt, int *start, int n, int *warp_tmp) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (n + T - 1) / T;
+    const int b0 = min(tid * per, n), b1 = min(b0 + per, n);
+    int s = 0;
+    for (int c = b0; c < b1; c++) s += cnt[c];
+    int incl = warp_incl_scan(s);
+    if (lane == 31) warp_tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < (T >> 5) ? warp_tmp[lane] : 0;
+        int vi = warp_incl_scan(v);
+        if (lane < (T >> 5)) warp_tmp[lane] = vi - v;
+    }
+    __syncthreads();
+    int off = warp_tmp[warp] + incl - s;
+    for (int c = b0; c < b1; c++) { start[c] = off; off += cnt[c]; }
+    if (tid == T - 1) start[n] = off;
+}
+
+// --------------------------------------------------------- descriptors ---
+// One batch: the daughters spawned from mother states of one size N.
+struct BatchDev {
+    int N, M, G, S;          // atoms, mappings per group, groups, samples
+    int maps[4];             // selected mappings (Eq. 3)
+    int nc[3];               // cells per side for the neighbour build
+    int ncell;
+    double L[3];
+    double V, Q, gT;         // volume, Nose-Hoover mass, g*T
+    double T;                // k_B T
+    long long d0;            // global index of daughter 0
+    const unsigned long long *mothers;   // [G][6][N] 8-byte slots
+    const double *m_alpha;   // [G]
+    const double *gamma;     // [G]
+    double *B;               // [D][S]
+    double *Omega;           // [D]
+    int *status;             // [D]
+    unsigned long long *pairs;   // [D]
+    unsigned int *rebuilds;  // [D]
+    double *scal;            // [D][4]: alpha_end, K2_end, e1, delta
+    unsigned long long *state;   // [D][6][N] slots, or null
+};
+
+struct RunArgs {
+    const BatchDev *batches;
+    const int *work;               // global daughter indices, launch order
+    const int *dbatch;             // batch of each global daughter
+    int n_work;
+    int *queue;                    // persistent work counter
+    unsigned short *nbr;           // [grid][CAP][nmax]
+    int nmax, ncellmax;
+    int step0, step1;              // run absolute steps step0+1 .. step1
+    int sample_every;
+    int fresh;                     // start from the mapped mother state
+    int save_state;                // write the loop state at step1
+    int reset_alpha;
+    double dt;
+    double delta0;                 // Lees-Edwards offset of fresh daughters
+    float skin;
+    const volatile int *abort_flag;  // host-mapped, may be null
+    double *snap;                  // mother mode: [D][n_snap][6][N] or null
+    double *snap_alpha;            // [D][n_snap]
+    int snap_first, snap_every, n_snap;
+    double *force_out;             // [D][3][N] forces at step0, or null
+    double *wxy_out;               // [D] virial W_xy at step0, or null
+};
+
+// Shared-memory bytes of a daughter CTA (must match the carve-up in
+// ttcf_daughter.cu).
+__host__ __device__ inline size_t daughter_smem_bytes(bool mixed, int nmax, int ncellmax) {
+    size_t b = mixed ? (size_t)nmax * 48 : (size_t)nmax * (24 + 16);
+    b += (size_t)ncellmax * 4 + (size_t)(ncellmax + 2) * 4;
+    b += ((size_t)nmax * 2 + 15) / 16 * 16;
+    b += 2048;   // coefficients, reduction slots and flags
+    return b;
+}
+
+}  // namespace ttcf

@@ -1,0 +1,54 @@
+// ttcf_internal.h -- host-side declarations shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ttcf.h"
+#include "ttcf_device.cuh"
+
+namespace ttcf {
+
+// persistent daughter kernel (ttcf_daughter.cu)
+cudaError_t launch_daughters(bool mixed, int apt, const RunArgs &a, int threads, int grid,
+                             size_t smem, cudaStream_t st);
+int daughter_occupancy(bool mixed, int apt, int threads, size_t smem);
+int max_threads_for_apt(int apt);
+
+// spawn (ttcf_spawn.cu): per mother group, IEEE-double pressure tensor of
+// the mother, B(0) and Omega(0) of its mapped daughters, conversion of the
+// mother into the state format of the daughter kernel.
+struct SpawnArgs {
+    int N, M, G;
+    int maps[4];
+    int nc[3];                 // cells per side, width >= r_c
+    int ncell;
+    double L[3], V, T;
+    int mixed;                 // 1: write float pairs, 0: doubles
+    const double *src;         // [G][6][N] mother phase points
+    const double *gamma;       // [G]
+    unsigned long long *mothers;  // [G][6][N] slots (out)
+    double *B;                 // [D][S]: writes B[d][0]
+    int S;
+    double *Omega;             // [D]
+    double *feat;              // [G][16]: P_ab (6), U, K2, or null
+    double delta;              // Lees-Edwards offset of the phase points
+};
+cudaError_t launch_spawn(const SpawnArgs &a, cudaStream_t st);
+size_t spawn_smem_bytes(int N, int ncell);
+
+// reduction (ttcf_reduce.cu): fixed-order ensemble averages of one batch.
+struct ReduceArgs {
+    int M, G, S;
+    const double *B;           // [G*M][S]
+    const double *Omega;       // [G*M]
+    const int *status;         // [G*M]
+    double ds;                 // sample spacing in time
+    double *Y, *Dg, *J;        // [G][S] work arrays
+    double *Og;                // [G]
+    double *valid;             // [G] 1 if every daughter of the group is OK
+    double *out;               // [9][S]: corr, corr_se, dav, dav_se, ttcf,
+                               //         ttcf_se, corr_c, ttcf_c, n_valid
+};
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
+
+}  // namespace ttcf

@@ -1,0 +1,122 @@
+// ttcf_reduce.cu -- ensemble averages of one batch, IEEE double, fixed
+// summation order (bitwise reproducible).
+//
+// Per mother group g (M mapped daughters m, Eq. 3):
+//   Y_g(s) = (1/M) sum_m Omega_m(0) B_m(s)      group integrand (Eq. 2)
+//   D_g(s) = (1/M) sum_m B_m(s)                 group direct average
+//   J_g(s) = D_g(0) + trapezoid int_0^s Y_g     group TTCF estimate (Eq. 1)
+//   O_g    = (1/M) sum_m Omega_m(0)
+// Ensemble: means over the groups whose daughters all finished, standard
+// errors std_g / sqrt(G) (ddof 1), and the Eq. 4 form
+//   corr_c(s) = corr(s) - <Omega(0)> dav(s),  ttcf_c = dav(0) + int corr_c.
+#include <math.h>
+
+#include "ttcf_internal.h"
+
+namespace ttcf {
+
+// pass 1: one CTA per group, threads over samples
+__global__ void reduce_groups_kernel(ReduceArgs a) {
+    __shared__ double wtmp[32];
+    const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+    const int M = a.M, S = a.S;
+    const size_t d0 = (size_t)g * M;
+    int ok = 1;
+    for (int k = 0; k < M; k++) ok &= (a.status[d0 + k] == 0);
+    double om[4];
+    for (int k = 0; k < M; k++) om[k] = a.Omega[d0 + k];
+    double *Y = a.Y + (size_t)g * S, *D = a.Dg + (size_t)g * S, *J = a.J + (size_t)g * S;
+    const double invM = 1.0 / M;
+    for (int s = tid; s < S; s += T) {
+        double y = 0.0, dsum = 0.0;
+        for (int k = 0; k < M; k++) {
+            const double bv = a.B[(d0 + k) * S + s];
+            y += om[k] * bv;
+            dsum += bv;
+        }
+        Y[s] = y * invM;
+        D[s] = dsum * invM;
+    }
+    __syncthreads();
+    // J = D(0) + cumulative trapezoid of Y: chunked CTA scan
+    const int per = (S + T - 1) / T;
+    const int b0 = min(tid * per, S), b1 = min(b0 + per, S);
+    double loc = 0.0;
+    for (int s = max(b0, 1); s < b1; s++) loc += 0.5 * a.ds * (Y[s - 1] + Y[s]);
+    double incl = warp_incl_scan(loc);
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 31) wtmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const double v = lane < (T >> 5) ? wtmp[lane] : 0.0;
+        const double vi = warp_incl_scan(v);
+        if (lane < (T >> 5)) wtmp[lane] = vi - v;
+    }
+    __syncthreads();
+    double run = D[0] + wtmp[warp] + incl - loc;
+    for (int s = b0; s < b1; s++) {
+        if (s >= 1) run += 0.5 * a.ds * (Y[s - 1] + Y[s]);
+        J[s] = run;
+    }
+    if (tid == 0) {
+        double o = 0.0;
+        for (int k = 0; k < M; k++) o += om[k];
+        a.Og[g] = o * invM;
+        a.valid[g] = ok ? 1.0 : 0.0;
+    }
+}
+
+// pass 2: one thread per sample, groups summed in index order (two passes)
+__global__ void reduce_samples_kernel(ReduceArgs a) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const int G = a.G, S = a.S;
+    double n = 0.0, sy = 0.0, sd = 0.0, sj = 0.0;
+    for (int g = 0; g < G; g++) {
+        const double v = a.valid[g];
+        if (v == 0.0) continue;
+        n += 1.0;
+        sy += a.Y[(size_t)g * S + s]; sd += a.Dg[(size_t)g * S + s]; sj += a.J[(size_t)g * S + s];
+    }
+    const double my = sy / n, md = sd / n, mj = sj / n;
+    double vy = 0.0, vd = 0.0, vj = 0.0;
+    for (int g = 0; g < G; g++) {
+        if (a.valid[g] == 0.0) continue;
+        const double ey = a.Y[(size_t)g * S + s] - my;
+        const double ed = a.Dg[(size_t)g * S + s] - md;
+        const double ej = a.J[(size_t)g * S + s] - mj;
+        vy += ey * ey; vd += ed * ed; vj += ej * ej;
+    }
+    const double se = n > 1.0 ? 1.0 / sqrt(n * (n - 1.0)) : NAN;
+    a.out[0 * S + s] = my; a.out[1 * S + s] = sqrt(vy) * se;
+    a.out[2 * S + s] = md; a.out[3 * S + s] = sqrt(vd) * se;
+    a.out[4 * S + s] = mj; a.out[5 * S + s] = sqrt(vj) * se;
+    a.out[8 * S + s] = n;
+}
+
+// pass 3: <Omega(0)> and the Eq. 4 form (one thread, sequential)
+__global__ void reduce_correct_kernel(ReduceArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int S = a.S;
+    double n = 0.0, so = 0.0;
+    for (int g = 0; g < a.G; g++)
+        if (a.valid[g] != 0.0) { n += 1.0; so += a.Og[g]; }
+    const double om = so / n;
+    const double *corr = a.out, *dav = a.out + 2 * S;
+    double *cc = a.out + 6 * S, *tc = a.out + 7 * S;
+    double run = dav[0];
+    for (int s = 0; s < S; s++) {
+        cc[s] = corr[s] - om * dav[s];
+        if (s >= 1) run += 0.5 * a.ds * (cc[s - 1] + cc[s]);
+        tc[s] = run;
+    }
+}
+
+cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st) {
+    reduce_groups_kernel<<<a.G, 256, 0, st>>>(a);
+    reduce_samples_kernel<<<(a.S + 127) / 128, 128, 0, st>>>(a);
+    reduce_correct_kernel<<<1, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ttcf

@@ -1,0 +1,155 @@
+// ttcf_spawn.cu -- switch-on of the field for one batch of daughters
+// (Figure 1; Algorithm 2 "load system state", "apply mapping", "switch on
+// ext. field").  One CTA per mother state, all arithmetic IEEE double:
+//   P_ab(0) = (1/V)[sum_i p_a p_b + sum_{i<j} r_ij,a F_ij,b]   (WCA, Eq. 6)
+//   B(0)    = P_xy(0) of each mapped daughter: mappings 0, 1 keep P_xy,
+//             mappings 2, 3 (x-reflections) negate it exactly (Eq. 3)
+//   Omega   = -gamma V B(0) / (k_B T)                        (Eq. 7)
+// so sum over the group of Omega(0) and of B(0) is exactly zero.
+#include "ttcf_internal.h"
+
+namespace ttcf {
+
+size_t spawn_smem_bytes(int N, int ncell) {
+    return (size_t)N * 24 + (size_t)(2 * ncell + 2) * 4 + ((size_t)N * 2 + 15) / 16 * 16 +
+           32 * 13 * 8 + 256;
+}
+
+__global__ void spawn_kernel(SpawnArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+    const int N = a.N;
+    const double *src = a.src + (size_t)g * 6 * N;
+    double *xd = (double *)smem, *yd = xd + N, *zd = yd + N;
+    int *cnt = (int *)(zd + N);
+    int *start = cnt + a.ncell;
+    unsigned short *catom = (unsigned short *)(start + a.ncell + 2);
+    double *red = (double *)((unsigned char *)catom + ((size_t)N * 2 + 15) / 16 * 16);
+    int *warp_tmp = (int *)(red + 32 * 13);
+
+    const double invL[3] = {1.0 / a.L[0], 1.0 / a.L[1], 1.0 / a.L[2]};
+    for (int i = tid; i < N; i += T) { xd[i] = src[i]; yd[i] = src[N + i]; zd[i] = src[2 * N + i]; }
+    for (int c = tid; c < a.ncell; c += T) cnt[c] = 0;
+    __syncthreads();
+    auto cell3 = [&](int i, int &cx, int &cy, int &cz) {
+        double y = yd[i] - a.L[1] * rint(yd[i] * invL[1]);
+        double x = xd[i] - rint(yd[i] * invL[1]) * a.delta;
+        x -= a.L[0] * rint(x * invL[0]);
+        double z = zd[i] - a.L[2] * rint(zd[i] * invL[2]);
+        cx = min(max((int)floor((x + 0.5 * a.L[0]) * a.nc[0] * invL[0]), 0), a.nc[0] - 1);
+        cy = min(max((int)floor((y + 0.5 * a.L[1]) * a.nc[1] * invL[1]), 0), a.nc[1] - 1);
+        cz = min(max((int)floor((z + 0.5 * a.L[2]) * a.nc[2] * invL[2]), 0), a.nc[2] - 1);
+    };
+    // counting sort of atoms into cells (N <= 4096 -> at most 16 per thread)
+    int slot[16], cid[16];
+    for (int q = 0, i = tid; i < N; i += T, q++) {
+        int cx, cy, cz;
+        cell3(i, cx, cy, cz);
+        cid[q] = (cz * a.nc[1] + cy) * a.nc[0] + cx;
+        slot[q] = atomicAdd(&cnt[cid[q]], 1);
+    }
+    __syncthreads();
+    cta_exclusive_scan(cnt, start, a.ncell, warp_tmp);
+    __syncthreads();
+    for (int q = 0, i = tid; i < N; i += T, q++) catom[start[cid[q]] + slot[q]] = (unsigned short)i;
+    __syncthreads();
+
+    // 13 partial sums: kinetic K_ab (6), virial W_ab (6), U
+    double acc[13];
+    for (int k = 0; k < 13; k++) acc[k] = 0.0;
+    const double rc2 = 1.2599210498948732;
+    for (int i = tid; i < N; i += T) {
+        const double px = src[3 * N + i], py = src[4 * N + i], pz = src[5 * N + i];
+        acc[0] += px * px; acc[1] += py * py; acc[2] += pz * pz;
+        acc[3] += px * py; acc[4] += px * pz; acc[5] += py * pz;
+        int cx, cy, cz;
+        cell3(i, cx, cy, cz);
+        for (int oy = -1; oy <= 1; oy++) {
+            int yy = cy + oy;
+            const int cross = yy < 0 ? -1 : (yy >= a.nc[1] ? 1 : 0);
+            yy = (yy + a.nc[1]) % a.nc[1];
+            // rows across the y face: scan the whole row (any offset delta)
+            const int x0 = cross ? 0 : cx - 1, x1 = cross ? a.nc[0] - 1 : cx + 1;
+            for (int oz = -1; oz <= 1; oz++) {
+                const int zz = (cz + oz + a.nc[2]) % a.nc[2];
+                for (int xc = x0; xc <= x1; xc++) {
+                    const int xx = ((xc % a.nc[0]) + a.nc[0]) % a.nc[0];
+                    const int c = (zz * a.nc[1] + yy) * a.nc[0] + xx;
+                    for (int t = start[c]; t < start[c + 1]; t++) {
+                        const int j = catom[t];
+                        if (j == i) continue;
+                        double dx = xd[i] - xd[j], dy = yd[i] - yd[j], dz = zd[i] - zd[j];
+                        const double ny = rint(dy * invL[1]);
+                        dy -= ny * a.L[1]; dx -= ny * a.delta;
+                        dx -= rint(dx * invL[0]) * a.L[0];
+                        dz -= rint(dz * invL[2]) * a.L[2];
+                        const double r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < rc2) {
+                            const double s = 1.0 / r2, s3 = s * s * s;
+                            const double f = s3 * s * (48.0 * s3 - 24.0);
+                            acc[6] += 0.5 * f * dx * dx; acc[7] += 0.5 * f * dy * dy;
+                            acc[8] += 0.5 * f * dz * dz; acc[9] += 0.5 * f * dx * dy;
+                            acc[10] += 0.5 * f * dx * dz; acc[11] += 0.5 * f * dy * dz;
+                            acc[12] += 0.5 * (4.0 * s3 * (s3 - 1.0) + 1.0);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // fixed-order CTA reduction
+    const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    for (int k = 0; k < 13; k++) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp * 13 + k] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double tot[13];
+        for (int k = 0; k < 13; k++) {
+            double v = 0.0;
+            for (int w = 0; w < nw; w++) v += red[w * 13 + k];
+            tot[k] = v;
+        }
+        const double pxy = (tot[3] + tot[9]) / a.V;
+        const double gm = a.gamma[g];
+        for (int k = 0; k < a.M; k++) {
+            const int m = a.maps[k];
+            const double b0 = (m == 2 || m == 3) ? -pxy : pxy;
+            const size_t d = (size_t)g * a.M + k;
+            a.B[d * a.S] = b0;
+            a.Omega[d] = -gm * a.V * b0 / a.T;
+        }
+        if (a.feat) {
+            double *f = a.feat + (size_t)g * 16;
+            for (int k = 0; k < 6; k++) f[k] = (tot[k] + tot[6 + k]) / a.V;
+            f[6] = tot[12];
+            f[7] = tot[0] + tot[1] + tot[2];
+            for (int k = 0; k < 6; k++) f[8 + k] = tot[6 + k] / a.V;
+            f[14] = f[15] = 0.0;
+        }
+    }
+    // mother into the daughter kernel's state format
+    unsigned long long *dst = a.mothers + (size_t)g * 6 * N;
+    for (int e = tid; e < 6 * N; e += T) {
+        const double v = src[e];
+        if (a.mixed) {
+            const float h = __double2float_rn(v);
+            const float l = __double2float_rn(v - (double)h);
+            reinterpret_cast<float2 *>(dst)[e] = make_float2(h, l);
+        } else {
+            reinterpret_cast<double *>(dst)[e] = v;
+        }
+    }
+}
+
+cudaError_t launch_spawn(const SpawnArgs &a, cudaStream_t st) {
+    const size_t smem = spawn_smem_bytes(a.N, a.ncell);
+    cudaError_t e = cudaFuncSetAttribute(spawn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    spawn_kernel<<<a.G, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ttcf

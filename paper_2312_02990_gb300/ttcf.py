@@ -1,0 +1,310 @@
+"""Thin ctypes binding of ``libttcf.so`` with the names of ``include/ttcf.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Host arrays are numpy float64; device arrays may be torch CUDA
+tensors.  PyTorch supplies device memory (its caching allocator, through the
+``dev_alloc``/``dev_free`` hooks) and the stream.  There is no CPU fallback:
+if the library or a GPU is missing, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TTCF_OK, TTCF_E_INVALID, TTCF_E_CUDA, TTCF_E_OOM, TTCF_E_NUMERIC, TTCF_E_TIMEOUT, TTCF_E_STATE = range(7)
+TTCF_BULK_WCA = 0
+TTCF_FP64, TTCF_MIXED = 0, 1
+D_OK, D_NONFINITE, D_NBR_OVERFLOW, D_FAST_ATOM, D_ABORTED = 0, 1, 2, 4, 8
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+# The C ABI exported by libttcf.so (kept in sync with include/ttcf.h).
+EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_run",
+           "ttcf_response", "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
+           "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces",
+           "ttcf_destroy", "ttcf_last_error", "ttcf_version")
+
+
+class Config(C.Structure):
+    _fields_ = [("system", C.c_int), ("precision", C.c_int), ("dt", C.c_double),
+                ("T", C.c_double), ("tau_T", C.c_double), ("dof_mode", C.c_int),
+                ("n_steps", C.c_int), ("sample_every", C.c_int), ("mapping_mask", C.c_uint),
+                ("reset_alpha", C.c_int), ("keep_state", C.c_int), ("skin", C.c_double),
+                ("block_threads", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
+                ("dev_free", FREE_FN), ("alloc_user", C.c_void_p), ("timeout_s", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("ms_run", C.c_double), ("ms_spawn", C.c_double), ("ms_reduce", C.c_double),
+                ("pairs_interacting", C.c_double), ("rebuilds", C.c_double),
+                ("atom_steps", C.c_double), ("launches", C.c_int), ("block_threads", C.c_int),
+                ("skin", C.c_double)]
+
+
+class TTCFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ttcf status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libttcf.so (optionally building it first).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"{path} is missing: run __graft_entry__.build() first")
+    L = C.CDLL(path)
+    vp, ip = C.c_void_p, C.POINTER(C.c_int)
+    L.ttcf_config_default.argtypes = [C.POINTER(Config)]
+    L.ttcf_config_default.restype = None
+    L.ttcf_create.argtypes = [C.POINTER(Config), C.POINTER(vp)]
+    L.ttcf_spawn_daughters.argtypes = [vp, C.c_int, _dp, C.c_int, vp, vp, vp, C.c_int, ip]
+    L.ttcf_run.argtypes = [vp, C.c_int]
+    L.ttcf_response.argtypes = [vp, C.c_int, C.c_int] + [_dp] * 7 + [C.c_int, ip]
+    L.ttcf_viscosity.argtypes = [vp, C.c_int] + [_dp] * 5 + [C.c_int, ip]
+    L.ttcf_daughter_series.argtypes = [vp, C.c_int, _dp, _dp, C.c_size_t]
+    L.ttcf_group_status.argtypes = [vp, C.c_int, ip, C.c_int]
+    L.ttcf_get_state.argtypes = [vp, C.c_int, C.c_int, _dp, _dp, _dp]
+    L.ttcf_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.ttcf_sample_mothers.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_int,
+                                      C.c_int, _dp, _dp]
+    L.ttcf_forces.argtypes = [vp, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp, _dp]
+    L.ttcf_destroy.argtypes = [vp]
+    L.ttcf_destroy.restype = None
+    L.ttcf_last_error.argtypes = [vp]
+    L.ttcf_last_error.restype = C.c_char_p
+    L.ttcf_version.restype = C.c_char_p
+    for name in ("ttcf_create", "ttcf_spawn_daughters", "ttcf_run", "ttcf_response",
+                 "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
+                 "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _box(box) -> np.ndarray:
+    b = _f64(box).reshape(-1)
+    if b.size != 3:
+        raise ValueError("box must have 3 entries")
+    return b
+
+
+def config_default() -> Config:
+    c = Config()
+    load().ttcf_config_default(C.byref(c))
+    return c
+
+
+class _TorchAllocator:
+    """dev_alloc/dev_free hooks backed by torch's caching allocator."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, user):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+class Context:
+    """Owns one ``ttcf_ctx``.  Methods mirror the C ABI names."""
+
+    def __init__(self, cfg: Config | None = None, use_torch_allocator: bool = True,
+                 torch_stream: bool = True, **overrides):
+        L = load()
+        self._L = L
+        self.cfg = cfg if cfg is not None else config_default()
+        for k, v in overrides.items():
+            setattr(self.cfg, k, v)
+        self._alloc = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                if torch_stream and not self.cfg.stream:
+                    self.cfg.stream = torch.cuda.current_stream().cuda_stream
+                if use_torch_allocator:
+                    self._alloc = _TorchAllocator()
+                    self.cfg.dev_alloc = self._alloc.alloc
+                    self.cfg.dev_free = self._alloc.free
+        except ImportError:
+            pass
+        h = C.c_void_p()
+        st = L.ttcf_create(C.byref(self.cfg), C.byref(h))
+        if st != TTCF_OK:
+            raise TTCFError(st, L.ttcf_last_error(None).decode())
+        self.h = h
+
+    # -- helpers --
+    def _check(self, st: int, allowed=(TTCF_OK,)):
+        if st not in allowed:
+            raise TTCFError(st, self._L.ttcf_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.ttcf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n_samples(self) -> int:
+        return self.cfg.n_steps // self.cfg.sample_every + 1
+
+    @property
+    def n_maps(self) -> int:
+        return bin(self.cfg.mapping_mask & 0xF).count("1")
+
+    # -- C ABI --
+    def spawn_daughters(self, mother_soa, mother_alpha=None, shear_rates=0.0, box=None) -> int:
+        """mother_soa [G, 6, N] (numpy host or torch CUDA tensor)."""
+        is_dev = hasattr(mother_soa, "is_cuda") and mother_soa.is_cuda
+        if is_dev:
+            import torch
+            ms = mother_soa.contiguous().to(torch.float64)
+            G, _, N = ms.shape
+            al = None if mother_alpha is None else torch.as_tensor(
+                mother_alpha, dtype=torch.float64, device=ms.device).expand(G).contiguous()
+            gm = torch.as_tensor(shear_rates, dtype=torch.float64, device=ms.device).expand(G).contiguous()
+            keep = (ms, al, gm)
+            p_ms, p_al, p_gm = ms.data_ptr(), (al.data_ptr() if al is not None else None), gm.data_ptr()
+        else:
+            ms = _f64(mother_soa)
+            G, _, N = ms.shape
+            al = None if mother_alpha is None else _f64(np.broadcast_to(mother_alpha, (G,)))
+            gm = _f64(np.broadcast_to(np.asarray(shear_rates, np.float64), (G,)))
+            keep = (ms, al, gm)
+            p_ms = ms.ctypes.data
+            p_al = al.ctypes.data if al is not None else None
+            p_gm = gm.ctypes.data
+        if box is None:
+            raise ValueError("box is required")
+        bx = _box(box)
+        bid = C.c_int(-1)
+        self._check(self._L.ttcf_spawn_daughters(self.h, int(N), _ptr(bx), int(G), p_ms, p_al,
+                                                 p_gm, 1 if is_dev else 0, C.byref(bid)))
+        del keep
+        return bid.value
+
+    def run(self, n_steps: int = 0, allow_numeric: bool = False) -> int:
+        allowed = (TTCF_OK, TTCF_E_NUMERIC) if allow_numeric else (TTCF_OK,)
+        return self._check(self._L.ttcf_run(self.h, int(n_steps)), allowed)
+
+    def response(self, batch: int, corrected: bool = False) -> dict:
+        S = self.n_samples
+        arr = {k: np.zeros(S) for k in ("t", "dav", "dav_se", "corr", "corr_se", "ttcf", "ttcf_se")}
+        n = C.c_int()
+        self._check(self._L.ttcf_response(self.h, batch, 1 if corrected else 0, _ptr(arr["t"]),
+                                          _ptr(arr["dav"]), _ptr(arr["dav_se"]), _ptr(arr["corr"]),
+                                          _ptr(arr["corr_se"]), _ptr(arr["ttcf"]),
+                                          _ptr(arr["ttcf_se"]), S, C.byref(n)))
+        return arr
+
+    def viscosity(self, batch: int) -> dict:
+        S = self.n_samples
+        arr = {k: np.zeros(S) for k in ("t", "eta_ttcf", "eta_ttcf_se", "eta_dav", "eta_dav_se")}
+        n = C.c_int()
+        self._check(self._L.ttcf_viscosity(self.h, batch, _ptr(arr["t"]), _ptr(arr["eta_ttcf"]),
+                                           _ptr(arr["eta_ttcf_se"]), _ptr(arr["eta_dav"]),
+                                           _ptr(arr["eta_dav_se"]), S, C.byref(n)))
+        return arr
+
+    def daughter_series(self, batch: int, n_daughters: int):
+        S = self.n_samples
+        B = np.zeros((n_daughters, S))
+        Om = np.zeros(n_daughters)
+        self._check(self._L.ttcf_daughter_series(self.h, batch, _ptr(B), _ptr(Om), B.size))
+        return B, Om
+
+    def group_status(self, batch: int, n_groups: int) -> np.ndarray:
+        st = np.zeros(n_groups, dtype=np.int32)
+        self._check(self._L.ttcf_group_status(self.h, batch,
+                                              st.ctypes.data_as(C.POINTER(C.c_int)), n_groups))
+        return st
+
+    def get_state(self, batch: int, daughter: int, n_atoms: int):
+        soa = np.zeros((6, n_atoms))
+        a, d = C.c_double(), C.c_double()
+        self._check(self._L.ttcf_get_state(self.h, batch, daughter, _ptr(soa), C.byref(a), C.byref(d)))
+        return soa, a.value, d.value
+
+    def get_stats(self) -> dict:
+        s = Stats()
+        self._check(self._L.ttcf_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def sample_mothers(self, init_soa, box, n_eq: int, n_states: int, spacing: int):
+        init = _f64(init_soa)
+        if init.ndim == 2:
+            init = init[None]
+        n_init, _, N = init.shape
+        out = np.zeros((n_init, n_states, 6, N))
+        al = np.zeros((n_init, n_states))
+        self._check(self._L.ttcf_sample_mothers(self.h, int(N), _ptr(_box(box)), int(n_init),
+                                                _ptr(init), int(n_eq), int(n_states), int(spacing),
+                                                _ptr(out), _ptr(al)))
+        return out, al
+
+    def forces(self, soa, box, delta: float = 0.0):
+        s = _f64(soa)
+        if s.ndim == 2:
+            s = s[None]
+        n, _, N = s.shape
+        F = np.zeros((n, 3, N))
+        W = np.zeros((n, 6))
+        U = np.zeros(n)
+        self._check(self._L.ttcf_forces(self.h, int(N), _ptr(_box(box)), int(n), float(delta),
+                                        _ptr(s), _ptr(F), _ptr(W), _ptr(U)))
+        return F, W, U
+
+
+def version() -> str:
+    return load().ttcf_version().decode()
