@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: daughter atom-steps/s of the TTCF daughter ensemble on GB300.
+
+Workload (bulk WCA, Example 1 state point; the 16384-daughter configuration):
+N = 2048 atoms, rho = 0.8442, T = 0.722, dt = 0.0025; 4096 mother states
+(64 independent mothers x 64 states 200 steps apart after 20000
+thermalisation steps), x4 mappings = 16384 daughters of 1000 steps, at each
+shear rate 1e-1 ... 1e-7 (the rates reuse the same mothers).  One benchmark
+step = one full pass of the hot path over that batch: spawn (mapping,
+Omega(0), B(0)), the persistent daughter run of every daughter at every
+rate in one launch, and the on-device reduction of <Omega(0)B(s)>, its
+integral and the direct average.  Inputs are synthetic and seeded.
+
+value  = sum over daughters of N * steps / device time of the step, inputs
+         resident in HBM (mothers made on the GPU before timing);
+e2e    = the same through the C ABI with host buffers: mothers copied from
+         pinned host memory and responses read back inside the timed region.
+
+Launch:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs the same per-GPU workload on its own mothers
+(weak scaling); the only exchange is a final merge of the per-sample
+ensemble statistics.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+RATES = [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7]
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (sm_103)
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+FLOPS_PER_PAIR = 36.0            # one unique WCA pair with virial (Newton 3)
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    return N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n-atoms", type=int, default=2048)
+    p.add_argument("--mothers", type=int, default=64)
+    p.add_argument("--states", type=int, default=64)
+    p.add_argument("--daughter-steps", type=int, default=1000)
+    p.add_argument("--rates", type=int, default=7, help="number of shear rates per step")
+    p.add_argument("--n-eq", type=int, default=20000)
+    p.add_argument("--spacing", type=int, default=200)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2])); power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "power_w_median": float(np.median(power)) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- GB300 --
+def make_mothers(T, torch, args, rank, N, L):
+    """Equilibrium mothers on the GPU (untimed set-up)."""
+    from paper_2312_02990_gb300 import inputs
+    init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 1000 * rank + k)
+                     for k in range(args.mothers)])
+    cfg = T.config_default()
+    cfg.precision = T.TTCF_MIXED
+    with T.Context(cfg) as c:
+        ms, al = c.sample_mothers(init, L, n_eq=args.n_eq, n_states=args.states,
+                                  spacing=args.spacing)
+    return ms.reshape(-1, 6, N), al.reshape(-1)
+
+
+def one_step(T, torch, args, L, mothers_dev, alpha_dev, rates, host=None):
+    """One pass of the hot path.  Device inputs, or host (pinned) inputs."""
+    cfg = T.config_default()
+    cfg.precision = T.TTCF_MIXED
+    cfg.n_steps = args.daughter_steps
+    c = T.Context(cfg)
+    ids = []
+    for g in rates:
+        if host is None:
+            ids.append(c.spawn_daughters(mothers_dev, alpha_dev, float(g), box=L))
+        else:
+            ids.append(c.spawn_daughters(host[0], host[1], float(g), box=L))
+    c.run()
+    out = []
+    if host is not None or True:
+        for bid in ids:
+            out.append(c.viscosity(bid))
+    stats = c.get_stats()
+    c.close()
+    return out, stats
+
+
+def bench_gb300(args):
+    import torch
+
+    from paper_2312_02990_gb300 import inputs
+    from paper_2312_02990_gb300 import ttcf as T
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    T.load(build_if_missing=(rank == 0))
+    N = args.n_atoms
+    L = inputs.bulk_box(N)
+    rates = RATES[:args.rates]
+
+    t0 = time.time()
+    ms, al = make_mothers(T, torch, args, rank, N, L)
+    t_mothers = time.time() - t0
+    G = ms.shape[0]
+    D = 4 * G * len(rates)
+    atom_steps = float(D) * N * args.daughter_steps
+    ms_dev = torch.from_numpy(ms).cuda()
+    al_dev = torch.from_numpy(al).cuda()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        one_step(T, torch, args, L, ms_dev, al_dev, rates)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    kernel_ms, pairs, rebuilds, launches = [], [], [], 0
+    results = None
+    for _ in range(args.steps):
+        results, s = one_step(T, torch, args, L, ms_dev, al_dev, rates)
+        kernel_ms.append(s["ms_run"])
+        pairs.append(s["pairs_interacting"])
+        rebuilds.append(s["rebuilds"])
+        launches += s["launches"] + len(rates)   # + one spawn kernel per batch
+    ev1.record(st)
+    barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = atom_steps * world / (ms_step * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin_ms = torch.from_numpy(ms).pin_memory()
+        pin_al = torch.from_numpy(al).pin_memory()
+        host = (pin_ms.numpy(), pin_al.numpy())
+        one_step(T, torch, args, L, None, None, rates, host=host)
+        barrier()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step(T, torch, args, L, None, None, rates, host=host)
+        barrier()
+        e2e_s = (time.perf_counter() - t1) / args.steps
+        if world > 1:
+            tt = torch.tensor([e2e_s], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": atom_steps * world / e2e_s, "unit": "atom-steps/s",
+               "h2d_bytes_per_step": int(len(rates) * (ms.nbytes + al.nbytes + G * 8)),
+               "d2h_bytes_per_step": int(len(rates) * 5 * (args.daughter_steps + 1) * 8),
+               "ms_per_step": e2e_s * 1e3}
+
+    # the dominant kernel: the persistent daughter launch
+    k_ms = float(np.mean(kernel_ms))
+    flops = float(np.mean(pairs)) / 2.0 * FLOPS_PER_PAIR
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "daughter_kernel", "kernel_ms": k_ms,
+                "algorithmic": "unique interacting pairs x 36 FP32 flops",
+                "peak_note": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
+    eta = {f"{g:.0e}": {"eta_ttcf": float(r["eta_ttcf"][-1]), "eta_ttcf_se": float(r["eta_ttcf_se"][-1]),
+                        "eta_dav": float(r["eta_dav"][-1]), "eta_dav_se": float(r["eta_dav_se"][-1])}
+           for g, r in zip(rates, results)}
+    line = {
+        "metric": "daughter atom-steps/s", "value": value, "unit": "atom-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "precision": "MIXED: FP32 pair forces; float-float positions and momenta; "
+                                     "FP64 alpha, delta, Omega(0), B(s) and accumulation",
+        "data": "synthetic (seeded FCC + Maxwell, GPU-thermalised mothers)",
+        "config": {"workload": f"bulk WCA N={N}, {G} mother states x 4 mappings x {len(rates)} shear "
+                               f"rates = {D} daughters x {args.daughter_steps} steps",
+                   "n_atoms": N, "mother_states": G, "daughters": D,
+                   "daughter_steps": args.daughter_steps, "shear_rates": rates,
+                   "rho": 0.8442, "T": 0.722, "dt": 0.0025,
+                   "l2": "inputs larger than L2 (mothers 403 MB, series 918 MB)"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "pairs_per_atom_step": float(np.mean(pairs)) / (atom_steps),
+        "rebuilds_per_daughter_step": float(np.mean(rebuilds)) / (D * args.daughter_steps),
+        "mother_setup_s": t_mothers,
+        "viscosity_t_end": eta,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, N)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# -------------------------------------------------------------- oracle --
+def oracle_sample(N, n_groups, n_steps, gamma, threads):
+    """Bounded oracle workload: n_groups thermalised mothers (oracle-made,
+    untimed) x 4 mappings x n_steps daughter steps (timed)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from paper_2312_02990_gb300 import inputs
+    b = oracle.Bulk(n=N, L=tuple(inputs.bulk_box(N)))
+
+    def one(k):
+        return oracle.mother(b, inputs.initial_state(N, inputs.BASE_SEED + 7 * k), n_eq=600,
+                             n_states=1, spacing=200)
+
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(one, range(n_groups)))
+    ms = np.concatenate([r[0] for r in res])
+    al = np.concatenate([r[1] for r in res])
+    t = time.perf_counter()
+    oracle.daughters(b, ms, al, gamma, n_steps, n_threads=threads)
+    el = time.perf_counter() - t
+    return 4 * n_groups * N * n_steps / el, el
+
+
+def cpu_baseline(args, N):
+    threads = os.cpu_count() or 1
+    groups = max(1, threads // 4) * 2
+    steps = 400
+    v, el = oracle_sample(N, groups, steps, 1e-3, threads)
+    return {"value": v, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{4 * groups} daughters x {steps} steps, N={N}, gamma=1e-3 "
+                      f"({el:.1f} s; oracle-made mothers)"}
+
+
+def bench_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    N = args.n_atoms
+    threads = os.cpu_count() or 1
+    groups = max(1, threads // 4)
+    steps = 200
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, el = oracle_sample(N, groups, steps, RATES[k % len(RATES)], threads)
+        if k >= args.warmup:
+            vals.append((v, el))
+    v = float(np.mean([x[0] for x in vals]))
+    ms = float(np.mean([x[1] for x in vals])) * 1e3
+    line = {"impl": "reference", "metric": "daughter atom-steps/s", "value": v,
+            "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded FCC + Maxwell, oracle-thermalised mothers)",
+            "config": {"workload": f"bulk WCA N={N}, bounded sample of {4 * groups} daughters x "
+                                   f"{steps} steps per step (FP64 CPU oracle)", "n_atoms": N},
+            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{4 * groups} daughters x {steps} steps per step"},
+            "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gb300(args)
+
+
+if __name__ == "__main__":
+    main()
