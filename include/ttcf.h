@@ -94,6 +94,11 @@ typedef struct {
                                device after ttcf_run (ttcf_get_state)        */
     double skin;            /* Verlet skin (sigma); <= 0 selects autotuned   */
     int block_threads;      /* threads per daughter CTA; 0 = autotuned       */
+    int kernel_variant;     /* 0 = automatic; k >= 1 selects launch variant
+                               k-1 (atoms per thread, block size, register
+                               budget): 1 (1,256,64r) 2 (2,512,64r)
+                               3 (2,1024,64r) 4 (4,512,64r) 5 (4,512,128r)
+                               6 (8,512,128r)                                 */
     void *stream;           /* cudaStream_t; NULL = legacy default stream    */
     ttcf_alloc_fn dev_alloc;/* NULL: cudaMalloc                              */
     ttcf_free_fn dev_free;  /* NULL: cudaFree                                */
@@ -214,6 +219,19 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
  * [n_states] (potential energy).  Host outputs.                            */
 ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
                         double delta, const double *soa, double *F, double *W, double *U);
+
+/* Autotuner (launch shape and Verlet skin).  Times n_steps of the
+ * daughter kernel on n_states phase points [n_states][6][N] (host; all four
+ * mappings, shear rate gamma) for every launch variant that holds n_atoms
+ * and Verlet skins {0.2, 0.3, 0.4}, with CUDA events on the context's
+ * stream, and remembers the fastest for batches of n_atoms spawned later on
+ * this context (explicit kernel_variant / skin in the config still win).
+ * Returns the choice (1-based variant as in ttcf_config.kernel_variant),
+ * the skin and its time in ms.  Errors: TTCF_E_INVALID if no variant can
+ * run the system.                                                          */
+ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
+                          const double *soa, double shear_rate, int n_steps, int *best_variant,
+                          double *best_skin, double *best_ms);
 
 /* Release the context and all its device memory.  NULL is ignored.       */
 void ttcf_destroy(ttcf_ctx *ctx);

@@ -28,7 +28,8 @@ struct BatchHost {
     int nc[3] = {0, 0, 0}, ncell = 0;     // list cells, width >= r_c + skin
     int snc[3] = {0, 0, 0}, sncell = 0;   // spawn cells, width >= r_c
     long long d0 = 0;
-    int apt = 1, threads = 256;
+    int variant = 0, threads = 256;
+    double skin = DEFAULT_SKIN;
     std::vector<double> gamma;
     unsigned long long *mothers = nullptr;
     double *m_alpha = nullptr, *gamma_d = nullptr, *B = nullptr, *Omega = nullptr;
@@ -46,6 +47,8 @@ struct BatchHost {
 
 }  // namespace
 
+struct TunedEntry { int N; int variant; double skin; };
+
 struct ttcf_ctx {
     ttcf_config cfg;
     std::string err;
@@ -53,6 +56,7 @@ struct ttcf_ctx {
     int device = 0, nsm = 0, smem_optin = 0;
     double skin = DEFAULT_SKIN;
     std::vector<BatchHost> batches;
+    std::vector<TunedEntry> tuned;   // autotuner results per atom count
     std::vector<void *> allocs;
     long long total_d = 0;
     int steps_done = 0;
@@ -64,8 +68,7 @@ struct ttcf_ctx {
     bool tables_ok = false;
     BatchDev *d_batches = nullptr;
     int *d_dbatch = nullptr, *d_work = nullptr, *d_queue = nullptr;
-    unsigned short *d_nbr = nullptr;
-    size_t nbr_elems = 0;
+
 };
 
 namespace {
@@ -124,31 +127,49 @@ struct Pool {
 
 int popcount4(unsigned m) { int k = 0; for (int i = 0; i < 4; i++) k += (m >> i) & 1; return k; }
 
-void choose_class(int N, int block_threads, int &apt, int &threads) {
-    if (block_threads > 0) {
-        threads = block_threads;
-        apt = 1;
-        while (apt < 8 && apt * threads < N) apt *= 2;
-        if (threads > max_threads_for_apt(apt)) threads = max_threads_for_apt(apt);
-        while (apt < 8 && apt * threads < N) apt *= 2;
-        return;
-    }
-    if (N <= 256) { apt = 1; threads = std::max(32, (N + 31) / 32 * 32); }
-    else if (N <= 512) { apt = 2; threads = 256; }
-    else if (N <= 1024) { apt = 2; threads = 512; }
-    else if (N <= 2048) { apt = 4; threads = 512; }
-    else { apt = 8; threads = 512; }
+// Launch variant, block size and Verlet skin for a daughter of N atoms:
+// explicit configuration first, then the autotuner's result for this N,
+// then the default table.
+ttcf_status choose_class(ttcf_ctx *ctx, int N, int force_variant, double force_skin,
+                         int &variant, int &threads, double &skin) {
+    const ttcf_config &cf = ctx->cfg;
+    const TunedEntry *tu = nullptr;
+    for (auto &e : ctx->tuned) if (e.N == N) tu = &e;
+    if (force_variant >= 0) variant = force_variant;
+    else if (cf.kernel_variant > 0) variant = cf.kernel_variant - 1;
+    else if (tu) variant = tu->variant;
+    else if (N <= 256) variant = 0;
+    else if (N <= 1024) variant = 1;
+    else if (N <= 2048) variant = 3;
+    else variant = 5;
+    if (force_skin > 0) skin = force_skin;
+    else if (cf.skin > 0) skin = cf.skin;
+    else if (tu) skin = tu->skin;
+    else skin = DEFAULT_SKIN;
+    if (variant < 0 || variant >= N_VARIANTS) return fail(ctx, TTCF_E_INVALID, "kernel_variant out of range");
+    const Variant v = variant_of(variant);
+    int t = cf.block_threads > 0 ? cf.block_threads : (N + v.apt - 1) / v.apt;
+    t = (t + 31) / 32 * 32;
+    if (t > v.maxt || t * v.apt < N)
+        return fail(ctx, TTCF_E_INVALID, "kernel_variant/block_threads cannot hold n_atoms");
+    threads = t;
+    return TTCF_OK;
 }
 
 // Allocate a batch, copy its mothers and run the spawn kernel.
 ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const double box[3], int G,
                        const double *soa, const double *alpha, const double *gamma,
-                       int is_dev, const int *maps, int M, int S, double delta0) {
+                       int is_dev, const int *maps, int M, int S, double delta0,
+                       int force_variant = -1, double force_skin = -1.0) {
     const ttcf_config &cf = ctx->cfg;
     if (N < 4 || N > 4096) return fail(ctx, TTCF_E_INVALID, "n_atoms must be in [4, 4096]");
     if (G <= 0) return fail(ctx, TTCF_E_INVALID, "n_mothers must be positive");
     if (!soa) return fail(ctx, TTCF_E_INVALID, "mother_soa is NULL");
-    const double rl = RC_WCA + ctx->skin;
+    {
+        ttcf_status cs = choose_class(ctx, N, force_variant, force_skin, b.variant, b.threads, b.skin);
+        if (cs != TTCF_OK) return cs;
+    }
+    const double rl = RC_WCA + b.skin;
     for (int k = 0; k < 3; k++) {
         if (!(box[k] > 0) || !isfinite(box[k])) return fail(ctx, TTCF_E_INVALID, "box edges must be positive");
         if (box[k] < 3.0 * rl)
@@ -167,8 +188,6 @@ ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const dou
     const double g = cf.dof_mode == 1 ? 3.0 * N - 3.0 : 3.0 * N;
     b.Q = g * cf.T * cf.tau_T * cf.tau_T;
     b.gT = g * cf.T;
-    choose_class(N, cf.block_threads, b.apt, b.threads);
-    if (b.apt * b.threads < N) return fail(ctx, TTCF_E_INVALID, "block_threads too small for n_atoms");
 
     // host copies of gamma (needed for viscosity) and the device arrays
     b.gamma.resize(G);
@@ -238,6 +257,7 @@ BatchDev to_dev(const BatchHost &b) {
     for (int k = 0; k < 3; k++) { d.nc[k] = b.nc[k]; d.L[k] = b.L[k]; }
     d.ncell = b.ncell;
     d.V = b.V; d.Q = b.Q; d.gT = b.gT; d.d0 = b.d0;
+    d.skin = (float)b.skin;
     d.mothers = b.mothers; d.m_alpha = b.m_alpha; d.gamma = b.gamma_d;
     d.B = b.B; d.Omega = b.Omega; d.status = b.status; d.pairs = b.pairs;
     d.rebuilds = b.rebuilds; d.scal = b.scal; d.state = b.state;
@@ -245,7 +265,7 @@ BatchDev to_dev(const BatchHost &b) {
 }
 
 struct ClassLaunch {
-    int apt, threads, nmax, ncellmax, grid;
+    int variant, threads, nmax, ncellmax, grid;
     size_t smem;
     std::vector<int> work;
 };
@@ -255,8 +275,8 @@ std::vector<ClassLaunch> plan_classes(ttcf_ctx *ctx, std::vector<BatchHost *> &b
     std::vector<ClassLaunch> cls;
     for (BatchHost *b : bs) {
         ClassLaunch *c = nullptr;
-        for (auto &x : cls) if (x.apt == b->apt && x.threads == b->threads) c = &x;
-        if (!c) { cls.push_back({b->apt, b->threads, 0, 0, 0, 0, {}}); c = &cls.back(); }
+        for (auto &x : cls) if (x.variant == b->variant && x.threads == b->threads) c = &x;
+        if (!c) { cls.push_back({b->variant, b->threads, 0, 0, 0, 0, {}}); c = &cls.back(); }
         c->nmax = std::max(c->nmax, b->N);
         c->ncellmax = std::max(c->ncellmax, b->ncell);
         for (long long k = 0; k < b->D(); k++) c->work.push_back((int)(b->d0 + k));
@@ -266,7 +286,7 @@ std::vector<ClassLaunch> plan_classes(ttcf_ctx *ctx, std::vector<BatchHost *> &b
         c.smem = daughter_smem_bytes(mixed, c.nmax, c.ncellmax);
         c.grid = 0;
         if (c.smem > (size_t)ctx->smem_optin) continue;   // rejected by the caller
-        int nb = daughter_occupancy(mixed, c.apt, c.threads, c.smem);
+        int nb = daughter_occupancy(mixed, c.variant, c.threads, c.smem);
         if (nb < 1) nb = 1;
         c.grid = (int)std::min<long long>((long long)c.work.size(), (long long)nb * ctx->nsm);
         if (c.grid < 1) c.grid = 1;
@@ -303,10 +323,10 @@ ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &
     CK(cudaMemcpyAsync(d_db, dbatch.data(), sizeof(int) * dbatch.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(d_q, 0, sizeof(int) * cls.size(), st));
     std::vector<int *> d_work(cls.size());
-    std::vector<unsigned short *> d_nbr(cls.size());
+    std::vector<unsigned int *> d_nbr(cls.size());
     for (size_t k = 0; k < cls.size(); k++) {
         d_work[k] = pool.get<int>(cls[k].work.size());
-        d_nbr[k] = pool.get<unsigned short>((size_t)cls[k].grid * CAP * cls[k].nmax);
+        d_nbr[k] = pool.get<unsigned int>((size_t)cls[k].grid * (CAP / 2) * cls[k].nmax);
         if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (work lists)");
         CK(cudaMemcpyAsync(d_work[k], cls[k].work.data(), sizeof(int) * cls[k].work.size(),
                            cudaMemcpyHostToDevice, st));
@@ -330,7 +350,7 @@ ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &
         a.n_work = (int)cls[k].work.size();
         a.queue = d_q + k;
         a.nbr = d_nbr[k]; a.nmax = cls[k].nmax; a.ncellmax = cls[k].ncellmax;
-        CK(launch_daughters(mixed, cls[k].apt, a, cls[k].threads, cls[k].grid, cls[k].smem, side[k]));
+        CK(launch_daughters(mixed, cls[k].variant, a, cls[k].threads, cls[k].grid, cls[k].smem, side[k]));
         launches++;
         ctx->stats.block_threads = std::max(ctx->stats.block_threads, cls[k].threads);
     }
@@ -420,6 +440,7 @@ void ttcf_config_default(ttcf_config *c) {
     c->keep_state = 0;
     c->skin = 0.0;
     c->block_threads = 0;
+    c->kernel_variant = 0;
     c->timeout_s = 0.0;
 }
 
@@ -442,8 +463,10 @@ ttcf_status ttcf_create(const ttcf_config *cfg, ttcf_ctx **out) {
         return fail(nullptr, TTCF_E_INVALID, "n_steps must be a positive multiple of sample_every");
     if ((c.mapping_mask & 0xF) == 0 || (c.mapping_mask & ~0xFu))
         return fail(nullptr, TTCF_E_INVALID, "mapping_mask must select mappings 0..3");
-    if (c.block_threads < 0 || c.block_threads % 32 || c.block_threads > 512)
-        return fail(nullptr, TTCF_E_INVALID, "block_threads must be 0 or a multiple of 32 <= 512");
+    if (c.block_threads < 0 || c.block_threads % 32 || c.block_threads > 1024)
+        return fail(nullptr, TTCF_E_INVALID, "block_threads must be 0 or a multiple of 32 <= 1024");
+    if (c.kernel_variant < 0 || c.kernel_variant > N_VARIANTS)
+        return fail(nullptr, TTCF_E_INVALID, "kernel_variant out of range");
     if (c.skin > 1.0) return fail(nullptr, TTCF_E_INVALID, "skin must be <= 1");
     if ((c.dev_alloc == nullptr) != (c.dev_free == nullptr))
         return fail(nullptr, TTCF_E_INVALID, "dev_alloc and dev_free must be set together");
@@ -535,7 +558,6 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
     a.reset_alpha = cf.reset_alpha;
     a.dt = cf.dt;
     a.delta0 = 0.0;
-    a.skin = (float)ctx->skin;
     a.abort_flag = ctx->d_abort;
 
     std::vector<BatchHost *> bs;
@@ -550,7 +572,7 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
     ctx->stats.ms_run = ms;
-    ctx->stats.skin = ctx->skin;
+    ctx->stats.skin = ctx->batches.empty() ? ctx->skin : ctx->batches[0].skin;
     ctx->steps_done = step1;
 
     // counters and failures
@@ -737,7 +759,7 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
     memset(&a, 0, sizeof(a));
     a.step0 = 0; a.step1 = (int)total;
     a.sample_every = (int)total + 1;
-    a.fresh = 1; a.dt = ctx->cfg.dt; a.skin = (float)ctx->skin;
+    a.fresh = 1; a.dt = ctx->cfg.dt;
     a.reset_alpha = 1;
     a.abort_flag = nullptr;
     a.snap = snap; a.snap_alpha = snap_a;
@@ -774,7 +796,7 @@ ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_s
     RunArgs a;
     memset(&a, 0, sizeof(a));
     a.step0 = 0; a.step1 = 0; a.sample_every = 1; a.fresh = 1;
-    a.dt = ctx->cfg.dt; a.skin = (float)ctx->skin; a.delta0 = delta;
+    a.dt = ctx->cfg.dt; a.delta0 = delta;
     a.force_out = fo; a.wxy_out = wo;
     std::vector<BatchHost *> bs = {&b};
     int launches = 0;
@@ -794,6 +816,58 @@ ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_s
         }
         if (U) U[k] = feat[16 * k + 6];
     }
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
+                          const double *soa, double shear_rate, int n_steps, int *best_variant,
+                          double *best_skin, double *best_ms) {
+    if (!ctx || !box || !soa || n_states < 1 || n_steps < 1)
+        return fail(ctx, TTCF_E_INVALID, "bad autotune arguments");
+    const double skins[3] = {0.2, 0.3, 0.4};
+    const int maps[4] = {0, 1, 2, 3};
+    std::vector<double> gam(n_states, shear_rate);
+    double best = 1e300;
+    int bv = -1;
+    double bskin = DEFAULT_SKIN;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int v = 0; v < N_VARIANTS; v++) {
+        const Variant var = variant_of(v);
+        if (var.apt * var.maxt < n_atoms) continue;
+        if (var.apt > 1 && (n_atoms + var.apt - 1) / var.apt < 64) continue;   // too few threads
+        for (double sk : skins) {
+            BatchHost b;
+            Pool pool(ctx);
+            ttcf_status s = make_batch(ctx, pool, b, n_atoms, box, n_states, soa, nullptr, gam.data(),
+                                       0, maps, 4, n_steps + 1, 0.0, v, sk);
+            if (s != TTCF_OK) continue;   // e.g. shared memory exceeded
+            b.d0 = 0;
+            RunArgs a;
+            memset(&a, 0, sizeof(a));
+            a.step0 = 0; a.step1 = n_steps; a.sample_every = 1; a.fresh = 1;
+            a.dt = ctx->cfg.dt; a.reset_alpha = ctx->cfg.reset_alpha;
+            std::vector<BatchHost *> bs = {&b};
+            int launches = 0;
+            s = launch_batches(ctx, pool, bs, a, launches, e0, e1);
+            if (s != TTCF_OK) { ctx->err.clear(); continue; }
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; bv = v; bskin = sk; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bv < 0) return fail(ctx, TTCF_E_INVALID, "no launch variant can run this system");
+    bool found = false;
+    for (auto &e : ctx->tuned)
+        if (e.N == n_atoms) { e.variant = bv; e.skin = bskin; found = true; }
+    if (!found) ctx->tuned.push_back({n_atoms, bv, bskin});
+    if (best_variant) *best_variant = bv + 1;
+    if (best_skin) *best_skin = bskin;
+    if (best_ms) *best_ms = best;
     return TTCF_OK;
 }
 

@@ -81,6 +81,9 @@ struct Coef {
 
 struct Misc {
     double slot[MAX_WARPS][3];   // per-warp partial sums (df packed or double)
+    // IEEE-double scalars of the daughter, touched by thread 0 only
+    double a_end, a_cur, K2_end, e1, delta, dsince;
+    unsigned int n_rebuild;
     int warp_tmp[MAX_WARPS];
     int flag_rebuild[2];
     int flag_fast;
@@ -190,13 +193,15 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     Coef<S> *cf = (Coef<S> *)sp; sp += (sizeof(Coef<S>) + 15) / 16 * 16;
     Misc *m = (Misc *)sp;
 
-    unsigned short *nbr = a.nbr + (size_t)blockIdx.x * CAP * nmax;
+    unsigned int *nbr = a.nbr + (size_t)blockIdx.x * (CAP / 2) * nmax;
 
-    // thread 0 keeps the IEEE-double scalars of the daughter in registers
-    double a_end = 0.0, a_cur = 0.0, K2_end = 0.0, e1 = 0.0, delta = 0.0, dsince = 0.0;
-    unsigned int n_rebuild = 0;
-    const double h = a.dt, hh = 0.5 * a.dt, hhQ = hh / b.Q;
+    // thread 0 keeps the IEEE-double scalars of the daughter in shared memory
+    double &a_end = m->a_end, &a_cur = m->a_cur, &K2_end = m->K2_end, &e1 = m->e1;
+    double &delta = m->delta, &dsince = m->dsince;
+    const double h = a.dt, hh = 0.5 * a.dt;
     if (tid == 0) {
+        a_end = a_cur = K2_end = e1 = delta = dsince = 0.0;
+        m->n_rebuild = 0;
         cf->h = sfrom<S>(h); cf->hh = sfrom<S>(hh);
         cf->gh = sfrom<S>(gamma * h); cf->chalf = sfrom<S>(gamma * hh);
         for (int k = 0; k < 3; k++) {
@@ -205,9 +210,9 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             cf->invLf[k] = (float)(1.0 / b.L[k]);
             cf->invL[k] = 1.0 / b.L[k];
         }
-        const float rl = (float)(1.1224620483093730 + (double)a.skin);
+        const float rl = (float)(1.1224620483093730 + (double)b.skin);
         cf->rl2 = rl * rl;
-        cf->fast2 = 0.25f * a.skin * a.skin;
+        cf->fast2 = 0.25f * b.skin * b.skin;
         cf->thr2 = -1.f;
         cf->stop = 0; cf->snap = -1; cf->fsnap = 1.0;
         m->flag_rebuild[0] = m->flag_rebuild[1] = 0;
@@ -386,7 +391,12 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                 }
             }
             if (ovf) m->flag_ovf = 1;
-            for (int t = 0; t < k; t++) nbr[(size_t)t * nmax + i] = lst[t];
+            // two entries per word; an odd tail is padded with i itself (r = 0
+            // is rejected by the force loop)
+            for (int t = 0; t < k; t += 2) {
+                const unsigned int lo = lst[t], hi = (t + 1 < k) ? lst[t + 1] : (unsigned int)i;
+                nbr[(size_t)(t >> 1) * nmax + i] = lo | (hi << 16);
+            }
             ncnt[q] = k;
         }
     };
@@ -401,19 +411,48 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             R fx = 0, fy = 0, fz = 0, w = 0;
             if (i < N) {
                 const int kk = ncnt[q];
-                for (int t = 0; t < kk; t++) {
-                    const int j = nbr[(size_t)t * nmax + i];
-                    R dx, dy, dz;
-                    pair_vec(i, j, dx, dy, dz);
-                    const R r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < rc2) {
-                        R s;
-                        if constexpr (MIXED) s = rcp_approx(r2); else s = 1.0 / r2;
-                        const R s3 = s * s * s;
-                        const R f = s3 * s * ((R)48 * s3 - (R)24);   // |F|/r
-                        fx += f * dx; fy += f * dy; fz += f * dz;
-                        w += f * dx * dy;
-                        npairs++;
+                if constexpr (MIXED) {
+                    const float4 u = pos4[i];
+                    const float Lx = cf->Lf[0], Ly = cf->Lf[1], Lz = cf->Lf[2];
+                    const float ix = cf->invLf[0], iy = cf->invLf[1], iz = cf->invLf[2];
+                    const float dl = cf->delta_f;
+                    for (int t = 0; t < kk; t += 2) {
+                        const unsigned int word = nbr[(size_t)(t >> 1) * nmax + i];
+#pragma unroll
+                        for (int hlf = 0; hlf < 2; hlf++) {
+                            const int j = hlf ? (int)(word >> 16) : (int)(word & 0xffffu);
+                            const float4 v = pos4[j];
+                            float dx = u.x - v.x, dy = u.y - v.y, dz = u.z - v.z;
+                            const float ny = rint_fma(dy, iy);
+                            dy = __fmaf_rn(-ny, Ly, dy);
+                            dx = __fmaf_rn(-ny, dl, dx);
+                            dx = __fmaf_rn(-rint_fma(dx, ix), Lx, dx);
+                            dz = __fmaf_rn(-rint_fma(dz, iz), Lz, dz);
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            const float s = rcp_approx(r2);
+                            const float s3 = s * s * s;
+                            const bool in = (r2 < rc2) && (r2 > 0.f);   // r = 0: padding
+                            const float f = in ? s3 * s * (48.f * s3 - 24.f) : 0.f;   // |F|/r
+                            fx = __fmaf_rn(f, dx, fx); fy = __fmaf_rn(f, dy, fy); fz = __fmaf_rn(f, dz, fz);
+                            w = __fmaf_rn(f * dx, dy, w);
+                            npairs += in ? 1u : 0u;
+                        }
+                    }
+                } else {
+                    for (int t = 0; t < kk; t++) {
+                        const unsigned int word = nbr[(size_t)(t >> 1) * nmax + i];
+                        const int j = (t & 1) ? (int)(word >> 16) : (int)(word & 0xffffu);
+                        R dx, dy, dz;
+                        pair_vec(i, j, dx, dy, dz);
+                        const R r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < rc2) {
+                            const R s = 1.0 / r2;
+                            const R s3 = s * s * s;
+                            const R f = s3 * s * ((R)48 * s3 - (R)24);   // |F|/r
+                            fx += f * dx; fy += f * dy; fz += f * dz;
+                            w += f * dx * dy;
+                            npairs++;
+                        }
                     }
                 }
             }
@@ -425,7 +464,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
 
     // thread 0: coefficients of the next step from K2_end, a_end, e1, delta
     auto next_step = [&]() {
-        const double inc = hhQ * (K2_end - b.gT);
+        const double inc = hh / b.Q * (K2_end - b.gT);
         a_cur = a_end + inc;                       // start-of-step alpha half-step
         const double e3 = expm1_small(-a_cur * hh);
         const double ec = e1 + e3 + e1 * e3;       // pending factor times new one
@@ -436,13 +475,13 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         delta -= b.L[0] * rint(delta * cf->invL[0]);
         dsince += dd;
         cf->delta_d = delta; cf->delta_s = sfrom<S>(delta); cf->delta_f = (float)delta;
-        const double thr = 0.5 * ((double)a.skin - fabs(dsince));
+        const double thr = 0.5 * ((double)b.skin - fabs(dsince));
         cf->thr2 = thr > 0.0 ? (float)(thr * thr) : -1.f;
     };
 
     // ---- forces and sums of the initial state ----
     build_list();
-    n_rebuild++;
+    if (tid == 0) m->n_rebuild++;
     R w0 = forces();
     if (a.force_out) {
         double *fo = a.force_out + (size_t)d * 3 * N;
@@ -486,27 +525,41 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             const int i = tid + q * T;
             if (i >= N) continue;
             S px = P[q][0], py = P[q][1], pz = P[q][2];
-            px = sadd(px, smul(px, e)); py = sadd(py, smul(py, e)); pz = sadd(pz, smul(pz, e));
-            px = sadd(px, sneg(smul(chalf, py)));
-            px = sadd(px, smulf(hhS, F[q][0]));
-            py = sadd(py, smulf(hhS, F[q][1]));
-            pz = sadd(pz, smulf(hhS, F[q][2]));
             S x, y, z;
+            float ddx, ddy, ddz;
             if constexpr (MIXED) {
+                // p *= 1 + e, p_x -= gamma h/2 p_y, p += h/2 F: the products are
+                // small beside p, so they are formed in float from the hi parts
+                const float ef = e.hi, cf_ = chalf.hi;
+                acc_add(px, px.hi * ef); acc_add(py, py.hi * ef); acc_add(pz, pz.hi * ef);
+                acc_add(px, -cf_ * py.hi);
+                acc_add(px, mul_cf(hhS, F[q][0]));
+                acc_add(py, mul_cf(hhS, F[q][1]));
+                acc_add(pz, mul_cf(hhS, F[q][2]));
+                renorm(px); renorm(py); renorm(pz);
                 const float4 hi = pos4[i], lo = plo4[i];
                 x = {hi.x, lo.x}; y = {hi.y, lo.y}; z = {hi.z, lo.z};
+                // drift: h p (to float precision of the increment) and the
+                // streaming term gamma h (y + h p_y/2) as its own increment
+                ddx = mul_cd(hS, px); ddy = mul_cd(hS, py); ddz = mul_cd(hS, pz);
+                const float ys = gh.hi * __fmaf_rn(hhS.hi, py.hi, y.hi);
+                acc_add(x, ddx); acc_add(x, ys); acc_add(y, ddy); acc_add(z, ddz);
+                renorm(x); renorm(y); renorm(z);
+                ddx += ys;
             } else {
+                px = px + px * e; py = py + py * e; pz = pz + pz * e;
+                px = px - chalf * py;
+                px += hhS * F[q][0]; py += hhS * F[q][1]; pz += hhS * F[q][2];
                 x = xd[i]; y = yd[i]; z = zd[i];
+                const double dxs = hS * px + gh * (y + hhS * py);
+                const double dys = hS * py, dzs = hS * pz;
+                x += dxs; y += dys; z += dzs;
+                ddx = (float)dxs; ddy = (float)dys; ddz = (float)dzs;
             }
-            const S ymid = sadd(y, smul(hhS, py));
-            const S dxs = sadd(smul(hS, px), smul(gh, ymid));
-            const S dys = smul(hS, py), dzs = smul(hS, pz);
-            {
-                const float a0 = (float)shi(dxs), a1 = (float)shi(dys), a2 = (float)shi(dzs);
-                if (a0 * a0 + a1 * a1 + a2 * a2 > fast2) m->flag_fast = 1;
-            }
-            x = sadd(x, dxs); y = sadd(y, dys); z = sadd(z, dzs);
-            if (wrap_now) {   // back into [-L/2, L/2) with the sliding-brick x shift
+            if (ddx * ddx + ddy * ddy + ddz * ddz > fast2) m->flag_fast = 1;
+            float4 r = ref4[i];
+            if (wrap_now) {   // back into [-L/2, L/2) with the sliding-brick x shift;
+                              // the reference moves with it (same periodic image)
                 R ny, nx, nz;
                 if constexpr (MIXED) ny = rint_fma(y.hi, cf->invLf[1]);
                 else ny = rint(y * cf->invL[1]);
@@ -518,6 +571,10 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                 if constexpr (MIXED) nz = rint_fma(z.hi, cf->invLf[2]);
                 else nz = rint(z * cf->invL[2]);
                 z = sadd(z, sneg(smulf(cf->L[2], nz)));
+                r.x -= (float)ny * cf->delta_f + (float)nx * cf->Lf[0];
+                r.y -= (float)ny * cf->Lf[1];
+                r.z -= (float)nz * cf->Lf[2];
+                ref4[i] = r;
             }
             if constexpr (MIXED) {
                 pos4[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
@@ -525,17 +582,15 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             } else {
                 xd[i] = x; yd[i] = y; zd[i] = z;
             }
-            const float4 r = ref4[i];
             const float ex = (float)shi(x) - r.x, ey = (float)shi(y) - r.y, ez = (float)shi(z) - r.z;
             if (ex * ex + ey * ey + ez * ez > thr2) m->flag_rebuild[fb] = 1;
             P[q][0] = px; P[q][1] = py; P[q][2] = pz;
         }
         __syncthreads();                                        // barrier 1
         if (m->flag_fast) break;
-        if (wrap_now || m->flag_rebuild[fb] || thr2 < 0.f) {
+        if (m->flag_rebuild[fb] || thr2 < 0.f) {
             build_list();
-            n_rebuild++;
-            if (tid == 0) dsince = 0.0;
+            if (tid == 0) { dsince = 0.0; m->n_rebuild++; }
         }
         // phase B
         const R wsum = forces();
@@ -544,10 +599,17 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         for (int q = 0; q < APT; q++) {
             const int i = tid + q * T;
             if (i >= N) continue;
-            S px = sadd(P[q][0], smulf(hhS, F[q][0]));
-            S py = sadd(P[q][1], smulf(hhS, F[q][1]));
-            S pz = sadd(P[q][2], smulf(hhS, F[q][2]));
-            px = sadd(px, sneg(smul(chalf, py)));
+            S px = P[q][0], py = P[q][1], pz = P[q][2];
+            if constexpr (MIXED) {
+                acc_add(px, mul_cf(hhS, F[q][0]));
+                acc_add(py, mul_cf(hhS, F[q][1]));
+                acc_add(pz, mul_cf(hhS, F[q][2]));
+                acc_add(px, -chalf.hi * py.hi);
+                renorm(px); renorm(py); renorm(pz);
+            } else {
+                px += hhS * F[q][0]; py += hhS * F[q][1]; pz += hhS * F[q][2];
+                px = px - chalf * py;
+            }
             P[q][0] = px; P[q][1] = py; P[q][2] = pz;
             const R hx = (R)shi(px), hy = (R)shi(py), hz = (R)shi(pz);
             s2 += hx * hx + hy * hy + hz * hz;
@@ -559,7 +621,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             // end of step s: pending factor (1+e1) from the scale half-step
             const double f1 = 1.0 + e1, f1sq = f1 * f1;
             K2_end = f1sq * sums[0];
-            a_end = a_cur + hhQ * (K2_end - b.gT);              // end-of-step alpha half-step
+            a_end = a_cur + hh / b.Q * (K2_end - b.gT);         // end-of-step alpha half-step
             const double pxy = (f1sq * sums[1] + 0.5 * sums[2]) / b.V;
             if (!isfinite(sums[0] + sums[1] + sums[2])) cf->stop |= TTCF_D_NONFINITE;
             if (m->flag_ovf) cf->stop |= TTCF_D_NBR_OVERFLOW;
@@ -638,7 +700,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         if (m->flag_ovf) st |= TTCF_D_NBR_OVERFLOW;
         if (m->flag_lost) st |= TTCF_D_NONFINITE;
         b.status[dl] |= st;
-        b.rebuilds[dl] += n_rebuild;
+        b.rebuilds[dl] += m->n_rebuild;
     }
     __syncthreads();
 }
@@ -679,24 +741,26 @@ static int occupancy_one(int threads, size_t smem) {
 }
 
 #define TTCF_DISPATCH(MIX, FN, ...)                                              \
-    switch (apt) {                                                               \
-    case 1: return FN<MIX, 1, 256, 4>(__VA_ARGS__);                              \
-    case 2: return FN<MIX, 2, 512, 2>(__VA_ARGS__);                              \
+    switch (variant) {                                                           \
+    case 0: return FN<MIX, 1, 256, 4>(__VA_ARGS__);                              \
+    case 1: return FN<MIX, 2, 512, 2>(__VA_ARGS__);                              \
+    case 2: return FN<MIX, 2, 1024, 1>(__VA_ARGS__);                             \
+    case 3: return FN<MIX, 4, 512, 2>(__VA_ARGS__);                              \
     case 4: return FN<MIX, 4, 512, 1>(__VA_ARGS__);                              \
     default: return FN<MIX, 8, 512, 1>(__VA_ARGS__);                             \
     }
 
-cudaError_t launch_daughters(bool mixed, int apt, const RunArgs &a, int threads, int grid,
+cudaError_t launch_daughters(bool mixed, int variant, const RunArgs &a, int threads, int grid,
                              size_t smem, cudaStream_t st) {
     if (mixed) { TTCF_DISPATCH(true, launch_one, a, threads, grid, smem, st) }
     TTCF_DISPATCH(false, launch_one, a, threads, grid, smem, st)
 }
 
-int daughter_occupancy(bool mixed, int apt, int threads, size_t smem) {
+int daughter_occupancy(bool mixed, int variant, int threads, size_t smem) {
     if (mixed) { TTCF_DISPATCH(true, occupancy_one, threads, smem) }
     TTCF_DISPATCH(false, occupancy_one, threads, smem)
 }
 
-int max_threads_for_apt(int apt) { return apt == 1 ? 256 : 512; }
+
 
 }  // namespace ttcf

@@ -61,6 +61,23 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
     e = __fmaf_rn(a.lo, b, e);
     return fast_two_sum(p, e);
 }
+// Lazy accumulation: add a float increment into an unnormalised pair with
+// TwoSum (the rounding error goes to lo), 7 FP32 operations; renorm() makes
+// |lo| <= ulp(hi)/2 again with Fast2Sum.
+__device__ __forceinline__ void acc_add(df &a, float t) {
+    const float s = __fadd_rn(a.hi, t);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+__device__ __forceinline__ void renorm(df &a) { a = fast_two_sum(a.hi, a.lo); }
+// Float product of a double-float constant c and a float v (one rounding).
+__device__ __forceinline__ float mul_cf(df c, float v) { return __fmaf_rn(c.hi, v, __fmul_rn(c.lo, v)); }
+// Float product c * a of two pairs, to float precision.
+__device__ __forceinline__ float mul_cd(df c, df a) {
+    return __fmaf_rn(c.hi, a.hi, __fmaf_rn(c.hi, a.lo, __fmul_rn(c.lo, a.hi)));
+}
 __device__ __forceinline__ df df_from_double(double x) {
     float h = __double2float_rn(x);
     return {h, __double2float_rn(x - (double)h)};
@@ -131,6 +148,8 @@ struct BatchDev {
     double L[3];
     double V, Q, gT;         // volume, Nose-Hoover mass, g*T
     double T;                // k_B T
+    float skin;              // Verlet skin of this batch
+    int pad_;
     long long d0;            // global index of daughter 0
     const unsigned long long *mothers;   // [G][6][N] 8-byte slots
     const double *m_alpha;   // [G]
@@ -150,7 +169,7 @@ struct RunArgs {
     const int *dbatch;             // batch of each global daughter
     int n_work;
     int *queue;                    // persistent work counter
-    unsigned short *nbr;           // [grid][CAP][nmax]
+    unsigned int *nbr;             // [grid][CAP/2][nmax], two uint16 entries per word
     int nmax, ncellmax;
     int step0, step1;              // run absolute steps step0+1 .. step1
     int sample_every;
@@ -159,7 +178,6 @@ struct RunArgs {
     int reset_alpha;
     double dt;
     double delta0;                 // Lees-Edwards offset of fresh daughters
-    float skin;
     const volatile int *abort_flag;  // host-mapped, may be null
     double *snap;                  // mother mode: [D][n_snap][6][N] or null
     double *snap_alpha;            // [D][n_snap]
@@ -167,6 +185,21 @@ struct RunArgs {
     double *force_out;             // [D][3][N] forces at step0, or null
     double *wxy_out;               // [D] virial W_xy at step0, or null
 };
+
+// Launch variants of the daughter kernel: atoms per thread, maximum block
+// size and minimum resident blocks per SM (register budget).
+struct Variant { int apt, maxt, minb; };
+constexpr int N_VARIANTS = 6;
+__host__ __device__ inline Variant variant_of(int v) {
+    switch (v) {
+    case 0: return {1, 256, 4};
+    case 1: return {2, 512, 2};
+    case 2: return {2, 1024, 1};
+    case 3: return {4, 512, 2};
+    case 4: return {4, 512, 1};
+    default: return {8, 512, 1};
+    }
+}
 
 // Shared-memory bytes of a daughter CTA (must match the carve-up in
 // ttcf_daughter.cu).

@@ -9,10 +9,9 @@
 namespace ttcf {
 
 // persistent daughter kernel (ttcf_daughter.cu)
-cudaError_t launch_daughters(bool mixed, int apt, const RunArgs &a, int threads, int grid,
+cudaError_t launch_daughters(bool mixed, int variant, const RunArgs &a, int threads, int grid,
                              size_t smem, cudaStream_t st);
-int daughter_occupancy(bool mixed, int apt, int threads, size_t smem);
-int max_threads_for_apt(int apt);
+int daughter_occupancy(bool mixed, int variant, int threads, size_t smem);
 
 // spawn (ttcf_spawn.cu): per mother group, IEEE-double pressure tensor of
 // the mother, B(0) and Omega(0) of its mapped daughters, conversion of the

@@ -53,6 +53,17 @@ __global__ void spawn_kernel(SpawnArgs a) {
     __syncthreads();
     for (int q = 0, i = tid; i < N; i += T, q++) catom[start[cid[q]] + slot[q]] = (unsigned short)i;
     __syncthreads();
+    // atomic slots depend on scheduling: sort each cell so that the double
+    // sums below run in one fixed order (bitwise reproducible B(0), Omega)
+    for (int c = tid; c < a.ncell; c += T) {
+        for (int u = start[c] + 1; u < start[c + 1]; u++) {
+            const unsigned short v = catom[u];
+            int w = u;
+            while (w > start[c] && catom[w - 1] > v) { catom[w] = catom[w - 1]; w--; }
+            catom[w] = v;
+        }
+    }
+    __syncthreads();
 
     // 13 partial sums: kinetic K_ab (6), virial W_ab (6), U
     double acc[13];

@@ -26,7 +26,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 # The C ABI exported by libttcf.so (kept in sync with include/ttcf.h).
 EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_run",
            "ttcf_response", "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
-           "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces",
+           "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces", "ttcf_autotune",
            "ttcf_destroy", "ttcf_last_error", "ttcf_version")
 
 
@@ -35,7 +35,7 @@ class Config(C.Structure):
                 ("T", C.c_double), ("tau_T", C.c_double), ("dof_mode", C.c_int),
                 ("n_steps", C.c_int), ("sample_every", C.c_int), ("mapping_mask", C.c_uint),
                 ("reset_alpha", C.c_int), ("keep_state", C.c_int), ("skin", C.c_double),
-                ("block_threads", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
+                ("block_threads", C.c_int), ("kernel_variant", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_user", C.c_void_p), ("timeout_s", C.c_double)]
 
 
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = False):
     L.ttcf_sample_mothers.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_int,
                                       C.c_int, _dp, _dp]
     L.ttcf_forces.argtypes = [vp, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp, _dp]
+    L.ttcf_autotune.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_int, ip, _dp, _dp]
     L.ttcf_destroy.argtypes = [vp]
     L.ttcf_destroy.restype = None
     L.ttcf_last_error.argtypes = [vp]
@@ -94,7 +95,8 @@ def load(build_if_missing: bool = False):
     L.ttcf_version.restype = C.c_char_p
     for name in ("ttcf_create", "ttcf_spawn_daughters", "ttcf_run", "ttcf_response",
                  "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
-                 "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces"):
+                 "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces",
+                 "ttcf_autotune"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -292,6 +294,19 @@ class Context:
                                                 _ptr(init), int(n_eq), int(n_states), int(spacing),
                                                 _ptr(out), _ptr(al)))
         return out, al
+
+    def autotune(self, soa, box, shear_rate: float = 1e-3, n_steps: int = 100):
+        """Pick the fastest launch variant and skin for this N (cached in the
+        context for later spawns); returns (variant, skin, ms)."""
+        s = _f64(soa)
+        if s.ndim == 2:
+            s = s[None]
+        n, _, N = s.shape
+        v, sk, ms = C.c_int(), C.c_double(), C.c_double()
+        self._check(self._L.ttcf_autotune(self.h, int(N), _ptr(_box(box)), int(n), _ptr(s),
+                                          float(shear_rate), int(n_steps), C.byref(v),
+                                          C.byref(sk), C.byref(ms)))
+        return v.value, sk.value, ms.value
 
     def forces(self, soa, box, delta: float = 0.0):
         s = _f64(soa)

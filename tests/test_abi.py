@@ -39,7 +39,7 @@ def test_create_rejects_bad_configs_before_touching_the_gpu():
     L = ttcf.load()
     h = C.c_void_p()
     for field, val in (("dt", -1.0), ("n_steps", 0), ("sample_every", 3), ("mapping_mask", 0),
-                       ("precision", 7), ("block_threads", 48)):
+                       ("precision", 7), ("block_threads", 48), ("kernel_variant", 9)):
         c = ttcf.config_default()
         setattr(c, field, val)
         st = L.ttcf_create(C.byref(c), C.byref(h))

@@ -298,3 +298,37 @@ def test_timeout_aborts_and_context_stays_usable(ttcf, eq_mothers_256):
     with ctx(T, precision=1, n_steps=20) as c:   # the device is still usable
         bid = c.spawn_daughters(ms[:1], al[:1], 0.01, box=b.L)
         c.run()
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+def test_every_launch_variant_follows_the_oracle(ttcf, variant):
+    """Each launch shape (atoms per thread, block size, register budget)
+    gives the same 30-step trajectory responses as the oracle (N = 500, so
+    that every variant is exercised with a ragged tail)."""
+    N = 500
+    b = bulk(N)
+    st = inputs.jittered_states(N, 2, seed=9, amp=0.05)
+    apt, maxt = [(1, 256), (2, 512), (2, 1024), (4, 512), (4, 512), (8, 512)][variant - 1]
+    if apt * maxt < N:
+        pytest.skip("variant cannot hold N")
+    with ctx(ttcf, precision=1, n_steps=30, kernel_variant=variant) as c:
+        bid = c.spawn_daughters(st, None, 0.02, box=b.L)
+        c.run()
+        B, _ = c.daughter_series(bid, 8)
+    for d in range(8):
+        Bo, _, _, _ = oracle.daughter(b, st[d // 4], 0.0, d % 4, 0.02, 30)
+        assert np.abs(B[d] - Bo).max() < 1e-4 * np.abs(Bo).max()
+
+
+def test_autotuner_choice_is_used_and_exact(ttcf, eq_mothers_256):
+    b, ms, al = eq_mothers_256
+    with ctx(ttcf, precision=1, n_steps=40, keep_state=1) as c:
+        v, skin, t = c.autotune(ms[:4], b.L, shear_rate=1e-3, n_steps=20)
+        assert 1 <= v <= 6 and skin in (0.2, 0.3, 0.4) and t > 0
+        bid = c.spawn_daughters(ms[:2], al[:2], 1e-3, box=b.L)
+        c.run()
+        assert c.get_stats()["skin"] == skin
+        s, a, _ = c.get_state(bid, 3, b.n)
+    _, _, fin, fa = oracle.daughter(b, ms[0], al[0], 3, 1e-3, 40)
+    L = np.asarray(b.L)[:, None]
+    assert np.abs(min_image_diff(s[:3], fin[:3], L)).max() < 1e-6
