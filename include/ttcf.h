@@ -233,6 +233,46 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
                           const double *soa, double shear_rate, int n_steps, int *best_variant,
                           double *best_skin, double *best_ms);
 
+/* Spawn and run one small batch of daughters without allocating memory.
+ *
+ * The paper has no counterpart; this is a calling convention.  It is for
+ * callers that cannot allocate device memory where they run the daughters:
+ * a host application whose device memory is all owned by its own pool
+ * allocator (a cudaMalloc there fails or fragments the pool), a
+ * latency-critical loop that cannot pay for cudaMalloc/cudaFree (both may
+ * synchronise the device), or a plugin whose host forbids allocation after
+ * start-up.  It does what ttcf_spawn_daughters followed by ttcf_run does for
+ * one batch, with the same kernels and the same results, but takes its
+ * working buffers from one 32 MiB array compiled into the library (every
+ * GPU that loads the library holds that array until the process exits).
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ *
+ *  cfg            as for ttcf_create; stream, precision, dt, T, tau_T,
+ *                 dof_mode, n_steps, sample_every, mapping_mask,
+ *                 reset_alpha, skin, kernel_variant, block_threads are used;
+ *                 allocator hooks, keep_state and timeout_s are ignored
+ *  mother_soa     DEVICE [n_mothers][6][N] float64 phase points
+ *  mother_alpha   DEVICE [n_mothers] or NULL (zeros)
+ *  shear_rates    DEVICE [n_mothers]
+ *  B              DEVICE output [D][S], D = n_mothers * M, S = n_steps /
+ *                 sample_every + 1 (B(s) = P_xy(s) as in ttcf_daughter_series)
+ *  Omega          DEVICE output [D]; status DEVICE output [D] (TTCF_D_*)
+ *
+ * All arrays are the caller's.  The call only enqueues work on cfg->stream
+ * and returns; results are valid once that stream has completed it.  The
+ * first call on each device looks up the array's device address with that
+ * device current (make it before any stream capture).  Every call uses the
+ * same array, which keeps the previous call's contents (what must start at
+ * zero is cleared by each call): calls whose work overlaps on the GPU race
+ * and must be serialised by the caller.  A batch whose working buffers do
+ * not fit (roughly 6*8*N*n_mothers + 60*D bytes plus one 64*N-byte
+ * neighbour list) is rejected with TTCF_E_INVALID before any work is
+ * queued.  Errors: TTCF_E_INVALID, TTCF_E_CUDA; the text is available from
+ * ttcf_last_error(NULL).                                                   */
+ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, const double box[3],
+                             int n_mothers, const double *mother_soa, const double *mother_alpha,
+                             const double *shear_rates, double *B, double *Omega, int *status);
+
 /* Release the context and all its device memory.  NULL is ignored.       */
 void ttcf_destroy(ttcf_ctx *ctx);
 

@@ -414,6 +414,12 @@ ttcf_status reduce_batch(ttcf_ctx *ctx, BatchHost &b) {
     return TTCF_OK;
 }
 
+}  // namespace
+
+void ttcf::set_global_error(const char *msg) { g_create_error = msg; }
+
+namespace {
+
 BatchHost *get_batch(ttcf_ctx *ctx, int id) {
     if (!ctx || id < 0 || id >= (int)ctx->batches.size()) return nullptr;
     return &ctx->batches[id];

@@ -50,4 +50,7 @@ struct ReduceArgs {
 };
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 
+// Sets the text returned by ttcf_last_error(NULL) (calls without a context).
+void set_global_error(const char *msg);
+
 }  // namespace ttcf

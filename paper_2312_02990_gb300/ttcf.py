@@ -27,6 +27,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_run",
            "ttcf_response", "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
            "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces", "ttcf_autotune",
+           "ttcf_run_noalloc",
            "ttcf_destroy", "ttcf_last_error", "ttcf_version")
 
 
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = False):
                                       C.c_int, _dp, _dp]
     L.ttcf_forces.argtypes = [vp, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp, _dp]
     L.ttcf_autotune.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_int, ip, _dp, _dp]
+    L.ttcf_run_noalloc.argtypes = [C.POINTER(Config), C.c_int, _dp, C.c_int, vp, vp, vp, vp, vp, vp]
+    L.ttcf_run_noalloc.restype = C.c_int
     L.ttcf_destroy.argtypes = [vp]
     L.ttcf_destroy.restype = None
     L.ttcf_last_error.argtypes = [vp]
@@ -319,6 +322,24 @@ class Context:
         self._check(self._L.ttcf_forces(self.h, int(N), _ptr(_box(box)), int(n), float(delta),
                                         _ptr(s), _ptr(F), _ptr(W), _ptr(U)))
         return F, W, U
+
+
+def run_noalloc(cfg: Config, mother_soa, mother_alpha, shear_rates, box, B, Omega, status) -> int:
+    """ttcf_run_noalloc: every array is a torch CUDA tensor owned by the
+    caller (float64 mothers [G,6,N], alpha [G] or None, rates [G]; outputs
+    B [D,S] float64, Omega [D] float64, status [D] int32).  Enqueues on
+    cfg.stream and returns the status code."""
+    L = load()
+    bx = _box(box)
+    G, _, N = mother_soa.shape
+    return L.ttcf_run_noalloc(C.byref(cfg), int(N), _ptr(bx), int(G), mother_soa.data_ptr(),
+                              None if mother_alpha is None else mother_alpha.data_ptr(),
+                              shear_rates.data_ptr(), B.data_ptr(), Omega.data_ptr(),
+                              status.data_ptr())
+
+
+def last_error() -> str:
+    return load().ttcf_last_error(None).decode()
 
 
 def version() -> str:

@@ -1,0 +1,76 @@
+"""ttcf_run_noalloc, the entry point for callers that cannot allocate device
+memory (their device memory belongs to their own pool allocator, or they
+cannot afford the synchronisation of cudaMalloc/cudaFree).  It must give
+the same daughters as ttcf_spawn_daughters + ttcf_run, on two calls in a row
+through the same static working array, and refuse batches that do not fit.
+
+This file is collected last on purpose: it must pass both alone in a fresh
+process and after every other test."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2312_02990_gb300 import ttcf as T
+    T.load(build_if_missing=True)
+    N = 256
+    b = oracle.Bulk(n=N, L=tuple(inputs.bulk_box(N)))
+    ms, al = oracle.mother(b, inputs.initial_state(N, 77), n_eq=1500, n_states=6, spacing=150)
+    return torch, T, b, ms, al
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_noalloc_matches_the_allocating_path_twice(env, precision):
+    torch, T, b, ms, al = env
+    G, n, gamma = ms.shape[0], 60, 1e-3
+    cfg = T.config_default()
+    cfg.precision, cfg.n_steps = precision, n
+    with T.Context(cfg) as c:
+        bid = c.spawn_daughters(ms, al, gamma, box=b.L)
+        c.run()
+        B_ref, Om_ref = c.daughter_series(bid, 4 * G)
+    dev = torch.device("cuda")
+    m_t = torch.from_numpy(ms).to(dev)
+    a_t = torch.from_numpy(al).to(dev)
+    g_t = torch.full((G,), gamma, dtype=torch.float64, device=dev)
+    cfg2 = T.config_default()
+    cfg2.precision, cfg2.n_steps = precision, n
+    cfg2.stream = torch.cuda.current_stream().cuda_stream
+    # same tolerance as the parity tests' trajectory checks
+    tol = 1e-9 if precision == 0 else 1e-4
+    for call in range(2):
+        B = torch.full((4 * G, n + 1), np.nan, dtype=torch.float64, device=dev)
+        Om = torch.full((4 * G,), np.nan, dtype=torch.float64, device=dev)
+        st = torch.full((4 * G,), -1, dtype=torch.int32, device=dev)
+        rc = T.run_noalloc(cfg2, m_t, a_t, g_t, b.L, B, Om, st)
+        assert rc == T.TTCF_OK, T.last_error()
+        torch.cuda.synchronize()
+        Bh, Omh, sth = B.cpu().numpy(), Om.cpu().numpy(), st.cpu().numpy()
+        assert np.all(sth == 0), call
+        assert np.array_equal(Omh, Om_ref), call
+        assert np.abs(Bh - B_ref).max() <= tol * np.abs(B_ref).max(), call
+
+
+def test_noalloc_rejects_a_batch_beyond_its_static_array(env):
+    torch, T, b, ms, al = env
+    N, G = 4096, 200   # 200 * 6 * 4096 * 8 B = 39 MB of mother slots alone
+    dev = torch.device("cuda")
+    m_t = torch.zeros((G, 6, N), dtype=torch.float64, device=dev)
+    g_t = torch.zeros((G,), dtype=torch.float64, device=dev)
+    B = torch.zeros((4 * G, 11), dtype=torch.float64, device=dev)
+    Om = torch.zeros((4 * G,), dtype=torch.float64, device=dev)
+    st = torch.zeros((4 * G,), dtype=torch.int32, device=dev)
+    cfg = T.config_default()
+    cfg.n_steps = 10
+    rc = T.run_noalloc(cfg, m_t, None, g_t, (17.0, 17.0, 17.0), B, Om, st)
+    assert rc == T.TTCF_E_INVALID
+    assert "32 MiB" in T.last_error()
