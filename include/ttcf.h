@@ -99,6 +99,9 @@ typedef struct {
                                budget): 1 (1,256,64r) 2 (2,512,64r)
                                3 (2,1024,64r) 4 (4,512,64r) 5 (4,512,128r)
                                6 (8,512,128r)                                 */
+    int use_graph;          /* 1: ttcf_run captures its persistent launches
+                               (one per size class, on forked streams) and
+                               the reductions into one CUDA graph            */
     void *stream;           /* cudaStream_t; NULL = legacy default stream    */
     ttcf_alloc_fn dev_alloc;/* NULL: cudaMalloc                              */
     ttcf_free_fn dev_free;  /* NULL: cudaFree                                */
@@ -108,7 +111,7 @@ typedef struct {
 
 /* Fill *cfg with the Example 1 defaults: MIXED, dt 0.0025, T 0.722,
  * tau_T 0.25, g = 3N, 1000 steps, sample_every 1, all four mappings,
- * alpha carried, autotuned skin and block size.                           */
+ * alpha carried, autotuned skin and block size, CUDA graph on.          */
 void ttcf_config_default(ttcf_config *cfg);
 
 /* Create a context.  *out receives an owned handle (ttcf_destroy frees it).
@@ -223,7 +226,7 @@ ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_s
 /* Autotuner (launch shape and Verlet skin).  Times n_steps of the
  * daughter kernel on n_states phase points [n_states][6][N] (host; all four
  * mappings, shear rate gamma) for every launch variant that holds n_atoms
- * and Verlet skins {0.2, 0.3, 0.4}, with CUDA events on the context's
+ * and Verlet skins {0.3, 0.4, 0.5, 0.6}, with CUDA events on the context's
  * stream, and remembers the fastest for batches of n_atoms spawned later on
  * this context (explicit kernel_variant / skin in the config still win).
  * Returns the choice (1-based variant as in ttcf_config.kernel_variant),
@@ -272,6 +275,64 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
 ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, const double box[3],
                              int n_mothers, const double *mother_soa, const double *mother_alpha,
                              const double *shear_rates, double *B, double *Omega, int *status);
+
+/* ------------------------------------------------------------------------
+ * Learned control variate.  The paper has no learned part; the estimator it
+ * improves is Eq. 1.  A network f: 32 -> 128 -> 128 -> 1 (tanh) learns, from
+ * the 32 features x of a mapped mother state, the per-daughter quantity
+ * z = Omega(0) I(t_end) / gamma (I: trapezoid integral of B = P_xy), whose
+ * group mean y_g = -(1/M) sum_m z is the group's TTCF viscosity at t_end.
+ * With h_g = -(1/M) sum_m f(x), the estimate
+ *     eta_cv = mean_D(y - c h) + c mean_aux(h)
+ * over an evaluation batch D and an independent auxiliary set of mother
+ * states is unbiased for any network and c.  Features (in order): kinetic
+ * and configurational pressure tensors P^K_ab, P^C_ab (xx yy zz xy xz yz),
+ * U/N, K/N, alpha, P_xy^2, then for q = 1..4 the (cos, sin) modes over 40
+ * slabs in y of the density and of the x momentum (each / N).  Weights are
+ * FP32 masters used through their BF16 rounding; FP32 accumulation.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int epochs;             /* passes over the training daughters            */
+    int batch;              /* minibatch size (a multiple of 32)             */
+    float lr, beta1, beta2, eps;   /* Adam                                   */
+    float holdout;          /* fraction of groups held out to fit c          */
+    unsigned long long seed;/* initialisation and shuffling                  */
+} ttcf_cv_config;
+
+/* Defaults: 40 epochs, batch 256, Adam(1e-3, 0.9, 0.999, 1e-8), hold-out
+ * 0.2, seed 20231205.                                                      */
+void ttcf_cv_config_default(ttcf_cv_config *cfg);
+
+/* Features [D][32] (unstandardised, float) and targets z [D] (double) of
+ * every daughter of a finished batch (host arrays; either may be NULL).     */
+ttcf_status ttcf_cv_data(ttcf_ctx *ctx, int batch_id, float *X, double *z, size_t capacity);
+
+/* Train the network on the daughters of a finished batch (all shear rates
+ * allowed; targets are normalised by gamma).  The last `holdout` fraction
+ * of its valid groups fits c instead.  Stores the network in the context;
+ * loss_curve (may be NULL) receives the mean training loss per epoch.     */
+ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg,
+                          double *loss_curve, int capacity);
+
+/* Control-variate estimate of eta(t_end) for a finished evaluation batch,
+ * with n_aux auxiliary mother states [n_aux][6][N] (host, same N and box;
+ * alpha may be NULL).  out[8]: eta_plain, se_plain, eta_cv, se_cv, c,
+ * gain = se_plain^2 / se_cv^2, n_groups, n_aux.                             */
+ttcf_status ttcf_cv_apply(ttcf_ctx *ctx, int batch_id, int n_aux, const double *aux_soa,
+                          const double *aux_alpha, double out[8]);
+
+/* The trained network: FP32 parameters [20865] (W1[128][32], b1, W2[128][128],
+ * b2, W3[128], b3), feature standardisation [32][2] (mean, std), target
+ * standardisation [2] and c.  Any pointer may be NULL.                      */
+ttcf_status ttcf_cv_get_model(ttcf_ctx *ctx, float *params, double *feat_stats, double *z_stats,
+                              double *c);
+
+/* The network at given FP32 parameters on n standardised inputs X [n][32]
+ * (host): outputs [n] (forward), or the mean-squared-loss gradient [20865]
+ * and loss for targets y [n] (gradient; n <= 65536).                        */
+ttcf_status ttcf_cv_forward(ttcf_ctx *ctx, const float *params, int n, const float *X, float *out);
+ttcf_status ttcf_cv_gradient(ttcf_ctx *ctx, const float *params, int n, const float *X,
+                             const float *y, float *grad, double *loss);
 
 /* Release the context and all its device memory.  NULL is ignored.       */
 void ttcf_destroy(ttcf_ctx *ctx);

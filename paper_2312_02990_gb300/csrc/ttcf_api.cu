@@ -4,11 +4,13 @@
 
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <new>
 #include <string>
 #include <thread>
 #include <vector>
 
+#include "ttcf_cv.h"
 #include "ttcf_internal.h"
 
 using namespace ttcf;
@@ -16,7 +18,6 @@ using namespace ttcf;
 namespace {
 
 constexpr double RC_WCA = 1.1224620483093730;   // 2^(1/6)
-constexpr double DEFAULT_SKIN = 0.3;
 
 thread_local std::string g_create_error;
 
@@ -49,19 +50,33 @@ struct BatchHost {
 
 struct TunedEntry { int N; int variant; double skin; };
 
+// The trained control-variate network (device buffers owned by the context).
+struct CvModel {
+    bool trained = false;
+    float *w = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *wb = nullptr;
+    double *fstats = nullptr;   // [CV_NF][2]
+    double *zstats = nullptr;   // [2]
+    double c = 0.0;
+    int N = 0;
+    double L[3] = {0, 0, 0};
+};
+
 struct ttcf_ctx {
     ttcf_config cfg;
     std::string err;
     cudaStream_t st = nullptr;
-    int device = 0, nsm = 0, smem_optin = 0;
+    int device = 0, nsm = 0, smem_optin = 0, smem_per_sm = 0;
     double skin = DEFAULT_SKIN;
     std::vector<BatchHost> batches;
     std::vector<TunedEntry> tuned;   // autotuner results per atom count
+    CvModel cv;
     std::vector<void *> allocs;
     long long total_d = 0;
     int steps_done = 0;
     bool ran = false;
     int *h_abort = nullptr, *d_abort = nullptr;
+    cudaStream_t cap_st = nullptr;   // private stream for CUDA-graph capture
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     ttcf_stats stats;
     // launch tables, rebuilt when batches change
@@ -79,7 +94,15 @@ ttcf_status fail(ttcf_ctx *c, ttcf_status s, const std::string &msg) {
 }
 
 ttcf_status cuda_fail(ttcf_ctx *c, cudaError_t e, const char *where) {
+    cudaGetLastError();   // clear a non-sticky error so later launch checks are not confused
     return fail(c, TTCF_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// An event that must be waited on or timed after a graph launch: inside a
+// stream capture it has to become an external event-record node.
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t st, bool capturing) {
+    return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                     : cudaEventRecord(ev, st);
 }
 
 #define CK(call)                                                     \
@@ -138,10 +161,7 @@ ttcf_status choose_class(ttcf_ctx *ctx, int N, int force_variant, double force_s
     if (force_variant >= 0) variant = force_variant;
     else if (cf.kernel_variant > 0) variant = cf.kernel_variant - 1;
     else if (tu) variant = tu->variant;
-    else if (N <= 256) variant = 0;
-    else if (N <= 1024) variant = 1;
-    else if (N <= 2048) variant = 3;
-    else variant = 5;
+    else variant = default_variant(N);
     if (force_skin > 0) skin = force_skin;
     else if (cf.skin > 0) skin = cf.skin;
     else if (tu) skin = tu->skin;
@@ -154,6 +174,26 @@ ttcf_status choose_class(ttcf_ctx *ctx, int N, int force_variant, double force_s
         return fail(ctx, TTCF_E_INVALID, "kernel_variant/block_threads cannot hold n_atoms");
     threads = t;
     return TTCF_OK;
+}
+
+// Cells of the neighbour build: the finest width in {r_l/2, 2r_l/3, r_l}
+// whose shared memory still lets the variant reach its target number of
+// resident CTAs per SM (finer cells = fewer candidates per list build).
+void pick_cells(ttcf_ctx *ctx, BatchHost &b, double rl) {
+    const bool mixed = ctx->cfg.precision == TTCF_MIXED;
+    const Variant v = variant_of(b.variant);
+    const double fracs[3] = {0.5, 2.0 / 3.0, 1.0};
+    for (int f = 0; f < 3; f++) {
+        int nc[3];
+        for (int k = 0; k < 3; k++) nc[k] = std::max(3, (int)floor(b.L[k] / (rl * fracs[f])));
+        const int ncell = nc[0] * nc[1] * nc[2];
+        const size_t sm = daughter_smem_bytes(mixed, b.N, ncell);
+        if (f == 2 || (size_t)v.minb * (sm + 1024) <= (size_t)ctx->smem_per_sm) {
+            for (int k = 0; k < 3; k++) b.nc[k] = nc[k];
+            b.ncell = ncell;
+            return;
+        }
+    }
 }
 
 // Allocate a batch, copy its mothers and run the spawn kernel.
@@ -180,10 +220,9 @@ ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const dou
     b.V = box[0] * box[1] * box[2];
     for (int k = 0; k < 3; k++) {
         b.L[k] = box[k];
-        b.nc[k] = (int)floor(box[k] / rl);
         b.snc[k] = (int)floor(box[k] / RC_WCA);
     }
-    b.ncell = b.nc[0] * b.nc[1] * b.nc[2];
+    pick_cells(ctx, b, rl);
     b.sncell = b.snc[0] * b.snc[1] * b.snc[2];
     const double g = cf.dof_mode == 1 ? 3.0 * N - 3.0 : 3.0 * N;
     b.Q = g * cf.T * cf.tau_T * cf.tau_T;
@@ -214,7 +253,7 @@ ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const dou
     b.pairs = pool.get<unsigned long long>(D);
     b.rebuilds = pool.get<unsigned int>(D);
     b.scal = pool.get<double>((size_t)D * 4);
-    b.feat = pool.get<double>((size_t)G * 16);
+    b.feat = pool.get<double>((size_t)G * FEAT_RAW);
     if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (batch)");
     cudaStream_t st = ctx->st;
     CK(cudaMemcpyAsync(b.m_alpha, alpha_h.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st));
@@ -298,7 +337,8 @@ std::vector<ClassLaunch> plan_classes(ttcf_ctx *ctx, std::vector<BatchHost *> &b
 // built in `pool`).  `proto` carries the run-wide fields.
 ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &bs,
                            RunArgs proto, int &launches, cudaEvent_t ev_begin = nullptr,
-                           cudaEvent_t ev_end = nullptr) {
+                           cudaEvent_t ev_end = nullptr,
+                           const std::function<ttcf_status()> &tail = nullptr) {
     const bool mixed = ctx->cfg.precision == TTCF_MIXED;
     if (bs.empty()) return TTCF_OK;
     long long dmax = 0;
@@ -331,44 +371,90 @@ ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &
         CK(cudaMemcpyAsync(d_work[k], cls[k].work.data(), sizeof(int) * cls[k].work.size(),
                            cudaMemcpyHostToDevice, st));
     }
-    if (ev_begin) CK(cudaEventRecord(ev_begin, st));
-    // classes run concurrently on forked streams joined back into st
+    // classes run concurrently on forked streams joined back into st; with
+    // use_graph the whole fork/join (and `tail`, e.g. the reductions) is
+    // captured once and launched as one CUDA graph
     std::vector<cudaStream_t> side(cls.size(), st);
-    std::vector<cudaEvent_t> done;
+    std::vector<cudaEvent_t> done(cls.size(), nullptr);
     cudaEvent_t fork = nullptr;
     if (cls.size() > 1) {
         CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        CK(cudaEventRecord(fork, st));
         for (size_t k = 1; k < cls.size(); k++) {
             CK(cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking));
-            CK(cudaStreamWaitEvent(side[k], fork, 0));
+            CK(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming));
         }
     }
-    for (size_t k = 0; k < cls.size(); k++) {
-        RunArgs a = proto;
-        a.batches = d_b; a.dbatch = d_db; a.work = d_work[k];
-        a.n_work = (int)cls[k].work.size();
-        a.queue = d_q + k;
-        a.nbr = d_nbr[k]; a.nmax = cls[k].nmax; a.ncellmax = cls[k].ncellmax;
-        CK(launch_daughters(mixed, cls[k].variant, a, cls[k].threads, cls[k].grid, cls[k].smem, side[k]));
-        launches++;
-        ctx->stats.block_threads = std::max(ctx->stats.block_threads, cls[k].threads);
-    }
-    for (size_t k = 1; k < cls.size(); k++) {
-        cudaEvent_t e;
-        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        CK(cudaEventRecord(e, side[k]));
-        CK(cudaStreamWaitEvent(st, e, 0));
-        done.push_back(e);
-    }
-    if (ev_end) CK(cudaEventRecord(ev_end, st));
-    // the side streams and events are released once st has passed them
-    if (!done.empty() || fork) {
-        CK(cudaStreamSynchronize(st));
-        for (auto e : done) cudaEventDestroy(e);
+    std::vector<cudaStream_t> owned(side.begin() + (side.empty() ? 0 : 1), side.end());
+    auto cleanup = [&]() {
+        for (auto e : done) if (e) cudaEventDestroy(e);
         if (fork) cudaEventDestroy(fork);
-        for (size_t k = 1; k < side.size(); k++) cudaStreamDestroy(side[k]);
+        for (cudaStream_t x : owned) if (x) cudaStreamDestroy(x);
+        owned.clear();
+    };
+    // The caller's stream may be the legacy default stream, which cannot be
+    // captured: capture on the context's own stream, launch on the caller's.
+    const bool graph = ctx->cfg.use_graph != 0;
+    const cudaStream_t user_st = st;
+    cudaGraph_t g = nullptr;
+    if (graph) {
+        if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+        st = ctx->cap_st;
+        for (size_t k = 0; k < side.size(); k++) if (k == 0 || side[k] == user_st) side[k] = st;
+        ctx->st = st;   // work issued by `tail` goes into the capture too
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            ctx->st = user_st;
+            cleanup();
+            return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+        }
     }
+    auto body = [&]() -> ttcf_status {
+        if (ev_begin) CK(record_event(ev_begin, st, graph));
+        if (fork) {
+            CK(cudaEventRecord(fork, st));
+            for (size_t k = 1; k < cls.size(); k++) CK(cudaStreamWaitEvent(side[k], fork, 0));
+        }
+        for (size_t k = 0; k < cls.size(); k++) {
+            RunArgs a = proto;
+            a.batches = d_b; a.dbatch = d_db; a.work = d_work[k];
+            a.n_work = (int)cls[k].work.size();
+            a.queue = d_q + k;
+            a.nbr = d_nbr[k]; a.nmax = cls[k].nmax; a.ncellmax = cls[k].ncellmax;
+            CK(launch_daughters(mixed, cls[k].variant, a, cls[k].threads, cls[k].grid, cls[k].smem, side[k]));
+            launches++;
+            ctx->stats.block_threads = std::max(ctx->stats.block_threads, cls[k].threads);
+        }
+        for (size_t k = 1; k < cls.size(); k++) {
+            CK(cudaEventRecord(done[k], side[k]));
+            CK(cudaStreamWaitEvent(st, done[k], 0));
+        }
+        if (ev_end) CK(record_event(ev_end, st, graph));
+        if (tail) {
+            ttcf_status ts = tail();
+            if (ts != TTCF_OK) return ts;
+        }
+        return TTCF_OK;
+    };
+    ttcf_status bs_ = body();
+    if (graph) {
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        ctx->st = user_st;
+        st = user_st;
+        if (bs_ == TTCF_OK && e != cudaSuccess) bs_ = cuda_fail(ctx, e, "cudaStreamEndCapture");
+        if (bs_ == TTCF_OK) {
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ex, user_st);
+            if (ex) cudaGraphExecDestroy(ex);   // freed once the launch completes
+            if (e != cudaSuccess) bs_ = cuda_fail(ctx, e, "CUDA graph launch");
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    if (bs_ != TTCF_OK) { cudaStreamSynchronize(st); cleanup(); return bs_; }
+    // without a graph the side streams and events are released once st has
+    // passed them; a captured graph no longer refers to them
+    if (fork && !graph) CK(cudaStreamSynchronize(st));
+    cleanup();
     return TTCF_OK;
 }
 
@@ -391,19 +477,24 @@ ttcf_status wait_with_timeout(ttcf_ctx *ctx, cudaEvent_t ev) {
     }
 }
 
+ttcf_status ensure_reduce_buffers(ttcf_ctx *ctx, BatchHost &b) {
+    if (b.out) return TTCF_OK;
+    Pool p(ctx);
+    b.Y = p.get<double>((size_t)b.G * b.S);
+    b.Dg = p.get<double>((size_t)b.G * b.S);
+    b.J = p.get<double>((size_t)b.G * b.S);
+    b.Og = p.get<double>(b.G);
+    b.valid = p.get<double>(b.G);
+    b.out = p.get<double>((size_t)9 * b.S);
+    if (p.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (reduction)");
+    p.keep();
+    return TTCF_OK;
+}
+
 ttcf_status reduce_batch(ttcf_ctx *ctx, BatchHost &b) {
     if (b.reduced) return TTCF_OK;
-    if (!b.out) {
-        Pool p(ctx);
-        b.Y = p.get<double>((size_t)b.G * b.S);
-        b.Dg = p.get<double>((size_t)b.G * b.S);
-        b.J = p.get<double>((size_t)b.G * b.S);
-        b.Og = p.get<double>(b.G);
-        b.valid = p.get<double>(b.G);
-        b.out = p.get<double>((size_t)9 * b.S);
-        if (p.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (reduction)");
-        p.keep();
-    }
+    ttcf_status rs = ensure_reduce_buffers(ctx, b);
+    if (rs != TTCF_OK) return rs;
     ReduceArgs r;
     r.M = b.M; r.G = b.G; r.S = b.S;
     r.B = b.B; r.Omega = b.Omega; r.status = b.status;
@@ -447,6 +538,7 @@ void ttcf_config_default(ttcf_config *c) {
     c->skin = 0.0;
     c->block_threads = 0;
     c->kernel_variant = 0;
+    c->use_graph = 1;
     c->timeout_s = 0.0;
 }
 
@@ -486,6 +578,8 @@ ttcf_status ttcf_create(const ttcf_config *cfg, ttcf_ctx **out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&ctx->h_abort, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) { *ctx->h_abort = 0; e = cudaHostGetDevicePointer((void **)&ctx->d_abort, ctx->h_abort, 0); }
     for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventCreate(&ctx->ev[k]);
@@ -504,6 +598,7 @@ void ttcf_destroy(ttcf_ctx *ctx) {
     cudaStreamSynchronize(ctx->st);
     for (void *p : ctx->allocs) dev_free_raw(ctx, p);
     for (int k = 0; k < 4; k++) if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
     if (ctx->h_abort) cudaFreeHost(ctx->h_abort);
     delete ctx;
 }
@@ -570,9 +665,29 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
     for (auto &b : ctx->batches) bs.push_back(&b);
     Pool pool(ctx);
     int launches = 0;
-    ttcf_status s = launch_batches(ctx, pool, bs, a, launches, ctx->ev[0], ctx->ev[1]);
+    const bool finishing = step1 >= cf.n_steps;
+    if (finishing) {   // reduction buffers exist before a graph is captured
+        for (auto &b : ctx->batches) {
+            ttcf_status r = ensure_reduce_buffers(ctx, b);
+            if (r != TTCF_OK) return r;
+        }
+    }
+    const bool capturing = cf.use_graph != 0;
+    auto tail = [&]() -> ttcf_status {
+        if (!finishing) return TTCF_OK;
+        CK(record_event(ctx->ev[2], ctx->st, capturing));
+        for (auto &b : ctx->batches) {
+            b.reduced = false;
+            ttcf_status r = reduce_batch(ctx, b);
+            if (r != TTCF_OK) return r;
+            launches += 3;
+        }
+        CK(record_event(ctx->ev[3], ctx->st, capturing));
+        return TTCF_OK;
+    };
+    ttcf_status s = launch_batches(ctx, pool, bs, a, launches, ctx->ev[0], ctx->ev[1], tail);
     if (s != TTCF_OK) return s;
-    s = wait_with_timeout(ctx, ctx->ev[1]);
+    s = wait_with_timeout(ctx, finishing ? ctx->ev[3] : ctx->ev[1]);
     if (s != TTCF_OK && s != TTCF_E_TIMEOUT) return s;
     const bool timed_out = s == TTCF_E_TIMEOUT;
     float ms = 0.f;
@@ -580,6 +695,11 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
     ctx->stats.ms_run = ms;
     ctx->stats.skin = ctx->batches.empty() ? ctx->skin : ctx->batches[0].skin;
     ctx->steps_done = step1;
+    if (finishing) {
+        float msr = 0.f;
+        cudaEventElapsedTime(&msr, ctx->ev[2], ctx->ev[3]);
+        ctx->stats.ms_reduce = msr;
+    }
 
     // counters and failures
     bool any_fail = false;
@@ -599,20 +719,6 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
         // counters are per run
         CK(cudaMemsetAsync(b.pairs, 0, sizeof(unsigned long long) * b.D(), ctx->st));
         CK(cudaMemsetAsync(b.rebuilds, 0, sizeof(unsigned int) * b.D(), ctx->st));
-    }
-    if (ctx->steps_done >= cf.n_steps) {
-        CK(cudaEventRecord(ctx->ev[2], ctx->st));
-        for (auto &b : ctx->batches) {
-            b.reduced = false;
-            ttcf_status r = reduce_batch(ctx, b);
-            if (r != TTCF_OK) return r;
-            launches += 3;
-        }
-        CK(cudaEventRecord(ctx->ev[3], ctx->st));
-        CK(cudaEventSynchronize(ctx->ev[3]));
-        float msr = 0.f;
-        cudaEventElapsedTime(&msr, ctx->ev[2], ctx->ev[3]);
-        ctx->stats.ms_reduce = msr;
     }
     ctx->stats.launches = launches;
     if (timed_out) return fail(ctx, TTCF_E_TIMEOUT, "ttcf_run exceeded timeout_s; daughters aborted");
@@ -809,7 +915,7 @@ ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_s
     s = launch_batches(ctx, pool, bs, a, launches);
     if (s != TTCF_OK) return s;
     CK(cudaStreamSynchronize(ctx->st));
-    std::vector<double> wxy(n_states), feat((size_t)n_states * 16);
+    std::vector<double> wxy(n_states), feat((size_t)n_states * FEAT_RAW);
     if (F) CK(cudaMemcpy(F, fo, sizeof(double) * (size_t)n_states * 3 * N, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(wxy.data(), wo, sizeof(double) * n_states, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(feat.data(), b.feat, sizeof(double) * feat.size(), cudaMemcpyDeviceToHost));
@@ -817,10 +923,10 @@ ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_s
         if (W) {
             // xy from the kernel under test; the other components from the
             // double-precision spawn pass (virial part only)
-            for (int c = 0; c < 6; c++) W[6 * k + c] = feat[16 * k + 8 + c] * b.V;
+            for (int c = 0; c < 6; c++) W[6 * k + c] = feat[(size_t)FEAT_RAW * k + 6 + c];
             W[6 * k + 3] = wxy[k];
         }
-        if (U) U[k] = feat[16 * k + 6];
+        if (U) U[k] = feat[(size_t)FEAT_RAW * k + 12];
     }
     return TTCF_OK;
 }
@@ -830,7 +936,7 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
                           double *best_skin, double *best_ms) {
     if (!ctx || !box || !soa || n_states < 1 || n_steps < 1)
         return fail(ctx, TTCF_E_INVALID, "bad autotune arguments");
-    const double skins[3] = {0.2, 0.3, 0.4};
+    const double skins[4] = {0.3, 0.4, 0.5, 0.6};
     const int maps[4] = {0, 1, 2, 3};
     std::vector<double> gam(n_states, shear_rate);
     double best = 1e300;
@@ -844,6 +950,7 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
         if (var.apt * var.maxt < n_atoms) continue;
         if (var.apt > 1 && (n_atoms + var.apt - 1) / var.apt < 64) continue;   // too few threads
         for (double sk : skins) {
+            if (3.0 * (RC_WCA + sk) > std::min(box[0], std::min(box[1], box[2]))) continue;
             BatchHost b;
             Pool pool(ctx);
             ttcf_status s = make_batch(ctx, pool, b, n_atoms, box, n_states, soa, nullptr, gam.data(),
@@ -874,6 +981,314 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
     if (best_variant) *best_variant = bv + 1;
     if (best_skin) *best_skin = bskin;
     if (best_ms) *best_ms = best;
+    return TTCF_OK;
+}
+
+
+// ======================================================= control variate ==
+namespace {
+
+uint64_t splitmix64(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double uniform01(uint64_t &x) { return (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0); }
+
+bool batch_finished(ttcf_ctx *ctx, BatchHost *b) { return b && b->reduced; }
+
+// Features X [D][32] (device, unstandardised) and targets z [D] (device).
+ttcf_status cv_batch_data(ttcf_ctx *ctx, Pool &pool, BatchHost &b, float *&X, double *&z) {
+    const long long D = b.D();
+    X = pool.get<float>((size_t)D * CV_NF);
+    z = pool.get<double>((size_t)D);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (cv data)");
+    CvFeatArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.raw = b.feat; fa.alpha = b.m_alpha; fa.reset_alpha = ctx->cfg.reset_alpha;
+    fa.M = b.M; for (int k = 0; k < 4; k++) fa.maps[k] = b.maps[k];
+    fa.D = D; fa.N = b.N; fa.V = b.V; fa.X = X;
+    CK(cv_launch_features(fa, ctx->st));
+    CK(cv_launch_targets(b.B, b.Omega, b.gamma_d, b.M, D, b.S,
+                         ctx->cfg.sample_every * ctx->cfg.dt, z, ctx->st));
+    return TTCF_OK;
+}
+
+std::vector<int> valid_groups(ttcf_ctx *ctx, BatchHost &b, ttcf_status &st) {
+    std::vector<int> stv(b.D()), out;
+    st = TTCF_OK;
+    if (cudaMemcpy(stv.data(), b.status, sizeof(int) * b.D(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        st = fail(ctx, TTCF_E_CUDA, "status read failed");
+        return out;
+    }
+    for (int g = 0; g < b.G; g++) {
+        int v = 0;
+        for (int k = 0; k < b.M; k++) v |= stv[(size_t)g * b.M + k];
+        if (v == 0) out.push_back(g);
+    }
+    return out;
+}
+
+}  // namespace
+
+void ttcf_cv_config_default(ttcf_cv_config *c) {
+    if (!c) return;
+    c->epochs = 40;
+    c->batch = 256;
+    c->lr = 1e-3f; c->beta1 = 0.9f; c->beta2 = 0.999f; c->eps = 1e-8f;
+    c->holdout = 0.2f;
+    c->seed = 20231205ull;
+}
+
+ttcf_status ttcf_cv_data(ttcf_ctx *ctx, int batch_id, float *X, double *z, size_t capacity) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (!batch_finished(ctx, b)) return fail(ctx, TTCF_E_STATE, "run not finished");
+    if (capacity < (size_t)b->D()) return fail(ctx, TTCF_E_INVALID, "capacity smaller than the daughter count");
+    Pool pool(ctx);
+    float *dX; double *dz;
+    ttcf_status s = cv_batch_data(ctx, pool, *b, dX, dz);
+    if (s != TTCF_OK) return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    if (X) CK(cudaMemcpy(X, dX, sizeof(float) * CV_NF * b->D(), cudaMemcpyDeviceToHost));
+    if (z) CK(cudaMemcpy(z, dz, sizeof(double) * b->D(), cudaMemcpyDeviceToHost));
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg, double *loss_curve,
+                          int capacity) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b || !cfg) return fail(ctx, TTCF_E_INVALID, "bad batch id or NULL config");
+    if (!batch_finished(ctx, b)) return fail(ctx, TTCF_E_STATE, "run not finished");
+    if (cfg->epochs < 1 || cfg->batch < 32 || cfg->batch % 32 || !(cfg->lr > 0) ||
+        !(cfg->holdout >= 0 && cfg->holdout < 1))
+        return fail(ctx, TTCF_E_INVALID, "bad control-variate configuration");
+    for (double g : b->gamma)
+        if (g == 0.0) return fail(ctx, TTCF_E_INVALID, "training needs a nonzero shear rate");
+    ttcf_status st;
+    std::vector<int> groups = valid_groups(ctx, *b, st);
+    if (st != TTCF_OK) return st;
+    const int ng = (int)groups.size();
+    const int nhold = std::max(2, (int)(cfg->holdout * ng));
+    const int ntrain_g = ng - nhold;
+    if (ntrain_g < 2) return fail(ctx, TTCF_E_INVALID, "too few valid groups to train");
+    Pool tmp(ctx);
+    float *X; double *z;
+    ttcf_status s = cv_batch_data(ctx, tmp, *b, X, z);
+    if (s != TTCF_OK) return s;
+    const long long D = b->D();
+    std::vector<int> rows;
+    for (int k = 0; k < ntrain_g; k++)
+        for (int m = 0; m < b->M; m++) rows.push_back(groups[k] * b->M + m);
+    const int nrows = (int)rows.size();
+    std::vector<int> hold(groups.begin() + ntrain_g, groups.end());
+    float *zf = tmp.get<float>(D), *y = tmp.get<float>(D), *f = tmp.get<float>(D);
+    int *d_rows = tmp.get<int>(nrows), *d_idx = tmp.get<int>(nrows), *d_hold = tmp.get<int>(nhold);
+    int *d_step = tmp.get<int>(1);
+    const int tiles = cfg->batch / 32;
+    float *part = tmp.get<float>((size_t)tiles * CV_NP);
+    double *lpart = tmp.get<double>(tiles), *loss = tmp.get<double>(1);
+    double *yg = tmp.get<double>(nhold), *hg = tmp.get<double>(nhold), *est = tmp.get<double>(8);
+    CvModel &cvm = ctx->cv;
+    if (!cvm.w) {
+        Pool keep(ctx);
+        cvm.w = keep.get<float>(CV_NP); cvm.m = keep.get<float>(CV_NP); cvm.v = keep.get<float>(CV_NP);
+        cvm.wb = keep.get<__nv_bfloat16>(CV_NP);
+        cvm.fstats = keep.get<double>(2 * CV_NF); cvm.zstats = keep.get<double>(2);
+        if (keep.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (cv model)");
+        keep.keep();
+    }
+    if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (cv training)");
+    cudaStream_t sm = ctx->st;
+    CK(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice, sm));
+    CK(cudaMemcpyAsync(d_hold, hold.data(), sizeof(int) * nhold, cudaMemcpyHostToDevice, sm));
+    // standardisation from the training rows
+    CK(cv_launch_colstats(X, CV_NF, d_rows, nrows, CV_NF, cvm.fstats, sm));
+    {
+        std::vector<double> zh(D);
+        CK(cudaStreamSynchronize(sm));
+        CK(cudaMemcpy(zh.data(), z, sizeof(double) * D, cudaMemcpyDeviceToHost));
+        std::vector<float> zfh(D);
+        for (long long d = 0; d < D; d++) zfh[d] = (float)zh[d];
+        CK(cudaMemcpy(zf, zfh.data(), sizeof(float) * D, cudaMemcpyHostToDevice));
+    }
+    CK(cv_launch_colstats(zf, 1, d_rows, nrows, 1, cvm.zstats, sm));
+    CK(cv_launch_standardize(X, D, cvm.fstats, y, cvm.zstats, z, sm));
+    // Xavier-uniform initialisation, zero biases (seeded splitmix64)
+    {
+        std::vector<float> w(CV_NP, 0.f);
+        uint64_t sd = cfg->seed;
+        auto fill = [&](int off, int fan_out, int fan_in) {
+            const double a = sqrt(6.0 / (fan_in + fan_out));
+            for (int k = 0; k < fan_out * fan_in; k++) w[off + k] = (float)((2.0 * uniform01(sd) - 1.0) * a);
+        };
+        fill(0, CV_H, CV_NF);
+        fill(CV_H * CV_NF + CV_H, CV_H, CV_H);
+        fill(CV_H * CV_NF + CV_H + CV_H * CV_H + CV_H, 1, CV_H);
+        CK(cudaMemcpyAsync(cvm.w, w.data(), sizeof(float) * CV_NP, cudaMemcpyHostToDevice, sm));
+        CK(cudaMemsetAsync(cvm.m, 0, sizeof(float) * CV_NP, sm));
+        CK(cudaMemsetAsync(cvm.v, 0, sizeof(float) * CV_NP, sm));
+        CK(cudaMemsetAsync(d_step, 0, sizeof(int), sm));
+        CK(cv_launch_to_bf16(cvm.w, cvm.wb, sm));
+        CK(cudaStreamSynchronize(sm));
+    }
+    // epochs over shuffled training rows (Fisher-Yates, splitmix64)
+    const int nb = nrows / cfg->batch;   // full minibatches only
+    if (nb < 1) return fail(ctx, TTCF_E_INVALID, "fewer training daughters than one minibatch");
+    std::vector<int> perm(rows);
+    uint64_t sh = cfg->seed ^ 0xA5A5A5A5A5A5A5A5ull;
+    for (int ep = 0; ep < cfg->epochs; ep++) {
+        for (int k = nrows - 1; k > 0; k--) {
+            const int j = (int)(splitmix64(sh) % (uint64_t)(k + 1));
+            std::swap(perm[k], perm[j]);
+        }
+        CK(cudaMemcpyAsync(d_idx, perm.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice, sm));
+        CK(cudaMemsetAsync(loss, 0, sizeof(double), sm));
+        for (int k = 0; k < nb; k++) {
+            CK(cv_launch_grad(cvm.wb, X, y, d_idx, (long long)k * cfg->batch, cfg->batch, part, lpart,
+                              d_step, sm));
+            CK(cv_launch_adam(part, tiles, lpart, nullptr, loss, cvm.w, cvm.m, cvm.v, cvm.wb, d_step,
+                              cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, sm));
+        }
+        double l = 0.0;
+        CK(cudaMemcpyAsync(&l, loss, sizeof(double), cudaMemcpyDeviceToHost, sm));
+        CK(cudaStreamSynchronize(sm));
+        if (loss_curve && ep < capacity) loss_curve[ep] = l / nb;
+    }
+    // c from the held-out groups
+    CK(cv_launch_predict(cvm.wb, X, D, f, ctx->nsm, sm));
+    CK(cv_launch_group(z, f, cvm.zstats, b->M, d_hold, nhold, yg, hg, sm));
+    CK(cv_launch_estimate(yg, hg, nhold, nullptr, 0, 1, 0.0, est, sm));
+    double eh[8];
+    CK(cudaMemcpyAsync(eh, est, sizeof(eh), cudaMemcpyDeviceToHost, sm));
+    CK(cudaStreamSynchronize(sm));
+    cvm.c = eh[4];
+    cvm.trained = true;
+    cvm.N = b->N;
+    for (int k = 0; k < 3; k++) cvm.L[k] = b->L[k];
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_cv_apply(ttcf_ctx *ctx, int batch_id, int n_aux, const double *aux_soa,
+                          const double *aux_alpha, double out[8]) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b || !out) return fail(ctx, TTCF_E_INVALID, "bad batch id or NULL output");
+    if (!ctx->cv.trained) return fail(ctx, TTCF_E_STATE, "control variate not trained");
+    if (!batch_finished(ctx, b)) return fail(ctx, TTCF_E_STATE, "run not finished");
+    if (b->N != ctx->cv.N) return fail(ctx, TTCF_E_INVALID, "evaluation batch N differs from training");
+    if (n_aux < 2 || !aux_soa) return fail(ctx, TTCF_E_INVALID, "need >= 2 auxiliary mother states");
+    for (double g : b->gamma)
+        if (g == 0.0) return fail(ctx, TTCF_E_INVALID, "evaluation needs a nonzero shear rate");
+    ttcf_status st;
+    std::vector<int> groups = valid_groups(ctx, *b, st);
+    if (st != TTCF_OK) return st;
+    const int ng = (int)groups.size();
+    if (ng < 2) return fail(ctx, TTCF_E_INVALID, "too few valid groups");
+    Pool tmp(ctx);
+    float *X; double *z;
+    ttcf_status s = cv_batch_data(ctx, tmp, *b, X, z);
+    if (s != TTCF_OK) return s;
+    const long long D = b->D();
+    CvModel &cvm = ctx->cv;
+    cudaStream_t sm = ctx->st;
+    float *f = tmp.get<float>(D);
+    int *d_g = tmp.get<int>(ng);
+    double *yg = tmp.get<double>(ng), *hg = tmp.get<double>(ng), *est = tmp.get<double>(8);
+    if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (cv apply)");
+    CK(cudaMemcpyAsync(d_g, groups.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, sm));
+    CK(cv_launch_standardize(X, D, cvm.fstats, nullptr, nullptr, nullptr, sm));
+    CK(cv_launch_predict(cvm.wb, X, D, f, ctx->nsm, sm));
+    CK(cv_launch_group(z, f, cvm.zstats, b->M, d_g, ng, yg, hg, sm));
+    // auxiliary mothers: spawn (features only), mapped features, predictions
+    BatchHost ab;
+    s = make_batch(ctx, tmp, ab, b->N, b->L, n_aux, aux_soa, aux_alpha, nullptr, 0, b->maps, b->M, 1, 0.0);
+    if (s != TTCF_OK) return s;
+    const long long DA = ab.D();
+    float *XA = tmp.get<float>((size_t)DA * CV_NF);
+    float *fA = tmp.get<float>(DA);
+    int *d_ga = tmp.get<int>(n_aux);
+    double *hA = tmp.get<double>(n_aux);
+    if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (cv auxiliary)");
+    CvFeatArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.raw = ab.feat; fa.alpha = ab.m_alpha; fa.reset_alpha = ctx->cfg.reset_alpha;
+    fa.M = ab.M; for (int k = 0; k < 4; k++) fa.maps[k] = ab.maps[k];
+    fa.D = DA; fa.N = ab.N; fa.V = ab.V; fa.X = XA;
+    CK(cv_launch_features(fa, sm));
+    CK(cv_launch_standardize(XA, DA, cvm.fstats, nullptr, nullptr, nullptr, sm));
+    CK(cv_launch_predict(cvm.wb, XA, DA, fA, ctx->nsm, sm));
+    {
+        std::vector<int> ga(n_aux);
+        for (int k = 0; k < n_aux; k++) ga[k] = k;
+        CK(cudaMemcpyAsync(d_ga, ga.data(), sizeof(int) * n_aux, cudaMemcpyHostToDevice, sm));
+        CK(cv_launch_group(nullptr, fA, cvm.zstats, ab.M, d_ga, n_aux, nullptr, hA, sm));
+        CK(cv_launch_estimate(yg, hg, ng, hA, n_aux, 0, cvm.c, est, sm));
+        CK(cudaMemcpyAsync(out, est, sizeof(double) * 8, cudaMemcpyDeviceToHost, sm));
+        CK(cudaStreamSynchronize(sm));
+    }
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_cv_get_model(ttcf_ctx *ctx, float *params, double *feat_stats, double *z_stats,
+                              double *c) {
+    if (!ctx) return fail(ctx, TTCF_E_INVALID, "NULL context");
+    if (!ctx->cv.trained) return fail(ctx, TTCF_E_STATE, "control variate not trained");
+    CK(cudaStreamSynchronize(ctx->st));
+    if (params) CK(cudaMemcpy(params, ctx->cv.w, sizeof(float) * CV_NP, cudaMemcpyDeviceToHost));
+    if (feat_stats) CK(cudaMemcpy(feat_stats, ctx->cv.fstats, sizeof(double) * 2 * CV_NF, cudaMemcpyDeviceToHost));
+    if (z_stats) CK(cudaMemcpy(z_stats, ctx->cv.zstats, sizeof(double) * 2, cudaMemcpyDeviceToHost));
+    if (c) *c = ctx->cv.c;
+    return TTCF_OK;
+}
+
+static ttcf_status cv_upload_params(ttcf_ctx *ctx, Pool &tmp, const float *params, __nv_bfloat16 *&wb) {
+    float *w = tmp.get<float>(CV_NP);
+    wb = tmp.get<__nv_bfloat16>(CV_NP);
+    if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (params)");
+    CK(cudaMemcpyAsync(w, params, sizeof(float) * CV_NP, cudaMemcpyHostToDevice, ctx->st));
+    CK(cv_launch_to_bf16(w, wb, ctx->st));
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_cv_forward(ttcf_ctx *ctx, const float *params, int n, const float *X, float *out) {
+    if (!ctx || !params || !X || !out || n < 1) return fail(ctx, TTCF_E_INVALID, "bad arguments");
+    Pool tmp(ctx);
+    __nv_bfloat16 *wb;
+    ttcf_status s = cv_upload_params(ctx, tmp, params, wb);
+    if (s != TTCF_OK) return s;
+    float *dX = tmp.get<float>((size_t)n * CV_NF), *df = tmp.get<float>(n);
+    if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (forward)");
+    CK(cudaMemcpyAsync(dX, X, sizeof(float) * n * CV_NF, cudaMemcpyHostToDevice, ctx->st));
+    CK(cv_launch_predict(wb, dX, n, df, ctx->nsm, ctx->st));
+    CK(cudaMemcpyAsync(out, df, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_cv_gradient(ttcf_ctx *ctx, const float *params, int n, const float *X,
+                             const float *y, float *grad, double *loss) {
+    if (!ctx || !params || !X || !y || n < 1 || n > 65536) return fail(ctx, TTCF_E_INVALID, "bad arguments");
+    Pool tmp(ctx);
+    __nv_bfloat16 *wb;
+    ttcf_status s = cv_upload_params(ctx, tmp, params, wb);
+    if (s != TTCF_OK) return s;
+    const int tiles = (n + 31) / 32;
+    float *dX = tmp.get<float>((size_t)n * CV_NF), *dy = tmp.get<float>(n);
+    float *part = tmp.get<float>((size_t)tiles * CV_NP), *dg = tmp.get<float>(CV_NP);
+    double *lpart = tmp.get<double>(tiles), *dl = tmp.get<double>(1);
+    if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (gradient)");
+    CK(cudaMemcpyAsync(dX, X, sizeof(float) * n * CV_NF, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(dy, y, sizeof(float) * n, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemsetAsync(dl, 0, sizeof(double), ctx->st));
+    CK(cv_launch_grad(wb, dX, dy, nullptr, 0, n, part, lpart, nullptr, ctx->st));
+    CK(cv_launch_adam(part, tiles, lpart, dg, dl, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
+                      0.f, 0.f, 0.f, ctx->st));
+    if (grad) CK(cudaMemcpyAsync(grad, dg, sizeof(float) * CV_NP, cudaMemcpyDeviceToHost, ctx->st));
+    double l = 0.0;
+    CK(cudaMemcpyAsync(&l, dl, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (loss) *loss = l;
     return TTCF_OK;
 }
 

@@ -82,7 +82,9 @@ struct Coef {
 struct Misc {
     double slot[MAX_WARPS][3];   // per-warp partial sums (df packed or double)
     // IEEE-double scalars of the daughter, touched by thread 0 only
-    double a_end, a_cur, K2_end, e1, delta, dsince;
+    double a_end, a_cur, K2_end, e1, delta, f1sq;
+    double hhQ, invV, ddelta, halfLx;   // per-daughter constants
+    float dsince;                       // |change of delta| since the list build
     unsigned int n_rebuild;
     int warp_tmp[MAX_WARPS];
     int flag_rebuild[2];
@@ -193,15 +195,23 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     Coef<S> *cf = (Coef<S> *)sp; sp += (sizeof(Coef<S>) + 15) / 16 * 16;
     Misc *m = (Misc *)sp;
 
-    unsigned int *nbr = a.nbr + (size_t)blockIdx.x * (CAP / 2) * nmax;
+    uint4 *nbr4 = reinterpret_cast<uint4 *>(a.nbr + (size_t)blockIdx.x * (CAP / 2) * nmax);
 
     // thread 0 keeps the IEEE-double scalars of the daughter in shared memory
     double &a_end = m->a_end, &a_cur = m->a_cur, &K2_end = m->K2_end, &e1 = m->e1;
-    double &delta = m->delta, &dsince = m->dsince;
+    double &delta = m->delta, &f1sq = m->f1sq;
+    float &dsince = m->dsince;
     const double h = a.dt, hh = 0.5 * a.dt;
     if (tid == 0) {
-        a_end = a_cur = K2_end = e1 = delta = dsince = 0.0;
+        a_end = a_cur = K2_end = e1 = delta = 0.0;
+        f1sq = 1.0;
+        dsince = 0.f;
         m->n_rebuild = 0;
+        // constants of the per-step lane-0 chain (no division in the loop)
+        m->hhQ = hh / b.Q;
+        m->invV = 1.0 / b.V;
+        m->ddelta = gamma * b.L[1] * h;
+        m->halfLx = 0.5 * b.L[0];
         cf->h = sfrom<S>(h); cf->hh = sfrom<S>(hh);
         cf->gh = sfrom<S>(gamma * h); cf->chalf = sfrom<S>(gamma * hh);
         for (int k = 0; k < 3; k++) {
@@ -225,6 +235,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         } else {
             const double *sc = b.scal + 4 * (size_t)dl;
             a_end = sc[0]; K2_end = sc[1]; e1 = sc[2]; delta = sc[3];
+            f1sq = (1.0 + e1) * (1.0 + e1);
         }
         cf->delta_d = delta; cf->delta_s = sfrom<S>(delta); cf->delta_f = (float)delta;
     }
@@ -345,36 +356,48 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             float wx, wy, wz;
             wrapped(i, wx, wy, wz);
             // a lost (non-finite or runaway) atom ends the daughter; it must
-            // not reach the loops below, whose bounds come from its position
-            if (!(fabsf(wx) <= cf->Lf[0] && fabsf(wy) <= cf->Lf[1] && fabsf(wz) <= cf->Lf[2])) {
+            // not reach the loops below, whose bounds come from its position.
+            // Wrapped coordinates satisfy |w| <= L/2; with |w| <= 3L/4 every
+            // window index below lies in (-2 nc, 2 nc).
+            if (!(fabsf(wx) <= 0.75f * cf->Lf[0] && fabsf(wy) <= 0.75f * cf->Lf[1] &&
+                  fabsf(wz) <= 0.75f * cf->Lf[2])) {
                 m->flag_lost = 1;
                 ncnt[q] = 0;
                 continue;
             }
-            const int cx = cell_of(wx, 0), cy = cell_of(wy, 1), cz = cell_of(wz, 2);
             unsigned short lst[CAP];
             int k = 0;
             bool ovf = false;
-            for (int oy = -1; oy <= 1; oy++) {
-                int yy = cy + oy;
-                const int cross = yy < 0 ? -1 : (yy >= nc[1] ? 1 : 0);
-                yy = (yy + nc[1]) % nc[1];
-                int x0 = cx - 1, x1 = cx + 1;
-                if (cross != 0) {
+            // windows [w - r_l, w + r_l] in cell units; |w| <= L keeps them small
+            const float hl0 = 0.5f * cf->Lf[0], hl1 = 0.5f * cf->Lf[1], hl2 = 0.5f * cf->Lf[2];
+            const float s0 = (float)nc[0] * cf->invLf[0], s1 = (float)nc[1] * cf->invLf[1],
+                        s2 = (float)nc[2] * cf->invLf[2];
+            const int z0 = (int)floorf((wz - rl + hl2) * s2);
+            const int z1 = min((int)floorf((wz + rl + hl2) * s2), z0 + nc[2] - 1);
+            const int y0 = (int)floorf((wy - rl + hl1) * s1);
+            const int y1 = min((int)floorf((wy + rl + hl1) * s1), y0 + nc[1] - 1);
+            // window indices lie in [-nc, 2nc): wrap by one conditional add
+            for (int zu = z0; zu <= z1; zu++) {
+                const int zz = zu < 0 ? zu + nc[2] : (zu >= nc[2] ? zu - nc[2] : zu);
+                for (int yu = y0; yu <= y1; yu++) {
+                    const int cross = yu < 0 ? -1 : (yu >= nc[1] ? 1 : 0);
+                    const int yy = yu - cross * nc[1];
                     // the row across the y face is seen shifted by cross*delta
                     const float xs = wx - (float)cross * cf->delta_f;
-                    const float s = (float)nc[0] * cf->invLf[0];
-                    const float hl = 0.5f * cf->Lf[0];
-                    x0 = (int)floorf((xs - rl + hl) * s);   // |xs| <= 2 L: small ints
-                    x1 = min((int)floorf((xs + rl + hl) * s), x0 + 2);
-                }
-                for (int oz = -1; oz <= 1; oz++) {
-                    const int zz = (cz + oz + nc[2]) % nc[2];
-                    for (int xc = x0; xc <= x1; xc++) {
-                        const int xx = ((xc % nc[0]) + nc[0]) % nc[0];
-                        const int c = (zz * nc[1] + yy) * nc[0] + xx;
-                        const int t1 = start[c + 1];
-                        for (int t = start[c]; t < t1; t++) {
+                    int x0 = (int)floorf((xs - rl + hl0) * s0);
+                    int x1 = min((int)floorf((xs + rl + hl0) * s0), x0 + nc[0] - 1);
+                    const int row = (zz * nc[1] + yy) * nc[0];
+                    // the x window as one or two contiguous runs of cell-sorted atoms
+                    int ra[2], rb[2], nr = 0;
+                    // x0 lies in [-2nc, 2nc): two conditional wraps
+                    int a0 = x0 < 0 ? x0 + nc[0] : (x0 >= nc[0] ? x0 - nc[0] : x0);
+                    a0 = a0 < 0 ? a0 + nc[0] : (a0 >= nc[0] ? a0 - nc[0] : a0);
+                    const int b0 = a0 + (x1 - x0);
+                    if (b0 < nc[0]) { ra[0] = a0; rb[0] = b0; nr = 1; }
+                    else { ra[0] = a0; rb[0] = nc[0] - 1; ra[1] = 0; rb[1] = b0 - nc[0]; nr = 2; }
+                    for (int r = 0; r < nr; r++) {
+                        const int t1 = start[row + rb[r] + 1];
+                        for (int t = start[row + ra[r]]; t < t1; t++) {
                             const int j = catom[t];
                             if (j == i) continue;
                             R dx, dy, dz;
@@ -391,11 +414,18 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                 }
             }
             if (ovf) m->flag_ovf = 1;
-            // two entries per word; an odd tail is padded with i itself (r = 0
-            // is rejected by the force loop)
-            for (int t = 0; t < k; t += 2) {
-                const unsigned int lo = lst[t], hi = (t + 1 < k) ? lst[t + 1] : (unsigned int)i;
-                nbr[(size_t)(t >> 1) * nmax + i] = lo | (hi << 16);
+            // eight entries per 16-byte chunk, two per word; an odd tail is
+            // padded with i itself (r = 0 is rejected by the force loop)
+            for (int t = 0; t < k; t += 8) {
+                unsigned int wv[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int e = t + 2 * u;
+                    const unsigned int lo = e < k ? lst[e] : (unsigned int)i;
+                    const unsigned int hi = e + 1 < k ? lst[e + 1] : (unsigned int)i;
+                    wv[u] = lo | (hi << 16);
+                }
+                nbr4[(size_t)(t >> 3) * nmax + i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
             }
             ncnt[q] = k;
         }
@@ -416,8 +446,13 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                     const float Lx = cf->Lf[0], Ly = cf->Lf[1], Lz = cf->Lf[2];
                     const float ix = cf->invLf[0], iy = cf->invLf[1], iz = cf->invLf[2];
                     const float dl = cf->delta_f;
-                    for (int t = 0; t < kk; t += 2) {
-                        const unsigned int word = nbr[(size_t)(t >> 1) * nmax + i];
+                    for (int t8 = 0; t8 < kk; t8 += 8) {
+                      const uint4 ch = nbr4[(size_t)(t8 >> 3) * nmax + i];
+                      const unsigned int wv[4] = {ch.x, ch.y, ch.z, ch.w};
+#pragma unroll
+                      for (int wq = 0; wq < 4; wq++) {
+                        if (t8 + 2 * wq >= kk) break;
+                        const unsigned int word = wv[wq];
 #pragma unroll
                         for (int hlf = 0; hlf < 2; hlf++) {
                             const int j = hlf ? (int)(word >> 16) : (int)(word & 0xffffu);
@@ -437,10 +472,13 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                             w = __fmaf_rn(f * dx, dy, w);
                             npairs += in ? 1u : 0u;
                         }
+                      }
                     }
                 } else {
                     for (int t = 0; t < kk; t++) {
-                        const unsigned int word = nbr[(size_t)(t >> 1) * nmax + i];
+                        const uint4 ch = nbr4[(size_t)(t >> 3) * nmax + i];
+                        const int u = (t >> 1) & 3;
+                        const unsigned int word = u == 0 ? ch.x : u == 1 ? ch.y : u == 2 ? ch.z : ch.w;
                         const int j = (t & 1) ? (int)(word >> 16) : (int)(word & 0xffffu);
                         R dx, dy, dz;
                         pair_vec(i, j, dx, dy, dz);
@@ -462,21 +500,24 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         return wsum;
     };
 
-    // thread 0: coefficients of the next step from K2_end, a_end, e1, delta
+    // thread 0: coefficients of the next step from K2_end, a_end, e1, delta.
+    // IEEE double throughout; on GB300 each double instruction of this
+    // serial chain costs tens of cycles, so divisions and rint are avoided.
     auto next_step = [&]() {
-        const double inc = hh / b.Q * (K2_end - b.gT);
+        const double inc = m->hhQ * (K2_end - b.gT);
         a_cur = a_end + inc;                       // start-of-step alpha half-step
         const double e3 = expm1_small(-a_cur * hh);
-        const double ec = e1 + e3 + e1 * e3;       // pending factor times new one
+        const double ec = fma(e1, e3, e1 + e3);    // (1+e1)(1+e3) - 1
         e1 = e3;
+        f1sq = (1.0 + e3) * (1.0 + e3);
         cf->e = sfrom<S>(ec);
-        const double dd = gamma * b.L[1] * h;      // sliding-brick offset advance
-        delta += dd;
-        delta -= b.L[0] * rint(delta * cf->invL[0]);
-        dsince += dd;
+        delta += m->ddelta;                        // sliding-brick offset advance
+        if (delta >= m->halfLx) delta -= b.L[0];
+        else if (delta < -m->halfLx) delta += b.L[0];
+        dsince += fabsf((float)m->ddelta);
         cf->delta_d = delta; cf->delta_s = sfrom<S>(delta); cf->delta_f = (float)delta;
-        const double thr = 0.5 * ((double)b.skin - fabs(dsince));
-        cf->thr2 = thr > 0.0 ? (float)(thr * thr) : -1.f;
+        const float thr = 0.5f * (b.skin - dsince);
+        cf->thr2 = thr > 0.f ? thr * thr : -1.f;
     };
 
     // ---- forces and sums of the initial state ----
@@ -590,7 +631,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         if (m->flag_fast) break;
         if (m->flag_rebuild[fb] || thr2 < 0.f) {
             build_list();
-            if (tid == 0) { dsince = 0.0; m->n_rebuild++; }
+            if (tid == 0) { dsince = 0.f; m->n_rebuild++; }
         }
         // phase B
         const R wsum = forces();
@@ -618,11 +659,10 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         double sums[3];
         cta_sum3<MIXED, R>(s2, sxy, wsum, m, sums);             // barrier 2
         if (tid == 0) {
-            // end of step s: pending factor (1+e1) from the scale half-step
-            const double f1 = 1.0 + e1, f1sq = f1 * f1;
+            // end of step s: pending factor (1+e1)^2 = f1sq from the scale half-step
             K2_end = f1sq * sums[0];
-            a_end = a_cur + hh / b.Q * (K2_end - b.gT);         // end-of-step alpha half-step
-            const double pxy = (f1sq * sums[1] + 0.5 * sums[2]) / b.V;
+            a_end = a_cur + m->hhQ * (K2_end - b.gT);           // end-of-step alpha half-step
+            const double pxy = fma(f1sq, sums[1], 0.5 * sums[2]) * m->invV;
             if (!isfinite(sums[0] + sums[1] + sums[2])) cf->stop |= TTCF_D_NONFINITE;
             if (m->flag_ovf) cf->stop |= TTCF_D_NBR_OVERFLOW;
             if (m->flag_lost) cf->stop |= TTCF_D_NONFINITE;
@@ -631,7 +671,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             if (a.snap && s >= a.snap_first && (s - a.snap_first) % a.snap_every == 0) {
                 const int k = (s - a.snap_first) / a.snap_every;
                 if (k < a.n_snap) {
-                    cf->snap = k; cf->fsnap = f1;
+                    cf->snap = k; cf->fsnap = 1.0 + e1;
                     a.snap_alpha[(size_t)d * a.n_snap + k] = a_end;
                 }
             }

@@ -201,6 +201,13 @@ __host__ __device__ inline Variant variant_of(int v) {
     }
 }
 
+// Default launch variant for a daughter of N atoms and the default skin
+// (measured on GB300; ttcf_autotune refines both per N).
+constexpr double DEFAULT_SKIN = 0.4;
+__host__ __device__ inline int default_variant(int N) {
+    return N <= 1024 ? 1 : N <= 2048 ? 2 : 5;
+}
+
 // Shared-memory bytes of a daughter CTA (must match the carve-up in
 // ttcf_daughter.cu).
 __host__ __device__ inline size_t daughter_smem_bytes(bool mixed, int nmax, int ncellmax) {

@@ -29,10 +29,16 @@ struct SpawnArgs {
     double *B;                 // [D][S]: writes B[d][0]
     int S;
     double *Omega;             // [D]
-    double *feat;              // [G][16]: P_ab (6), U, K2, or null
+    double *feat;              // [G][FEAT_RAW] raw features, or null
     double delta;              // Lees-Edwards offset of the phase points
 };
 cudaError_t launch_spawn(const SpawnArgs &a, cudaStream_t st);
+
+// Raw per-mother features written by the spawn kernel: K_ab = sum p_a p_b
+// (6: xx yy zz xy xz yz), W_ab virial sums (6), U, sum p^2, then for
+// q = 1..4 (cos, sin) modes over 40 slabs in y of the density (8) and of the
+// x momentum (8), each divided by N; two unused slots.
+constexpr int FEAT_RAW = 32;
 size_t spawn_smem_bytes(int N, int ncell);
 
 // reduction (ttcf_reduce.cu): fixed-order ensemble averages of one batch.

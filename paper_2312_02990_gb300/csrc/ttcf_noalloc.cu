@@ -69,7 +69,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     if (n_atoms < 4 || n_atoms > 4096 || n_mothers < 1)
         return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: n_atoms must be in [4, 4096], n_mothers >= 1");
     const double rc = 1.1224620483093730;
-    const double skin = c.skin > 0 ? c.skin : 0.3;
+    const double skin = c.skin > 0 ? c.skin : DEFAULT_SKIN;
     const int N = n_atoms, G = n_mothers;
     int maps[4], M = 0;
     for (int m = 0; m < 4; m++) if (c.mapping_mask & (1u << m)) maps[M++] = m;
@@ -77,8 +77,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     const int S = c.n_steps / c.sample_every + 1;
 
     // launch shape: the default table of the context path
-    int variant = c.kernel_variant > 0 ? c.kernel_variant - 1
-                  : N <= 256 ? 0 : N <= 1024 ? 1 : N <= 2048 ? 3 : 5;
+    int variant = c.kernel_variant > 0 ? c.kernel_variant - 1 : default_variant(N);
     const Variant v = variant_of(variant);
     int threads = c.block_threads > 0 ? c.block_threads : (N + v.apt - 1) / v.apt;
     threads = (threads + 31) / 32 * 32;
@@ -116,7 +115,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     const size_t o_queue = off; off += align256(sizeof(int));
     const size_t o_alpha = off; off += align256(sizeof(double) * G);
     const size_t o_moth = off; off += align256(sizeof(unsigned long long) * G * 6 * N);
-    const size_t o_feat = off; off += align256(sizeof(double) * G * 16);
+    const size_t o_feat = off; off += align256(sizeof(double) * G * FEAT_RAW);
     const size_t o_pairs = off; off += align256(sizeof(unsigned long long) * D);
     const size_t o_reb = off; off += align256(sizeof(unsigned int) * D);
     const size_t o_scal = off; off += align256(sizeof(double) * D * 4);

@@ -10,9 +10,11 @@
 
 namespace ttcf {
 
+constexpr int NSLAB = 40, NMODE = 4, NACC = 13 + 4 * NMODE;
+
 size_t spawn_smem_bytes(int N, int ncell) {
     return (size_t)N * 24 + (size_t)(2 * ncell + 2) * 4 + ((size_t)N * 2 + 15) / 16 * 16 +
-           32 * 13 * 8 + 256;
+           32 * NACC * 8 + 256;
 }
 
 __global__ void spawn_kernel(SpawnArgs a) {
@@ -25,7 +27,7 @@ __global__ void spawn_kernel(SpawnArgs a) {
     int *start = cnt + a.ncell;
     unsigned short *catom = (unsigned short *)(start + a.ncell + 2);
     double *red = (double *)((unsigned char *)catom + ((size_t)N * 2 + 15) / 16 * 16);
-    int *warp_tmp = (int *)(red + 32 * 13);
+    int *warp_tmp = (int *)(red + 32 * NACC);
 
     const double invL[3] = {1.0 / a.L[0], 1.0 / a.L[1], 1.0 / a.L[2]};
     for (int i = tid; i < N; i += T) { xd[i] = src[i]; yd[i] = src[N + i]; zd[i] = src[2 * N + i]; }
@@ -65,14 +67,33 @@ __global__ void spawn_kernel(SpawnArgs a) {
     }
     __syncthreads();
 
-    // 13 partial sums: kinetic K_ab (6), virial W_ab (6), U
-    double acc[13];
-    for (int k = 0; k < 13; k++) acc[k] = 0.0;
+    // cosine/sine of 2 pi q (k + 1/2) / 40 for the 40 slabs in y, q = 1..4
+    __shared__ double cs_tab[NSLAB][2 * NMODE];
+    for (int e = tid; e < NSLAB * NMODE; e += T) {
+        const int k = e / NMODE, q = e % NMODE + 1;
+        double sn, c;
+        sincospi(2.0 * q * (k + 0.5) / NSLAB, &sn, &c);
+        cs_tab[k][2 * (q - 1)] = c;
+        cs_tab[k][2 * (q - 1) + 1] = sn;
+    }
+    __syncthreads();
+    // partial sums: kinetic K_ab (6), virial W_ab (6), U, then the density
+    // modes (8) and x-momentum modes (8) over the slabs
+    double acc[NACC];
+    for (int k = 0; k < NACC; k++) acc[k] = 0.0;
     const double rc2 = 1.2599210498948732;
     for (int i = tid; i < N; i += T) {
         const double px = src[3 * N + i], py = src[4 * N + i], pz = src[5 * N + i];
         acc[0] += px * px; acc[1] += py * py; acc[2] += pz * pz;
         acc[3] += px * py; acc[4] += px * pz; acc[5] += py * pz;
+        {
+            int k = (int)floor((yd[i] + 0.5 * a.L[1]) * invL[1] * NSLAB);
+            k = min(max(k, 0), NSLAB - 1);
+            for (int u = 0; u < 2 * NMODE; u++) {
+                acc[13 + u] += cs_tab[k][u];
+                acc[13 + 2 * NMODE + u] += px * cs_tab[k][u];
+            }
+        }
         int cx, cy, cz;
         cell3(i, cx, cy, cz);
         for (int oy = -1; oy <= 1; oy++) {
@@ -110,17 +131,17 @@ __global__ void spawn_kernel(SpawnArgs a) {
     }
     // fixed-order CTA reduction
     const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-    for (int k = 0; k < 13; k++) {
+    for (int k = 0; k < NACC; k++) {
         double v = acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp * 13 + k] = v;
+        if (lane == 0) red[warp * NACC + k] = v;
     }
     __syncthreads();
     if (tid == 0) {
-        double tot[13];
-        for (int k = 0; k < 13; k++) {
+        double tot[NACC];
+        for (int k = 0; k < NACC; k++) {
             double v = 0.0;
-            for (int w = 0; w < nw; w++) v += red[w * 13 + k];
+            for (int w = 0; w < nw; w++) v += red[w * NACC + k];
             tot[k] = v;
         }
         const double pxy = (tot[3] + tot[9]) / a.V;
@@ -132,13 +153,13 @@ __global__ void spawn_kernel(SpawnArgs a) {
             a.B[d * a.S] = b0;
             a.Omega[d] = -gm * a.V * b0 / a.T;
         }
-        if (a.feat) {
-            double *f = a.feat + (size_t)g * 16;
-            for (int k = 0; k < 6; k++) f[k] = (tot[k] + tot[6 + k]) / a.V;
-            f[6] = tot[12];
-            f[7] = tot[0] + tot[1] + tot[2];
-            for (int k = 0; k < 6; k++) f[8 + k] = tot[6 + k] / a.V;
-            f[14] = f[15] = 0.0;
+        if (a.feat) {   // raw features of the unmapped mother (FEAT_RAW doubles)
+            double *f = a.feat + (size_t)g * FEAT_RAW;
+            for (int k = 0; k < 12; k++) f[k] = tot[k];          // K_ab, W_ab
+            f[12] = tot[12];                                      // U
+            f[13] = tot[0] + tot[1] + tot[2];                     // sum p^2
+            for (int u = 0; u < 4 * NMODE; u++) f[14 + u] = tot[13 + u] / N;   // modes
+            f[30] = f[31] = 0.0;
         }
     }
     // mother into the daughter kernel's state format

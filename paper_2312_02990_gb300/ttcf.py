@@ -27,7 +27,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_run",
            "ttcf_response", "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
            "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces", "ttcf_autotune",
-           "ttcf_run_noalloc",
+           "ttcf_run_noalloc", "ttcf_cv_config_default", "ttcf_cv_data", "ttcf_cv_train",
+           "ttcf_cv_apply", "ttcf_cv_get_model", "ttcf_cv_forward", "ttcf_cv_gradient",
            "ttcf_destroy", "ttcf_last_error", "ttcf_version")
 
 
@@ -36,8 +37,17 @@ class Config(C.Structure):
                 ("T", C.c_double), ("tau_T", C.c_double), ("dof_mode", C.c_int),
                 ("n_steps", C.c_int), ("sample_every", C.c_int), ("mapping_mask", C.c_uint),
                 ("reset_alpha", C.c_int), ("keep_state", C.c_int), ("skin", C.c_double),
-                ("block_threads", C.c_int), ("kernel_variant", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
+                ("block_threads", C.c_int), ("kernel_variant", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_user", C.c_void_p), ("timeout_s", C.c_double)]
+
+
+class CvConfig(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("holdout", C.c_float),
+                ("seed", C.c_ulonglong)]
+
+
+CV_NF, CV_NP = 32, 20865
 
 
 class Stats(C.Structure):
@@ -91,6 +101,18 @@ def load(build_if_missing: bool = False):
     L.ttcf_autotune.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_int, ip, _dp, _dp]
     L.ttcf_run_noalloc.argtypes = [C.POINTER(Config), C.c_int, _dp, C.c_int, vp, vp, vp, vp, vp, vp]
     L.ttcf_run_noalloc.restype = C.c_int
+    fp = C.POINTER(C.c_float)
+    L.ttcf_cv_config_default.argtypes = [C.POINTER(CvConfig)]
+    L.ttcf_cv_config_default.restype = None
+    L.ttcf_cv_data.argtypes = [vp, C.c_int, fp, _dp, C.c_size_t]
+    L.ttcf_cv_train.argtypes = [vp, C.c_int, C.POINTER(CvConfig), _dp, C.c_int]
+    L.ttcf_cv_apply.argtypes = [vp, C.c_int, C.c_int, _dp, _dp, _dp]
+    L.ttcf_cv_get_model.argtypes = [vp, fp, _dp, _dp, _dp]
+    L.ttcf_cv_forward.argtypes = [vp, fp, C.c_int, fp, fp]
+    L.ttcf_cv_gradient.argtypes = [vp, fp, C.c_int, fp, fp, fp, _dp]
+    for name in ("ttcf_cv_data", "ttcf_cv_train", "ttcf_cv_apply", "ttcf_cv_get_model",
+                 "ttcf_cv_forward", "ttcf_cv_gradient"):
+        getattr(L, name).restype = C.c_int
     L.ttcf_destroy.argtypes = [vp]
     L.ttcf_destroy.restype = None
     L.ttcf_last_error.argtypes = [vp]
@@ -311,6 +333,53 @@ class Context:
                                           C.byref(sk), C.byref(ms)))
         return v.value, sk.value, ms.value
 
+    # -- learned control variate --
+    def cv_data(self, batch: int, n_daughters: int):
+        X = np.zeros((n_daughters, CV_NF), dtype=np.float32)
+        z = np.zeros(n_daughters)
+        self._check(self._L.ttcf_cv_data(self.h, batch, _fptr(X), _ptr(z), n_daughters))
+        return X, z
+
+    def cv_train(self, batch: int, cfg: CvConfig | None = None) -> np.ndarray:
+        cfg = cfg or cv_config_default()
+        loss = np.zeros(cfg.epochs)
+        self._check(self._L.ttcf_cv_train(self.h, batch, C.byref(cfg), _ptr(loss), cfg.epochs))
+        return loss
+
+    def cv_apply(self, batch: int, aux_soa, aux_alpha=None) -> dict:
+        a = _f64(aux_soa)
+        al = None if aux_alpha is None else _f64(aux_alpha)
+        out = np.zeros(8)
+        self._check(self._L.ttcf_cv_apply(self.h, batch, int(a.shape[0]), _ptr(a),
+                                          None if al is None else _ptr(al), _ptr(out)))
+        keys = ("eta_plain", "se_plain", "eta_cv", "se_cv", "c", "gain", "n_groups", "n_aux")
+        return dict(zip(keys, out.tolist()))
+
+    def cv_get_model(self):
+        p = np.zeros(CV_NP, dtype=np.float32)
+        fs = np.zeros((CV_NF, 2))
+        zs = np.zeros(2)
+        c = C.c_double()
+        self._check(self._L.ttcf_cv_get_model(self.h, _fptr(p), _ptr(fs), _ptr(zs), C.byref(c)))
+        return p, fs, zs, c.value
+
+    def cv_forward(self, params, X):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        Xf = np.ascontiguousarray(X, dtype=np.float32)
+        out = np.zeros(Xf.shape[0], dtype=np.float32)
+        self._check(self._L.ttcf_cv_forward(self.h, _fptr(p), int(Xf.shape[0]), _fptr(Xf), _fptr(out)))
+        return out
+
+    def cv_gradient(self, params, X, y):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        Xf = np.ascontiguousarray(X, dtype=np.float32)
+        yf = np.ascontiguousarray(y, dtype=np.float32)
+        g = np.zeros(CV_NP, dtype=np.float32)
+        loss = C.c_double()
+        self._check(self._L.ttcf_cv_gradient(self.h, _fptr(p), int(Xf.shape[0]), _fptr(Xf), _fptr(yf),
+                                             _fptr(g), C.byref(loss)))
+        return g, loss.value
+
     def forces(self, soa, box, delta: float = 0.0):
         s = _f64(soa)
         if s.ndim == 2:
@@ -322,6 +391,17 @@ class Context:
         self._check(self._L.ttcf_forces(self.h, int(N), _ptr(_box(box)), int(n), float(delta),
                                         _ptr(s), _ptr(F), _ptr(W), _ptr(U)))
         return F, W, U
+
+
+def cv_config_default() -> CvConfig:
+    c = CvConfig()
+    load().ttcf_cv_config_default(C.byref(c))
+    return c
+
+
+def _fptr(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_float))
 
 
 def run_noalloc(cfg: Config, mother_soa, mother_alpha, shear_rates, box, B, Omega, status) -> int:

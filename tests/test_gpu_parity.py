@@ -324,7 +324,7 @@ def test_autotuner_choice_is_used_and_exact(ttcf, eq_mothers_256):
     b, ms, al = eq_mothers_256
     with ctx(ttcf, precision=1, n_steps=40, keep_state=1) as c:
         v, skin, t = c.autotune(ms[:4], b.L, shear_rate=1e-3, n_steps=20)
-        assert 1 <= v <= 6 and skin in (0.2, 0.3, 0.4) and t > 0
+        assert 1 <= v <= 6 and skin in (0.3, 0.4, 0.5, 0.6) and t > 0
         bid = c.spawn_daughters(ms[:2], al[:2], 1e-3, box=b.L)
         c.run()
         assert c.get_stats()["skin"] == skin
@@ -332,3 +332,22 @@ def test_autotuner_choice_is_used_and_exact(ttcf, eq_mothers_256):
     _, _, fin, fa = oracle.daughter(b, ms[0], al[0], 3, 1e-3, 40)
     L = np.asarray(b.L)[:, None]
     assert np.abs(min_image_diff(s[:3], fin[:3], L)).max() < 1e-6
+
+
+def test_graph_and_stream_launches_agree_bitwise(ttcf):
+    """One CUDA graph per run (persistent launches of two size classes on
+    forked streams plus the reductions) gives the same bits as plain
+    stream launches."""
+    out = []
+    for use_graph in (1, 0):
+        with ctx(ttcf, precision=1, n_steps=50, use_graph=use_graph) as c:
+            ids = []
+            for N in (256, 864):
+                b = bulk(N)
+                ids.append((c.spawn_daughters(inputs.jittered_states(N, 3, seed=N, amp=0.05), None,
+                                              1e-3, box=b.L), N))
+            c.run()
+            out.append([c.daughter_series(i, 12)[0] for i, _ in ids] + [c.response(i)["ttcf"] for i, _ in ids])
+            assert c.get_stats()["launches"] == 2 + 3 * 2
+    for a, b_ in zip(out[0], out[1]):
+        assert np.array_equal(a, b_)
