@@ -61,6 +61,12 @@ def parse():
     p.add_argument("--n-eq", type=int, default=20000)
     p.add_argument("--spacing", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-cv", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--cv-train-groups", type=int, default=16384)
+    p.add_argument("--cv-eval-groups", type=int, default=4096)
+    p.add_argument("--cv-aux", type=int, default=65536)
+    p.add_argument("--cv-steps", type=int, default=500)
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
@@ -153,10 +159,7 @@ def one_step(T, torch, args, L, mothers_dev, alpha_dev, rates, host=None):
         else:
             ids.append(c.spawn_daughters(host[0], host[1], float(g), box=L))
     c.run()
-    out = []
-    if host is not None or True:
-        for bid in ids:
-            out.append(c.viscosity(bid))
+    out = [(c.viscosity(bid), c.response(bid)) for bid in ids]
     stats = c.get_stats()
     c.close()
     return out, stats
@@ -253,9 +256,17 @@ def bench_gb300(args):
                 "kernel": "daughter_kernel", "kernel_ms": k_ms,
                 "algorithmic": "unique interacting pairs x 36 FP32 flops",
                 "peak_note": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
-    eta = {f"{g:.0e}": {"eta_ttcf": float(r["eta_ttcf"][-1]), "eta_ttcf_se": float(r["eta_ttcf_se"][-1]),
-                        "eta_dav": float(r["eta_dav"][-1]), "eta_dav_se": float(r["eta_dav_se"][-1])}
-           for g, r in zip(rates, results)}
+    # the one exchange of the weak-scaled job: per-rate ensemble statistics
+    # merged over ranks (each rank's groups are independent)
+    if world > 1:
+        from paper_2312_02990_gb300 import merge
+        merged = [merge.merge_ranks(resp, G) for _, resp in results]
+    else:
+        merged = [resp for _, resp in results]
+    eta = {f"{g:.0e}": {"eta_ttcf": float(-m["ttcf"][-1] / g), "eta_ttcf_se": float(m["ttcf_se"][-1] / g),
+                        "eta_dav": float(-m["dav"][-1] / g), "eta_dav_se": float(m["dav_se"][-1] / g)}
+           for g, m in zip(rates, merged)}
+    results = [v for v, _ in results]
     line = {
         "metric": "daughter atom-steps/s", "value": value, "unit": "atom-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -278,12 +289,101 @@ def bench_gb300(args):
         "mother_setup_s": t_mothers,
         "viscosity_t_end": eta,
     }
+    # viscosity variance per GPU-second against plain GPU TTCF
+    if not args.no_plain:
+        rate_plain, _ = plain_gpu_rate(T, torch, N, L, ms_dev, al_dev)
+        per_rate_s = ms_step * 1e-3 / len(rates)
+        eff = {}
+        for g, r in zip(rates, results):
+            var = float(r["eta_ttcf_se"][-1]) ** 2
+            t_plain = (atom_steps / len(rates)) / rate_plain
+            eff[f"{g:.0e}"] = {"per_gpu_second": 1.0 / (var * per_rate_s),
+                               "plain_per_gpu_second": 1.0 / (var * t_plain),
+                               "ratio": t_plain / per_rate_s}
+        line["plain_gpu_ttcf"] = {"value": rate_plain, "unit": "atom-steps/s",
+                                  "definition": "FP64 mode, one non-persistent launch per MD step, "
+                                                "no graph, no control variate",
+                                  "sample": "608 daughters x 29 steps, N=2048"}
+        line["viscosity_variance_per_gpu_second"] = eff
+    if not args.no_cv and rank == 0:
+        line["control_variate"] = cv_section(T, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, N)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def plain_gpu_rate(T, torch, N, L, ms_dev, al_dev, n_groups=152, n_steps=30):
+    """Plain GPU TTCF: the same kernels in FP64 mode, one non-persistent
+    launch per MD step (chunked runs of one step: state saved and reloaded,
+    list rebuilt), no graph, no control variate.  Atom-steps/s."""
+    cfg = T.config_default()
+    cfg.precision, cfg.n_steps, cfg.use_graph = T.TTCF_FP64, n_steps, 0
+    with T.Context(cfg) as c:
+        c.spawn_daughters(ms_dev[:n_groups], al_dev[:n_groups], 1e-3, box=L)
+        c.run(1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(n_steps - 1):
+            c.run(1)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+    return 4 * n_groups * N * (n_steps - 1) / el, el
+
+
+def cv_section(T, torch, args):
+    """Learned control variate on the N=256 system: train on 16384 groups
+    (65536 daughters) at gamma = 1e-3, evaluate at gamma = 1e-6 on 4096
+    disjoint groups with 65536 independent auxiliary mother states."""
+    from paper_2312_02990_gb300 import inputs
+    N = 256
+    L = inputs.bulk_box(N)
+    n_tr, n_ev, n_aux = args.cv_train_groups, args.cv_eval_groups, args.cv_aux
+    total = n_tr + n_ev + n_aux
+    n_moth = 64
+    per = (total + n_moth - 1) // n_moth
+    cfg = T.config_default()
+    cfg.precision, cfg.n_steps = T.TTCF_MIXED, args.cv_steps
+    t0 = time.perf_counter()
+    with T.Context(cfg) as c:
+        init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 50000 + k) for k in range(n_moth)])
+        ms, al = c.sample_mothers(init, L, n_eq=args.n_eq, n_states=per, spacing=args.spacing)
+    t_moth = time.perf_counter() - t0
+    order = np.arange(n_moth * per).reshape(n_moth, per).T.ravel()
+    ms, al = ms.reshape(-1, 6, N)[order], al.reshape(-1)[order]
+    tr, ev = slice(0, n_tr), slice(n_tr, n_tr + n_ev)
+    aux = slice(n_tr + n_ev, total)
+    with T.Context(cfg) as c:
+        bt = c.spawn_daughters(ms[tr], al[tr], 1e-3, box=L)
+        be = c.spawn_daughters(ms[ev], al[ev], 1e-6, box=L)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        c.run()
+        torch.cuda.synchronize()
+        t_run = time.perf_counter() - t
+        t = time.perf_counter()
+        loss = c.cv_train(bt)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t
+        t = time.perf_counter()
+        r = c.cv_apply(be, ms[aux], al[aux])
+        torch.cuda.synchronize()
+        t_apply = time.perf_counter() - t
+    t_eval_run = t_run * n_ev / (n_tr + n_ev)
+    # efficiency 1/(Var * T_GPU) of the evaluation estimate, with and without
+    # the network's training time amortised into it
+    e_plain = 1.0 / (r["se_plain"] ** 2 * t_eval_run)
+    e_cv = 1.0 / (r["se_cv"] ** 2 * (t_eval_run + t_apply))
+    e_cv_train = 1.0 / (r["se_cv"] ** 2 * (t_eval_run + t_apply + t_train))
+    return {"eta_plain": r["eta_plain"], "se_plain": r["se_plain"], "eta_cv": r["eta_cv"],
+            "se_cv": r["se_cv"], "c": r["c"], "variance_gain": r["gain"],
+            "efficiency_gain_cv_vs_same_kernels": e_cv / e_plain,
+            "efficiency_gain_cv_with_training": e_cv_train / e_plain,
+            "train_loss_first_last": [float(loss[0]), float(loss[-1])],
+            "groups": {"train": n_tr, "eval": n_ev, "aux": n_aux}, "daughter_steps": args.cv_steps,
+            "seconds": {"mothers": t_moth, "run": t_run, "train": t_train, "apply": t_apply}}
 
 
 # -------------------------------------------------------------- oracle --
@@ -312,8 +412,8 @@ def oracle_sample(N, n_groups, n_steps, gamma, threads):
 
 def cpu_baseline(args, N):
     threads = os.cpu_count() or 1
-    groups = max(1, threads // 4) * 2
-    steps = 400
+    groups = 2 * threads
+    steps = 1000
     v, el = oracle_sample(N, groups, steps, 1e-3, threads)
     return {"value": v, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{4 * groups} daughters x {steps} steps, N={N}, gamma=1e-3 "
