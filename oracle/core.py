@@ -14,6 +14,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ttcf_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "ttcf_confined.c")]
 _SO = os.path.join(_HERE, "libttcf_oracle.so")
 _lib = None
 
@@ -22,9 +23,10 @@ RC_WCA = 2.0 ** (1.0 / 6.0)
 
 def build(force: bool = False) -> str:
     """Compile the oracle (portable flags: it builds on x86_64 and aarch64)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
-               "-o", _SO, _SRC, "-lm"]
+               "-o", _SO, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
     return _SO
 
