@@ -53,7 +53,22 @@ typedef enum {
     TTCF_E_STATE = 6     /* call out of order (e.g. response before run)     */
 } ttcf_status;
 
-enum { TTCF_BULK_WCA = 0 };
+/* Systems.
+ *  TTCF_BULK_WCA     Example 1: WCA fluid under SLLOD shear with
+ *                    Lees-Edwards boundaries and a Nose-Hoover thermostat.
+ *  TTCF_CONFINED_LJ  Example 2: Lennard-Jones fluid between two walls of
+ *                    tethered atoms whose lattices slide at +-v in x
+ *                    (Eq. 9, 10); MIXED precision only.                  */
+enum { TTCF_BULK_WCA = 0, TTCF_CONFINED_LJ = 1 };
+
+/* Responses per sample of a confined daughter (TTCF_CONFINED_LJ):
+ *  0              x force of the fluid on the bottom wall per wall area
+ *  1              the same on the top wall
+ *  2 + k          sum of fluid p_x in slab k (k < TTCF_CONF_NSLAB) of
+ *                 equal slabs spanning y in [-Ly/2, Ly/2)
+ *  2 + NSLAB + k  number of fluid atoms in slab k
+ * (slab velocity profile: response 2+k divided by response 2+NSLAB+k).  */
+enum { TTCF_CONF_NSLAB = 40, TTCF_CONF_NOBS = 2 + 2 * 40 };
 
 /* Arithmetic of the daughter integrator.
  *  TTCF_FP64:  every per-atom quantity in IEEE double (slow on GB300).
@@ -77,7 +92,7 @@ typedef void (*ttcf_free_fn)(void *ptr, void *stream, void *user);
 
 /* Plain-old-data configuration; copied by ttcf_create. */
 typedef struct {
-    int system;             /* TTCF_BULK_WCA                                 */
+    int system;             /* TTCF_BULK_WCA or TTCF_CONFINED_LJ             */
     int precision;          /* TTCF_FP64 or TTCF_MIXED                       */
     double dt;              /* time step h (Example 1: 0.0025)               */
     double T;               /* thermostat k_B T (Example 1: 0.722)           */
@@ -146,7 +161,9 @@ ttcf_status ttcf_spawn_daughters(ttcf_ctx *ctx, int n_atoms, const double box[3]
  * Hoover, Eq. 5; pair forces, Eq. 6) in one persistent launch per size
  * class, recording B(s) on device.  May be called in chunks; chunks give
  * bitwise the same result as one call.  n_steps = 0 or more than remain:
- * runs the rest.  Returns after the stream is synchronised.
+ * runs the rest.  Returns after the stream is synchronised.  Confined
+ * daughters (Eq. 10) run all n_steps in one call (a smaller n_steps is
+ * TTCF_E_INVALID) and keep_state does not apply to them.
  * Errors: TTCF_E_STATE (nothing spawned), TTCF_E_NUMERIC (some daughters
  * failed; see ttcf_group_status), TTCF_E_TIMEOUT, TTCF_E_CUDA.             */
 ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps);
@@ -175,8 +192,10 @@ ttcf_status ttcf_viscosity(ttcf_ctx *ctx, int batch_id, double *t, double *eta_t
                            double *eta_ttcf_se, double *eta_dav, double *eta_dav_se,
                            int capacity, int *n_samples);
 
-/* Raw per-daughter outputs of a batch: B [D][S] and Omega [D] (host
- * arrays, D = n_mothers * M).  capacity_B is the element count of B.      */
+/* Raw per-daughter outputs of a batch: B [D][n_obs][S] and Omega [D]
+ * (host arrays, D = n_mothers * M; n_obs = 1 for the bulk system, so B is
+ * [D][S] there, TTCF_CONF_NOBS for the confined one).  capacity_B is the
+ * element count of B.                                                     */
 ttcf_status ttcf_daughter_series(ttcf_ctx *ctx, int batch_id, double *B, double *Omega,
                                  size_t capacity_B);
 
@@ -235,6 +254,66 @@ ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_s
 ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
                           const double *soa, double shear_rate, int n_steps, int *best_variant,
                           double *best_skin, double *best_ms);
+
+/* ------------------------------------------------------------------------
+ * Confined system (Example 2; contexts created with system =
+ * TTCF_CONFINED_LJ).  Pair potential 4[r^-12 - c_ij r^-6] cut at r_c
+ * (Eq. 9) between fluid-fluid (c_ff) and wall-fluid (c_wf) pairs; wall atoms
+ * do not interact with each other.  Wall atoms are tethered to lattice
+ * sites by springs k and carry a Nose-Hoover thermostat at cfg.T with
+ * Q = 3 N_w T tau_T^2 (Eq. 10); during a daughter the bottom lattice moves
+ * at -v and the top one at +v in x with v = gamma h / 2.  The dissipation
+ * function is Omega = -(1/T) sum_w k (x_w - x_l) s_w v (Eq. 11; s_w = -1
+ * bottom, +1 top).  x and z are periodic, y is open.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double k;               /* tether stiffness                              */
+    double rc;              /* cut-off radius (Example 2: 2.5)                */
+    double c_ff, c_wf;      /* wetting coefficients (Example 2: 1.2, 0.6325)  */
+    double h;               /* channel width: v = gamma h / 2 (Example 2: 10) */
+} ttcf_confined_params;
+
+/* Example 2 values: k 150, r_c 2.5, c_ff 1.2, c_wf 0.6325, h 10.           */
+void ttcf_confined_params_default(ttcf_confined_params *p);
+
+/* Append one batch of confined daughters (as ttcf_spawn_daughters, Eq. 3):
+ *  n_atoms       N (4 <= N <= 12288, limited by shared memory)
+ *  box           [3] Lx, Ly, Lz: x and z periodic (each >= 3 (r_c + skin));
+ *                Ly is the extent of the slab profile (walls inside it)
+ *  types         [N] 0 fluid, 1 bottom wall, 2 top wall (>= 1 wall atom)
+ *  lattice       [3][N] tether sites at t = 0 (rows of fluid atoms unused)
+ *  params        potential, tether and channel width; NULL = defaults
+ *  mother_soa    [n_mothers][6][N] float64 phase points (x y z px py pz)
+ *  mother_alpha  [n_mothers] wall thermostat multipliers, or NULL (zeros)
+ *  shear_rates   [n_mothers] gamma of each group (v = gamma h / 2)
+ *  ptr_is_device 1 if the five arrays are device pointers, else host
+ * Computes, in IEEE double, Omega(0) and the TTCF_CONF_NOBS responses at
+ * t = 0 of each mapped daughter.  The mappings reflect x (with the tether
+ * sites) and the momenta as in Eq. 3.  Errors: TTCF_E_INVALID (also for a
+ * TTCF_BULK_WCA context), TTCF_E_OOM, TTCF_E_CUDA, TTCF_E_STATE.            */
+ttcf_status ttcf_spawn_confined(ttcf_ctx *ctx, int n_atoms, const double box[3], const int *types,
+                                const double *lattice, const ttcf_confined_params *params,
+                                int n_mothers, const double *mother_soa,
+                                const double *mother_alpha, const double *shear_rates,
+                                int ptr_is_device, int *batch_id);
+
+/* Equilibrium mothers of the confined system on the GPU (lattice at rest):
+ * from each of n_init initial phase points [n_init][6][N] (host), n_eq
+ * steps, then n_states phase points `spacing` steps apart (x, z wrapped).
+ * The thermostat starts from alpha = 0.  out_soa [n_init][n_states][6][N]
+ * and out_alpha [n_init][n_states] are host arrays.                       */
+ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const double box[3],
+                                         const int *types, const double *lattice,
+                                         const ttcf_confined_params *params, int n_init,
+                                         const double *init_soa, int n_eq, int n_states,
+                                         int spacing, double *out_soa, double *out_alpha);
+
+/* ttcf_response for response `observable` of a batch (0 for the bulk
+ * system's P_xy; 0 .. TTCF_CONF_NOBS-1 for the confined system).          */
+ttcf_status ttcf_response_obs(ttcf_ctx *ctx, int batch_id, int observable, int corrected,
+                              double *t, double *dav, double *dav_se, double *corr,
+                              double *corr_se, double *ttcf, double *ttcf_se, int capacity,
+                              int *n_samples);
 
 /* Spawn and run one small batch of daughters without allocating memory.
  *

@@ -10,6 +10,7 @@
 #include <thread>
 #include <vector>
 
+#include "ttcf_confined.h"
 #include "ttcf_cv.h"
 #include "ttcf_internal.h"
 
@@ -23,6 +24,8 @@ thread_local std::string g_create_error;
 
 struct BatchHost {
     int N = 0, M = 0, G = 0, S = 0;
+    int n_obs = 1;                        // observables per sample
+    bool confined = false;                // Example 2 batch (ttcf_confined.cu)
     int maps[4] = {0, 0, 0, 0};
     double L[3] = {0, 0, 0};
     double V = 0, Q = 0, gT = 0;
@@ -40,6 +43,10 @@ struct BatchHost {
     double *scal = nullptr;
     unsigned long long *state = nullptr;
     double *feat = nullptr;
+    // confined system
+    int *types = nullptr;
+    double *lattice = nullptr;
+    double A = 0, rc = 0, k_tether = 0, c_ff = 0, c_wf = 0, half_h = 0;
     // reduction
     bool reduced = false;
     double *Y = nullptr, *Dg = nullptr, *J = nullptr, *Og = nullptr, *valid = nullptr, *out = nullptr;
@@ -148,7 +155,6 @@ struct Pool {
     }
 };
 
-int popcount4(unsigned m) { int k = 0; for (int i = 0; i < 4; i++) k += (m >> i) & 1; return k; }
 
 // Launch variant, block size and Verlet skin for a daughter of N atoms:
 // explicit configuration first, then the autotuner's result for this N,
@@ -480,12 +486,12 @@ ttcf_status wait_with_timeout(ttcf_ctx *ctx, cudaEvent_t ev) {
 ttcf_status ensure_reduce_buffers(ttcf_ctx *ctx, BatchHost &b) {
     if (b.out) return TTCF_OK;
     Pool p(ctx);
-    b.Y = p.get<double>((size_t)b.G * b.S);
-    b.Dg = p.get<double>((size_t)b.G * b.S);
-    b.J = p.get<double>((size_t)b.G * b.S);
+    b.Y = p.get<double>((size_t)b.n_obs * b.G * b.S);
+    b.Dg = p.get<double>((size_t)b.n_obs * b.G * b.S);
+    b.J = p.get<double>((size_t)b.n_obs * b.G * b.S);
     b.Og = p.get<double>(b.G);
     b.valid = p.get<double>(b.G);
-    b.out = p.get<double>((size_t)9 * b.S);
+    b.out = p.get<double>((size_t)9 * b.n_obs * b.S);
     if (p.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (reduction)");
     p.keep();
     return TTCF_OK;
@@ -496,7 +502,7 @@ ttcf_status reduce_batch(ttcf_ctx *ctx, BatchHost &b) {
     ttcf_status rs = ensure_reduce_buffers(ctx, b);
     if (rs != TTCF_OK) return rs;
     ReduceArgs r;
-    r.M = b.M; r.G = b.G; r.S = b.S;
+    r.M = b.M; r.G = b.G; r.S = b.S; r.n_obs = b.n_obs;
     r.B = b.B; r.Omega = b.Omega; r.status = b.status;
     r.ds = ctx->cfg.sample_every * ctx->cfg.dt;
     r.Y = b.Y; r.Dg = b.Dg; r.J = b.J; r.Og = b.Og; r.valid = b.valid; r.out = b.out;
@@ -514,6 +520,272 @@ namespace {
 BatchHost *get_batch(ttcf_ctx *ctx, int id) {
     if (!ctx || id < 0 || id >= (int)ctx->batches.size()) return nullptr;
     return &ctx->batches[id];
+}
+
+}  // namespace
+
+// ======================================================= confined system ==
+namespace {
+
+// Cells of the confined list build: the finest width in {r_l/2, 2r_l/3, r_l}
+// whose shared memory still fits one CTA (one daughter per SM).
+bool conf_pick_cells(ttcf_ctx *ctx, BatchHost &b, double rl) {
+    const double fracs[3] = {0.5, 2.0 / 3.0, 1.0};
+    for (int f = 0; f < 3; f++) {
+        int nc[3];
+        for (int k = 0; k < 3; k++) nc[k] = std::max(1, (int)floor(b.L[k] / (rl * fracs[f])));
+        const int ncell = nc[0] * nc[1] * nc[2];
+        if (conf_smem_bytes(b.N, ncell) <= (size_t)ctx->smem_optin) {
+            for (int k = 0; k < 3; k++) b.nc[k] = nc[k];
+            b.ncell = ncell;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Allocate a confined batch, copy its inputs and run the spawn kernel.
+ttcf_status make_conf_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const double box[3],
+                            const int *types, const double *lattice,
+                            const ttcf_confined_params &p, int G, const double *soa,
+                            const double *alpha, const double *gamma, int is_dev,
+                            const int *maps, int M, int S) {
+    const ttcf_config &cf = ctx->cfg;
+    if (N < 4 || N > CONF_NMAX) return fail(ctx, TTCF_E_INVALID, "n_atoms must be in [4, 12288]");
+    if (G <= 0) return fail(ctx, TTCF_E_INVALID, "n_mothers must be positive");
+    if (!soa || !types || !lattice) return fail(ctx, TTCF_E_INVALID, "NULL array");
+    if (!(p.rc > 0) || !(p.k >= 0) || !(p.h > 0) || !isfinite(p.rc) || !isfinite(p.k) ||
+        !isfinite(p.h) || !isfinite(p.c_ff) || !isfinite(p.c_wf))
+        return fail(ctx, TTCF_E_INVALID, "bad confined parameters");
+    b.confined = true;
+    b.n_obs = CONF_NOBS;
+    b.skin = cf.skin > 0 ? cf.skin : DEFAULT_SKIN;
+    const double rl = p.rc + b.skin;
+    for (int k = 0; k < 3; k++)
+        if (!(box[k] > 0) || !isfinite(box[k])) return fail(ctx, TTCF_E_INVALID, "box edges must be positive");
+    if (box[0] < 3.0 * rl || box[2] < 3.0 * rl)
+        return fail(ctx, TTCF_E_INVALID, "Lx and Lz must be >= 3*(r_c+skin)");
+    b.N = N; b.G = G; b.M = M; b.S = S;
+    for (int k = 0; k < M; k++) b.maps[k] = maps[k];
+    for (int k = 0; k < 3; k++) b.L[k] = box[k];
+    b.V = box[0] * box[1] * box[2];
+    b.A = box[0] * box[2];
+    b.rc = p.rc; b.k_tether = p.k; b.c_ff = p.c_ff; b.c_wf = p.c_wf; b.half_h = 0.5 * p.h;
+    if (!conf_pick_cells(ctx, b, rl))
+        return fail(ctx, TTCF_E_INVALID, "n_atoms too large for one CTA's shared memory");
+    for (int k = 0; k < 3; k++) b.snc[k] = std::max(1, (int)floor(box[k] / p.rc));
+    b.sncell = b.snc[0] * b.snc[1] * b.snc[2];
+    if (conf_spawn_smem_bytes(N, b.sncell) > (size_t)ctx->smem_optin)
+        return fail(ctx, TTCF_E_INVALID, "too many spawn cells");
+
+    // host copies: types (wall count), gamma, alpha
+    std::vector<int> types_h(N);
+    b.gamma.resize(G);
+    std::vector<double> alpha_h(G, 0.0);
+    if (is_dev) {
+        CK(cudaMemcpy(types_h.data(), types, sizeof(int) * N, cudaMemcpyDeviceToHost));
+        if (gamma) CK(cudaMemcpy(b.gamma.data(), gamma, sizeof(double) * G, cudaMemcpyDeviceToHost));
+        else std::fill(b.gamma.begin(), b.gamma.end(), 0.0);
+        if (alpha) CK(cudaMemcpy(alpha_h.data(), alpha, sizeof(double) * G, cudaMemcpyDeviceToHost));
+    } else {
+        std::copy(types, types + N, types_h.begin());
+        for (int k = 0; k < G; k++) b.gamma[k] = gamma ? gamma[k] : 0.0;
+        if (alpha) for (int k = 0; k < G; k++) alpha_h[k] = alpha[k];
+    }
+    int n_wall = 0;
+    for (int t : types_h) {
+        if (t < 0 || t > 2) return fail(ctx, TTCF_E_INVALID, "types must be 0, 1 or 2");
+        n_wall += t != 0;
+    }
+    if (n_wall == 0) return fail(ctx, TTCF_E_INVALID, "no wall atoms");
+    for (int k = 0; k < G; k++)
+        if (!isfinite(b.gamma[k]) || !isfinite(alpha_h[k]))
+            return fail(ctx, TTCF_E_INVALID, "non-finite shear rate or alpha");
+    const double g = 3.0 * n_wall;
+    b.Q = g * cf.T * cf.tau_T * cf.tau_T;
+    b.gT = g * cf.T;
+
+    const long long D = b.D();
+    const size_t slots = (size_t)G * 6 * N;
+    b.mothers = pool.get<unsigned long long>(slots);
+    b.m_alpha = pool.get<double>(G);
+    b.gamma_d = pool.get<double>(G);
+    b.B = pool.get<double>((size_t)D * b.n_obs * S);
+    b.Omega = pool.get<double>(D);
+    b.status = pool.get<int>(D);
+    b.pairs = pool.get<unsigned long long>(D);
+    b.rebuilds = pool.get<unsigned int>(D);
+    b.types = pool.get<int>(N);
+    b.lattice = pool.get<double>((size_t)3 * N);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (batch)");
+    cudaStream_t st = ctx->st;
+    const cudaMemcpyKind kind = is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(b.m_alpha, alpha_h.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b.gamma_d, b.gamma.data(), sizeof(double) * G, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b.types, types_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b.lattice, lattice, sizeof(double) * 3 * N, kind, st));
+    CK(cudaMemsetAsync(b.B, 0, sizeof(double) * D * b.n_obs * S, st));
+    CK(cudaMemsetAsync(b.status, 0, sizeof(int) * D, st));
+    CK(cudaMemsetAsync(b.pairs, 0, sizeof(unsigned long long) * D, st));
+    CK(cudaMemsetAsync(b.rebuilds, 0, sizeof(unsigned int) * D, st));
+
+    Pool tmp(ctx);
+    const double *src = soa;
+    if (!is_dev) {
+        double *s = tmp.get<double>(slots);
+        if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (mother copy)");
+        CK(cudaMemcpyAsync(s, soa, sizeof(double) * slots, cudaMemcpyHostToDevice, st));
+        src = s;
+    }
+    ConfSpawnArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.N = N; sa.M = M; sa.G = G; sa.S = S; sa.n_obs = b.n_obs;
+    for (int k = 0; k < 4; k++) sa.maps[k] = b.maps[k];
+    for (int k = 0; k < 3; k++) { sa.nc[k] = b.snc[k]; sa.L[k] = b.L[k]; }
+    sa.ncell = b.sncell;
+    sa.A = b.A; sa.Tw = cf.T; sa.rc = b.rc; sa.k = b.k_tether; sa.c_wf = b.c_wf; sa.half_h = b.half_h;
+    sa.src = src; sa.gamma = b.gamma_d; sa.types = b.types; sa.lattice = b.lattice;
+    sa.mothers = b.mothers; sa.B = b.B; sa.Omega = b.Omega;
+    CK(launch_conf_spawn(sa, st));
+    CK(cudaStreamSynchronize(st));   // before the temporary copy is released
+    return TTCF_OK;
+}
+
+ConfBatchDev conf_to_dev(const BatchHost &b) {
+    ConfBatchDev d;
+    memset(&d, 0, sizeof(d));
+    d.N = b.N; d.M = b.M; d.G = b.G; d.S = b.S; d.n_obs = b.n_obs;
+    for (int k = 0; k < 4; k++) d.maps[k] = b.maps[k];
+    for (int k = 0; k < 3; k++) { d.nc[k] = b.nc[k]; d.L[k] = b.L[k]; }
+    d.ncell = b.ncell;
+    d.A = b.A; d.Q = b.Q; d.gT = b.gT;
+    d.rc = b.rc; d.k = b.k_tether; d.c_ff = b.c_ff; d.c_wf = b.c_wf; d.half_h = b.half_h;
+    d.skin = (float)b.skin;
+    d.d0 = b.d0;
+    d.mothers = b.mothers; d.m_alpha = b.m_alpha; d.gamma = b.gamma_d;
+    d.types = b.types; d.lattice = b.lattice;
+    d.B = b.B; d.Omega = b.Omega; d.status = b.status; d.pairs = b.pairs; d.rebuilds = b.rebuilds;
+    return d;
+}
+
+// One persistent launch over every daughter of the given confined batches
+// (one CTA per SM, work queue), timed by ev0/ev1 on the context's stream.
+ttcf_status launch_conf_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &bs,
+                                ConfRunArgs proto, int &launches, cudaEvent_t ev0 = nullptr,
+                                cudaEvent_t ev1 = nullptr) {
+    long long dmax = 0;
+    int nmax = 0, ncellmax = 0;
+    std::vector<ConfBatchDev> hb;
+    for (BatchHost *b : bs) {
+        dmax = std::max(dmax, b->d0 + b->D());
+        nmax = std::max(nmax, b->N);
+        ncellmax = std::max(ncellmax, b->ncell);
+        hb.push_back(conf_to_dev(*b));
+    }
+    std::vector<int> dbatch((size_t)dmax, 0), work;
+    for (size_t k = 0; k < bs.size(); k++)
+        for (long long d = 0; d < bs[k]->D(); d++) {
+            dbatch[(size_t)(bs[k]->d0 + d)] = (int)k;
+            work.push_back((int)(bs[k]->d0 + d));
+        }
+    const size_t smem = conf_smem_bytes(nmax, ncellmax);
+    if (smem > (size_t)ctx->smem_optin)
+        return fail(ctx, TTCF_E_INVALID, "confined batches need more shared memory than a CTA has");
+    const int grid = (int)std::max<long long>(1, std::min<long long>((long long)work.size(), ctx->nsm));
+    ConfBatchDev *d_b = pool.get<ConfBatchDev>(hb.size());
+    int *d_db = pool.get<int>(dbatch.size());
+    int *d_work = pool.get<int>(work.size());
+    int *d_q = pool.get<int>(1);
+    float4 *scratch = pool.get<float4>((size_t)grid * CONF_SCRATCH_F4 * nmax);
+    unsigned short *nbr = pool.get<unsigned short>((size_t)grid * CONF_CAP * nmax);
+    int *ncnt = pool.get<int>((size_t)grid * nmax);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (confined tables)");
+    cudaStream_t st = ctx->st;
+    CK(cudaMemcpyAsync(d_b, hb.data(), sizeof(ConfBatchDev) * hb.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_db, dbatch.data(), sizeof(int) * dbatch.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_q, 0, sizeof(int), st));
+    ConfRunArgs a = proto;
+    a.batches = d_b; a.dbatch = d_db; a.work = d_work; a.n_work = (int)work.size();
+    a.queue = d_q; a.scratch = scratch; a.nbr = nbr; a.ncnt = ncnt;
+    a.nmax = nmax; a.ncellmax = ncellmax;
+    if (ev0) CK(cudaEventRecord(ev0, st));
+    CK(launch_confined(a, grid, smem, st));
+    launches++;
+    if (ev1) CK(cudaEventRecord(ev1, st));
+    ctx->stats.block_threads = CONF_THREADS;
+    return TTCF_OK;
+}
+
+ttcf_status run_confined(ttcf_ctx *ctx, int n_steps) {
+    const ttcf_config &cf = ctx->cfg;
+    if (ctx->steps_done >= cf.n_steps) return TTCF_OK;
+    if (n_steps > 0 && n_steps < cf.n_steps)
+        return fail(ctx, TTCF_E_INVALID, "confined daughters run all n_steps in one ttcf_run");
+    ctx->ran = true;
+    *(volatile int *)ctx->h_abort = 0;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    for (auto &b : ctx->batches) {
+        ttcf_status r = ensure_reduce_buffers(ctx, b);
+        if (r != TTCF_OK) return r;
+    }
+    ConfRunArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n_steps = cf.n_steps;
+    a.sample_every = cf.sample_every;
+    a.reset_alpha = cf.reset_alpha;
+    a.dt = cf.dt;
+    a.abort_flag = ctx->d_abort;
+    std::vector<BatchHost *> bs;
+    for (auto &b : ctx->batches) bs.push_back(&b);
+    Pool pool(ctx);
+    int launches = 0;
+    ttcf_status s = launch_conf_batches(ctx, pool, bs, a, launches, ctx->ev[0], ctx->ev[1]);
+    if (s != TTCF_OK) return s;
+    CK(cudaEventRecord(ctx->ev[2], ctx->st));
+    for (auto &b : ctx->batches) {
+        b.reduced = false;
+        s = reduce_batch(ctx, b);
+        if (s != TTCF_OK) return s;
+        launches += 3;
+    }
+    CK(cudaEventRecord(ctx->ev[3], ctx->st));
+    s = wait_with_timeout(ctx, ctx->ev[3]);
+    if (s != TTCF_OK && s != TTCF_E_TIMEOUT) return s;
+    const bool timed_out = s == TTCF_E_TIMEOUT;
+    float ms = 0.f, msr = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&msr, ctx->ev[2], ctx->ev[3]);
+    ctx->stats.ms_run = ms;
+    ctx->stats.ms_reduce = msr;
+    ctx->stats.skin = ctx->batches[0].skin;
+    ctx->steps_done = cf.n_steps;
+    bool any_fail = false;
+    for (auto &b : ctx->batches) {
+        std::vector<int> stv(b.D());
+        std::vector<unsigned long long> pr(b.D());
+        std::vector<unsigned int> rb(b.D());
+        CK(cudaMemcpy(stv.data(), b.status, sizeof(int) * b.D(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(pr.data(), b.pairs, sizeof(unsigned long long) * b.D(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(rb.data(), b.rebuilds, sizeof(unsigned int) * b.D(), cudaMemcpyDeviceToHost));
+        for (long long d = 0; d < b.D(); d++) {
+            any_fail |= stv[d] != 0;
+            ctx->stats.pairs_interacting += (double)pr[d];
+            ctx->stats.rebuilds += (double)rb[d];
+        }
+        ctx->stats.atom_steps += (double)b.D() * b.N * cf.n_steps;
+    }
+    ctx->stats.launches = launches;
+    if (timed_out) return fail(ctx, TTCF_E_TIMEOUT, "ttcf_run exceeded timeout_s; daughters aborted");
+    if (any_fail) return fail(ctx, TTCF_E_NUMERIC, "some daughters failed; see ttcf_group_status");
+    return TTCF_OK;
+}
+
+ttcf_confined_params conf_params_or_default(const ttcf_confined_params *p) {
+    ttcf_confined_params q;
+    if (p) return *p;
+    q.k = 150.0; q.rc = 2.5; q.c_ff = 1.2; q.c_wf = 0.6325; q.h = 10.0;
+    return q;
 }
 
 }  // namespace
@@ -552,7 +824,10 @@ ttcf_status ttcf_create(const ttcf_config *cfg, ttcf_ctx **out) {
     if (!cfg || !out) return fail(nullptr, TTCF_E_INVALID, "NULL argument");
     *out = nullptr;
     const ttcf_config &c = *cfg;
-    if (c.system != TTCF_BULK_WCA) return fail(nullptr, TTCF_E_INVALID, "unknown system");
+    if (c.system != TTCF_BULK_WCA && c.system != TTCF_CONFINED_LJ)
+        return fail(nullptr, TTCF_E_INVALID, "unknown system");
+    if (c.system == TTCF_CONFINED_LJ && c.precision != TTCF_MIXED)
+        return fail(nullptr, TTCF_E_INVALID, "the confined system runs in TTCF_MIXED precision only");
     if (c.precision != TTCF_FP64 && c.precision != TTCF_MIXED)
         return fail(nullptr, TTCF_E_INVALID, "precision must be TTCF_FP64 or TTCF_MIXED");
     if (!(c.dt > 0) || !(c.T > 0) || !(c.tau_T > 0))
@@ -607,6 +882,8 @@ ttcf_status ttcf_spawn_daughters(ttcf_ctx *ctx, int n_atoms, const double box[3]
                                  const double *mother_soa, const double *mother_alpha,
                                  const double *shear_rates, int ptr_is_device, int *batch_id) {
     if (!ctx || !box) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (ctx->cfg.system != TTCF_BULK_WCA)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_spawn_daughters needs a TTCF_BULK_WCA context");
     if (ctx->ran) return fail(ctx, TTCF_E_STATE, "ttcf_spawn_daughters after ttcf_run");
     int maps[4], M = 0;
     for (int m = 0; m < 4; m++) if (ctx->cfg.mapping_mask & (1u << m)) maps[M++] = m;
@@ -629,6 +906,7 @@ ttcf_status ttcf_spawn_daughters(ttcf_ctx *ctx, int n_atoms, const double box[3]
 ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
     if (!ctx) return fail(ctx, TTCF_E_INVALID, "NULL context");
     if (ctx->batches.empty()) return fail(ctx, TTCF_E_STATE, "ttcf_run before ttcf_spawn_daughters");
+    if (ctx->cfg.system == TTCF_CONFINED_LJ) return run_confined(ctx, n_steps);
     const ttcf_config &cf = ctx->cfg;
     const int step0 = ctx->steps_done;
     if (step0 >= cf.n_steps) return TTCF_OK;
@@ -726,18 +1004,21 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
     return TTCF_OK;
 }
 
-ttcf_status ttcf_response(ttcf_ctx *ctx, int batch_id, int corrected, double *t, double *dav,
-                          double *dav_se, double *corr, double *corr_se, double *ttcf,
-                          double *ttcf_se, int capacity, int *n_samples) {
+ttcf_status ttcf_response_obs(ttcf_ctx *ctx, int batch_id, int observable, int corrected,
+                              double *t, double *dav, double *dav_se, double *corr,
+                              double *corr_se, double *ttcf, double *ttcf_se, int capacity,
+                              int *n_samples) {
     BatchHost *b = get_batch(ctx, batch_id);
     if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (observable < 0 || observable >= b->n_obs) return fail(ctx, TTCF_E_INVALID, "bad observable index");
     if (!b->reduced) return fail(ctx, TTCF_E_STATE, "run not finished");
     if (n_samples) *n_samples = b->S;
     if (capacity < b->S) return fail(ctx, TTCF_E_INVALID, "capacity smaller than the sample count");
-    std::vector<double> h((size_t)9 * b->S);
-    CK(cudaMemcpyAsync(h.data(), b->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
     const int S = b->S;
+    std::vector<double> h((size_t)9 * S);
+    CK(cudaMemcpyAsync(h.data(), b->out + (size_t)observable * 9 * S, sizeof(double) * h.size(),
+                       cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
     const double ds = ctx->cfg.sample_every * ctx->cfg.dt;
     for (int s = 0; s < S; s++) {
         if (t) t[s] = s * ds;
@@ -751,11 +1032,19 @@ ttcf_status ttcf_response(ttcf_ctx *ctx, int batch_id, int corrected, double *t,
     return TTCF_OK;
 }
 
+ttcf_status ttcf_response(ttcf_ctx *ctx, int batch_id, int corrected, double *t, double *dav,
+                          double *dav_se, double *corr, double *corr_se, double *ttcf,
+                          double *ttcf_se, int capacity, int *n_samples) {
+    return ttcf_response_obs(ctx, batch_id, 0, corrected, t, dav, dav_se, corr, corr_se, ttcf,
+                             ttcf_se, capacity, n_samples);
+}
+
 ttcf_status ttcf_viscosity(ttcf_ctx *ctx, int batch_id, double *t, double *eta_ttcf,
                            double *eta_ttcf_se, double *eta_dav, double *eta_dav_se, int capacity,
                            int *n_samples) {
     BatchHost *b = get_batch(ctx, batch_id);
     if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (b->confined) return fail(ctx, TTCF_E_INVALID, "viscosity of a confined batch is not defined");
     const double g = b->gamma.empty() ? 0.0 : b->gamma[0];
     for (double x : b->gamma)
         if (x != g) return fail(ctx, TTCF_E_INVALID, "shear rate differs between groups");
@@ -779,7 +1068,7 @@ ttcf_status ttcf_daughter_series(ttcf_ctx *ctx, int batch_id, double *B, double 
                                  size_t capacity_B) {
     BatchHost *b = get_batch(ctx, batch_id);
     if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
-    const size_t n = (size_t)b->D() * b->S;
+    const size_t n = (size_t)b->D() * b->n_obs * b->S;
     if (B && capacity_B < n) return fail(ctx, TTCF_E_INVALID, "capacity_B too small");
     CK(cudaStreamSynchronize(ctx->st));
     if (B) CK(cudaMemcpy(B, b->B, sizeof(double) * n, cudaMemcpyDeviceToHost));
@@ -853,6 +1142,8 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
                                 const double *init_soa, int n_eq, int n_states, int spacing,
                                 double *out_soa, double *out_alpha) {
     if (!ctx || !box || !init_soa || !out_soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (ctx->cfg.system != TTCF_BULK_WCA)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_sample_mothers needs a TTCF_BULK_WCA context");
     if (n_eq < 0 || n_states < 1 || spacing < 1) return fail(ctx, TTCF_E_INVALID, "bad sampling schedule");
     const long long total = (long long)n_eq + (long long)n_states * spacing;
     if (total > 2000000000LL) return fail(ctx, TTCF_E_INVALID, "trajectory too long");
@@ -894,6 +1185,8 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
 ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
                         double delta, const double *soa, double *F, double *W, double *U) {
     if (!ctx || !box || !soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (ctx->cfg.system != TTCF_BULK_WCA)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_forces needs a TTCF_BULK_WCA context");
     const int maps[1] = {0};
     BatchHost b;
     Pool pool(ctx);
@@ -936,6 +1229,8 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
                           double *best_skin, double *best_ms) {
     if (!ctx || !box || !soa || n_states < 1 || n_steps < 1)
         return fail(ctx, TTCF_E_INVALID, "bad autotune arguments");
+    if (ctx->cfg.system != TTCF_BULK_WCA)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_autotune needs a TTCF_BULK_WCA context");
     const double skins[4] = {0.3, 0.4, 0.5, 0.6};
     const int maps[4] = {0, 1, 2, 3};
     std::vector<double> gam(n_states, shear_rate);
@@ -985,6 +1280,84 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
 }
 
 
+void ttcf_confined_params_default(ttcf_confined_params *p) {
+    if (p) *p = conf_params_or_default(nullptr);
+}
+
+ttcf_status ttcf_spawn_confined(ttcf_ctx *ctx, int n_atoms, const double box[3], const int *types,
+                                const double *lattice, const ttcf_confined_params *params,
+                                int n_mothers, const double *mother_soa,
+                                const double *mother_alpha, const double *shear_rates,
+                                int ptr_is_device, int *batch_id) {
+    if (!ctx || !box) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (ctx->cfg.system != TTCF_CONFINED_LJ)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_spawn_confined needs a TTCF_CONFINED_LJ context");
+    if (ctx->ran) return fail(ctx, TTCF_E_STATE, "ttcf_spawn_confined after ttcf_run");
+    int maps[4], M = 0;
+    for (int m = 0; m < 4; m++) if (ctx->cfg.mapping_mask & (1u << m)) maps[M++] = m;
+    const int S = ctx->cfg.n_steps / ctx->cfg.sample_every + 1;
+    BatchHost b;
+    Pool pool(ctx);
+    ttcf_status s = make_conf_batch(ctx, pool, b, n_atoms, box, types, lattice,
+                                    conf_params_or_default(params), n_mothers, mother_soa,
+                                    mother_alpha, shear_rates, ptr_is_device, maps, M, S);
+    if (s != TTCF_OK) return s;
+    if (ctx->total_d + b.D() > 2000000000LL) return fail(ctx, TTCF_E_INVALID, "too many daughters");
+    b.d0 = ctx->total_d;
+    ctx->total_d += b.D();
+    pool.keep();
+    ctx->batches.push_back(b);
+    if (batch_id) *batch_id = (int)ctx->batches.size() - 1;
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const double box[3],
+                                         const int *types, const double *lattice,
+                                         const ttcf_confined_params *params, int n_init,
+                                         const double *init_soa, int n_eq, int n_states,
+                                         int spacing, double *out_soa, double *out_alpha) {
+    if (!ctx || !box || !init_soa || !out_soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (ctx->cfg.system != TTCF_CONFINED_LJ)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_sample_mothers_confined needs a TTCF_CONFINED_LJ context");
+    if (n_eq < 0 || n_states < 1 || spacing < 1) return fail(ctx, TTCF_E_INVALID, "bad sampling schedule");
+    const long long total = (long long)n_eq + (long long)n_states * spacing;
+    if (total > 2000000000LL) return fail(ctx, TTCF_E_INVALID, "trajectory too long");
+    const int maps[1] = {0};
+    BatchHost b;
+    Pool pool(ctx);
+    ttcf_status s = make_conf_batch(ctx, pool, b, n_atoms, box, types, lattice,
+                                    conf_params_or_default(params), n_init, init_soa, nullptr,
+                                    nullptr, 0, maps, 1, 1);
+    if (s != TTCF_OK) return s;
+    b.d0 = 0;
+    const int N = n_atoms;
+    double *snap = pool.get<double>((size_t)n_init * n_states * 6 * N);
+    double *snap_a = pool.get<double>((size_t)n_init * n_states);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (mother snapshots)");
+    ConfRunArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n_steps = (int)total;
+    a.sample_every = (int)total + 1;
+    a.reset_alpha = 1;
+    a.dt = ctx->cfg.dt;
+    a.snap = snap; a.snap_alpha = snap_a;
+    a.snap_first = n_eq + spacing; a.snap_every = spacing; a.n_snap = n_states;
+    std::vector<BatchHost *> bs = {&b};
+    int launches = 0;
+    s = launch_conf_batches(ctx, pool, bs, a, launches);
+    if (s != TTCF_OK) return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<int> stv(b.D());
+    CK(cudaMemcpy(stv.data(), b.status, sizeof(int) * b.D(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out_soa, snap, sizeof(double) * (size_t)n_init * n_states * 6 * N, cudaMemcpyDeviceToHost));
+    if (out_alpha)
+        CK(cudaMemcpy(out_alpha, snap_a, sizeof(double) * (size_t)n_init * n_states, cudaMemcpyDeviceToHost));
+    for (int v : stv)
+        if (v) return fail(ctx, TTCF_E_NUMERIC, "a mother trajectory failed");
+    return TTCF_OK;
+}
+
+
 // ======================================================= control variate ==
 namespace {
 
@@ -1000,6 +1373,7 @@ bool batch_finished(ttcf_ctx *ctx, BatchHost *b) { return b && b->reduced; }
 
 // Features X [D][32] (device, unstandardised) and targets z [D] (device).
 ttcf_status cv_batch_data(ttcf_ctx *ctx, Pool &pool, BatchHost &b, float *&X, double *&z) {
+    if (b.confined || !b.feat) return fail(ctx, TTCF_E_INVALID, "the control variate needs a bulk batch");
     const long long D = b.D();
     X = pool.get<float>((size_t)D * CV_NF);
     z = pool.get<double>((size_t)D);

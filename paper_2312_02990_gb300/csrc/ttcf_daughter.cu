@@ -144,22 +144,6 @@ __device__ __forceinline__ void cta_sum3(R a0, R a1, R a2, Misc *m, double out[3
     }
 }
 
-// exp(x) - 1 for the small arguments -alpha h/2 (Taylor to x^7 when
-// |x| < 1e-2: truncation below 1e-18 relative), else the library routine.
-__device__ __forceinline__ double expm1_small(double x) {
-    if (fabs(x) < 1e-2) {
-        double t = 1.0 / 5040.0;
-        t = t * x + 1.0 / 720.0;
-        t = t * x + 1.0 / 120.0;
-        t = t * x + 1.0 / 24.0;
-        t = t * x + 1.0 / 6.0;
-        t = t * x + 0.5;
-        t = t * x + 1.0;
-        return t * x;
-    }
-    return expm1(x);
-}
-
 // ------------------------------------------------------- one daughter --
 template <bool MIXED, int APT>
 __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned char *smem) {

@@ -97,6 +97,22 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// exp(x) - 1 for the small arguments -alpha h/2 (Taylor to x^7 when
+// |x| < 1e-2: truncation below 1e-18 relative), else the library routine.
+__device__ __forceinline__ double expm1_small(double x) {
+    if (fabs(x) < 1e-2) {
+        double t = 1.0 / 5040.0;
+        t = t * x + 1.0 / 720.0;
+        t = t * x + 1.0 / 120.0;
+        t = t * x + 1.0 / 24.0;
+        t = t * x + 1.0 / 6.0;
+        t = t * x + 0.5;
+        t = t * x + 1.0;
+        return t * x;
+    }
+    return expm1(x);
+}
+
 // ----------------------------------------------------- warp/CTA helpers --
 __device__ __forceinline__ int warp_incl_scan(int v) {
     const int lane = threadIdx.x & 31;

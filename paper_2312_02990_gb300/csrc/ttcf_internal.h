@@ -44,15 +44,16 @@ size_t spawn_smem_bytes(int N, int ncell);
 // reduction (ttcf_reduce.cu): fixed-order ensemble averages of one batch.
 struct ReduceArgs {
     int M, G, S;
-    const double *B;           // [G*M][S]
+    int n_obs;                 // observables per sample (1 for the bulk P_xy)
+    const double *B;           // [G*M][n_obs][S]
     const double *Omega;       // [G*M]
     const int *status;         // [G*M]
     double ds;                 // sample spacing in time
-    double *Y, *Dg, *J;        // [G][S] work arrays
+    double *Y, *Dg, *J;        // [n_obs][G][S] work arrays
     double *Og;                // [G]
     double *valid;             // [G] 1 if every daughter of the group is OK
-    double *out;               // [9][S]: corr, corr_se, dav, dav_se, ttcf,
-                               //         ttcf_se, corr_c, ttcf_c, n_valid
+    double *out;               // [n_obs][9][S]: corr, corr_se, dav, dav_se,
+                               //   ttcf, ttcf_se, corr_c, ttcf_c, n_valid
 };
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 

@@ -18,19 +18,20 @@ namespace ttcf {
 // pass 1: one CTA per group, threads over samples
 __global__ void reduce_groups_kernel(ReduceArgs a) {
     __shared__ double wtmp[32];
-    const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
-    const int M = a.M, S = a.S;
+    const int g = blockIdx.x, o = blockIdx.y, tid = threadIdx.x, T = blockDim.x;
+    const int M = a.M, S = a.S, K = a.n_obs;
     const size_t d0 = (size_t)g * M;
     int ok = 1;
     for (int k = 0; k < M; k++) ok &= (a.status[d0 + k] == 0);
     double om[4];
     for (int k = 0; k < M; k++) om[k] = a.Omega[d0 + k];
-    double *Y = a.Y + (size_t)g * S, *D = a.Dg + (size_t)g * S, *J = a.J + (size_t)g * S;
+    const size_t w0 = ((size_t)o * a.G + g) * S;
+    double *Y = a.Y + w0, *D = a.Dg + w0, *J = a.J + w0;
     const double invM = 1.0 / M;
     for (int s = tid; s < S; s += T) {
         double y = 0.0, dsum = 0.0;
         for (int k = 0; k < M; k++) {
-            const double bv = a.B[(d0 + k) * S + s];
+            const double bv = a.B[((d0 + k) * K + o) * S + s];
             y += om[k] * bv;
             dsum += bv;
         }
@@ -58,10 +59,10 @@ __global__ void reduce_groups_kernel(ReduceArgs a) {
         if (s >= 1) run += 0.5 * a.ds * (Y[s - 1] + Y[s]);
         J[s] = run;
     }
-    if (tid == 0) {
-        double o = 0.0;
-        for (int k = 0; k < M; k++) o += om[k];
-        a.Og[g] = o * invM;
+    if (tid == 0 && o == 0) {
+        double os = 0.0;
+        for (int k = 0; k < M; k++) os += om[k];
+        a.Og[g] = os * invM;
         a.valid[g] = ok ? 1.0 : 0.0;
     }
 }
@@ -70,40 +71,43 @@ __global__ void reduce_groups_kernel(ReduceArgs a) {
 __global__ void reduce_samples_kernel(ReduceArgs a) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.S) return;
-    const int G = a.G, S = a.S;
+    const int G = a.G, S = a.S, o = blockIdx.y;
+    const double *Yb = a.Y + (size_t)o * G * S, *Db = a.Dg + (size_t)o * G * S, *Jb = a.J + (size_t)o * G * S;
+    double *out = a.out + (size_t)o * 9 * S;
     double n = 0.0, sy = 0.0, sd = 0.0, sj = 0.0;
     for (int g = 0; g < G; g++) {
         const double v = a.valid[g];
         if (v == 0.0) continue;
         n += 1.0;
-        sy += a.Y[(size_t)g * S + s]; sd += a.Dg[(size_t)g * S + s]; sj += a.J[(size_t)g * S + s];
+        sy += Yb[(size_t)g * S + s]; sd += Db[(size_t)g * S + s]; sj += Jb[(size_t)g * S + s];
     }
     const double my = sy / n, md = sd / n, mj = sj / n;
     double vy = 0.0, vd = 0.0, vj = 0.0;
     for (int g = 0; g < G; g++) {
         if (a.valid[g] == 0.0) continue;
-        const double ey = a.Y[(size_t)g * S + s] - my;
-        const double ed = a.Dg[(size_t)g * S + s] - md;
-        const double ej = a.J[(size_t)g * S + s] - mj;
+        const double ey = Yb[(size_t)g * S + s] - my;
+        const double ed = Db[(size_t)g * S + s] - md;
+        const double ej = Jb[(size_t)g * S + s] - mj;
         vy += ey * ey; vd += ed * ed; vj += ej * ej;
     }
     const double se = n > 1.0 ? 1.0 / sqrt(n * (n - 1.0)) : NAN;
-    a.out[0 * S + s] = my; a.out[1 * S + s] = sqrt(vy) * se;
-    a.out[2 * S + s] = md; a.out[3 * S + s] = sqrt(vd) * se;
-    a.out[4 * S + s] = mj; a.out[5 * S + s] = sqrt(vj) * se;
-    a.out[8 * S + s] = n;
+    out[0 * S + s] = my; out[1 * S + s] = sqrt(vy) * se;
+    out[2 * S + s] = md; out[3 * S + s] = sqrt(vd) * se;
+    out[4 * S + s] = mj; out[5 * S + s] = sqrt(vj) * se;
+    out[8 * S + s] = n;
 }
 
 // pass 3: <Omega(0)> and the Eq. 4 form (one thread, sequential)
 __global__ void reduce_correct_kernel(ReduceArgs a) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int S = a.S;
+    if (threadIdx.x != 0) return;
+    const int S = a.S, o = blockIdx.x;
     double n = 0.0, so = 0.0;
     for (int g = 0; g < a.G; g++)
         if (a.valid[g] != 0.0) { n += 1.0; so += a.Og[g]; }
     const double om = so / n;
-    const double *corr = a.out, *dav = a.out + 2 * S;
-    double *cc = a.out + 6 * S, *tc = a.out + 7 * S;
+    double *out = a.out + (size_t)o * 9 * S;
+    const double *corr = out, *dav = out + 2 * S;
+    double *cc = out + 6 * S, *tc = out + 7 * S;
     double run = dav[0];
     for (int s = 0; s < S; s++) {
         cc[s] = corr[s] - om * dav[s];
@@ -113,9 +117,9 @@ __global__ void reduce_correct_kernel(ReduceArgs a) {
 }
 
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st) {
-    reduce_groups_kernel<<<a.G, 256, 0, st>>>(a);
-    reduce_samples_kernel<<<(a.S + 127) / 128, 128, 0, st>>>(a);
-    reduce_correct_kernel<<<1, 32, 0, st>>>(a);
+    reduce_groups_kernel<<<dim3(a.G, a.n_obs), 256, 0, st>>>(a);
+    reduce_samples_kernel<<<dim3((a.S + 127) / 128, a.n_obs), 128, 0, st>>>(a);
+    reduce_correct_kernel<<<a.n_obs, 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 

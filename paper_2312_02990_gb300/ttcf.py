@@ -16,7 +16,9 @@ import numpy as np
 from . import build as _build
 
 TTCF_OK, TTCF_E_INVALID, TTCF_E_CUDA, TTCF_E_OOM, TTCF_E_NUMERIC, TTCF_E_TIMEOUT, TTCF_E_STATE = range(7)
-TTCF_BULK_WCA = 0
+TTCF_BULK_WCA, TTCF_CONFINED_LJ = 0, 1
+CONF_NSLAB = 40
+CONF_NOBS = 2 + 2 * CONF_NSLAB
 TTCF_FP64, TTCF_MIXED = 0, 1
 D_OK, D_NONFINITE, D_NBR_OVERFLOW, D_FAST_ATOM, D_ABORTED = 0, 1, 2, 4, 8
 
@@ -29,7 +31,8 @@ EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_r
            "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces", "ttcf_autotune",
            "ttcf_run_noalloc", "ttcf_cv_config_default", "ttcf_cv_data", "ttcf_cv_train",
            "ttcf_cv_apply", "ttcf_cv_get_model", "ttcf_cv_forward", "ttcf_cv_gradient",
-           "ttcf_destroy", "ttcf_last_error", "ttcf_version")
+           "ttcf_confined_params_default", "ttcf_spawn_confined", "ttcf_sample_mothers_confined",
+           "ttcf_response_obs", "ttcf_destroy", "ttcf_last_error", "ttcf_version")
 
 
 class Config(C.Structure):
@@ -39,6 +42,11 @@ class Config(C.Structure):
                 ("reset_alpha", C.c_int), ("keep_state", C.c_int), ("skin", C.c_double),
                 ("block_threads", C.c_int), ("kernel_variant", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_user", C.c_void_p), ("timeout_s", C.c_double)]
+
+
+class ConfinedParams(C.Structure):
+    _fields_ = [("k", C.c_double), ("rc", C.c_double), ("c_ff", C.c_double), ("c_wf", C.c_double),
+                ("h", C.c_double)]
 
 
 class CvConfig(C.Structure):
@@ -113,6 +121,15 @@ def load(build_if_missing: bool = False):
     for name in ("ttcf_cv_data", "ttcf_cv_train", "ttcf_cv_apply", "ttcf_cv_get_model",
                  "ttcf_cv_forward", "ttcf_cv_gradient"):
         getattr(L, name).restype = C.c_int
+    L.ttcf_confined_params_default.argtypes = [C.POINTER(ConfinedParams)]
+    L.ttcf_confined_params_default.restype = None
+    L.ttcf_spawn_confined.argtypes = [vp, C.c_int, _dp, vp, vp, C.POINTER(ConfinedParams), C.c_int,
+                                      vp, vp, vp, C.c_int, ip]
+    L.ttcf_sample_mothers_confined.argtypes = [vp, C.c_int, _dp, vp, vp, C.POINTER(ConfinedParams),
+                                               C.c_int, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp]
+    L.ttcf_response_obs.argtypes = [vp, C.c_int, C.c_int, C.c_int] + [_dp] * 7 + [C.c_int, ip]
+    for f in ("ttcf_spawn_confined", "ttcf_sample_mothers_confined", "ttcf_response_obs"):
+        getattr(L, f).restype = C.c_int
     L.ttcf_destroy.argtypes = [vp]
     L.ttcf_destroy.restype = None
     L.ttcf_last_error.argtypes = [vp]
@@ -284,12 +301,59 @@ class Context:
                                            _ptr(arr["eta_dav_se"]), S, C.byref(n)))
         return arr
 
-    def daughter_series(self, batch: int, n_daughters: int):
+    def daughter_series(self, batch: int, n_daughters: int, n_obs: int = 1):
+        """B [D, S] (n_obs = 1) or [D, n_obs, S], Omega [D]."""
         S = self.n_samples
-        B = np.zeros((n_daughters, S))
+        B = np.zeros((n_daughters, S) if n_obs == 1 else (n_daughters, n_obs, S))
         Om = np.zeros(n_daughters)
         self._check(self._L.ttcf_daughter_series(self.h, batch, _ptr(B), _ptr(Om), B.size))
         return B, Om
+
+    def response_obs(self, batch: int, observable: int, corrected: bool = False) -> dict:
+        S = self.n_samples
+        arr = {k: np.zeros(S) for k in ("t", "dav", "dav_se", "corr", "corr_se", "ttcf", "ttcf_se")}
+        n = C.c_int()
+        self._check(self._L.ttcf_response_obs(self.h, batch, int(observable), 1 if corrected else 0,
+                                              _ptr(arr["t"]), _ptr(arr["dav"]), _ptr(arr["dav_se"]),
+                                              _ptr(arr["corr"]), _ptr(arr["corr_se"]),
+                                              _ptr(arr["ttcf"]), _ptr(arr["ttcf_se"]), S, C.byref(n)))
+        return arr
+
+    def spawn_confined(self, mother_soa, types, lattice, box, mother_alpha=None, shear_rates=0.0,
+                       params: "ConfinedParams | None" = None) -> int:
+        """Confined daughters (Example 2) from host arrays: mother_soa
+        [G, 6, N], types [N] (0 fluid, 1 bottom, 2 top wall), lattice [3, N]."""
+        ms = _f64(mother_soa)
+        if ms.ndim == 2:
+            ms = ms[None]
+        G, _, N = ms.shape
+        ty = np.ascontiguousarray(types, dtype=np.int32)
+        lt = _f64(lattice)
+        al = None if mother_alpha is None else _f64(np.broadcast_to(mother_alpha, (G,)))
+        gm = _f64(np.broadcast_to(np.asarray(shear_rates, np.float64), (G,)))
+        pr = params if params is not None else confined_params_default()
+        bid = C.c_int(-1)
+        self._check(self._L.ttcf_spawn_confined(self.h, int(N), _ptr(_box(box)), ty.ctypes.data,
+                                                lt.ctypes.data, C.byref(pr), int(G), ms.ctypes.data,
+                                                al.ctypes.data if al is not None else None,
+                                                gm.ctypes.data, 0, C.byref(bid)))
+        return bid.value
+
+    def sample_mothers_confined(self, init_soa, types, lattice, box, n_eq: int, n_states: int,
+                                spacing: int, params: "ConfinedParams | None" = None):
+        init = _f64(init_soa)
+        if init.ndim == 2:
+            init = init[None]
+        n_init, _, N = init.shape
+        ty = np.ascontiguousarray(types, dtype=np.int32)
+        lt = _f64(lattice)
+        out = np.zeros((n_init, n_states, 6, N))
+        al = np.zeros((n_init, n_states))
+        pr = params if params is not None else confined_params_default()
+        self._check(self._L.ttcf_sample_mothers_confined(
+            self.h, int(N), _ptr(_box(box)), ty.ctypes.data, lt.ctypes.data, C.byref(pr),
+            int(n_init), _ptr(init), int(n_eq), int(n_states), int(spacing), _ptr(out), _ptr(al)))
+        return out, al
 
     def group_status(self, batch: int, n_groups: int) -> np.ndarray:
         st = np.zeros(n_groups, dtype=np.int32)
@@ -391,6 +455,12 @@ class Context:
         self._check(self._L.ttcf_forces(self.h, int(N), _ptr(_box(box)), int(n), float(delta),
                                         _ptr(s), _ptr(F), _ptr(W), _ptr(U)))
         return F, W, U
+
+
+def confined_params_default() -> ConfinedParams:
+    p = ConfinedParams()
+    load().ttcf_confined_params_default(C.byref(p))
+    return p
 
 
 def cv_config_default() -> CvConfig:
