@@ -41,6 +41,8 @@ FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (sm_103)
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 FLOPS_PER_PAIR = 36.0            # one unique WCA pair with virial (Newton 3)
+FLOPS_PER_PAIR_LJ = 25.0         # one unique LJ-c_ij pair of the confined system (no virial)
+CONF_RATES = [1e-1, 1e-3, 1e-5, 1e-7]
 
 
 def fp32_peak_tflops(mhz=SM_MAX_MHZ):
@@ -68,6 +70,12 @@ def parse():
     p.add_argument("--cv-aux", type=int, default=65536)
     p.add_argument("--cv-steps", type=int, default=500)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-confined", action="store_true")
+    p.add_argument("--conf-chains", type=int, default=38, help="independent confined mother chains")
+    p.add_argument("--conf-states", type=int, default=4, help="mother states per chain")
+    p.add_argument("--conf-eq", type=int, default=4000)
+    p.add_argument("--conf-spacing", type=int, default=200)
+    p.add_argument("--conf-steps", type=int, default=2000)
     return p.parse_args()
 
 
@@ -307,6 +315,8 @@ def bench_gb300(args):
         line["viscosity_variance_per_gpu_second"] = eff
     if not args.no_cv and rank == 0:
         line["control_variate"] = cv_section(T, torch, args)
+    if not args.no_confined and rank == 0:
+        line["confined"] = confined_section(T, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, N)
     if rank == 0:
@@ -384,6 +394,72 @@ def cv_section(T, torch, args):
             "train_loss_first_last": [float(loss[0]), float(loss[-1])],
             "groups": {"train": n_tr, "eval": n_ev, "aux": n_aux}, "daughter_steps": args.cv_steps,
             "seconds": {"mothers": t_moth, "run": t_run, "train": t_train, "apply": t_apply}}
+
+
+def confined_section(T, torch, args):
+    """Confined channel of Example 2 (6048 fluid + 4200 tethered wall atoms,
+    dt = 0.005): GPU-thermalised mothers (lattices at rest), then every
+    mother x 4 mappings x 4 shear rates 1e-1 ... 1e-7 as daughters of
+    conf_steps steps in one persistent launch.  Reports daughter
+    atom-steps/s of that launch and the wall-stress and slab responses."""
+    from paper_2312_02990_gb300 import inputs
+    sysd = inputs.confined_system()
+    N, box = sysd["state"].shape[1], sysd["box"]
+    cfg = T.config_default()
+    cfg.system, cfg.precision = T.TTCF_CONFINED_LJ, T.TTCF_MIXED
+    cfg.dt, cfg.T, cfg.tau_T = 0.005, 1.0, 0.25
+    cfg.n_steps, cfg.sample_every = args.conf_steps, 10
+    rng = np.random.default_rng(inputs.BASE_SEED + 777)
+    init = np.repeat(sysd["state"][None], args.conf_chains, axis=0)
+    # independent chains: fresh Maxwell momenta per chain (same temperature)
+    init[:, 3:] = rng.standard_normal((args.conf_chains, 3, N))
+    for t in (0, 1, 2):
+        sel = sysd["types"] == t
+        init[:, 3:, sel] -= init[:, 3:, sel].mean(axis=2, keepdims=True)
+    t0 = time.perf_counter()
+    with T.Context(cfg) as c:
+        ms, al = c.sample_mothers_confined(init, sysd["types"], sysd["lattice"], box,
+                                           n_eq=args.conf_eq, n_states=args.conf_states,
+                                           spacing=args.conf_spacing)
+    t_moth = time.perf_counter() - t0
+    ms, al = ms.reshape(-1, 6, N), al.reshape(-1)
+    G = ms.shape[0]
+    with T.Context(cfg) as c:
+        ids = [c.spawn_confined(ms, sysd["types"], sysd["lattice"], box, al, g) for g in CONF_RATES]
+        # a group whose daughter fails (e.g. a fluid atom pushed through a
+        # wall at the highest rate) is excluded from the averages and counted
+        c.run(allow_numeric=True)
+        st = c.get_stats()
+        resp = {}
+        for g, b in zip(CONF_RATES, ids):
+            gs = c.group_status(b, G)
+            top = c.response_obs(b, 1)
+            bot = c.response_obs(b, 0)
+            resp[f"{g:.0e}"] = {"wall_stress_top_ttcf": float(top["ttcf"][-1]),
+                                "wall_stress_top_ttcf_se": float(top["ttcf_se"][-1]),
+                                "wall_stress_top_dav": float(top["dav"][-1]),
+                                "wall_stress_top_dav_se": float(top["dav_se"][-1]),
+                                "wall_stress_bottom_ttcf": float(bot["ttcf"][-1]),
+                                "wall_stress_bottom_ttcf_se": float(bot["ttcf_se"][-1]),
+                                "excluded_groups": int(np.count_nonzero(gs)),
+                                "status_flags": int(np.bitwise_or.reduce(gs))}
+    D = 4 * G * len(CONF_RATES)
+    atom_steps = float(D) * N * args.conf_steps
+    k_ms = st["ms_run"]
+    flops = st["pairs_interacting"] / 2.0 * FLOPS_PER_PAIR_LJ
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    return {"value": atom_steps / (k_ms * 1e-3), "unit": "atom-steps/s",
+            "workload": f"confined LJ channel N={N} ({sysd['n_fluid']} fluid + {sysd['n_wall']} wall), "
+                        f"{G} mother states x 4 mappings x {len(CONF_RATES)} shear rates = {D} daughters "
+                        f"x {args.conf_steps} steps (dt 0.005), MIXED",
+            "kernel_ms": k_ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "kernel": "conf_kernel",
+                         "algorithmic": "unique interacting pairs x 25 FP32 flops"},
+            "pairs_per_atom_step": st["pairs_interacting"] / atom_steps,
+            "rebuilds_per_daughter_step": st["rebuilds"] / (D * args.conf_steps),
+            "mother_setup_s": t_moth, "responses_t_end": resp}
 
 
 # -------------------------------------------------------------- oracle --

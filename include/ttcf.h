@@ -84,7 +84,10 @@ enum {
     TTCF_D_NONFINITE = 1,      /* NaN or Inf in a reduced sum                 */
     TTCF_D_NBR_OVERFLOW = 2,   /* an atom had more Verlet neighbours than fit */
     TTCF_D_FAST_ATOM = 4,      /* an atom moved more than skin/2 in one step  */
-    TTCF_D_ABORTED = 8         /* stopped by the host (timeout)               */
+    TTCF_D_ABORTED = 8,        /* stopped by the host (timeout)               */
+    TTCF_D_ESCAPED = 16        /* confined system: a fluid atom left the
+                                  channel (|y| > Ly/2) or an atom became
+                                  non-finite                                   */
 };
 
 typedef void *(*ttcf_alloc_fn)(size_t bytes, void *stream, void *user);

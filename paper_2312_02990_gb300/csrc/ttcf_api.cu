@@ -559,7 +559,7 @@ ttcf_status make_conf_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, cons
         return fail(ctx, TTCF_E_INVALID, "bad confined parameters");
     b.confined = true;
     b.n_obs = CONF_NOBS;
-    b.skin = cf.skin > 0 ? cf.skin : DEFAULT_SKIN;
+    b.skin = cf.skin > 0 ? cf.skin : CONF_DEFAULT_SKIN;
     const double rl = p.rc + b.skin;
     for (int k = 0; k < 3; k++)
         if (!(box[k] > 0) || !isfinite(box[k])) return fail(ctx, TTCF_E_INVALID, "box edges must be positive");
@@ -697,7 +697,7 @@ ttcf_status launch_conf_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost
     int *d_work = pool.get<int>(work.size());
     int *d_q = pool.get<int>(1);
     float4 *scratch = pool.get<float4>((size_t)grid * CONF_SCRATCH_F4 * nmax);
-    unsigned short *nbr = pool.get<unsigned short>((size_t)grid * CONF_CAP * nmax);
+    uint4 *nbr = pool.get<uint4>((size_t)grid * CONF_GROUPS * nmax);
     int *ncnt = pool.get<int>((size_t)grid * nmax);
     if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (confined tables)");
     cudaStream_t st = ctx->st;

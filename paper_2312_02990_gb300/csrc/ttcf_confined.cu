@@ -48,7 +48,7 @@ struct ConfCoef {
     df disp;                   // lattice displacement v t at the current step
     df Ldf[3];
     float Lf[3], invLf[3];
-    float thr2, fast2, rl2;
+    float skin_eff, fast2, rl2;   // rebuild threshold on |d1| + |d2|
     int stop;
 };
 
@@ -57,11 +57,27 @@ struct ConfMisc {
     double a_end, a_cur, K2_end, e1, f1sq, disp, hhQ, vh, snap_f;
     unsigned int n_rebuild;
     int warp_tmp[MAX_WARPS];
-    int flag_rebuild[2];
+    float2 dtop[MAX_WARPS];       // per-warp two largest squared displacements
     int flag_fast, flag_ovf, flag_lost;
     unsigned long long slab_px[CONF_NSLAB];   // fixed point, units of 2^-40
     int slab_n[CONF_NSLAB];
 };
+
+// Shared-memory carve-up of a daughter CTA; every region starts on a
+// 16-byte boundary (ConfMisc holds 8-byte fields, whatever the cell count).
+__host__ __device__ inline size_t r16(size_t b) { return (b + 15) & ~(size_t)15; }
+struct ConfSmem { size_t cnt, start, catom, coef, misc, total; };
+__host__ __device__ inline ConfSmem conf_layout(int nmax, int ncm) {
+    ConfSmem l;
+    size_t o = r16((size_t)(nmax + 1) * 16);   // positions + ghost
+    l.cnt = o;   o += r16((size_t)ncm * 4);
+    l.start = o; o += r16((size_t)(ncm + 2) * 4);
+    l.catom = o; o += r16((size_t)nmax * 2);
+    l.coef = o;  o += r16(sizeof(ConfCoef));
+    l.misc = o;  o += r16(sizeof(ConfMisc));
+    l.total = o;
+    return l;
+}
 
 __device__ __forceinline__ df shfl_down_df(df v, int o) {
     return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
@@ -108,18 +124,23 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
     const int nmax = a.nmax, ncm = a.ncellmax;
     const int nc0 = b.nc[0], nc1 = b.nc[1], nc2 = b.nc[2];
 
-    unsigned char *sp = smem;
-    float4 *pos4 = reinterpret_cast<float4 *>(sp); sp += (size_t)nmax * 16;
-    int *cnt = reinterpret_cast<int *>(sp); sp += (size_t)ncm * 4;
-    int *start = reinterpret_cast<int *>(sp); sp += ((size_t)(ncm + 2) * 4 + 15) / 16 * 16;
-    unsigned short *catom = reinterpret_cast<unsigned short *>(sp); sp += ((size_t)nmax * 2 + 15) / 16 * 16;
-    ConfCoef *cf = reinterpret_cast<ConfCoef *>(sp); sp += (sizeof(ConfCoef) + 15) / 16 * 16;
-    ConfMisc *m = reinterpret_cast<ConfMisc *>(sp);
+    const ConfSmem lay = conf_layout(nmax, ncm);
+    float4 *pos4 = reinterpret_cast<float4 *>(smem);   // [nmax] + ghost
+    int *cnt = reinterpret_cast<int *>(smem + lay.cnt);
+    int *start = reinterpret_cast<int *>(smem + lay.start);
+    unsigned short *catom = reinterpret_cast<unsigned short *>(smem + lay.catom);
+    ConfCoef *cf = reinterpret_cast<ConfCoef *>(smem + lay.coef);
+    ConfMisc *m = reinterpret_cast<ConfMisc *>(smem + lay.misc);
 
+    // per-slot state in the CTA's global scratch: two copies of the five
+    // permuted rows (the list build sorts atoms into cell order), forces and
+    // list references; plo.w carries the atom's original index
     float4 *scr = a.scratch + (size_t)blockIdx.x * CONF_SCRATCH_F4 * nmax;
-    float4 *plo = scr, *phi = scr + nmax, *pml = scr + 2 * (size_t)nmax, *F4 = scr + 3 * (size_t)nmax;
-    float4 *ref = scr + 4 * (size_t)nmax, *lath = scr + 5 * (size_t)nmax, *latl = scr + 6 * (size_t)nmax;
-    unsigned short *nbr = a.nbr + (size_t)blockIdx.x * CONF_CAP * nmax;
+    float4 *plo = scr, *phi = scr + nmax, *pml = scr + 2 * (size_t)nmax;
+    float4 *lath = scr + 3 * (size_t)nmax, *latl = scr + 4 * (size_t)nmax;
+    float4 *alt = scr + 5 * (size_t)nmax;   // second copy of the five rows
+    float4 *F4 = scr + 10 * (size_t)nmax, *ref = scr + 11 * (size_t)nmax;
+    uint4 *nbr = a.nbr + (size_t)blockIdx.x * CONF_GROUPS * nmax;
     int *ncnt = a.ncnt + (size_t)blockIdx.x * nmax;
 
     const double h = a.dt, hh = 0.5 * a.dt;
@@ -135,11 +156,9 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
         const float rl = (float)(b.rc + b.skin);
         cf->rl2 = rl * rl;
         cf->fast2 = 0.25f * b.skin * b.skin;
-        const float thr = 0.5f * b.skin;
-        cf->thr2 = thr * thr;
+        cf->skin_eff = b.skin * 0.9999f;
         cf->stop = 0;
         cf->disp = df_from_double(0.0);
-        m->flag_rebuild[0] = m->flag_rebuild[1] = 0;
         m->flag_fast = m->flag_ovf = m->flag_lost = 0;
         m->n_rebuild = 0;
         const double sa = (map == 1 || map == 3) ? -1.0 : 1.0;
@@ -150,6 +169,9 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
         m->hhQ = hh / b.Q;
         m->vh = b.gamma[gl] * b.half_h * h;   // lattice advance per step
         m->snap_f = 1.0;
+        // the ghost that pads neighbour groups: far outside the channel in y
+        // (y is not periodic), so every pair with it is out of range
+        pos4[nmax] = make_float4(0.f, 1.0e4f, 0.f, 0.f);
     }
     for (int k = tid; k < CONF_NSLAB; k += T) { m->slab_px[k] = 0ull; m->slab_n[k] = 0; }
     __syncthreads();
@@ -176,7 +198,7 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             if (flippx) px = df_neg(px);
             if (flippyz) { py = df_neg(py); pz = df_neg(pz); }
             pos4[i] = make_float4(x.hi, y.hi, z.hi, (float)b.types[i]);
-            plo[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
+            plo[i] = make_float4(x.lo, y.lo, z.lo, __int_as_float(i));
             phi[i] = make_float4(px.hi, py.hi, pz.hi, 0.f);
             pml[i] = make_float4(px.lo, py.lo, pz.lo, 0.f);
             lath[i] = make_float4(xl.hi, yl.hi, zl.hi, 0.f);
@@ -189,23 +211,29 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
     const float hl0 = 0.5f * cf->Lf[0], hl1 = 0.5f * cf->Lf[1], hl2 = 0.5f * cf->Lf[2];
     auto clampc = [](int c, int n) { return min(max(c, 0), n - 1); };
 
-    // ---- Verlet lists (no wall-wall pairs) in a fixed order ----
-    // Cells: x and z wrapped, y clamped to the edge cells.  Each cell's atoms
-    // are sorted by index and candidates are visited in cell order, so the
-    // lists (and the force sums) do not depend on atomic ordering.
+    // ---- cell sort and Verlet lists (no wall-wall pairs) ----
+    // Atoms are binned (x and z wrapped, y clamped to the edge cells), each
+    // cell's atoms ordered by their current slot, and the per-atom state is
+    // permuted into that cell order: a warp's atoms are then neighbours in
+    // space, so they scan the same cells and read nearby positions.  A
+    // cell's candidates are a contiguous slot range; every step is in a fixed
+    // order, so lists and force sums do not depend on atomic ordering.
     auto build_list = [&]() {
         const int ncell = b.ncell;
+        const float Lx = cf->Lf[0], iLx = cf->invLf[0], Ly = cf->Lf[1], Lz = cf->Lf[2], iLz = cf->invLf[2];
+        const float rl2 = cf->rl2;
         for (int c = tid; c < ncell; c += T) cnt[c] = 0;
         __syncthreads();
         for (int i = tid; i < N; i += T) {
             const float4 u = pos4[i];
-            const float wx = pbc_f(u.x, cf->Lf[0], cf->invLf[0]);
-            const float wz = pbc_f(u.z, cf->Lf[2], cf->invLf[2]);
+            const float wx = pbc_f(u.x, Lx, iLx);
+            const float wz = pbc_f(u.z, Lz, iLz);
             int c = 0;
-            if (fabsf(wx) <= cf->Lf[0] && fabsf(u.y) <= cf->Lf[1] && fabsf(wz) <= cf->Lf[2])
+            if (fabsf(wx) <= Lx && fabsf(u.y) <= Ly && fabsf(wz) <= Lz)
                 c = (clampc((int)floorf((wz + hl2) * s2), nc2) * nc1 + clampc((int)floorf((u.y + hl1) * s1), nc1)) * nc0 +
                     clampc((int)floorf((wx + hl0) * s0), nc0);
-            ref[i] = make_float4(u.x, u.y, u.z, __int_as_float(c));
+            ref[i] = u;
+            ncnt[i] = c;   // cell of the slot until the lists are written
             atomicAdd(&cnt[c], 1);
         }
         __syncthreads();
@@ -213,7 +241,7 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
         __syncthreads();
         for (int c = tid; c < ncell; c += T) cnt[c] = start[c];
         __syncthreads();
-        for (int i = tid; i < N; i += T) catom[atomicAdd(&cnt[__float_as_int(ref[i].w)], 1)] = (unsigned short)i;
+        for (int i = tid; i < N; i += T) catom[atomicAdd(&cnt[ncnt[i]], 1)] = (unsigned short)i;
         __syncthreads();
         for (int c = tid; c < ncell; c += T)
             for (int u = start[c] + 1; u < start[c + 1]; u++) {
@@ -223,15 +251,34 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                 catom[w] = v;
             }
         __syncthreads();
-        const float rl = sqrtf(cf->rl2);
+        // permutation: new slot k takes old slot catom[k]
+        for (int k = tid; k < N; k += T) {
+            const int o = catom[k];
+            pos4[k] = ref[o];
+            alt[k] = plo[o];
+            alt[(size_t)nmax + k] = phi[o];
+            alt[2 * (size_t)nmax + k] = pml[o];
+            alt[3 * (size_t)nmax + k] = lath[o];
+            alt[4 * (size_t)nmax + k] = latl[o];
+        }
+        {
+            float4 *t = plo;
+            plo = alt; phi = alt + nmax; pml = alt + 2 * (size_t)nmax;
+            lath = alt + 3 * (size_t)nmax; latl = alt + 4 * (size_t)nmax;
+            alt = t;
+        }
+        __syncthreads();
+        const float rl = sqrtf(rl2);
         for (int i = tid; i < N; i += T) {
             const float4 u = pos4[i];
-            const int ti = (int)u.w;
-            const float wx = pbc_f(u.x, cf->Lf[0], cf->invLf[0]);
+            ref[i] = u;
+            const bool wall_i = u.w != 0.f;
+            const float wx = pbc_f(u.x, Lx, iLx);
             const float wy = u.y;
-            const float wz = pbc_f(u.z, cf->Lf[2], cf->invLf[2]);
-            // a non-finite or escaped atom stops the daughter (and bounds the loops)
-            if (!(fabsf(wx) <= cf->Lf[0] && fabsf(wy) <= cf->Lf[1] && fabsf(wz) <= cf->Lf[2])) {
+            const float wz = pbc_f(u.z, Lz, iLz);
+            // a non-finite atom, or a fluid atom outside the channel, stops
+            // the daughter (and bounds the loops below)
+            if (!(fabsf(wx) <= Lx && fabsf(wy) <= (wall_i ? Ly : hl1) && fabsf(wz) <= Lz)) {
                 m->flag_lost = 1;
                 ncnt[i] = 0;
                 continue;
@@ -247,22 +294,33 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             int ra[2], rb[2], nr;
             if (b0 < nc0) { ra[0] = a0; rb[0] = b0; ra[1] = rb[1] = 0; nr = 1; }
             else { ra[0] = a0; rb[0] = nc0 - 1; ra[1] = 0; rb[1] = b0 - nc0; nr = 2; }
+            // entries enter a 128-bit shift register (w0 holds the oldest)
+            // and leave as one 16-byte store per group of 8
             int k = 0;
+            unsigned int w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+            auto push = [&](unsigned int j) {
+                w0 = __byte_perm(w0, w1, 0x5432);
+                w1 = __byte_perm(w1, w2, 0x5432);
+                w2 = __byte_perm(w2, w3, 0x5432);
+                w3 = __byte_perm(w3, j, 0x5432);
+            };
             for (int zu = z0; zu <= z1; zu++) {
                 const int zz = zu < 0 ? zu + nc2 : (zu >= nc2 ? zu - nc2 : zu);
                 for (int yy = y0; yy <= y1; yy++) {
                     const int row = (zz * nc1 + yy) * nc0;
                     for (int r = 0; r < nr; r++) {
                         const int t1 = start[row + rb[r] + 1];
-                        for (int t = start[row + ra[r]]; t < t1; t++) {
-                            const int j = catom[t];
+                        for (int j = start[row + ra[r]]; j < t1; j++) {
                             const float4 v = pos4[j];
-                            if (j == i || (ti != 0 && (int)v.w != 0)) continue;   // walls do not interact
-                            const float dx = pbc_f(u.x - v.x, cf->Lf[0], cf->invLf[0]);
+                            if (j == i || (wall_i && v.w != 0.f)) continue;   // walls do not interact
+                            const float dx = pbc_f(u.x - v.x, Lx, iLx);
                             const float dy = u.y - v.y;
-                            const float dz = pbc_f(u.z - v.z, cf->Lf[2], cf->invLf[2]);
-                            if (dx * dx + dy * dy + dz * dz < cf->rl2) {
-                                if (k < CONF_CAP) nbr[(size_t)k * nmax + i] = (unsigned short)j;
+                            const float dz = pbc_f(u.z - v.z, Lz, iLz);
+                            if (dx * dx + dy * dy + dz * dz < rl2) {
+                                if (k < CONF_CAP) {
+                                    push((unsigned int)j);
+                                    if ((k & 7) == 7) nbr[(size_t)(k >> 3) * nmax + i] = make_uint4(w0, w1, w2, w3);
+                                }
                                 k++;
                             }
                         }
@@ -270,7 +328,12 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                 }
             }
             if (k > CONF_CAP) m->flag_ovf = 1;
-            ncnt[i] = min(k, CONF_CAP);
+            k = min(k, CONF_CAP);
+            if (k & 7) {   // pad the last group with the ghost
+                for (int q = k & 7; q < 8; q++) push((unsigned int)nmax);
+                nbr[(size_t)(k >> 3) * nmax + i] = make_uint4(w0, w1, w2, w3);
+            }
+            ncnt[i] = (k + 7) >> 3;   // groups
         }
     };
 
@@ -279,28 +342,36 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
     auto forces = [&](float &swb, float &swt) {
         swb = swt = 0.f;
         const float Lx = cf->Lf[0], iLx = cf->invLf[0], Lz = cf->Lf[2], iLz = cf->invLf[2];
-        const float cff = (float)b.c_ff, cwf = (float)b.c_wf, kt = (float)b.k;
+        const float m24cwf = -24.f * (float)b.c_wf, kt = (float)b.k;
         const df disp = cf->disp;
         for (int i = tid; i < N; i += T) {
             const float4 u = pos4[i];
             const int ti = (int)u.w;
-            const int kk = ncnt[i];
+            const int kg = ncnt[i];
+            // -24 c_ij: c_ff for a fluid pair, c_wf otherwise
+            const float m24c_fluid = ti == 0 ? -24.f * (float)b.c_ff : m24cwf;
             float fx = 0.f, fy = 0.f, fz = 0.f;
-            for (int t = 0; t < kk; t++) {
-                const int j = nbr[(size_t)t * nmax + i];
+            auto pair = [&](unsigned int j) {
                 const float4 v = pos4[j];
                 const float dx = pbc_f(u.x - v.x, Lx, iLx);
                 const float dy = u.y - v.y;
                 const float dz = pbc_f(u.z - v.z, Lz, iLz);
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const bool in = r2 < rc2;
-                const float c = (ti == 0 && (int)v.w == 0) ? cff : cwf;
+                const float m24c = v.w == 0.f ? m24c_fluid : m24cwf;
                 const float s = rcp_approx(r2), s3 = s * s * s;
-                const float f = in ? s3 * s * (48.f * s3 - 24.f * c) : 0.f;
+                const float f = in ? s3 * s * __fmaf_rn(48.f, s3, m24c) : 0.f;
                 fx = __fmaf_rn(f, dx, fx);
                 fy = __fmaf_rn(f, dy, fy);
                 fz = __fmaf_rn(f, dz, fz);
                 npairs += in ? 1u : 0u;
+            };
+            for (int t = 0; t < kg; t++) {
+                const uint4 q = nbr[(size_t)t * nmax + i];
+                pair(q.x & 0xffffu); pair(q.x >> 16);
+                pair(q.y & 0xffffu); pair(q.y >> 16);
+                pair(q.z & 0xffffu); pair(q.z >> 16);
+                pair(q.w & 0xffffu); pair(q.w >> 16);
             }
             if (ti != 0) {
                 // a wall atom's pair force comes from the fluid alone
@@ -347,7 +418,8 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
         if (tid == 0) {
             m->K2_end = sums[0];
             if (m->flag_ovf) cf->stop |= TTCF_D_NBR_OVERFLOW;
-            if (m->flag_lost || !isfinite(sums[0] + sums[1] + sums[2])) cf->stop |= TTCF_D_NONFINITE;
+            if (m->flag_lost) cf->stop |= TTCF_D_ESCAPED;
+            if (!isfinite(sums[0] + sums[1] + sums[2])) cf->stop |= TTCF_D_NONFINITE;
             next_step();
         }
     }
@@ -359,8 +431,8 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
     for (int s = 1; s <= a.n_steps; s++) {
         if (cf->stop) break;
         const df e = cf->e, hS = cf->h, hhS = cf->hh;
-        const int fb = s & 1;
-        const float thr2 = cf->thr2, fast2 = cf->fast2;
+        const float fast2 = cf->fast2;
+        float t1 = 0.f, t2 = 0.f;   // two largest squared displacements since the build
         // phase A: wall factor (end of the previous step and start of this
         // one), half kick, drift
         for (int i = tid; i < N; i += T) {
@@ -376,17 +448,40 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             renorm(x); renorm(y); renorm(z);
             if (!(ddx * ddx + ddy * ddy + ddz * ddz <= fast2)) m->flag_fast = 1;
             pos4[i] = make_float4(x.hi, y.hi, z.hi, u.w);
-            plo[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
+            plo[i] = make_float4(x.lo, y.lo, z.lo, xo.w);   // w: original index
             phi[i] = make_float4(px.hi, py.hi, pz.hi, 0.f);
             pml[i] = make_float4(px.lo, py.lo, pz.lo, 0.f);
             const float4 r = ref[i];
             const float ex = pbc_f(x.hi - r.x, cf->Lf[0], cf->invLf[0]), ey = y.hi - r.y,
                         ez = pbc_f(z.hi - r.z, cf->Lf[2], cf->invLf[2]);
-            if (!(ex * ex + ey * ey + ez * ez <= thr2)) m->flag_rebuild[fb] = 1;
+            const float e2 = ex * ex + ey * ey + ez * ez;
+            t2 = fmaxf(t2, fminf(t1, e2));   // (a NaN position stops the daughter
+            t1 = fmaxf(t1, e2);              //  through the step's sums)
+        }
+        {
+            for (int o = 16; o > 0; o >>= 1) {
+                const float a1 = __shfl_down_sync(0xffffffffu, t1, o), a2 = __shfl_down_sync(0xffffffffu, t2, o);
+                const float n2 = fmaxf(fminf(t1, a1), fmaxf(t2, a2));
+                t1 = fmaxf(t1, a1);
+                t2 = n2;
+            }
+            if ((tid & 31) == 0) m->dtop[tid >> 5] = make_float2(t1, t2);
         }
         __syncthreads();                                        // barrier 1
         if (m->flag_fast) break;
-        if (m->flag_rebuild[fb]) {
+        // Rebuild when two atoms may together have closed the skin: the
+        // largest plus the second largest displacement since the build.
+        bool rebuild;
+        {
+            float m1 = 0.f, m2 = 0.f;
+            for (int w = 0; w < (T >> 5); w++) {
+                const float2 q = m->dtop[w];
+                m2 = fmaxf(fmaxf(m2, q.y), fminf(m1, q.x));
+                m1 = fmaxf(m1, q.x);
+            }
+            rebuild = !(sqrtf(m1) + sqrtf(m2) <= cf->skin_eff);
+        }
+        if (rebuild) {
             build_list();
             if (tid == 0) m->n_rebuild++;
             __syncthreads();
@@ -422,7 +517,7 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             m->a_end = m->a_cur + m->hhQ * (m->K2_end - b.gT);
             if (!isfinite(sums[0] + sums[1] + sums[2])) cf->stop |= TTCF_D_NONFINITE;
             if (m->flag_ovf) cf->stop |= TTCF_D_NBR_OVERFLOW;
-            if (m->flag_lost) cf->stop |= TTCF_D_NONFINITE;
+            if (m->flag_lost) cf->stop |= TTCF_D_ESCAPED;
             if (sample) {
                 const int si = s / a.sample_every;
                 Bo[si] = sums[1] * iA;
@@ -438,7 +533,6 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             m->snap_f = 1.0 + m->e1;   // wall factor still owed to this step's momenta
             if (snap_now) a.snap_alpha[(size_t)dl * a.n_snap + (s - a.snap_first) / a.snap_every] = m->a_end;
             next_step();
-            m->flag_rebuild[fb ^ 1] = 0;
         }
         __syncthreads();                                        // barrier 3
         if (snap_now) {
@@ -453,10 +547,11 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                 x -= b.L[0] * floor((x + 0.5 * b.L[0]) / b.L[0]);
                 z -= b.L[2] * floor((z + 0.5 * b.L[2]) / b.L[2]);
                 const double w = (int)u.w != 0 ? f : 1.0;
-                o[i] = x; o[(size_t)N + i] = y; o[2 * (size_t)N + i] = z;
-                o[3 * (size_t)N + i] = w * ((double)ph.x + (double)pl.x);
-                o[4 * (size_t)N + i] = w * ((double)ph.y + (double)pl.y);
-                o[5 * (size_t)N + i] = w * ((double)ph.z + (double)pl.z);
+                const int id = __float_as_int(xo.w);   // original index of the slot
+                o[id] = x; o[(size_t)N + id] = y; o[2 * (size_t)N + id] = z;
+                o[3 * (size_t)N + id] = w * ((double)ph.x + (double)pl.x);
+                o[4 * (size_t)N + id] = w * ((double)ph.y + (double)pl.y);
+                o[5 * (size_t)N + id] = w * ((double)ph.z + (double)pl.z);
             }
         }
     }
@@ -469,7 +564,7 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
         int st = cf->stop;
         if (m->flag_fast) st |= TTCF_D_FAST_ATOM;
         if (m->flag_ovf) st |= TTCF_D_NBR_OVERFLOW;
-        if (m->flag_lost) st |= TTCF_D_NONFINITE;
+        if (m->flag_lost) st |= TTCF_D_ESCAPED;
         b.status[dl] |= st;
         b.rebuilds[dl] += m->n_rebuild;
     }
@@ -628,10 +723,7 @@ __global__ void conf_spawn_kernel(ConfSpawnArgs a) {
 
 }  // namespace
 
-size_t conf_smem_bytes(int nmax, int ncellmax) {
-    return (size_t)nmax * 16 + (size_t)ncellmax * 4 + ((size_t)(ncellmax + 2) * 4 + 15) / 16 * 16 +
-           ((size_t)nmax * 2 + 15) / 16 * 16 + (sizeof(ConfCoef) + 15) / 16 * 16 + sizeof(ConfMisc);
-}
+size_t conf_smem_bytes(int nmax, int ncellmax) { return conf_layout(nmax, ncellmax).total; }
 
 size_t conf_spawn_smem_bytes(int N, int ncell) {
     return 32 * 4 * sizeof(double) + CONF_NSLAB * 12 + 32 * 4 + (size_t)ncell * 4 + (size_t)(ncell + 2) * 4 +

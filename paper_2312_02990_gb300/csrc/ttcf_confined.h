@@ -12,9 +12,11 @@ namespace ttcf {
 constexpr int CONF_NSLAB = 40;                     // slabs of the velocity profile
 constexpr int CONF_NOBS = 2 + 2 * CONF_NSLAB;      // responses per sample
 constexpr int CONF_CAP = 128;                      // Verlet neighbours per atom
+constexpr int CONF_GROUPS = CONF_CAP / 8;          // 16-byte groups of 8 uint16 entries
 constexpr int CONF_THREADS = 1024;                 // one CTA per daughter
 constexpr int CONF_NMAX = 12288;                   // atoms per daughter
-constexpr int CONF_SCRATCH_F4 = 7;                 // float4 rows of per-CTA scratch
+constexpr int CONF_SCRATCH_F4 = 12;                // float4 rows of per-CTA scratch
+constexpr double CONF_DEFAULT_SKIN = 0.5;          // fastest measured for the Example 2 channel
 
 // One batch of confined daughters (same geometry and types).
 struct ConfBatchDev {
@@ -48,7 +50,8 @@ struct ConfRunArgs {
     int n_work;
     int *queue;
     float4 *scratch;           // [grid][CONF_SCRATCH_F4][nmax]
-    unsigned short *nbr;       // [grid][CONF_CAP][nmax]
+    uint4 *nbr;                // [grid][CONF_GROUPS][nmax]: 8 uint16 per entry,
+                               // padded with the ghost index nmax
     int *ncnt;                 // [grid][nmax]
     int nmax, ncellmax;
     int n_steps, sample_every, reset_alpha;

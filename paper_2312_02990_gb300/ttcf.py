@@ -20,7 +20,7 @@ TTCF_BULK_WCA, TTCF_CONFINED_LJ = 0, 1
 CONF_NSLAB = 40
 CONF_NOBS = 2 + 2 * CONF_NSLAB
 TTCF_FP64, TTCF_MIXED = 0, 1
-D_OK, D_NONFINITE, D_NBR_OVERFLOW, D_FAST_ATOM, D_ABORTED = 0, 1, 2, 4, 8
+D_OK, D_NONFINITE, D_NBR_OVERFLOW, D_FAST_ATOM, D_ABORTED, D_ESCAPED = 0, 1, 2, 4, 8, 16
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)

@@ -153,6 +153,24 @@ def test_full_size_channel_short_run(ttcf):
         assert_profiles_close(Bg[d], Bo[d], s["n_fluid"])
 
 
+def test_odd_cell_count(ttcf):
+    """A channel whose list grid has an odd number of cells (9 x 9 x 7): the
+    shared-memory regions after the cell counts must stay 8-byte aligned."""
+    s = inputs.confined_system(nx=11, nz=10, layers=2, seed=5)
+    sy = oc.Confined(types=s["types"], box=tuple(s["box"]))
+    ms, al = s["state"][None], np.zeros(1)
+    with cctx(ttcf, n_steps=30, skin=0.4) as c:
+        bid = c.spawn_confined(ms, s["types"], s["lattice"], sy.box, al, 0.02)
+        c.run()
+        Bg, Om = c.daughter_series(bid, 4, NOBS)
+    Bo, Omo = oracle_daughters(sy, ms, s["lattice"], al, 0.02, 30)
+    for d in range(4):
+        for w in (0, 1):
+            rms = np.sqrt(np.mean(Bo[d, w] ** 2))
+            assert np.abs(Bg[d, w] - Bo[d, w]).max() < 5e-4 * rms
+        assert_profiles_close(Bg[d], Bo[d], s["n_fluid"])
+
+
 def test_zero_field_has_zero_dissipation(ttcf, chan):
     s, sy, ms, al = chan
     with cctx(ttcf, n_steps=20) as c:
