@@ -18,7 +18,8 @@ class _Conf(C.Structure):
     _fields_ = [("n", C.c_int), ("nslab", C.c_int), ("use_cells", C.c_int), ("pad_", C.c_int),
                 ("L", C.c_double * 3), ("dt", C.c_double), ("Tw", C.c_double), ("Q", C.c_double),
                 ("g", C.c_double), ("k", C.c_double), ("rc", C.c_double), ("c_ff", C.c_double),
-                ("c_wf", C.c_double), ("vwall", C.c_double)]
+                ("c_wf", C.c_double), ("c_ww", C.c_double), ("vwall", C.c_double),
+                ("ww_on", C.c_int), ("pad2_", C.c_int)]
 
 
 def lib():
@@ -66,6 +67,8 @@ class Confined:
     rc: float = 2.5
     c_ff: float = 1.2
     c_wf: float = 0.6325
+    c_ww: float = 1.0          # wall-wall (not given in the paper: plain LJ)
+    ww_on: bool = True         # False: the tethers alone hold the walls
     vwall: float = 0.0
     use_cells: bool = True
     nslab: int = N_SLAB
@@ -96,7 +99,8 @@ class Confined:
         for d in range(3):
             s.L[d] = float(self.box[d])
         s.dt, s.Tw, s.Q, s.g, s.k, s.rc = self.dt, self.Tw, self.Q, self.g, self.k, self.rc
-        s.c_ff, s.c_wf = self.c_ff, self.c_wf
+        s.c_ff, s.c_wf, s.c_ww = self.c_ff, self.c_wf, self.c_ww
+        s.ww_on = 1 if self.ww_on else 0
         s.vwall = self.vwall if vwall is None else vwall
         return s
 

@@ -4,9 +4,11 @@
  * TEST INFRASTRUCTURE ONLY (see ttcf_oracle.c).
  *
  * System (arXiv:2312.02990, Example 2):
- *   - pair potential 4[r^-12 - c_ij r^-6] truncated at r_c (Eq. 9); fluid-
- *     fluid c_ff, wall-fluid c_wf; wall atoms do not interact with each other
- *     (they are held by their tethers);
+ *   - pair potential 4[r^-12 - c_ij r^-6] truncated at r_c (Eq. 9) between
+ *     every pair of atoms: fluid-fluid c_ff, wall-fluid c_wf (the two values
+ *     the paper gives), wall-wall c_ww (not given: plain Lennard-Jones,
+ *     c_ww = 1, by default; ww_on = 0 switches wall-wall pairs off so that
+ *     only the tethers hold the walls);
  *   - equations of motion as printed in Eq. 10: fluid ṙ = p, ṗ = F; wall
  *     ṙ = p, ṗ = F - k (r - r_l) - alpha p, alpha' = (sum_w p^2 - g T_w)/Q,
  *     lattice sites ṙ_l = (+-v_wall, 0, 0) (bottom -, top +);
@@ -33,8 +35,10 @@ typedef struct {
     int pad_;
     double L[3];      /* Lx, Ly (slab extent; y is not periodic), Lz          */
     double dt, Tw, Q, g, k, rc;
-    double c_ff, c_wf;
+    double c_ff, c_wf, c_ww;
     double vwall;     /* lattice speed: bottom wall -vwall, top wall +vwall  */
+    int ww_on;        /* 1: wall-wall pairs interact with c_ww               */
+    int pad2_;
 } orc_conf;
 
 static int is_wall(int t) { return t != 0; }
@@ -46,10 +50,10 @@ static double pbc(double d, double L) { return d - L * rint(d / L); }
 static void cf_pair(const orc_conf *c, int ti, int tj, double dx, double dy, double dz,
                     double *fx, double *fy, double *fz, double *U, double *swx)
 {
-    if (is_wall(ti) && is_wall(tj)) return;
+    if (is_wall(ti) && is_wall(tj) && !c->ww_on) return;
     double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= c->rc * c->rc) return;
-    double cij = (ti == 0 && tj == 0) ? c->c_ff : c->c_wf;
+    double cij = (ti == 0 && tj == 0) ? c->c_ff : ((ti == 0 || tj == 0) ? c->c_wf : c->c_ww);
     double s = 1.0 / r2, s3 = s * s * s;
     double f = s3 * s * (48.0 * s3 - 24.0 * cij);   /* -(1/r) dphi/dr */
     *fx += f * dx; *fy += f * dy; *fz += f * dz;

@@ -29,6 +29,31 @@ def test_geometry_is_x_reflection_symmetric_and_ordered():
     assert f.max() <= 0.5 * s["h"] - 1.0 + 1e-12 and f.min() >= -(0.5 * s["h"] - 1.0) - 1e-12
 
 
+@pytest.mark.parametrize("types,c_key", [((0, 0), "c_ff"), ((0, 1), "c_wf"), ((2, 0), "c_wf"), ((2, 1), "c_ww"),
+                                           ((1, 1), "c_ww"), ((2, 2), "c_ww")])
+def test_pair_force_and_energy_closed_forms(types, c_key):
+    """Two atoms at distance r: force -dphi/dr of Eq. 9 with the c of the
+    pair's types, energy phi(r) - phi(r_c); tethers sit on the atoms."""
+    r = 1.17
+    st = np.zeros((6, 2))
+    st[0] = [-0.3, -0.3 + r]
+    lat = st[:3].copy()
+    sy = oc.Confined(types=np.array(types, np.int32), box=(10.0, 10.0, 10.0))
+    c = getattr(sy, c_key)
+    F, U, Ut, _ = oc.forces(sy, st, lat, cells=False)
+    dphi = 48.0 * r ** -13 - 24.0 * c * r ** -7          # -dphi/dr
+    assert F[0, 0] == pytest.approx(-dphi, rel=1e-13)   # x force on atom 0
+    assert F[0, 1] == pytest.approx(dphi, rel=1e-13)    # x force on atom 1
+    assert np.all(F[1:] == 0.0)
+    phi = lambda x: 4.0 * (x ** -12 - c * x ** -6)
+    assert U == pytest.approx(phi(r) - phi(sy.rc), rel=1e-13)
+    assert Ut == 0.0
+    if c_key == "c_ww":   # switched off, the tethers alone hold the walls
+        sy.ww_on = False
+        F, U, _, _ = oc.forces(sy, st, lat, cells=False)
+        assert np.all(F == 0.0) and U == 0.0
+
+
 def test_cells_equal_all_pairs(small):
     s, sy, ms, al = small
     F1, U1, T1, w1 = oc.forces(sy, ms[0], s["lattice"], cells=True)

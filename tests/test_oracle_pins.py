@@ -265,6 +265,25 @@ def test_ttcf_reduces_to_green_kubo_at_weak_field(eq_mothers_256):
     assert np.allclose(eta[1:], gk[1:], rtol=1e-5, atol=1e-7 * np.abs(gk).max())
 
 
+def test_standard_errors_scale_with_the_field_as_in_eq_13_to_16(eq_mothers_256):
+    """In the linear regime the integrand's spread grows in proportion to the
+    field (Eq. 13: sigma(Omega(0) P_xy) = k1 gamma sqrt(...)), so the standard
+    error of <Omega(0)B(s)> scales with gamma while that of the TTCF
+    viscosity does not (Eq. 15-16).  (The direct average's spread is
+    field-independent only in the steady state, not in this transient.)"""
+    b, ms, al = eq_mothers_256
+    n = 160
+    r = {}
+    for g in (1e-3, 1e-4):
+        B, Om = oracle.daughters(b, ms[:24], al[:24], g, n)
+        r[g] = oracle.responses(B, Om, 4, b.dt)
+    s = slice(20, None)
+    ratio = r[1e-3]["corr_se"][s] / r[1e-4]["corr_se"][s]
+    assert np.all(np.abs(ratio / 10.0 - 1.0) < 0.02), ratio.min()
+    eta_se = {g: r[g]["ttcf_se"][s] / g for g in r}
+    assert np.all(np.abs(eta_se[1e-3] / eta_se[1e-4] - 1.0) < 0.02)
+
+
 def test_ttcf_agrees_with_direct_average_at_high_shear(eq_mothers_256):
     """At strong field the direct average is precise and TTCF must agree
     with it (Example 1, Fig. 3; Example 2 at gamma = 1e-1)."""
