@@ -418,11 +418,13 @@ def confined_section(T, torch, args):
         init[:, 3:, sel] -= init[:, 3:, sel].mean(axis=2, keepdims=True)
     t0 = time.perf_counter()
     with T.Context(cfg) as c:
-        ms, al = c.sample_mothers_confined(init, sysd["types"], sysd["lattice"], box,
-                                           n_eq=args.conf_eq, n_states=args.conf_states,
-                                           spacing=args.conf_spacing)
+        ms, al, cs = c.sample_mothers_confined(init, sysd["types"], sysd["lattice"], box,
+                                               n_eq=args.conf_eq, n_states=args.conf_states,
+                                               spacing=args.conf_spacing, allow_numeric=True)
     t_moth = time.perf_counter() - t0
-    ms, al = ms.reshape(-1, 6, N), al.reshape(-1)
+    # a chain in which a fluid atom entered a wall is dropped
+    keep = cs == 0
+    ms, al = ms[keep].reshape(-1, 6, N), al[keep].reshape(-1)
     G = ms.shape[0]
     with T.Context(cfg) as c:
         ids = [c.spawn_confined(ms, sysd["types"], sysd["lattice"], box, al, g) for g in CONF_RATES]
@@ -459,7 +461,8 @@ def confined_section(T, torch, args):
                          "algorithmic": "unique interacting pairs x 25 FP32 flops"},
             "pairs_per_atom_step": st["pairs_interacting"] / atom_steps,
             "rebuilds_per_daughter_step": st["rebuilds"] / (D * args.conf_steps),
-            "mother_setup_s": t_moth, "responses_t_end": resp}
+            "mother_setup_s": t_moth, "mother_chains_dropped": int(np.count_nonzero(~keep)),
+            "responses_t_end": resp}
 
 
 # -------------------------------------------------------------- oracle --

@@ -85,9 +85,9 @@ enum {
     TTCF_D_NBR_OVERFLOW = 2,   /* an atom had more Verlet neighbours than fit */
     TTCF_D_FAST_ATOM = 4,      /* an atom moved more than skin/2 in one step  */
     TTCF_D_ABORTED = 8,        /* stopped by the host (timeout)               */
-    TTCF_D_ESCAPED = 16        /* confined system: a fluid atom left the
-                                  channel (|y| > Ly/2) or an atom became
-                                  non-finite                                   */
+    TTCF_D_ESCAPED = 16        /* confined system: an atom left the slab
+                                  extent by more than Ly/2 (|y| > Ly) or
+                                  became non-finite                            */
 };
 
 typedef void *(*ttcf_alloc_fn)(size_t bytes, void *stream, void *user);
@@ -261,8 +261,8 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
 /* ------------------------------------------------------------------------
  * Confined system (Example 2; contexts created with system =
  * TTCF_CONFINED_LJ).  Pair potential 4[r^-12 - c_ij r^-6] cut at r_c
- * (Eq. 9) between fluid-fluid (c_ff) and wall-fluid (c_wf) pairs; wall atoms
- * do not interact with each other.  Wall atoms are tethered to lattice
+ * (Eq. 9) between fluid-fluid (c_ff), wall-fluid (c_wf) and wall-wall (c_ww,
+ * optional) pairs.  Wall atoms are tethered to lattice
  * sites by springs k and carry a Nose-Hoover thermostat at cfg.T with
  * Q = 3 N_w T tau_T^2 (Eq. 10); during a daughter the bottom lattice moves
  * at -v and the top one at +v in x with v = gamma h / 2.  The dissipation
@@ -273,10 +273,14 @@ typedef struct {
     double k;               /* tether stiffness                              */
     double rc;              /* cut-off radius (Example 2: 2.5)                */
     double c_ff, c_wf;      /* wetting coefficients (Example 2: 1.2, 0.6325)  */
+    double c_ww;            /* wall-wall coefficient (not given: 1, plain LJ) */
     double h;               /* channel width: v = gamma h / 2 (Example 2: 10) */
+    int ww_on;              /* 1: wall-wall pairs interact; 0: tethers only   */
+    int pad_;
 } ttcf_confined_params;
 
-/* Example 2 values: k 150, r_c 2.5, c_ff 1.2, c_wf 0.6325, h 10.           */
+/* Example 2 values: k 150, r_c 2.5, c_ff 1.2, c_wf 0.6325, h 10; wall-wall
+ * pairs interact with c_ww = 1.                                           */
 void ttcf_confined_params_default(ttcf_confined_params *p);
 
 /* Append one batch of confined daughters (as ttcf_spawn_daughters, Eq. 3):
@@ -304,12 +308,16 @@ ttcf_status ttcf_spawn_confined(ttcf_ctx *ctx, int n_atoms, const double box[3],
  * from each of n_init initial phase points [n_init][6][N] (host), n_eq
  * steps, then n_states phase points `spacing` steps apart (x, z wrapped).
  * The thermostat starts from alpha = 0.  out_soa [n_init][n_states][6][N]
- * and out_alpha [n_init][n_states] are host arrays.                       */
+ * and out_alpha [n_init][n_states] are host arrays.  chain_status
+ * [n_init] (host, may be NULL) receives each chain's TTCF_D_* flags: a
+ * flagged chain stopped there and its unwritten states stay zero.  Errors: TTCF_E_NUMERIC if any chain
+ * was flagged (the other chains' states are valid), as for ttcf_spawn_*. */
 ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const double box[3],
                                          const int *types, const double *lattice,
                                          const ttcf_confined_params *params, int n_init,
                                          const double *init_soa, int n_eq, int n_states,
-                                         int spacing, double *out_soa, double *out_alpha);
+                                         int spacing, double *out_soa, double *out_alpha,
+                                         int *chain_status);
 
 /* ttcf_response for response `observable` of a batch (0 for the bulk
  * system's P_xy; 0 .. TTCF_CONF_NOBS-1 for the confined system).          */

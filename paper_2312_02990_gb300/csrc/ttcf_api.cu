@@ -46,7 +46,8 @@ struct BatchHost {
     // confined system
     int *types = nullptr;
     double *lattice = nullptr;
-    double A = 0, rc = 0, k_tether = 0, c_ff = 0, c_wf = 0, half_h = 0;
+    double A = 0, rc = 0, k_tether = 0, c_ff = 0, c_wf = 0, c_ww = 0, half_h = 0;
+    int ww_on = 0;
     // reduction
     bool reduced = false;
     double *Y = nullptr, *Dg = nullptr, *J = nullptr, *Og = nullptr, *valid = nullptr, *out = nullptr;
@@ -555,7 +556,8 @@ ttcf_status make_conf_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, cons
     if (G <= 0) return fail(ctx, TTCF_E_INVALID, "n_mothers must be positive");
     if (!soa || !types || !lattice) return fail(ctx, TTCF_E_INVALID, "NULL array");
     if (!(p.rc > 0) || !(p.k >= 0) || !(p.h > 0) || !isfinite(p.rc) || !isfinite(p.k) ||
-        !isfinite(p.h) || !isfinite(p.c_ff) || !isfinite(p.c_wf))
+        !isfinite(p.h) || !isfinite(p.c_ff) || !isfinite(p.c_wf) || !isfinite(p.c_ww) ||
+        (p.ww_on != 0 && p.ww_on != 1))
         return fail(ctx, TTCF_E_INVALID, "bad confined parameters");
     b.confined = true;
     b.n_obs = CONF_NOBS;
@@ -570,7 +572,8 @@ ttcf_status make_conf_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, cons
     for (int k = 0; k < 3; k++) b.L[k] = box[k];
     b.V = box[0] * box[1] * box[2];
     b.A = box[0] * box[2];
-    b.rc = p.rc; b.k_tether = p.k; b.c_ff = p.c_ff; b.c_wf = p.c_wf; b.half_h = 0.5 * p.h;
+    b.rc = p.rc; b.k_tether = p.k; b.c_ff = p.c_ff; b.c_wf = p.c_wf; b.c_ww = p.c_ww;
+    b.ww_on = p.ww_on; b.half_h = 0.5 * p.h;
     if (!conf_pick_cells(ctx, b, rl))
         return fail(ctx, TTCF_E_INVALID, "n_atoms too large for one CTA's shared memory");
     for (int k = 0; k < 3; k++) b.snc[k] = std::max(1, (int)floor(box[k] / p.rc));
@@ -659,7 +662,8 @@ ConfBatchDev conf_to_dev(const BatchHost &b) {
     for (int k = 0; k < 3; k++) { d.nc[k] = b.nc[k]; d.L[k] = b.L[k]; }
     d.ncell = b.ncell;
     d.A = b.A; d.Q = b.Q; d.gT = b.gT;
-    d.rc = b.rc; d.k = b.k_tether; d.c_ff = b.c_ff; d.c_wf = b.c_wf; d.half_h = b.half_h;
+    d.rc = b.rc; d.k = b.k_tether; d.c_ff = b.c_ff; d.c_wf = b.c_wf; d.c_ww = b.c_ww;
+    d.ww_on = b.ww_on; d.half_h = b.half_h;
     d.skin = (float)b.skin;
     d.d0 = b.d0;
     d.mothers = b.mothers; d.m_alpha = b.m_alpha; d.gamma = b.gamma_d;
@@ -784,7 +788,8 @@ ttcf_status run_confined(ttcf_ctx *ctx, int n_steps) {
 ttcf_confined_params conf_params_or_default(const ttcf_confined_params *p) {
     ttcf_confined_params q;
     if (p) return *p;
-    q.k = 150.0; q.rc = 2.5; q.c_ff = 1.2; q.c_wf = 0.6325; q.h = 10.0;
+    memset(&q, 0, sizeof(q));
+    q.k = 150.0; q.rc = 2.5; q.c_ff = 1.2; q.c_wf = 0.6325; q.c_ww = 1.0; q.h = 10.0; q.ww_on = 1;
     return q;
 }
 
@@ -1315,7 +1320,8 @@ ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const doubl
                                          const int *types, const double *lattice,
                                          const ttcf_confined_params *params, int n_init,
                                          const double *init_soa, int n_eq, int n_states,
-                                         int spacing, double *out_soa, double *out_alpha) {
+                                         int spacing, double *out_soa, double *out_alpha,
+                                         int *chain_status) {
     if (!ctx || !box || !init_soa || !out_soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
     if (ctx->cfg.system != TTCF_CONFINED_LJ)
         return fail(ctx, TTCF_E_INVALID, "ttcf_sample_mothers_confined needs a TTCF_CONFINED_LJ context");
@@ -1334,6 +1340,8 @@ ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const doubl
     double *snap = pool.get<double>((size_t)n_init * n_states * 6 * N);
     double *snap_a = pool.get<double>((size_t)n_init * n_states);
     if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (mother snapshots)");
+    CK(cudaMemsetAsync(snap, 0, sizeof(double) * (size_t)n_init * n_states * 6 * N, ctx->st));
+    CK(cudaMemsetAsync(snap_a, 0, sizeof(double) * (size_t)n_init * n_states, ctx->st));
     ConfRunArgs a;
     memset(&a, 0, sizeof(a));
     a.n_steps = (int)total;
@@ -1352,8 +1360,9 @@ ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const doubl
     CK(cudaMemcpy(out_soa, snap, sizeof(double) * (size_t)n_init * n_states * 6 * N, cudaMemcpyDeviceToHost));
     if (out_alpha)
         CK(cudaMemcpy(out_alpha, snap_a, sizeof(double) * (size_t)n_init * n_states, cudaMemcpyDeviceToHost));
+    if (chain_status) for (int k = 0; k < n_init; k++) chain_status[k] = stv[k];
     for (int v : stv)
-        if (v) return fail(ctx, TTCF_E_NUMERIC, "a mother trajectory failed");
+        if (v) return fail(ctx, TTCF_E_NUMERIC, "a mother chain failed; see chain_status");
     return TTCF_OK;
 }
 

@@ -222,6 +222,7 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
         const int ncell = b.ncell;
         const float Lx = cf->Lf[0], iLx = cf->invLf[0], Ly = cf->Lf[1], Lz = cf->Lf[2], iLz = cf->invLf[2];
         const float rl2 = cf->rl2;
+        const bool ww_on = b.ww_on != 0;
         for (int c = tid; c < ncell; c += T) cnt[c] = 0;
         __syncthreads();
         for (int i = tid; i < N; i += T) {
@@ -276,9 +277,12 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             const float wx = pbc_f(u.x, Lx, iLx);
             const float wy = u.y;
             const float wz = pbc_f(u.z, Lz, iLz);
-            // a non-finite atom, or a fluid atom outside the channel, stops
-            // the daughter (and bounds the loops below)
-            if (!(fabsf(wx) <= Lx && fabsf(wy) <= (wall_i ? Ly : hl1) && fabsf(wz) <= Lz)) {
+            // a non-finite atom, or one that left the slab extent by more
+            // than Ly/2 (an atom that crossed a wall into the vacuum behind
+            // it), stops the daughter and bounds the loops below.  Fluid
+            // atoms inside a wall are allowed: with non-interacting tethered
+            // wall atoms the model lets them through the first layers.
+            if (!(fabsf(wx) <= Lx && fabsf(wy) <= Ly && fabsf(wz) <= Lz)) {
                 m->flag_lost = 1;
                 ncnt[i] = 0;
                 continue;
@@ -294,9 +298,13 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             int ra[2], rb[2], nr;
             if (b0 < nc0) { ra[0] = a0; rb[0] = b0; ra[1] = rb[1] = 0; nr = 1; }
             else { ra[0] = a0; rb[0] = nc0 - 1; ra[1] = 0; rb[1] = b0 - nc0; nr = 2; }
-            // entries enter a 128-bit shift register (w0 holds the oldest)
-            // and leave as one 16-byte store per group of 8
-            int k = 0;
+            // Entries enter a 128-bit shift register (w0 holds the oldest)
+            // and leave as one 16-byte store per group of 8, from group 0 up.
+            // A wall atom's wall neighbours go to the last groups instead
+            // (one 2-byte store each, from the last group down), so that the
+            // force loop meets its fluid and wall neighbours separately.
+            int k = 0, kw = 0;
+            unsigned short *nbr16 = reinterpret_cast<unsigned short *>(nbr);
             unsigned int w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
             auto push = [&](unsigned int j) {
                 w0 = __byte_perm(w0, w1, 0x5432);
@@ -312,28 +320,42 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                         const int t1 = start[row + rb[r] + 1];
                         for (int j = start[row + ra[r]]; j < t1; j++) {
                             const float4 v = pos4[j];
-                            if (j == i || (wall_i && v.w != 0.f)) continue;   // walls do not interact
+                            const bool ww = wall_i && v.w != 0.f;
+                            if (j == i || (ww && !ww_on)) continue;
                             const float dx = pbc_f(u.x - v.x, Lx, iLx);
                             const float dy = u.y - v.y;
                             const float dz = pbc_f(u.z - v.z, Lz, iLz);
                             if (dx * dx + dy * dy + dz * dz < rl2) {
-                                if (k < CONF_CAP) {
-                                    push((unsigned int)j);
-                                    if ((k & 7) == 7) nbr[(size_t)(k >> 3) * nmax + i] = make_uint4(w0, w1, w2, w3);
+                                if (ww) {
+                                    if (kw < CONF_CAP)
+                                        nbr16[((size_t)(CONF_GROUPS - 1 - (kw >> 3)) * nmax + i) * 8 + (kw & 7)] =
+                                            (unsigned short)j;
+                                    kw++;
+                                } else {
+                                    if (k < CONF_CAP) {
+                                        push((unsigned int)j);
+                                        if ((k & 7) == 7) nbr[(size_t)(k >> 3) * nmax + i] = make_uint4(w0, w1, w2, w3);
+                                    }
+                                    k++;
                                 }
-                                k++;
                             }
                         }
                     }
                 }
             }
-            if (k > CONF_CAP) m->flag_ovf = 1;
-            k = min(k, CONF_CAP);
-            if (k & 7) {   // pad the last group with the ghost
+            const int gf = (k + 7) >> 3, gw = (kw + 7) >> 3;   // groups used
+            if (gf + gw > CONF_GROUPS) {   // the two ends met: overflow
+                m->flag_ovf = 1;
+                ncnt[i] = 0;
+                continue;
+            }
+            if (k & 7) {   // pad the last groups with the ghost
                 for (int q = k & 7; q < 8; q++) push((unsigned int)nmax);
                 nbr[(size_t)(k >> 3) * nmax + i] = make_uint4(w0, w1, w2, w3);
             }
-            ncnt[i] = (k + 7) >> 3;   // groups
+            for (int q = kw; q < gw * 8; q++)
+                nbr16[((size_t)(CONF_GROUPS - 1 - (q >> 3)) * nmax + i) * 8 + (q & 7)] = (unsigned short)nmax;
+            ncnt[i] = gf | (gw << 16);
         }
     };
 
@@ -342,14 +364,16 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
     auto forces = [&](float &swb, float &swt) {
         swb = swt = 0.f;
         const float Lx = cf->Lf[0], iLx = cf->invLf[0], Lz = cf->Lf[2], iLz = cf->invLf[2];
-        const float m24cwf = -24.f * (float)b.c_wf, kt = (float)b.k;
+        const float m24cwf = -24.f * (float)b.c_wf, m24cww = -24.f * (float)b.c_ww, kt = (float)b.k;
         const df disp = cf->disp;
         for (int i = tid; i < N; i += T) {
             const float4 u = pos4[i];
             const int ti = (int)u.w;
-            const int kg = ncnt[i];
-            // -24 c_ij: c_ff for a fluid pair, c_wf otherwise
-            const float m24c_fluid = ti == 0 ? -24.f * (float)b.c_ff : m24cwf;
+            const int kgf = ncnt[i] & 0xffff, kgw = ncnt[i] >> 16;
+            // -24 c_ij for a fluid neighbour (c_fj) and a wall neighbour
+            // (c_wj); a wall atom meets walls only in its last groups
+            const float m24c_fj = ti == 0 ? -24.f * (float)b.c_ff : m24cwf;
+            float m24c_wj = m24cwf;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             auto pair = [&](unsigned int j) {
                 const float4 v = pos4[j];
@@ -358,7 +382,7 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                 const float dz = pbc_f(u.z - v.z, Lz, iLz);
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const bool in = r2 < rc2;
-                const float m24c = v.w == 0.f ? m24c_fluid : m24cwf;
+                const float m24c = v.w == 0.f ? m24c_fj : m24c_wj;
                 const float s = rcp_approx(r2), s3 = s * s * s;
                 const float f = in ? s3 * s * __fmaf_rn(48.f, s3, m24c) : 0.f;
                 fx = __fmaf_rn(f, dx, fx);
@@ -366,16 +390,19 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                 fz = __fmaf_rn(f, dz, fz);
                 npairs += in ? 1u : 0u;
             };
-            for (int t = 0; t < kg; t++) {
+            auto group = [&](int t) {
                 const uint4 q = nbr[(size_t)t * nmax + i];
                 pair(q.x & 0xffffu); pair(q.x >> 16);
                 pair(q.y & 0xffffu); pair(q.y >> 16);
                 pair(q.z & 0xffffu); pair(q.z >> 16);
                 pair(q.w & 0xffffu); pair(q.w >> 16);
-            }
+            };
+            for (int t = 0; t < kgf; t++) group(t);
             if (ti != 0) {
-                // a wall atom's pair force comes from the fluid alone
+                // so far the fluid's force on this wall atom
                 if (ti == 2) swt += fx; else swb += fx;
+                m24c_wj = m24cww;
+                for (int t = CONF_GROUPS - kgw; t < CONF_GROUPS; t++) group(t);
                 // tether to the site x_l(t) = x_l(0) + s_w v t
                 const float4 lh = lath[i], ll = latl[i], xo = plo[i];
                 const df xl = df_add({lh.x, ll.x}, ti == 2 ? disp : df_neg(disp));

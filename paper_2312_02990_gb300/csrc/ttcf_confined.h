@@ -26,7 +26,9 @@ struct ConfBatchDev {
     double L[3];               // Lx, Ly (slab extent, y not periodic), Lz
     double A;                  // wall area Lx * Lz
     double Q, gT;              // wall thermostat: Q = g T tau^2, g = 3 N_w
-    double rc, k, c_ff, c_wf;  // Eq. 9 cut-off and wetting, tether stiffness
+    double rc, k, c_ff, c_wf, c_ww;   // Eq. 9 cut-off and wetting, tether stiffness
+    int ww_on;                 // wall-wall pairs interact (c_ww)
+    int pad2_;
     double half_h;             // v_wall = gamma * half_h
     float skin;
     int pad_;

@@ -46,7 +46,7 @@ class Config(C.Structure):
 
 class ConfinedParams(C.Structure):
     _fields_ = [("k", C.c_double), ("rc", C.c_double), ("c_ff", C.c_double), ("c_wf", C.c_double),
-                ("h", C.c_double)]
+                ("c_ww", C.c_double), ("h", C.c_double), ("ww_on", C.c_int), ("pad_", C.c_int)]
 
 
 class CvConfig(C.Structure):
@@ -126,7 +126,7 @@ def load(build_if_missing: bool = False):
     L.ttcf_spawn_confined.argtypes = [vp, C.c_int, _dp, vp, vp, C.POINTER(ConfinedParams), C.c_int,
                                       vp, vp, vp, C.c_int, ip]
     L.ttcf_sample_mothers_confined.argtypes = [vp, C.c_int, _dp, vp, vp, C.POINTER(ConfinedParams),
-                                               C.c_int, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp]
+                                               C.c_int, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, ip]
     L.ttcf_response_obs.argtypes = [vp, C.c_int, C.c_int, C.c_int] + [_dp] * 7 + [C.c_int, ip]
     for f in ("ttcf_spawn_confined", "ttcf_sample_mothers_confined", "ttcf_response_obs"):
         getattr(L, f).restype = C.c_int
@@ -340,7 +340,10 @@ class Context:
         return bid.value
 
     def sample_mothers_confined(self, init_soa, types, lattice, box, n_eq: int, n_states: int,
-                                spacing: int, params: "ConfinedParams | None" = None):
+                                spacing: int, params: "ConfinedParams | None" = None,
+                                allow_numeric: bool = False):
+        """(states [n_init, n_states, 6, N], alpha [n_init, n_states]); with
+        allow_numeric also the per-chain status (flagged chains: TTCF_D_*)."""
         init = _f64(init_soa)
         if init.ndim == 2:
             init = init[None]
@@ -350,9 +353,14 @@ class Context:
         out = np.zeros((n_init, n_states, 6, N))
         al = np.zeros((n_init, n_states))
         pr = params if params is not None else confined_params_default()
+        cs = np.zeros(n_init, dtype=np.int32)
+        allowed = (TTCF_OK, TTCF_E_NUMERIC) if allow_numeric else (TTCF_OK,)
         self._check(self._L.ttcf_sample_mothers_confined(
             self.h, int(N), _ptr(_box(box)), ty.ctypes.data, lt.ctypes.data, C.byref(pr),
-            int(n_init), _ptr(init), int(n_eq), int(n_states), int(spacing), _ptr(out), _ptr(al)))
+            int(n_init), _ptr(init), int(n_eq), int(n_states), int(spacing), _ptr(out), _ptr(al),
+            cs.ctypes.data_as(C.POINTER(C.c_int))), allowed)
+        if allow_numeric:
+            return out, al, cs
         return out, al
 
     def group_status(self, batch: int, n_groups: int) -> np.ndarray:

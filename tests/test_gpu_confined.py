@@ -130,6 +130,27 @@ def test_daughters_follow_oracle(ttcf, chan, gamma):
         assert_profiles_close(Bg[d], Bo[d], int(np.sum(s["types"] == 0)))
 
 
+def test_walls_held_by_tethers_alone(ttcf, chan):
+    """Wall-wall pairs switched off on both sides (the reading in which only
+    the tethers hold the walls)."""
+    s, sy, ms, al = chan
+    n, g = 30, 0.05
+    p = ttcf.confined_params_default()
+    p.ww_on = 0
+    with cctx(ttcf, n_steps=n) as c:
+        bid = c.spawn_confined(ms[:1], s["types"], s["lattice"], sy.box, al[:1], g, params=p)
+        c.run()
+        Bg, Om = c.daughter_series(bid, 4, NOBS)
+    sys2 = oc.Confined(types=sy.types, box=sy.box, vwall=g * H / 2, ww_on=False)
+    Bo, Omo = oc.daughters(sys2, ms[:1], s["lattice"], al[:1], n, 1)
+    Bo = Bo.transpose(0, 2, 1)
+    for d in range(4):
+        for w in (0, 1):
+            rms = np.sqrt(np.mean(Bo[d, w] ** 2))
+            assert np.abs(Bg[d, w] - Bo[d, w]).max() < 5e-4 * rms
+        assert_profiles_close(Bg[d], Bo[d], int(np.sum(s["types"] == 0)))
+
+
 def test_full_size_channel_short_run(ttcf):
     """The Example 2 geometry (10248 atoms, one daughter per CTA at the shared
     memory limit) from the generator's initial state, 20 steps."""
@@ -169,6 +190,24 @@ def test_odd_cell_count(ttcf):
             rms = np.sqrt(np.mean(Bo[d, w] ** 2))
             assert np.abs(Bg[d, w] - Bo[d, w]).max() < 5e-4 * rms
         assert_profiles_close(Bg[d], Bo[d], s["n_fluid"])
+
+
+def test_escaped_atom_is_reported(ttcf, chan):
+    """A fluid atom far behind a wall (|y| > Ly) flags its group
+    TTCF_D_ESCAPED at the first list build; the other groups are unaffected
+    and the reduction excludes the flagged one."""
+    s, sy, ms, al = chan
+    bad = ms[:2].copy()
+    f = np.nonzero(s["types"] == 0)[0][0]
+    bad[1, 1, f] = -1.2 * sy.box[1]
+    with cctx(ttcf, n_steps=20) as c:
+        bid = c.spawn_confined(bad, s["types"], s["lattice"], sy.box, al[:2], 0.01)
+        st = c.run(allow_numeric=True)
+        gs = c.group_status(bid, 2)
+        r = c.response_obs(bid, 0)
+    assert st == ttcf.TTCF_E_NUMERIC
+    assert gs[0] == 0 and gs[1] & ttcf.D_ESCAPED
+    assert np.all(np.isfinite(r["ttcf"]))
 
 
 def test_zero_field_has_zero_dissipation(ttcf, chan):
