@@ -430,6 +430,12 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                     const float Lx = cf->Lf[0], Ly = cf->Lf[1], Lz = cf->Lf[2];
                     const float ix = cf->invLf[0], iy = cf->invLf[1], iz = cf->invLf[2];
                     const float dl = cf->delta_f;
+                    const float2 ux2 = make_float2(u.x, u.x), uy2 = make_float2(u.y, u.y),
+                                 uz2 = make_float2(u.z, u.z);
+                    const float2 Lx2 = make_float2(Lx, Lx), Ly2 = make_float2(Ly, Ly), Lz2 = make_float2(Lz, Lz);
+                    const float2 ix2 = make_float2(ix, ix), iy2 = make_float2(iy, iy), iz2 = make_float2(iz, iz);
+                    const float2 dl2 = make_float2(dl, dl);
+                    const float2 c48 = make_float2(48.f, 48.f), cm24 = make_float2(-24.f, -24.f);
                     for (int t8 = 0; t8 < kk; t8 += 8) {
                       const uint4 ch = nbr4[(size_t)(t8 >> 3) * nmax + i];
                       const unsigned int wv[4] = {ch.x, ch.y, ch.z, ch.w};
@@ -437,25 +443,34 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                       for (int wq = 0; wq < 4; wq++) {
                         if (t8 + 2 * wq >= kk) break;
                         const unsigned int word = wv[wq];
-#pragma unroll
-                        for (int hlf = 0; hlf < 2; hlf++) {
-                            const int j = hlf ? (int)(word >> 16) : (int)(word & 0xffffu);
-                            const float4 v = pos4[j];
-                            float dx = u.x - v.x, dy = u.y - v.y, dz = u.z - v.z;
-                            const float ny = rint_fma(dy, iy);
-                            dy = __fmaf_rn(-ny, Ly, dy);
-                            dx = __fmaf_rn(-ny, dl, dx);
-                            dx = __fmaf_rn(-rint_fma(dx, ix), Lx, dx);
-                            dz = __fmaf_rn(-rint_fma(dz, iz), Lz, dz);
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            const float s = rcp_approx(r2);
-                            const float s3 = s * s * s;
-                            const bool in = (r2 < rc2) && (r2 > 0.f);   // r = 0: padding
-                            const float f = in ? s3 * s * (48.f * s3 - 24.f) : 0.f;   // |F|/r
-                            fx = __fmaf_rn(f, dx, fx); fy = __fmaf_rn(f, dy, fy); fz = __fmaf_rn(f, dz, fz);
-                            w = __fmaf_rn(f * dx, dy, w);
-                            npairs += in ? 1u : 0u;
-                        }
+                        // the word's two entries as one packed float pair
+                        // (FADD2/FFMA2/FMUL2: half the issue slots); the sums
+                        // stay in list order, entry 0 then entry 1
+                        const float4 v0 = pos4[word & 0xffffu], v1 = pos4[word >> 16];
+                        float2 dx = __fadd2_rn(ux2, make_float2(-v0.x, -v1.x));
+                        float2 dy = __fadd2_rn(uy2, make_float2(-v0.y, -v1.y));
+                        float2 dz = __fadd2_rn(uz2, make_float2(-v0.z, -v1.z));
+                        const float2 mny = neg2(rint2(dy, iy2));
+                        dy = __ffma2_rn(mny, Ly2, dy);
+                        dx = __ffma2_rn(mny, dl2, dx);
+                        dx = __ffma2_rn(neg2(rint2(dx, ix2)), Lx2, dx);
+                        dz = __ffma2_rn(neg2(rint2(dz, iz2)), Lz2, dz);
+                        float2 r2 = __fmul2_rn(dx, dx);
+                        r2 = __ffma2_rn(dy, dy, r2);
+                        r2 = __ffma2_rn(dz, dz, r2);
+                        const float2 sv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+                        const float2 s3 = __fmul2_rn(__fmul2_rn(sv, sv), sv);
+                        float2 f = __fmul2_rn(__fmul2_rn(s3, sv), __ffma2_rn(c48, s3, cm24));   // |F|/r
+                        const bool in0 = (r2.x < rc2) && (r2.x > 0.f);   // r = 0: padding
+                        const bool in1 = (r2.y < rc2) && (r2.y > 0.f);
+                        f.x = in0 ? f.x : 0.f;
+                        f.y = in1 ? f.y : 0.f;
+                        const float2 fdx = __fmul2_rn(f, dx);
+                        fx = __fmaf_rn(f.x, dx.x, fx); fy = __fmaf_rn(f.x, dy.x, fy); fz = __fmaf_rn(f.x, dz.x, fz);
+                        w = __fmaf_rn(fdx.x, dy.x, w);
+                        fx = __fmaf_rn(f.y, dx.y, fx); fy = __fmaf_rn(f.y, dy.y, fy); fz = __fmaf_rn(f.y, dz.y, fz);
+                        w = __fmaf_rn(fdx.y, dy.y, w);
+                        npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
                       }
                     }
                 } else {

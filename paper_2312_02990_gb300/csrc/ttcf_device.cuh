@@ -91,6 +91,14 @@ __device__ __forceinline__ float rint_fma(float v, float s) {
     return __fsub_rn(__fmaf_rn(v, s, M), M);
 }
 
+// Packed float pairs (sm_100+ FADD2/FFMA2/FMUL2, each lane IEEE round to
+// nearest): rint_fma on both halves, and negation.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 rint2(float2 v, float2 s) {
+    const float2 M = make_float2(12582912.0f, 12582912.0f);
+    return __fadd2_rn(__ffma2_rn(v, s, M), neg2(M));
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

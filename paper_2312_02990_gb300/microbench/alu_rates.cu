@@ -10,8 +10,10 @@ __device__ double g_sinkd[1<<20];
 __device__ long long g_sinkl[1<<20];
 
 template<int OP> __global__ void k(float seed, int n) {
-  float f[8]; double d[8]; long long l[8]; int ii[8];
-  for (int i=0;i<8;i++){ f[i]=seed+i*0.001f+threadIdx.x*1e-6f; d[i]=f[i]; l[i]=i+threadIdx.x; ii[i]=i*3+threadIdx.x; }
+  float f[8]; double d[8]; long long l[8]; int ii[8]; float2 f2[8];
+  for (int i=0;i<8;i++){ f[i]=seed+i*0.001f+threadIdx.x*1e-6f; d[i]=f[i]; l[i]=i+threadIdx.x; ii[i]=i*3+threadIdx.x;
+                         f2[i]=make_float2(f[i], f[i]+0.5f); }
+  const float2 c1 = make_float2(0.9999f, 0.9998f), c2 = make_float2(0.0001f, 0.0002f);
   __syncthreads();
   unsigned long long t0 = clock64();
   for (int it=0; it<n; it++) {
@@ -29,11 +31,14 @@ template<int OP> __global__ void k(float seed, int n) {
       if (OP==9) { l[i] += (long long)ii[i]; ii[i] += 1; }                // 64-bit add
       if (OP==10) { f[i] = f[i] + 12582912.0f; f[i] -= 12582911.0f; }    // 2 FADD (magic round)
       if (OP==11) { d[i] = d[i] + 1.0000001; }                            // DADD
+      if (OP==12) { f2[i] = __ffma2_rn(f2[i], c1, c2); }                  // FFMA2 (2 lanes of work)
+      if (OP==13) { f2[i] = __fadd2_rn(f2[i], c2); }                      // FADD2
+      if (OP==14) { f2[i] = __fmul2_rn(f2[i], c1); }                      // FMUL2
     }
   }
   unsigned long long t1 = clock64();
   float sf=0; double sd=0; long long sl=0;
-  for (int i=0;i<8;i++){ sf+=f[i]+ii[i]; sd+=d[i]; sl+=l[i]; }
+  for (int i=0;i<8;i++){ sf+=f[i]+ii[i]+f2[i].x+f2[i].y; sd+=d[i]; sl+=l[i]; }
   int gid = blockIdx.x*blockDim.x+threadIdx.x;
   if (sf==12345.678f) g_sinkf[gid&1023]=sf;
   if (sd==12345.678) g_sinkd[gid&1023]=sd;
@@ -74,5 +79,8 @@ int main(){
   run<8>("IMAD i32",n,4,256,1);
   run<9>("IADD64 (+IADD)",n,4,256,1);
   run<10>("2xFADD magic",n,4,256,2);
+  run<12>("FFMA2 (2 FMA per instr)",n,4,256,2);
+  run<13>("FADD2 (2 adds per instr)",n,4,256,2);
+  run<14>("FMUL2 (2 muls per instr)",n,4,256,2);
   return 0;
 }
