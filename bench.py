@@ -71,6 +71,7 @@ def parse():
     p.add_argument("--cv-steps", type=int, default=500)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-confined", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--conf-chains", type=int, default=38, help="independent confined mother chains")
     p.add_argument("--conf-states", type=int, default=4, help="mother states per chain")
     p.add_argument("--conf-eq", type=int, default=4000)
@@ -159,6 +160,8 @@ def one_step(T, torch, args, L, mothers_dev, alpha_dev, rates, host=None):
     cfg = T.config_default()
     cfg.precision = T.TTCF_MIXED
     cfg.n_steps = args.daughter_steps
+    if args.tuned:   # launch variant and skin chosen by the autotuner (set-up)
+        cfg.kernel_variant, cfg.skin = args.tuned
     c = T.Context(cfg)
     ids = []
     for g in rates:
@@ -197,6 +200,15 @@ def bench_gb300(args):
     atom_steps = float(D) * N * args.daughter_steps
     ms_dev = torch.from_numpy(ms).cuda()
     al_dev = torch.from_numpy(al).cuda()
+    # the autotuner times every launch variant and Verlet skin on a sample of
+    # these mothers (untimed set-up) and the run uses its choice
+    args.tuned = None
+    if not args.no_autotune:
+        cfg = T.config_default()
+        cfg.precision, cfg.n_steps = T.TTCF_MIXED, args.daughter_steps
+        with T.Context(cfg) as c:
+            v, sk, _ = c.autotune(ms[:min(G, 152)], L, shear_rate=1e-3, n_steps=200)
+        args.tuned = (v, sk)
     torch.cuda.synchronize()
 
     def barrier():
@@ -287,6 +299,8 @@ def bench_gb300(args):
                    "n_atoms": N, "mother_states": G, "daughters": D,
                    "daughter_steps": args.daughter_steps, "shear_rates": rates,
                    "rho": 0.8442, "T": 0.722, "dt": 0.0025,
+                   "autotuned": None if not args.tuned else {"kernel_variant": args.tuned[0],
+                                                             "skin": args.tuned[1]},
                    "l2": "inputs larger than L2 (mothers 403 MB, series 918 MB)"},
         "roofline": roofline,
         "e2e": e2e,

@@ -231,8 +231,8 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             const float wz = pbc_f(u.z, Lz, iLz);
             int c = 0;
             if (fabsf(wx) <= Lx && fabsf(u.y) <= Ly && fabsf(wz) <= Lz)
-                c = (clampc((int)floorf((wz + hl2) * s2), nc2) * nc1 + clampc((int)floorf((u.y + hl1) * s1), nc1)) * nc0 +
-                    clampc((int)floorf((wx + hl0) * s0), nc0);
+                c = (clampc(ifloor((wz + hl2) * s2), nc2) * nc1 + clampc(ifloor((u.y + hl1) * s1), nc1)) * nc0 +
+                    clampc(ifloor((wx + hl0) * s0), nc0);
             ref[i] = u;
             ncnt[i] = c;   // cell of the slot until the lists are written
             atomicAdd(&cnt[c], 1);
@@ -287,12 +287,12 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                 ncnt[i] = 0;
                 continue;
             }
-            const int z0 = (int)floorf((wz - rl + hl2) * s2);
-            const int z1 = min((int)floorf((wz + rl + hl2) * s2), z0 + nc2 - 1);
-            const int y0 = max((int)floorf((wy - rl + hl1) * s1), 0);
-            const int y1 = min((int)floorf((wy + rl + hl1) * s1), nc1 - 1);
-            const int x0 = (int)floorf((wx - rl + hl0) * s0);
-            const int x1 = min((int)floorf((wx + rl + hl0) * s0), x0 + nc0 - 1);
+            const int z0 = ifloor((wz - rl + hl2) * s2);
+            const int z1 = min(ifloor((wz + rl + hl2) * s2), z0 + nc2 - 1);
+            const int y0 = max(ifloor((wy - rl + hl1) * s1), 0);
+            const int y1 = min(ifloor((wy + rl + hl1) * s1), nc1 - 1);
+            const int x0 = ifloor((wx - rl + hl0) * s0);
+            const int x1 = min(ifloor((wx + rl + hl0) * s0), x0 + nc0 - 1);
             const int a0 = x0 < 0 ? x0 + nc0 : (x0 >= nc0 ? x0 - nc0 : x0);
             const int b0 = a0 + (x1 - x0);
             int ra[2], rb[2], nr;

@@ -302,7 +302,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         wx = (float)x; wy = (float)y; wz = (float)z;
     };
     auto cell_of = [&](float w, int k) {
-        int c = (int)floorf((w + 0.5f * cf->Lf[k]) * ((float)nc[k] * cf->invLf[k]));
+        int c = ifloor((w + 0.5f * cf->Lf[k]) * ((float)nc[k] * cf->invLf[k]));
         return min(max(c, 0), nc[k] - 1);
     };
 
@@ -356,10 +356,10 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             const float hl0 = 0.5f * cf->Lf[0], hl1 = 0.5f * cf->Lf[1], hl2 = 0.5f * cf->Lf[2];
             const float s0 = (float)nc[0] * cf->invLf[0], s1 = (float)nc[1] * cf->invLf[1],
                         s2 = (float)nc[2] * cf->invLf[2];
-            const int z0 = (int)floorf((wz - rl + hl2) * s2);
-            const int z1 = min((int)floorf((wz + rl + hl2) * s2), z0 + nc[2] - 1);
-            const int y0 = (int)floorf((wy - rl + hl1) * s1);
-            const int y1 = min((int)floorf((wy + rl + hl1) * s1), y0 + nc[1] - 1);
+            const int z0 = ifloor((wz - rl + hl2) * s2);
+            const int z1 = min(ifloor((wz + rl + hl2) * s2), z0 + nc[2] - 1);
+            const int y0 = ifloor((wy - rl + hl1) * s1);
+            const int y1 = min(ifloor((wy + rl + hl1) * s1), y0 + nc[1] - 1);
             // window indices lie in [-nc, 2nc): wrap by one conditional add
             for (int zu = z0; zu <= z1; zu++) {
                 const int zz = zu < 0 ? zu + nc[2] : (zu >= nc[2] ? zu - nc[2] : zu);
@@ -368,8 +368,8 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                     const int yy = yu - cross * nc[1];
                     // the row across the y face is seen shifted by cross*delta
                     const float xs = wx - (float)cross * cf->delta_f;
-                    int x0 = (int)floorf((xs - rl + hl0) * s0);
-                    int x1 = min((int)floorf((xs + rl + hl0) * s0), x0 + nc[0] - 1);
+                    int x0 = ifloor((xs - rl + hl0) * s0);
+                    int x1 = min(ifloor((xs + rl + hl0) * s0), x0 + nc[0] - 1);
                     const int row = (zz * nc[1] + yy) * nc[0];
                     // the x window as one or two contiguous runs of cell-sorted atoms
                     int ra[2], rb[2], nr = 0;

@@ -91,6 +91,14 @@ __device__ __forceinline__ float rint_fma(float v, float s) {
     return __fsub_rn(__fmaf_rn(v, s, M), M);
 }
 
+// floor(x) as an int for |x| < 2^22 on the FP32 add pipe: x + 1.5*2^23
+// rounded down has floor(x) in its low mantissa bits (float->int
+// conversions run at 1/8 of the FP32 rate).  NaN gives some int, which the
+// callers clamp or have excluded before.
+__device__ __forceinline__ int ifloor(float x) {
+    return __float_as_int(__fadd_rd(x, 12582912.0f)) - 0x4B400000;
+}
+
 // Packed float pairs (sm_100+ FADD2/FFMA2/FMUL2, each lane IEEE round to
 // nearest): rint_fma on both halves, and negation.
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
