@@ -42,6 +42,13 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 FLOPS_PER_PAIR = 36.0            # one unique WCA pair with virial (Newton 3)
 FLOPS_PER_PAIR_LJ = 25.0         # one unique LJ-c_ij pair of the confined system (no virial)
+# DRAM bytes of the dominant kernels from one ncu capture each (small cases,
+# profiles/*.md), scaled to a launch by the units it processes:
+# daughter_kernel reads its mothers (per daughter) and writes the series (per
+# sample); conf_kernel streams its per-CTA scratch (per atom-step).
+BULK_READ_PER_DAUGHTER = 34.9e3
+BULK_WRITE_PER_SAMPLE = 8.16
+CONF_BYTES_PER_ATOM_STEP = 395.0
 CONF_RATES = [1e-1, 1e-3, 1e-5, 1e-7]
 
 
@@ -72,6 +79,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-confined", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--confined-only", action="store_true",
+                   help="run only the confined-channel section and print its JSON")
     p.add_argument("--conf-chains", type=int, default=38, help="independent confined mother chains")
     p.add_argument("--conf-states", type=int, default=4, help="mother states per chain")
     p.add_argument("--conf-eq", type=int, default=4000)
@@ -271,8 +280,9 @@ def bench_gb300(args):
     flops = float(np.mean(pairs)) / 2.0 * FLOPS_PER_PAIR
     achieved = flops / (k_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
+    traffic = D * (BULK_READ_PER_DAUGHTER + BULK_WRITE_PER_SAMPLE * (args.daughter_steps + 1))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "daughter_kernel", "kernel_ms": k_ms,
                 "algorithmic": "unique interacting pairs x 36 FP32 flops",
                 "peak_note": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
@@ -472,6 +482,7 @@ def confined_section(T, torch, args):
             "kernel_ms": k_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "kernel": "conf_kernel",
+                         "traffic": CONF_BYTES_PER_ATOM_STEP * atom_steps,
                          "algorithmic": "unique interacting pairs x 25 FP32 flops"},
             "pairs_per_atom_step": st["pairs_interacting"] / atom_steps,
             "rebuilds_per_daughter_step": st["rebuilds"] / (D * args.conf_steps),
@@ -545,6 +556,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.confined_only:
+        import torch
+
+        from paper_2312_02990_gb300 import ttcf as T
+        T.load(build_if_missing=True)
+        print(json.dumps(confined_section(T, torch, args)))
     else:
         bench_gb300(args)
 

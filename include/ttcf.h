@@ -326,6 +326,22 @@ ttcf_status ttcf_response_obs(ttcf_ctx *ctx, int batch_id, int observable, int c
                               double *corr_se, double *ttcf, double *ttcf_se, int capacity,
                               int *n_samples);
 
+/* Checkpoints (the paper's runs restart from written states, Algorithm 1
+ * "write_restart"/"read_restart"; here the whole ensemble).  ttcf_save
+ * writes every batch of the context — mothers, shear rates, alphas, the
+ * series B and Omega so far, statuses, the loop state of a chunked run —
+ * and the step count to the file `path` (host file I/O; device data copied
+ * through host memory).  ttcf_load fills a freshly created context (same
+ * system, precision, dt, T, tau_T, dof_mode, n_steps, sample_every,
+ * mapping_mask, reset_alpha) from such a file; ttcf_run then continues
+ * where the saved run stopped, giving bitwise the same series as a run
+ * never interrupted.  A finished run is reduced again on load.  The control
+ * variate's network is not saved.  Errors: TTCF_E_INVALID (unreadable file,
+ * other configuration, malformed contents), TTCF_E_STATE (ttcf_load on a
+ * used context), TTCF_E_OOM, TTCF_E_CUDA.                                */
+ttcf_status ttcf_save(ttcf_ctx *ctx, const char *path);
+ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path);
+
 /* Spawn and run one small batch of daughters without allocating memory.
  *
  * The paper has no counterpart; this is a calling convention.  It is for

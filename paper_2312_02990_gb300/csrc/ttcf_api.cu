@@ -1,5 +1,6 @@
 // ttcf_api.cu -- host implementation of the C ABI declared in ttcf.h.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -1366,6 +1367,203 @@ ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const doubl
     return TTCF_OK;
 }
 
+
+// ============================================================ checkpoints ==
+extern "C++" {
+namespace {
+
+constexpr char CKPT_MAGIC[8] = {'T', 'T', 'C', 'F', 'C', 'K', 'P', '1'};
+constexpr int CKPT_VERSION = 1;
+
+struct FileW {
+    FILE *f;
+    bool ok = true;
+    template <class T> void put(const T &v) { ok = ok && fwrite(&v, sizeof(T), 1, f) == 1; }
+    void bytes(const void *p, size_t n) { ok = ok && (n == 0 || fwrite(p, 1, n, f) == n); }
+};
+struct FileR {
+    FILE *f;
+    bool ok = true;
+    template <class T> void get(T &v) { ok = ok && fread(&v, sizeof(T), 1, f) == 1; }
+    void bytes(void *p, size_t n) { ok = ok && (n == 0 || fread(p, 1, n, f) == n); }
+};
+
+// The configuration fields that define the daughters' dynamics and samples.
+bool same_dynamics(const ttcf_config &a, const ttcf_config &b) {
+    return a.system == b.system && a.precision == b.precision && a.dt == b.dt && a.T == b.T &&
+           a.tau_T == b.tau_T && a.dof_mode == b.dof_mode && a.n_steps == b.n_steps &&
+           a.sample_every == b.sample_every && a.mapping_mask == b.mapping_mask &&
+           a.reset_alpha == b.reset_alpha;
+}
+
+// One device array: its element count, then the bytes (0 = absent).
+ttcf_status save_dev(ttcf_ctx *ctx, FileW &w, const void *d, size_t bytes) {
+    unsigned long long n = d ? bytes : 0ull;
+    w.put(n);
+    if (!n) return TTCF_OK;
+    std::vector<unsigned char> h(bytes);
+    CK(cudaMemcpy(h.data(), d, bytes, cudaMemcpyDeviceToHost));
+    w.bytes(h.data(), bytes);
+    return TTCF_OK;
+}
+
+template <class T>
+ttcf_status load_dev(ttcf_ctx *ctx, FileR &r, Pool &pool, T *&d, size_t expect_bytes, bool optional) {
+    unsigned long long n = 0;
+    r.get(n);
+    if (!r.ok) return fail(ctx, TTCF_E_INVALID, "checkpoint truncated");
+    if (n == 0) {
+        d = nullptr;
+        if (!optional) return fail(ctx, TTCF_E_INVALID, "checkpoint misses a required array");
+        return TTCF_OK;
+    }
+    if (n != expect_bytes) return fail(ctx, TTCF_E_INVALID, "checkpoint array of unexpected size");
+    std::vector<unsigned char> h(n);
+    r.bytes(h.data(), n);
+    if (!r.ok) return fail(ctx, TTCF_E_INVALID, "checkpoint truncated");
+    d = pool.get<T>(n / sizeof(T));
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (checkpoint)");
+    CK(cudaMemcpy(d, h.data(), n, cudaMemcpyHostToDevice));
+    return TTCF_OK;
+}
+
+}  // namespace
+}  // extern "C++"
+
+ttcf_status ttcf_save(ttcf_ctx *ctx, const char *path) {
+    if (!ctx || !path) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    CK(cudaStreamSynchronize(ctx->st));
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(ctx, TTCF_E_INVALID, std::string("cannot open ") + path + " for writing");
+    FileW w{f};
+    w.bytes(CKPT_MAGIC, 8);
+    w.put(CKPT_VERSION);
+    ttcf_config c = ctx->cfg;
+    c.stream = nullptr; c.dev_alloc = nullptr; c.dev_free = nullptr; c.alloc_user = nullptr;
+    w.put(c);
+    w.put(ctx->steps_done);
+    w.put(ctx->total_d);
+    const int nb = (int)ctx->batches.size();
+    w.put(nb);
+    ttcf_status st = TTCF_OK;
+    for (const BatchHost &b : ctx->batches) {
+        if (st != TTCF_OK) break;
+        w.put(b.N); w.put(b.M); w.put(b.G); w.put(b.S); w.put(b.n_obs);
+        const int conf = b.confined ? 1 : 0;
+        w.put(conf);
+        w.bytes(b.maps, sizeof(b.maps)); w.bytes(b.L, sizeof(b.L));
+        w.put(b.V); w.put(b.Q); w.put(b.gT);
+        w.bytes(b.nc, sizeof(b.nc)); w.put(b.ncell); w.bytes(b.snc, sizeof(b.snc)); w.put(b.sncell);
+        w.put(b.d0); w.put(b.variant); w.put(b.threads); w.put(b.skin);
+        w.bytes(b.gamma.data(), sizeof(double) * b.G);
+        w.put(b.A); w.put(b.rc); w.put(b.k_tether); w.put(b.c_ff); w.put(b.c_wf); w.put(b.c_ww);
+        w.put(b.ww_on); w.put(b.half_h);
+        const size_t D = (size_t)b.D();
+        if ((st = save_dev(ctx, w, b.mothers, sizeof(unsigned long long) * b.G * 6 * b.N)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.m_alpha, sizeof(double) * b.G)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.gamma_d, sizeof(double) * b.G)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.B, sizeof(double) * D * b.n_obs * b.S)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.Omega, sizeof(double) * D)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.status, sizeof(int) * D)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.scal, sizeof(double) * D * 4)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.state, sizeof(unsigned long long) * D * 6 * b.N)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.feat, sizeof(double) * b.G * FEAT_RAW)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.types, sizeof(int) * b.N)) != TTCF_OK) break;
+        if ((st = save_dev(ctx, w, b.lattice, sizeof(double) * 3 * b.N)) != TTCF_OK) break;
+    }
+    const bool ok = w.ok;
+    if (fclose(f) != 0 || !ok) {
+        if (st == TTCF_OK) st = fail(ctx, TTCF_E_INVALID, std::string("write to ") + path + " failed");
+    }
+    return st;
+}
+
+ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path) {
+    if (!ctx || !path) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (!ctx->batches.empty() || ctx->ran)
+        return fail(ctx, TTCF_E_STATE, "ttcf_load needs a freshly created context");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(ctx, TTCF_E_INVALID, std::string("cannot open ") + path);
+    FileR r{f};
+    char magic[8];
+    int ver = 0;
+    r.bytes(magic, 8);
+    r.get(ver);
+    ttcf_config c;
+    r.get(c);
+    int steps_done = 0, nb = 0;
+    long long total_d = 0;
+    r.get(steps_done); r.get(total_d); r.get(nb);
+    auto bad = [&](ttcf_status s, const char *msg) { fclose(f); return fail(ctx, s, msg); };
+    if (!r.ok || memcmp(magic, CKPT_MAGIC, 8) != 0 || ver != CKPT_VERSION)
+        return bad(TTCF_E_INVALID, "not a ttcf checkpoint (or another version)");
+    if (!same_dynamics(c, ctx->cfg))
+        return bad(TTCF_E_INVALID, "checkpoint was written under another configuration");
+    if (nb < 0 || nb > 1 << 20 || steps_done < 0 || steps_done > c.n_steps || total_d < 0)
+        return bad(TTCF_E_INVALID, "checkpoint header out of range");
+    std::vector<BatchHost> loaded;
+    Pool pool(ctx);
+    for (int k = 0; k < nb; k++) {
+        BatchHost b;
+        int conf = 0;
+        r.get(b.N); r.get(b.M); r.get(b.G); r.get(b.S); r.get(b.n_obs); r.get(conf);
+        r.bytes(b.maps, sizeof(b.maps)); r.bytes(b.L, sizeof(b.L));
+        r.get(b.V); r.get(b.Q); r.get(b.gT);
+        r.bytes(b.nc, sizeof(b.nc)); r.get(b.ncell); r.bytes(b.snc, sizeof(b.snc)); r.get(b.sncell);
+        r.get(b.d0); r.get(b.variant); r.get(b.threads); r.get(b.skin);
+        if (!r.ok || b.N < 1 || b.N > CONF_NMAX || b.M < 1 || b.M > 4 || b.G < 1 || b.S < 1 ||
+            b.S != c.n_steps / c.sample_every + 1 || b.n_obs < 1 || b.n_obs > CONF_NOBS ||
+            b.ncell < 1 || b.sncell < 1 || b.d0 < 0 || b.variant < 0 || b.variant >= N_VARIANTS)
+            return bad(TTCF_E_INVALID, "checkpoint batch header out of range");
+        b.confined = conf != 0;
+        b.gamma.resize(b.G);
+        r.bytes(b.gamma.data(), sizeof(double) * b.G);
+        r.get(b.A); r.get(b.rc); r.get(b.k_tether); r.get(b.c_ff); r.get(b.c_wf); r.get(b.c_ww);
+        r.get(b.ww_on); r.get(b.half_h);
+        if (!r.ok) return bad(TTCF_E_INVALID, "checkpoint truncated");
+        const size_t D = (size_t)b.D();
+        ttcf_status s;
+        if ((s = load_dev(ctx, r, pool, b.mothers, sizeof(unsigned long long) * b.G * 6 * b.N, false)) ||
+            (s = load_dev(ctx, r, pool, b.m_alpha, sizeof(double) * b.G, false)) ||
+            (s = load_dev(ctx, r, pool, b.gamma_d, sizeof(double) * b.G, false)) ||
+            (s = load_dev(ctx, r, pool, b.B, sizeof(double) * D * b.n_obs * b.S, false)) ||
+            (s = load_dev(ctx, r, pool, b.Omega, sizeof(double) * D, false)) ||
+            (s = load_dev(ctx, r, pool, b.status, sizeof(int) * D, false)) ||
+            (s = load_dev(ctx, r, pool, b.scal, sizeof(double) * D * 4, true)) ||
+            (s = load_dev(ctx, r, pool, b.state, sizeof(unsigned long long) * D * 6 * b.N, true)) ||
+            (s = load_dev(ctx, r, pool, b.feat, sizeof(double) * b.G * FEAT_RAW, true)) ||
+            (s = load_dev(ctx, r, pool, b.types, sizeof(int) * b.N, true)) ||
+            (s = load_dev(ctx, r, pool, b.lattice, sizeof(double) * 3 * b.N, true))) {
+            fclose(f);
+            return s;
+        }
+        if (b.confined != (b.types != nullptr) || (b.confined && !b.lattice))
+            return bad(TTCF_E_INVALID, "checkpoint batch is inconsistent");
+        if (steps_done > 0 && steps_done < c.n_steps && !b.confined && !b.state)
+            return bad(TTCF_E_INVALID, "checkpoint of a partial run lacks the loop state");
+        b.pairs = pool.get<unsigned long long>(D);
+        b.rebuilds = pool.get<unsigned int>(D);
+        if (pool.oom) return bad(TTCF_E_OOM, "device allocation failed (checkpoint)");
+        CK(cudaMemsetAsync(b.pairs, 0, sizeof(unsigned long long) * D, ctx->st));
+        CK(cudaMemsetAsync(b.rebuilds, 0, sizeof(unsigned int) * D, ctx->st));
+        loaded.push_back(b);
+    }
+    fclose(f);
+    pool.keep();
+    ctx->batches = loaded;
+    ctx->steps_done = steps_done;
+    ctx->total_d = total_d;
+    ctx->ran = steps_done > 0;
+    ctx->tables_ok = false;
+    if (steps_done >= c.n_steps) {   // a finished run: its reductions again
+        for (auto &b : ctx->batches) {
+            ttcf_status s = reduce_batch(ctx, b);
+            if (s != TTCF_OK) return s;
+        }
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return TTCF_OK;
+}
 
 // ======================================================= control variate ==
 namespace {

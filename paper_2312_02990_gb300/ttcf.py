@@ -32,7 +32,8 @@ EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_r
            "ttcf_run_noalloc", "ttcf_cv_config_default", "ttcf_cv_data", "ttcf_cv_train",
            "ttcf_cv_apply", "ttcf_cv_get_model", "ttcf_cv_forward", "ttcf_cv_gradient",
            "ttcf_confined_params_default", "ttcf_spawn_confined", "ttcf_sample_mothers_confined",
-           "ttcf_response_obs", "ttcf_destroy", "ttcf_last_error", "ttcf_version")
+           "ttcf_response_obs", "ttcf_save", "ttcf_load", "ttcf_destroy", "ttcf_last_error",
+           "ttcf_version")
 
 
 class Config(C.Structure):
@@ -128,7 +129,10 @@ def load(build_if_missing: bool = False):
     L.ttcf_sample_mothers_confined.argtypes = [vp, C.c_int, _dp, vp, vp, C.POINTER(ConfinedParams),
                                                C.c_int, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, ip]
     L.ttcf_response_obs.argtypes = [vp, C.c_int, C.c_int, C.c_int] + [_dp] * 7 + [C.c_int, ip]
-    for f in ("ttcf_spawn_confined", "ttcf_sample_mothers_confined", "ttcf_response_obs"):
+    L.ttcf_save.argtypes = [vp, C.c_char_p]
+    L.ttcf_load.argtypes = [vp, C.c_char_p]
+    for f in ("ttcf_spawn_confined", "ttcf_sample_mothers_confined", "ttcf_response_obs",
+              "ttcf_save", "ttcf_load"):
         getattr(L, f).restype = C.c_int
     L.ttcf_destroy.argtypes = [vp]
     L.ttcf_destroy.restype = None
@@ -318,6 +322,12 @@ class Context:
                                               _ptr(arr["corr"]), _ptr(arr["corr_se"]),
                                               _ptr(arr["ttcf"]), _ptr(arr["ttcf_se"]), S, C.byref(n)))
         return arr
+
+    def save(self, path: str):
+        self._check(self._L.ttcf_save(self.h, os.fsencode(path)))
+
+    def load(self, path: str):
+        self._check(self._L.ttcf_load(self.h, os.fsencode(path)))
 
     def spawn_confined(self, mother_soa, types, lattice, box, mother_alpha=None, shear_rates=0.0,
                        params: "ConfinedParams | None" = None) -> int:
