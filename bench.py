@@ -79,6 +79,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-confined", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-floor", action="store_true", help="skip the precision-floor sweep")
     p.add_argument("--confined-only", action="store_true",
                    help="run only the confined-channel section and print its JSON")
     p.add_argument("--conf-chains", type=int, default=38, help="independent confined mother chains")
@@ -341,6 +342,8 @@ def bench_gb300(args):
         line["control_variate"] = cv_section(T, torch, args)
     if not args.no_confined and rank == 0:
         line["confined"] = confined_section(T, torch, args)
+    if not args.no_floor and rank == 0:
+        line["precision_floor"] = precision_floor_section(T, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, N)
     if rank == 0:
@@ -418,6 +421,42 @@ def cv_section(T, torch, args):
             "train_loss_first_last": [float(loss[0]), float(loss[-1])],
             "groups": {"train": n_tr, "eval": n_ev, "aux": n_aux}, "daughter_steps": args.cv_steps,
             "seconds": {"mothers": t_moth, "run": t_run, "train": t_train, "apply": t_apply}}
+
+
+def precision_floor_section(T, torch, args):
+    """TTCF viscosity of the N=256 system at shear rates 1e-3 ... 1e-15 in
+    MIXED and FP64 arithmetic on the same 256 mother states (64 GPU mother
+    chains x 4 states), 4 mappings, 500 steps: the estimate and its standard
+    error stay flat down to 1e-15 (Omega(0) is exactly proportional to the
+    rate and the products are accumulated in IEEE double), while the direct
+    average's error grows as 1/rate."""
+    from paper_2312_02990_gb300 import inputs
+    N = 256
+    L = inputs.bulk_box(N)
+    rates = [1e-3, 1e-7, 1e-11, 1e-15]
+    cfg = T.config_default()
+    cfg.precision = T.TTCF_MIXED
+    init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 90000 + k) for k in range(64)])
+    with T.Context(cfg) as c:
+        ms, al = c.sample_mothers(init, L, n_eq=4000, n_states=4, spacing=200)
+    ms, al = ms.reshape(-1, 6, N), al.reshape(-1)
+    out = {}
+    for name, prec in (("mixed", T.TTCF_MIXED), ("fp64", T.TTCF_FP64)):
+        cfg = T.config_default()
+        cfg.precision, cfg.n_steps = prec, 500
+        with T.Context(cfg) as c:
+            ids = [c.spawn_daughters(ms, al, g, box=L) for g in rates]
+            c.run()
+            res = {}
+            for g, b in zip(rates, ids):
+                v = c.viscosity(b)
+                res[f"{g:.0e}"] = {"eta_ttcf": float(v["eta_ttcf"][-1]),
+                                   "eta_ttcf_se": float(v["eta_ttcf_se"][-1]),
+                                   "eta_dav": float(v["eta_dav"][-1]),
+                                   "eta_dav_se": float(v["eta_dav_se"][-1])}
+            out[name] = res
+    return {"workload": "bulk WCA N=256, 256 mother states x 4 mappings, 500 steps, t_end = 1.25",
+            "results": out}
 
 
 def confined_section(T, torch, args):

@@ -326,6 +326,19 @@ ttcf_status ttcf_response_obs(ttcf_ctx *ctx, int batch_id, int observable, int c
                               double *corr_se, double *ttcf, double *ttcf_se, int capacity,
                               int *n_samples);
 
+/* Slip velocity and friction coefficient at one wall of a confined batch
+ * (Eq. 12, <F_x> = xi A <dv>), from its TTCF and direct-average responses:
+ * v(t) = sum_k <P_k(t)> / sum_k <n_k(t)> over the slabs whose centres lie
+ * within one sigma of the wall's innermost layer on the fluid side,
+ * slip(t) = v(t) - s_w gamma h / 2 (s_w = -1 bottom, +1 top), and
+ * xi(t) = <sigma_w(t)> / slip(t) with sigma_w the x force of the fluid on
+ * the wall per area.  wall: 0 bottom, 1 top.  Arrays as in ttcf_response
+ * (any may be NULL).  Errors: TTCF_E_INVALID (not a confined batch, shear
+ * rate differing between groups, bad wall), TTCF_E_STATE (run not done). */
+ttcf_status ttcf_friction(ttcf_ctx *ctx, int batch_id, int wall, double *t, double *slip_ttcf,
+                          double *slip_dav, double *xi_ttcf, double *xi_dav, int capacity,
+                          int *n_samples);
+
 /* Checkpoints (the paper's runs restart from written states, Algorithm 1
  * "write_restart"/"read_restart"; here the whole ensemble).  ttcf_save
  * writes every batch of the context — mothers, shear rates, alphas, the

@@ -73,3 +73,33 @@ def viscosity(resp: dict, gamma: float) -> dict:
         "eta_ttcf": -resp["ttcf"] / gamma, "eta_ttcf_se": resp["ttcf_se"] / abs(gamma),
         "eta_dav": -resp["dav"] / gamma, "eta_dav_se": resp["dav_se"] / abs(gamma),
     }
+
+
+def adjacent_slabs(Ly: float, h: float, wall: int, nslab: int = 40, width: float = 1.0):
+    """Slabs whose centres lie within `width` of the innermost layer of a
+    wall, on the fluid side (wall 0: bottom at y = -h/2, 1: top at +h/2)."""
+    w = Ly / nslab
+    centres = -0.5 * Ly + (np.arange(nslab) + 0.5) * w
+    if wall == 1:
+        sel = (centres > 0.5 * h - width) & (centres < 0.5 * h)
+    else:
+        sel = (centres < -0.5 * h + width) & (centres > -0.5 * h)
+    return np.nonzero(sel)[0]
+
+
+def friction(resp_obs, gamma: float, Ly: float, h: float, wall: int, nslab: int = 40,
+             estimator: str = "ttcf") -> dict:
+    """Slip velocity and friction coefficient of Eq. 12 at one wall from the
+    confined responses (resp_obs[o] = responses of observable o):
+    v(t) = sum_k <P_k> / sum_k <n_k> over the slabs adjacent to the wall,
+    slip = v - s_w gamma h / 2, xi = <sigma_w> / slip (sigma_w: x force of
+    the fluid on the wall per area; s_w = -1 bottom, +1 top)."""
+    ks = adjacent_slabs(Ly, h, wall, nslab)
+    P = sum(resp_obs[2 + k][estimator] for k in ks)
+    n = sum(resp_obs[2 + nslab + k][estimator] for k in ks)
+    sw = 1.0 if wall == 1 else -1.0
+    slip = P / n - sw * gamma * 0.5 * h
+    sigma = resp_obs[wall][estimator]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        xi = sigma / slip
+    return {"slip": slip, "xi": xi, "slabs": ks}

@@ -1368,6 +1368,50 @@ ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const doubl
 }
 
 
+ttcf_status ttcf_friction(ttcf_ctx *ctx, int batch_id, int wall, double *t, double *slip_ttcf,
+                          double *slip_dav, double *xi_ttcf, double *xi_dav, int capacity,
+                          int *n_samples) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (!b->confined) return fail(ctx, TTCF_E_INVALID, "friction needs a confined batch");
+    if (wall != 0 && wall != 1) return fail(ctx, TTCF_E_INVALID, "wall must be 0 or 1");
+    const double g = b->gamma.empty() ? 0.0 : b->gamma[0];
+    for (double x : b->gamma)
+        if (x != g) return fail(ctx, TTCF_E_INVALID, "shear rate differs between groups");
+    if (!b->reduced) return fail(ctx, TTCF_E_STATE, "run not finished");
+    const int S = b->S;
+    if (n_samples) *n_samples = S;
+    if (capacity < S) return fail(ctx, TTCF_E_INVALID, "capacity smaller than the sample count");
+    // slabs adjacent to the wall: centres within 1 sigma of its innermost layer
+    const double Ly = b->L[1], w = Ly / CONF_NSLAB, hh = b->half_h;
+    std::vector<int> ks;
+    for (int k = 0; k < CONF_NSLAB; k++) {
+        const double c = -0.5 * Ly + (k + 0.5) * w;
+        if (wall == 1 ? (c > hh - 1.0 && c < hh) : (c < -hh + 1.0 && c > -hh)) ks.push_back(k);
+    }
+    if (ks.empty()) return fail(ctx, TTCF_E_INVALID, "no slab lies next to the wall");
+    std::vector<double> h((size_t)b->n_obs * 9 * S);
+    CK(cudaMemcpyAsync(h.data(), b->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    auto col = [&](int o, int q, int s) { return h[((size_t)o * 9 + q) * S + s]; };   // q: 2 dav, 4 ttcf
+    const double vw = (wall == 1 ? 1.0 : -1.0) * g * hh;
+    const double ds = ctx->cfg.sample_every * ctx->cfg.dt;
+    for (int s = 0; s < S; s++) {
+        double P[2] = {0.0, 0.0}, n[2] = {0.0, 0.0};
+        for (int e = 0; e < 2; e++) {
+            const int q = e == 0 ? 4 : 2;
+            for (int k : ks) { P[e] += col(2 + k, q, s); n[e] += col(2 + CONF_NSLAB + k, q, s); }
+        }
+        const double sl_t = P[0] / n[0] - vw, sl_d = P[1] / n[1] - vw;
+        if (t) t[s] = s * ds;
+        if (slip_ttcf) slip_ttcf[s] = sl_t;
+        if (slip_dav) slip_dav[s] = sl_d;
+        if (xi_ttcf) xi_ttcf[s] = col(wall, 4, s) / sl_t;
+        if (xi_dav) xi_dav[s] = col(wall, 2, s) / sl_d;
+    }
+    return TTCF_OK;
+}
+
 // ============================================================ checkpoints ==
 extern "C++" {
 namespace {

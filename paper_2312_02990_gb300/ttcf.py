@@ -32,7 +32,8 @@ EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_r
            "ttcf_run_noalloc", "ttcf_cv_config_default", "ttcf_cv_data", "ttcf_cv_train",
            "ttcf_cv_apply", "ttcf_cv_get_model", "ttcf_cv_forward", "ttcf_cv_gradient",
            "ttcf_confined_params_default", "ttcf_spawn_confined", "ttcf_sample_mothers_confined",
-           "ttcf_response_obs", "ttcf_save", "ttcf_load", "ttcf_destroy", "ttcf_last_error",
+           "ttcf_response_obs", "ttcf_friction", "ttcf_save", "ttcf_load", "ttcf_destroy",
+           "ttcf_last_error",
            "ttcf_version")
 
 
@@ -129,6 +130,8 @@ def load(build_if_missing: bool = False):
     L.ttcf_sample_mothers_confined.argtypes = [vp, C.c_int, _dp, vp, vp, C.POINTER(ConfinedParams),
                                                C.c_int, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, ip]
     L.ttcf_response_obs.argtypes = [vp, C.c_int, C.c_int, C.c_int] + [_dp] * 7 + [C.c_int, ip]
+    L.ttcf_friction.argtypes = [vp, C.c_int, C.c_int] + [_dp] * 5 + [C.c_int, ip]
+    L.ttcf_friction.restype = C.c_int
     L.ttcf_save.argtypes = [vp, C.c_char_p]
     L.ttcf_load.argtypes = [vp, C.c_char_p]
     for f in ("ttcf_spawn_confined", "ttcf_sample_mothers_confined", "ttcf_response_obs",
@@ -321,6 +324,17 @@ class Context:
                                               _ptr(arr["t"]), _ptr(arr["dav"]), _ptr(arr["dav_se"]),
                                               _ptr(arr["corr"]), _ptr(arr["corr_se"]),
                                               _ptr(arr["ttcf"]), _ptr(arr["ttcf_se"]), S, C.byref(n)))
+        return arr
+
+    def friction(self, batch: int, wall: int) -> dict:
+        """Slip velocity and friction coefficient at wall 0 (bottom) or 1
+        (top) of a confined batch (Eq. 12), TTCF and direct average."""
+        S = self.n_samples
+        arr = {k: np.zeros(S) for k in ("t", "slip_ttcf", "slip_dav", "xi_ttcf", "xi_dav")}
+        n = C.c_int()
+        self._check(self._L.ttcf_friction(self.h, batch, int(wall), _ptr(arr["t"]),
+                                          _ptr(arr["slip_ttcf"]), _ptr(arr["slip_dav"]),
+                                          _ptr(arr["xi_ttcf"]), _ptr(arr["xi_dav"]), S, C.byref(n)))
         return arr
 
     def save(self, path: str):

@@ -265,6 +265,28 @@ def test_ensemble_responses_match_oracle(ttcf, chan):
         assert np.all(np.abs(r["ttcf"] - ref["ttcf"]) <= tol)
 
 
+def test_friction_matches_the_oracle_formula(ttcf, chan):
+    """Eq. 12 from the device responses: slip velocity and friction at both
+    walls against oracle/reduce.friction on the same responses."""
+    s, sy, ms, al = chan
+    g = 0.05
+    with cctx(ttcf, n_steps=100, sample_every=5) as c:
+        bid = c.spawn_confined(ms, s["types"], s["lattice"], sy.box, al, g)
+        c.run()
+        resp = {o: c.response_obs(bid, o) for o in range(NOBS)}
+        got = [c.friction(bid, w) for w in (0, 1)]
+        with pytest.raises(ttcf.TTCFError):
+            c.friction(bid, 2)
+    for w in (0, 1):
+        for est, key in (("ttcf", "ttcf"), ("dav", "dav")):
+            ref = orr.friction(resp, g, sy.box[1], H, w, estimator=key)
+            assert np.allclose(got[w]["slip_" + est], ref["slip"], rtol=1e-12, atol=1e-15)
+            ok = np.isfinite(ref["xi"])
+            assert np.allclose(got[w]["xi_" + est][ok], ref["xi"][ok], rtol=1e-10)
+        # the fluid starts at rest: the slip is minus the wall velocity
+        assert got[w]["slip_dav"][0] == pytest.approx(-(1 if w else -1) * g * H / 2, rel=1e-9, abs=1e-12)
+
+
 # ------------------------------------------------------------- errors ----
 def test_invalid_inputs_are_rejected(ttcf, chan):
     T = ttcf

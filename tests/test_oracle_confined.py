@@ -152,3 +152,27 @@ def test_omega_is_beta_times_the_adiabatic_energy_rate(small):
         rate0 = 2 * rates[1] - rates[0]
         assert rate0 / sy.Tw == pytest.approx(om, rel=2e-3), (m, rate0, om)
         assert abs(om) > 1e-3
+
+
+def test_friction_of_constructed_responses():
+    """Eq. 12 on responses built so that the slab velocity, slip and wall
+    stress are known: xi = sigma / (v - s_w gamma h / 2)."""
+    from oracle import reduce as orr
+    Ly, h, g, ns = 15.95, 10.0, 0.02, oc.N_SLAB
+    t = np.linspace(0.0, 1.0, 11)
+    for wall, sw in ((0, -1.0), (1, 1.0)):
+        ks = orr.adjacent_slabs(Ly, h, wall, ns)
+        centres = -0.5 * Ly + (ks + 0.5) * Ly / ns
+        assert len(ks) >= 2 and np.all(np.abs(np.abs(centres) - 0.5 * h) < 1.0)
+        v_fluid = 0.3 * sw * g * t            # fluid lags the wall
+        # the fluid drags the wall backwards: sigma has the sign of the slip
+        sigma = 2.5 * (v_fluid - sw * g * 0.5 * h)
+        resp = {o: {"ttcf": np.zeros_like(t)} for o in range(2 + 2 * ns)}
+        resp[wall]["ttcf"] = sigma
+        for j, k in enumerate(ks):
+            n_k = 10.0 + j
+            resp[2 + ns + k]["ttcf"] = np.full_like(t, n_k)
+            resp[2 + k]["ttcf"] = n_k * v_fluid
+        f = orr.friction(resp, g, Ly, h, wall, ns)
+        assert np.allclose(f["slip"], v_fluid - sw * g * 0.5 * h, rtol=1e-14, atol=1e-16)
+        assert np.allclose(f["xi"], 2.5, rtol=1e-13)
