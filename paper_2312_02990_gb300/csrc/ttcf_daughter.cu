@@ -108,9 +108,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // CTA sums of three per-thread partials in a fixed order (float partials
 // summed as double-float in MIXED mode).  Contains one __syncthreads; the
-// result is valid in thread 0 only.
+// result is valid in lane 0 of warp 0 and of warp `w2` (both reduce the
+// per-warp slots in the same fixed order, so their results are identical).
 template <bool MIXED, class R>
-__device__ __forceinline__ void cta_sum3(R a0, R a1, R a2, Misc *m, double out[3]) {
+__device__ __forceinline__ void cta_sum3(R a0, R a1, R a2, Misc *m, double out[3], int w2 = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     if constexpr (MIXED) {
@@ -122,7 +123,7 @@ __device__ __forceinline__ void cta_sum3(R a0, R a1, R a2, Misc *m, double out[3
             sl[2] = make_float2(s2.hi, s2.lo);
         }
         __syncthreads();
-        if (warp == 0) {
+        if (warp == 0 || warp == w2) {
             df t0 = {0.f, 0.f}, t1 = {0.f, 0.f}, t2 = {0.f, 0.f};
             if (lane < nw) {
                 const float2 *sl = reinterpret_cast<const float2 *>(&m->slot[lane][0]);
@@ -135,7 +136,7 @@ __device__ __forceinline__ void cta_sum3(R a0, R a1, R a2, Misc *m, double out[3
         double s0 = warp_sum((double)a0), s1 = warp_sum((double)a1), s2 = warp_sum((double)a2);
         if (lane == 0) { m->slot[warp][0] = s0; m->slot[warp][1] = s1; m->slot[warp][2] = s2; }
         __syncthreads();
-        if (warp == 0) {
+        if (warp == 0 || warp == w2) {
             double t0 = 0, t1 = 0, t2 = 0;
             if (lane < nw) { t0 = m->slot[lane][0]; t1 = m->slot[lane][1]; t2 = m->slot[lane][2]; }
             t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2);
@@ -502,7 +503,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     // thread 0: coefficients of the next step from K2_end, a_end, e1, delta.
     // IEEE double throughout; on GB300 each double instruction of this
     // serial chain costs tens of cycles, so divisions and rint are avoided.
-    auto next_step = [&]() {
+    auto next_alpha = [&]() {
         const double inc = m->hhQ * (K2_end - b.gT);
         a_cur = a_end + inc;                       // start-of-step alpha half-step
         const double e3 = expm1_small(-a_cur * hh);
@@ -510,6 +511,8 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         e1 = e3;
         f1sq = (1.0 + e3) * (1.0 + e3);
         cf->e = sfrom<S>(ec);
+    };
+    auto next_delta = [&]() {
         delta += m->ddelta;                        // sliding-brick offset advance
         if (delta >= m->halfLx) delta -= b.L[0];
         else if (delta < -m->halfLx) delta += b.L[0];
@@ -518,6 +521,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         const float thr = 0.5f * (b.skin - dsince);
         cf->thr2 = thr > 0.f ? thr * thr : -1.f;
     };
+    auto next_step = [&]() { next_alpha(); next_delta(); };
 
     // ---- forces and sums of the initial state ----
     build_list();
@@ -655,31 +659,44 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             s2 += hx * hx + hy * hy + hz * hz;
             sxy += hx * hy;
         }
+        // step end, on three lanes at once (warp 0: the alpha chain; warp
+        // wo: B(s), flags, snapshots; warp wd: the Lees-Edwards offset),
+        // each reading only what the others do not write before barrier 3
+        const int nw = T >> 5;
+        const int wo = nw > 1 ? 1 : 0, wd = nw > 2 ? 2 : 0;
+        double f1sq_s = 0.0, e1_s = 0.0;
+        if (tid == 32 * wo) { f1sq_s = f1sq; e1_s = e1; }        // this step's values
         double sums[3];
-        cta_sum3<MIXED, R>(s2, sxy, wsum, m, sums);             // barrier 2
-        if (tid == 0) {
+        cta_sum3<MIXED, R>(s2, sxy, wsum, m, sums, wo);         // barrier 2
+        const bool last_save = s == a.step1 && a.save_state;
+        int snap_k = -1;
+        if (a.snap && s >= a.snap_first && (s - a.snap_first) % a.snap_every == 0 &&
+            (s - a.snap_first) / a.snap_every < a.n_snap)
+            snap_k = (s - a.snap_first) / a.snap_every;
+        double *sc = last_save ? b.scal + 4 * (size_t)dl : nullptr;
+        if (tid == 32 * wo) {
             // end of step s: pending factor (1+e1)^2 = f1sq from the scale half-step
+            const double pxy = fma(f1sq_s, sums[1], 0.5 * sums[2]) * m->invV;
+            int st = 0;
+            if (!isfinite(sums[0] + sums[1] + sums[2])) st |= TTCF_D_NONFINITE;
+            if (m->flag_ovf) st |= TTCF_D_NBR_OVERFLOW;
+            if (m->flag_lost) st |= TTCF_D_NONFINITE;
+            if (a.abort_flag && (s & 63) == 0 && *a.abort_flag) st |= TTCF_D_ABORTED;
+            if (st) atomicOr(&cf->stop, st);
+            if (s % a.sample_every == 0) b.B[series + s / a.sample_every] = pxy;
+            cf->snap = snap_k;
+            if (snap_k >= 0) cf->fsnap = 1.0 + e1_s;
+        }
+        if (tid == 32 * wd) {
+            if (last_save) sc[3] = delta;
+            next_delta();
+        }
+        if (tid == 0) {
             K2_end = f1sq * sums[0];
             a_end = a_cur + m->hhQ * (K2_end - b.gT);           // end-of-step alpha half-step
-            const double pxy = fma(f1sq, sums[1], 0.5 * sums[2]) * m->invV;
-            if (!isfinite(sums[0] + sums[1] + sums[2])) cf->stop |= TTCF_D_NONFINITE;
-            if (m->flag_ovf) cf->stop |= TTCF_D_NBR_OVERFLOW;
-            if (m->flag_lost) cf->stop |= TTCF_D_NONFINITE;
-            if (s % a.sample_every == 0) b.B[series + s / a.sample_every] = pxy;
-            cf->snap = -1;
-            if (a.snap && s >= a.snap_first && (s - a.snap_first) % a.snap_every == 0) {
-                const int k = (s - a.snap_first) / a.snap_every;
-                if (k < a.n_snap) {
-                    cf->snap = k; cf->fsnap = 1.0 + e1;
-                    a.snap_alpha[(size_t)d * a.n_snap + k] = a_end;
-                }
-            }
-            if (s == a.step1 && a.save_state) {
-                double *sc = b.scal + 4 * (size_t)dl;
-                sc[0] = a_end; sc[1] = K2_end; sc[2] = e1; sc[3] = delta;
-            }
-            if (a.abort_flag && (s & 63) == 0 && *a.abort_flag) cf->stop |= TTCF_D_ABORTED;
-            next_step();
+            if (snap_k >= 0) a.snap_alpha[(size_t)d * a.n_snap + snap_k] = a_end;
+            if (last_save) { sc[0] = a_end; sc[1] = K2_end; sc[2] = e1; }
+            next_alpha();
             m->flag_rebuild[fb ^ 1] = 0;
         }
         __syncthreads();                                        // barrier 3
