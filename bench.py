@@ -171,7 +171,7 @@ def one_step(T, torch, args, L, mothers_dev, alpha_dev, rates, host=None):
     cfg.precision = T.TTCF_MIXED
     cfg.n_steps = args.daughter_steps
     if args.tuned:   # launch variant and skin chosen by the autotuner (set-up)
-        cfg.kernel_variant, cfg.skin = args.tuned
+        cfg.kernel_variant, cfg.skin, cfg.cell_frac = args.tuned
     c = T.Context(cfg)
     ids = []
     for g in rates:
@@ -217,8 +217,8 @@ def bench_gb300(args):
         cfg = T.config_default()
         cfg.precision, cfg.n_steps = T.TTCF_MIXED, args.daughter_steps
         with T.Context(cfg) as c:
-            v, sk, _ = c.autotune(ms[:min(G, 152)], L, shear_rate=1e-3, n_steps=200)
-        args.tuned = (v, sk)
+            v, sk, fr, _ = c.autotune(ms[:min(G, 152)], L, shear_rate=1e-3, n_steps=200)
+        args.tuned = (v, sk, fr)
     torch.cuda.synchronize()
 
     def barrier():
@@ -311,7 +311,8 @@ def bench_gb300(args):
                    "daughter_steps": args.daughter_steps, "shear_rates": rates,
                    "rho": 0.8442, "T": 0.722, "dt": 0.0025,
                    "autotuned": None if not args.tuned else {"kernel_variant": args.tuned[0],
-                                                             "skin": args.tuned[1]},
+                                                             "skin": args.tuned[1],
+                                                             "cell_frac": args.tuned[2]},
                    "l2": "inputs larger than L2 (mothers 403 MB, series 918 MB)"},
         "roofline": roofline,
         "e2e": e2e,

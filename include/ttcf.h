@@ -125,6 +125,8 @@ typedef struct {
     ttcf_free_fn dev_free;  /* NULL: cudaFree                                */
     void *alloc_user;       /* passed to dev_alloc / dev_free                */
     double timeout_s;       /* ttcf_run wall-clock limit; <= 0: none         */
+    double cell_frac;       /* bulk list cells of width cell_frac (r_c+skin),
+                               in [0.4, 1]; 0 = autotuned, else 2/3          */
 } ttcf_config;
 
 /* Fill *cfg with the Example 1 defaults: MIXED, dt 0.0025, T 0.722,
@@ -245,18 +247,20 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
 ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
                         double delta, const double *soa, double *F, double *W, double *U);
 
-/* Autotuner (launch shape and Verlet skin).  Times n_steps of the
- * daughter kernel on n_states phase points [n_states][6][N] (host; all four
- * mappings, shear rate gamma) for every launch variant that holds n_atoms
- * and Verlet skins {0.3, 0.4, 0.5, 0.6}, with CUDA events on the context's
- * stream, and remembers the fastest for batches of n_atoms spawned later on
- * this context (explicit kernel_variant / skin in the config still win).
- * Returns the choice (1-based variant as in ttcf_config.kernel_variant),
- * the skin and its time in ms.  Errors: TTCF_E_INVALID if no variant can
+/* Autotuner (launch shape, Verlet skin and list-cell width).  Times
+ * n_steps of the daughter kernel on n_states phase points [n_states][6][N]
+ * (host; all four mappings, shear rate gamma) for every launch variant that
+ * holds n_atoms, Verlet skins {0.3, 0.4, 0.5, 0.6} and cell widths
+ * {1/2, 2/3} (r_c + skin), with CUDA events on the context's stream, and
+ * remembers the fastest for batches of n_atoms spawned later on this
+ * context (explicit kernel_variant / skin / cell_frac in the config still
+ * win).  Returns the choice (1-based variant as in
+ * ttcf_config.kernel_variant), the skin, the cell width and its time in
+ * ms (any output may be NULL).  Errors: TTCF_E_INVALID if no variant can
  * run the system.                                                          */
 ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
                           const double *soa, double shear_rate, int n_steps, int *best_variant,
-                          double *best_skin, double *best_ms);
+                          double *best_skin, double *best_cell_frac, double *best_ms);
 
 /* ------------------------------------------------------------------------
  * Confined system (Example 2; contexts created with system =

@@ -57,7 +57,11 @@ struct BatchHost {
 
 }  // namespace
 
-struct TunedEntry { int N; int variant; double skin; };
+struct TunedEntry { int N; int variant; double skin; double cell_frac; };
+
+// Default cell width of the bulk list build, in units of r_c + skin
+// (measured fastest for N = 2048 among r_l/2, 2r_l/3 and r_l).
+constexpr double DEFAULT_CELL_FRAC = 2.0 / 3.0;
 
 // The trained control-variate network (device buffers owned by the context).
 struct CvModel {
@@ -184,13 +188,14 @@ ttcf_status choose_class(ttcf_ctx *ctx, int N, int force_variant, double force_s
     return TTCF_OK;
 }
 
-// Cells of the neighbour build: the finest width in {r_l/2, 2r_l/3, r_l}
-// whose shared memory still lets the variant reach its target number of
-// resident CTAs per SM (finer cells = fewer candidates per list build).
-void pick_cells(ttcf_ctx *ctx, BatchHost &b, double rl) {
+// Cells of the neighbour build: width `frac` r_l (finer cells: fewer
+// candidates but more, shorter and more divergent rows per atom), or the
+// next coarser of {2r_l/3, r_l} whose shared memory still lets the variant
+// reach its target number of resident CTAs per SM.
+void pick_cells(ttcf_ctx *ctx, BatchHost &b, double rl, double frac) {
     const bool mixed = ctx->cfg.precision == TTCF_MIXED;
     const Variant v = variant_of(b.variant);
-    const double fracs[3] = {0.5, 2.0 / 3.0, 1.0};
+    const double fracs[3] = {frac, std::max(frac, 2.0 / 3.0), 1.0};
     for (int f = 0; f < 3; f++) {
         int nc[3];
         for (int k = 0; k < 3; k++) nc[k] = std::max(3, (int)floor(b.L[k] / (rl * fracs[f])));
@@ -208,7 +213,8 @@ void pick_cells(ttcf_ctx *ctx, BatchHost &b, double rl) {
 ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const double box[3], int G,
                        const double *soa, const double *alpha, const double *gamma,
                        int is_dev, const int *maps, int M, int S, double delta0,
-                       int force_variant = -1, double force_skin = -1.0) {
+                       int force_variant = -1, double force_skin = -1.0,
+                       double force_frac = -1.0) {
     const ttcf_config &cf = ctx->cfg;
     if (N < 4 || N > 4096) return fail(ctx, TTCF_E_INVALID, "n_atoms must be in [4, 4096]");
     if (G <= 0) return fail(ctx, TTCF_E_INVALID, "n_mothers must be positive");
@@ -230,7 +236,13 @@ ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const dou
         b.L[k] = box[k];
         b.snc[k] = (int)floor(box[k] / RC_WCA);
     }
-    pick_cells(ctx, b, rl);
+    {
+        double frac = DEFAULT_CELL_FRAC;
+        for (auto &e : ctx->tuned) if (e.N == N) frac = e.cell_frac;
+        if (cf.cell_frac > 0) frac = cf.cell_frac;
+        if (force_frac > 0) frac = force_frac;
+        pick_cells(ctx, b, rl, frac);
+    }
     b.sncell = b.snc[0] * b.snc[1] * b.snc[2];
     const double g = cf.dof_mode == 1 ? 3.0 * N - 3.0 : 3.0 * N;
     b.Q = g * cf.T * cf.tau_T * cf.tau_T;
@@ -847,6 +859,8 @@ ttcf_status ttcf_create(const ttcf_config *cfg, ttcf_ctx **out) {
     if (c.kernel_variant < 0 || c.kernel_variant > N_VARIANTS)
         return fail(nullptr, TTCF_E_INVALID, "kernel_variant out of range");
     if (c.skin > 1.0) return fail(nullptr, TTCF_E_INVALID, "skin must be <= 1");
+    if (c.cell_frac != 0.0 && !(c.cell_frac >= 0.4 && c.cell_frac <= 1.0))
+        return fail(nullptr, TTCF_E_INVALID, "cell_frac must be 0 or in [0.4, 1]");
     if ((c.dev_alloc == nullptr) != (c.dev_free == nullptr))
         return fail(nullptr, TTCF_E_INVALID, "dev_alloc and dev_free must be set together");
     ttcf_ctx *ctx = new (std::nothrow) ttcf_ctx();
@@ -1232,7 +1246,7 @@ ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_s
 
 ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
                           const double *soa, double shear_rate, int n_steps, int *best_variant,
-                          double *best_skin, double *best_ms) {
+                          double *best_skin, double *best_cell_frac, double *best_ms) {
     if (!ctx || !box || !soa || n_states < 1 || n_steps < 1)
         return fail(ctx, TTCF_E_INVALID, "bad autotune arguments");
     if (ctx->cfg.system != TTCF_BULK_WCA)
@@ -1242,7 +1256,8 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
     std::vector<double> gam(n_states, shear_rate);
     double best = 1e300;
     int bv = -1;
-    double bskin = DEFAULT_SKIN;
+    double bskin = DEFAULT_SKIN, bfrac = DEFAULT_CELL_FRAC;
+    const double fracs[2] = {0.5, 2.0 / 3.0};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1250,12 +1265,13 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
         const Variant var = variant_of(v);
         if (var.apt * var.maxt < n_atoms) continue;
         if (var.apt > 1 && (n_atoms + var.apt - 1) / var.apt < 64) continue;   // too few threads
-        for (double sk : skins) {
+        for (double sk : skins)
+        for (double fr : fracs) {
             if (3.0 * (RC_WCA + sk) > std::min(box[0], std::min(box[1], box[2]))) continue;
             BatchHost b;
             Pool pool(ctx);
             ttcf_status s = make_batch(ctx, pool, b, n_atoms, box, n_states, soa, nullptr, gam.data(),
-                                       0, maps, 4, n_steps + 1, 0.0, v, sk);
+                                       0, maps, 4, n_steps + 1, 0.0, v, sk, fr);
             if (s != TTCF_OK) continue;   // e.g. shared memory exceeded
             b.d0 = 0;
             RunArgs a;
@@ -1269,7 +1285,7 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; bv = v; bskin = sk; }
+            if (ms < best) { best = ms; bv = v; bskin = sk; bfrac = fr; }
         }
     }
     cudaEventDestroy(e0);
@@ -1277,10 +1293,11 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
     if (bv < 0) return fail(ctx, TTCF_E_INVALID, "no launch variant can run this system");
     bool found = false;
     for (auto &e : ctx->tuned)
-        if (e.N == n_atoms) { e.variant = bv; e.skin = bskin; found = true; }
-    if (!found) ctx->tuned.push_back({n_atoms, bv, bskin});
+        if (e.N == n_atoms) { e.variant = bv; e.skin = bskin; e.cell_frac = bfrac; found = true; }
+    if (!found) ctx->tuned.push_back({n_atoms, bv, bskin, bfrac});
     if (best_variant) *best_variant = bv + 1;
     if (best_skin) *best_skin = bskin;
+    if (best_cell_frac) *best_cell_frac = bfrac;
     if (best_ms) *best_ms = best;
     return TTCF_OK;
 }

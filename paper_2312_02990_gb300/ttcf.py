@@ -43,7 +43,8 @@ class Config(C.Structure):
                 ("n_steps", C.c_int), ("sample_every", C.c_int), ("mapping_mask", C.c_uint),
                 ("reset_alpha", C.c_int), ("keep_state", C.c_int), ("skin", C.c_double),
                 ("block_threads", C.c_int), ("kernel_variant", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
-                ("dev_free", FREE_FN), ("alloc_user", C.c_void_p), ("timeout_s", C.c_double)]
+                ("dev_free", FREE_FN), ("alloc_user", C.c_void_p), ("timeout_s", C.c_double),
+                ("cell_frac", C.c_double)]
 
 
 class ConfinedParams(C.Structure):
@@ -108,7 +109,7 @@ def load(build_if_missing: bool = False):
     L.ttcf_sample_mothers.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_int,
                                       C.c_int, _dp, _dp]
     L.ttcf_forces.argtypes = [vp, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp, _dp]
-    L.ttcf_autotune.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_int, ip, _dp, _dp]
+    L.ttcf_autotune.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_int, ip, _dp, _dp, _dp]
     L.ttcf_run_noalloc.argtypes = [C.POINTER(Config), C.c_int, _dp, C.c_int, vp, vp, vp, vp, vp, vp]
     L.ttcf_run_noalloc.restype = C.c_int
     fp = C.POINTER(C.c_float)
@@ -417,17 +418,18 @@ class Context:
         return out, al
 
     def autotune(self, soa, box, shear_rate: float = 1e-3, n_steps: int = 100):
-        """Pick the fastest launch variant and skin for this N (cached in the
-        context for later spawns); returns (variant, skin, ms)."""
+        """Pick the fastest launch variant, skin and list-cell width for this
+        N (cached in the context for later spawns); returns (variant, skin,
+        cell_frac, ms)."""
         s = _f64(soa)
         if s.ndim == 2:
             s = s[None]
         n, _, N = s.shape
-        v, sk, ms = C.c_int(), C.c_double(), C.c_double()
+        v, sk, fr, ms = C.c_int(), C.c_double(), C.c_double(), C.c_double()
         self._check(self._L.ttcf_autotune(self.h, int(N), _ptr(_box(box)), int(n), _ptr(s),
                                           float(shear_rate), int(n_steps), C.byref(v),
-                                          C.byref(sk), C.byref(ms)))
-        return v.value, sk.value, ms.value
+                                          C.byref(sk), C.byref(fr), C.byref(ms)))
+        return v.value, sk.value, fr.value, ms.value
 
     # -- learned control variate --
     def cv_data(self, batch: int, n_daughters: int):
