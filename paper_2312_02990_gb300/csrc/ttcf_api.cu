@@ -1572,11 +1572,26 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path) {
         r.get(b.V); r.get(b.Q); r.get(b.gT);
         r.bytes(b.nc, sizeof(b.nc)); r.get(b.ncell); r.bytes(b.snc, sizeof(b.snc)); r.get(b.sncell);
         r.get(b.d0); r.get(b.variant); r.get(b.threads); r.get(b.skin);
-        if (!r.ok || b.N < 1 || b.N > CONF_NMAX || b.M < 1 || b.M > 4 || b.G < 1 || b.S < 1 ||
-            b.S != c.n_steps / c.sample_every + 1 || b.n_obs < 1 || b.n_obs > CONF_NOBS ||
-            b.ncell < 1 || b.sncell < 1 || b.d0 < 0 || b.variant < 0 || b.variant >= N_VARIANTS)
-            return bad(TTCF_E_INVALID, "checkpoint batch header out of range");
         b.confined = conf != 0;
+        // the kernels index shared arrays with these numbers: check that they
+        // are the ones the spawn calls would have chosen
+        bool okh = r.ok && b.M >= 1 && b.M <= 4 && b.G >= 1 && b.S == c.n_steps / c.sample_every + 1 &&
+                   b.d0 >= 0 && b.skin > 0 && b.skin <= 1.0 &&
+                   b.n_obs == (b.confined ? CONF_NOBS : 1) && b.confined == (c.system == TTCF_CONFINED_LJ) &&
+                   b.N >= 4 && b.N <= (b.confined ? CONF_NMAX : 4096);
+        for (int k = 0; k < 3 && okh; k++)
+            okh = isfinite(b.L[k]) && b.L[k] > 0 && b.nc[k] >= (b.confined ? 1 : 3) && b.nc[k] <= 4096 &&
+                  b.snc[k] >= 1 && b.snc[k] <= 4096;
+        okh = okh && b.ncell == b.nc[0] * b.nc[1] * b.nc[2] && b.sncell == b.snc[0] * b.snc[1] * b.snc[2];
+        for (int k = 0; k < b.M && okh; k++) okh = b.maps[k] >= 0 && b.maps[k] <= 3;
+        if (okh && !b.confined) {
+            okh = b.variant >= 0 && b.variant < N_VARIANTS;
+            if (okh) {
+                const Variant v = variant_of(b.variant);
+                okh = b.threads >= 32 && b.threads % 32 == 0 && b.threads <= v.maxt && b.threads * v.apt >= b.N;
+            }
+        }
+        if (!okh) return bad(TTCF_E_INVALID, "checkpoint batch header out of range");
         b.gamma.resize(b.G);
         r.bytes(b.gamma.data(), sizeof(double) * b.G);
         r.get(b.A); r.get(b.rc); r.get(b.k_tether); r.get(b.c_ff); r.get(b.c_wf); r.get(b.c_ww);

@@ -1,6 +1,9 @@
 """Checkpoints (ttcf_save / ttcf_load) through the C ABI: a run interrupted,
 written to disk and continued in a new context gives bitwise the series of
 an uninterrupted run; a finished run reloads with identical responses."""
+import ctypes
+import struct
+
 import numpy as np
 import pytest
 
@@ -114,4 +117,27 @@ def test_checkpoint_errors(T, eq_mothers_256, tmp_path):
     with ctx(T, n_steps=40) as c:
         with pytest.raises(T.TTCFError) as e:
             c.load(str(trunc))
+        assert e.value.status == T.TTCF_E_INVALID
+
+
+def test_tampered_header_is_rejected(T, eq_mothers_256, tmp_path):
+    """A checkpoint whose cell count disagrees with its cell grid (the
+    kernels index shared memory with it) is refused, not run."""
+    b, ms, al = eq_mothers_256
+    path = tmp_path / "t.ckpt"
+    with ctx(T, n_steps=40) as c:
+        c.spawn_daughters(ms[:2], al[:2], 1e-3, box=b.L)
+        c.run(10)
+        c.save(str(path))
+    raw = bytearray(path.read_bytes())
+    off = 8 + 4 + ctypes.sizeof(T.Config) + 4 + 8 + 4 + 6 * 4 + 16 + 24 + 24 + 12   # ncell
+    ncell = struct.unpack_from("<i", raw, off)[0]
+    nc = struct.unpack_from("<3i", raw, off - 12)
+    assert ncell == nc[0] * nc[1] * nc[2]
+    struct.pack_into("<i", raw, off, ncell + 7)
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(bytes(raw))
+    with ctx(T, n_steps=40) as c:
+        with pytest.raises(T.TTCFError) as e:
+            c.load(str(bad))
         assert e.value.status == T.TTCF_E_INVALID
