@@ -80,6 +80,7 @@ def parse():
     p.add_argument("--no-confined", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-floor", action="store_true", help="skip the precision-floor sweep")
+    p.add_argument("--no-gk", action="store_true", help="skip the Green-Kubo cross-check")
     p.add_argument("--confined-only", action="store_true",
                    help="run only the confined-channel section and print its JSON")
     p.add_argument("--conf-chains", type=int, default=38, help="independent confined mother chains")
@@ -345,6 +346,8 @@ def bench_gb300(args):
         line["confined"] = confined_section(T, torch, args)
     if not args.no_floor and rank == 0:
         line["precision_floor"] = precision_floor_section(T, torch, args)
+    if not args.no_gk and rank == 0:
+        line["green_kubo"] = green_kubo_section(T, torch, args, N, L)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, N)
     if rank == 0:
@@ -422,6 +425,29 @@ def cv_section(T, torch, args):
             "train_loss_first_last": [float(loss[0]), float(loss[-1])],
             "groups": {"train": n_tr, "eval": n_ev, "aux": n_aux}, "daughter_steps": args.cv_steps,
             "seconds": {"mothers": t_moth, "run": t_run, "train": t_train, "apply": t_apply}}
+
+
+def green_kubo_section(T, torch, args, N, L):
+    """Zero-field cross-check of the TTCF viscosity: the Green-Kubo integral
+    (V/T) int <P_xy(0)P_xy(t)> dt over 152 GPU mother chains of the same
+    system (4000 thermalisation steps, then 20000 recorded steps), at the
+    TTCF daughters' t_end; standard error over chains."""
+    from paper_2312_02990_gb300 import inputs
+    chains, n_eq, n, lag = 152, 4000, 20000, args.daughter_steps
+    init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 70000 + k) for k in range(chains)])
+    t0 = time.perf_counter()
+    with T.Context(T.config_default()) as c:
+        r = c.mother_acf(init, L, n_eq=n_eq, n_steps=n, max_lag=lag, want_series=True)
+    el = time.perf_counter() - t0
+    B = r["series"]
+    V, dt, Tt = float(np.prod(L)), 0.0025, 0.722
+    per = []
+    for g in range(chains):   # each chain's own estimate, for the spread
+        b = B[g]
+        acf = np.array([np.mean(b[:n - k] * b[k:]) for k in range(0, lag + 1, 10)])
+        per.append(V / Tt * float(np.sum(0.5 * (acf[1:] + acf[:-1])) * 10 * dt))
+    return {"eta_gk_t_end": float(r["eta_gk"][-1]), "eta_gk_se": float(np.std(per, ddof=1) / np.sqrt(chains)),
+            "t_end": lag * dt, "chains": chains, "steps_per_chain": n, "seconds": el}
 
 
 def precision_floor_section(T, torch, args):

@@ -239,6 +239,23 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
                                 const double *init_soa, int n_eq, int n_states, int spacing,
                                 double *out_soa, double *out_alpha);
 
+/* Equilibrium correlations along GPU mother trajectories (the mother-side
+ * tool for choosing the spacing of mother states, cf. Fig. 7, and the
+ * Green-Kubo form of Eq. 8 at zero field): from each of n_init initial
+ * phase points [n_init][6][N] (host), n_eq zero-field Nose-Hoover steps,
+ * then n_steps steps recording B(s) = P_xy(s) every step.  Averaged over
+ * trajectories and time origins, for lags k = 0 .. max_lag steps:
+ *   acf_pxy[k]  = <P_xy(t) P_xy(t+k)>   (the correlation of Omega for the
+ *                 shear field, Omega being proportional to P_xy),
+ *   acf_pxy2[k] = autocovariance of P_xy^2 (that of Omega P_xy),
+ *   eta_gk[k]   = (V/T) trapezoid integral of acf_pxy up to lag k.
+ * series (may be NULL) receives P_xy [n_init][n_steps].  Host outputs of
+ * length max_lag + 1 (any may be NULL).  Errors: TTCF_E_INVALID,
+ * TTCF_E_NUMERIC (a trajectory failed), TTCF_E_OOM, TTCF_E_CUDA.          */
+ttcf_status ttcf_mother_acf(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_init,
+                            const double *init_soa, int n_eq, int n_steps, int max_lag,
+                            double *acf_pxy, double *acf_pxy2, double *eta_gk, double *series);
+
 /* Pair forces of n_states phase points [n_states][6][N] (host; rows 0-2
  * used) at Lees-Edwards offset delta, with the context's precision and the
  * same device code the daughters use: F [n_states][3][N] and virial

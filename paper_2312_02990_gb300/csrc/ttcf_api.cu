@@ -1202,6 +1202,68 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
     return TTCF_OK;
 }
 
+ttcf_status ttcf_mother_acf(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_init,
+                            const double *init_soa, int n_eq, int n_steps, int max_lag,
+                            double *acf_pxy, double *acf_pxy2, double *eta_gk, double *series) {
+    if (!ctx || !box || !init_soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (ctx->cfg.system != TTCF_BULK_WCA)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_mother_acf needs a TTCF_BULK_WCA context");
+    if (n_eq < 0 || n_steps < 2 || max_lag < 0 || max_lag >= n_steps || n_init < 1 ||
+        (long long)n_eq + n_steps > 2000000000LL)
+        return fail(ctx, TTCF_E_INVALID, "bad correlation schedule");
+    const int maps[1] = {0};
+    const int S = n_steps + 1;
+    BatchHost b;
+    Pool pool(ctx);
+    ttcf_status s = make_batch(ctx, pool, b, n_atoms, box, n_init, init_soa, nullptr, nullptr, 0,
+                               maps, 1, S, 0.0);
+    if (s != TTCF_OK) return s;
+    b.d0 = 0;
+    b.state = pool.get<unsigned long long>((size_t)n_init * 6 * n_atoms);
+    double *acf = pool.get<double>((size_t)max_lag + 1), *acf2 = pool.get<double>((size_t)max_lag + 1);
+    double *m2 = pool.get<double>(1);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (correlations)");
+    std::vector<BatchHost *> bs = {&b};
+    int launches = 0;
+    RunArgs a;
+    memset(&a, 0, sizeof(a));
+    a.dt = ctx->cfg.dt;
+    a.reset_alpha = 1;
+    if (n_eq > 0) {   // thermalisation, no samples, state kept
+        a.step0 = 0; a.step1 = n_eq; a.sample_every = n_eq + 1; a.fresh = 1; a.save_state = 1;
+        s = launch_batches(ctx, pool, bs, a, launches);
+        if (s != TTCF_OK) return s;
+    }
+    // production: B(s) = P_xy(s) every step, s = 1 .. n_steps (row index s)
+    a.step0 = 0; a.step1 = n_steps; a.sample_every = 1; a.fresh = n_eq > 0 ? 0 : 1; a.save_state = 0;
+    s = launch_batches(ctx, pool, bs, a, launches);
+    if (s != TTCF_OK) return s;
+    CK(launch_acf(b.B, n_init, S, 1, n_steps, max_lag, acf, acf2, m2, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<int> stv(n_init);
+    CK(cudaMemcpy(stv.data(), b.status, sizeof(int) * n_init, cudaMemcpyDeviceToHost));
+    for (int v : stv)
+        if (v) return fail(ctx, TTCF_E_NUMERIC, "a mother trajectory failed");
+    std::vector<double> h((size_t)max_lag + 1);
+    CK(cudaMemcpy(h.data(), acf, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    if (acf_pxy) memcpy(acf_pxy, h.data(), sizeof(double) * h.size());
+    if (acf_pxy2) CK(cudaMemcpy(acf_pxy2, acf2, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    if (eta_gk) {   // Green-Kubo running integral (V/T) int_0^t C(s) ds, trapezoid
+        const double f = b.V / ctx->cfg.T;
+        double run = 0.0;
+        eta_gk[0] = 0.0;
+        for (int k = 1; k <= max_lag; k++) {
+            run += 0.5 * ctx->cfg.dt * (h[k - 1] + h[k]);
+            eta_gk[k] = f * run;
+        }
+    }
+    if (series)
+        for (int g = 0; g < n_init; g++)
+            CK(cudaMemcpy(series + (size_t)g * n_steps, b.B + (size_t)g * S + 1, sizeof(double) * n_steps,
+                          cudaMemcpyDeviceToHost));
+    return TTCF_OK;
+}
+
 ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
                         double delta, const double *soa, double *F, double *W, double *U) {
     if (!ctx || !box || !soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");

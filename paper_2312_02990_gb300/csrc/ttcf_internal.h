@@ -57,6 +57,12 @@ struct ReduceArgs {
 };
 cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 
+// Time autocorrelations of B[g][s0 .. s0+n) (row stride S) over G
+// trajectories for lags 0 .. max_lag (< n): acf = <B(t)B(t+k)>, acf2 of
+// B^2 - <B^2>; m2 (device scalar) receives <B^2>.
+cudaError_t launch_acf(const double *B, int G, int S, int s0, int n, int max_lag, double *acf,
+                       double *acf2, double *m2, cudaStream_t st);
+
 // Sets the text returned by ttcf_last_error(NULL) (calls without a context).
 void set_global_error(const char *msg);
 

@@ -123,4 +123,60 @@ cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------- equilibrium correlations --
+// Time autocorrelation of the series B[g][s0 .. s0+n) of G trajectories,
+// averaged over trajectories and time origins (one CTA per lag, fixed-order
+// sums):  acf[k]  = <B(t) B(t+k)>,
+//         acf2[k] = <(B^2(t) - m2)(B^2(t+k) - m2)>,  m2 = <B^2>.
+__device__ double block_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+    __syncthreads();
+    return t;   // valid in thread 0
+}
+
+__global__ void acf_mean2_kernel(const double *B, int G, int S, int s0, int n, double *m2) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (long long q = threadIdx.x; q < (long long)G * n; q += blockDim.x) {
+        const double b = B[(q / n) * S + s0 + q % n];
+        v += b * b;
+    }
+    const double t = block_sum(v, sh);
+    if (threadIdx.x == 0) *m2 = t / ((double)G * n);
+}
+
+__global__ void acf_kernel(const double *B, int G, int S, int s0, int n, const double *m2p,
+                           double *acf, double *acf2) {
+    __shared__ double sh[32];
+    const int k = blockIdx.x;
+    const int m = n - k;   // time origins at lag k
+    const double m2 = *m2p;
+    double v1 = 0.0, v2 = 0.0;
+    for (long long q = threadIdx.x; q < (long long)G * m; q += blockDim.x) {
+        const double *b = B + (q / m) * S + s0 + q % m;
+        const double a0 = b[0], ak = b[k];
+        v1 += a0 * ak;
+        v2 += (a0 * a0 - m2) * (ak * ak - m2);
+    }
+    const double t1 = block_sum(v1, sh);
+    const double t2 = block_sum(v2, sh);
+    if (threadIdx.x == 0) {
+        acf[k] = t1 / ((double)G * m);
+        acf2[k] = t2 / ((double)G * m);
+    }
+}
+
+cudaError_t launch_acf(const double *B, int G, int S, int s0, int n, int max_lag, double *acf,
+                       double *acf2, double *m2, cudaStream_t st) {
+    acf_mean2_kernel<<<1, 256, 0, st>>>(B, G, S, s0, n, m2);
+    acf_kernel<<<max_lag + 1, 256, 0, st>>>(B, G, S, s0, n, m2, acf, acf2);
+    return cudaGetLastError();
+}
+
 }  // namespace ttcf

@@ -28,7 +28,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 # The C ABI exported by libttcf.so (kept in sync with include/ttcf.h).
 EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_run",
            "ttcf_response", "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
-           "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_forces", "ttcf_autotune",
+           "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_mother_acf",
+           "ttcf_forces", "ttcf_autotune",
            "ttcf_run_noalloc", "ttcf_cv_config_default", "ttcf_cv_data", "ttcf_cv_train",
            "ttcf_cv_apply", "ttcf_cv_get_model", "ttcf_cv_forward", "ttcf_cv_gradient",
            "ttcf_confined_params_default", "ttcf_spawn_confined", "ttcf_sample_mothers_confined",
@@ -131,6 +132,9 @@ def load(build_if_missing: bool = False):
     L.ttcf_sample_mothers_confined.argtypes = [vp, C.c_int, _dp, vp, vp, C.POINTER(ConfinedParams),
                                                C.c_int, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, ip]
     L.ttcf_response_obs.argtypes = [vp, C.c_int, C.c_int, C.c_int] + [_dp] * 7 + [C.c_int, ip]
+    L.ttcf_mother_acf.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_int, C.c_int,
+                                  _dp, _dp, _dp, _dp]
+    L.ttcf_mother_acf.restype = C.c_int
     L.ttcf_friction.argtypes = [vp, C.c_int, C.c_int] + [_dp] * 5 + [C.c_int, ip]
     L.ttcf_friction.restype = C.c_int
     L.ttcf_save.argtypes = [vp, C.c_char_p]
@@ -416,6 +420,25 @@ class Context:
                                                 _ptr(init), int(n_eq), int(n_states), int(spacing),
                                                 _ptr(out), _ptr(al)))
         return out, al
+
+    def mother_acf(self, init_soa, box, n_eq: int, n_steps: int, max_lag: int,
+                   want_series: bool = False) -> dict:
+        """Equilibrium P_xy correlations and the Green-Kubo integral along
+        GPU mother trajectories (see ttcf_mother_acf)."""
+        init = _f64(init_soa)
+        if init.ndim == 2:
+            init = init[None]
+        n_init, _, N = init.shape
+        out = {k: np.zeros(max_lag + 1) for k in ("acf_pxy", "acf_pxy2", "eta_gk")}
+        ser = np.zeros((n_init, n_steps)) if want_series else None
+        self._check(self._L.ttcf_mother_acf(self.h, int(N), _ptr(_box(box)), int(n_init), _ptr(init),
+                                            int(n_eq), int(n_steps), int(max_lag),
+                                            _ptr(out["acf_pxy"]), _ptr(out["acf_pxy2"]),
+                                            _ptr(out["eta_gk"]),
+                                            _ptr(ser) if ser is not None else None))
+        if ser is not None:
+            out["series"] = ser
+        return out
 
     def autotune(self, soa, box, shear_rate: float = 1e-3, n_steps: int = 100):
         """Pick the fastest launch variant, skin and list-cell width for this
