@@ -324,7 +324,7 @@ BatchDev to_dev(const BatchHost &b) {
 }
 
 struct ClassLaunch {
-    int variant, threads, nmax, ncellmax, grid;
+    int variant, threads, nmax, ncellmax, grid, cpos;
     size_t smem;
     std::vector<int> work;
 };
@@ -335,7 +335,7 @@ std::vector<ClassLaunch> plan_classes(ttcf_ctx *ctx, std::vector<BatchHost *> &b
     for (BatchHost *b : bs) {
         ClassLaunch *c = nullptr;
         for (auto &x : cls) if (x.variant == b->variant && x.threads == b->threads) c = &x;
-        if (!c) { cls.push_back({b->variant, b->threads, 0, 0, 0, 0, {}}); c = &cls.back(); }
+        if (!c) { cls.push_back({b->variant, b->threads, 0, 0, 0, 0, 0, {}}); c = &cls.back(); }
         c->nmax = std::max(c->nmax, b->N);
         c->ncellmax = std::max(c->ncellmax, b->ncell);
         for (long long k = 0; k < b->D(); k++) c->work.push_back((int)(b->d0 + k));
@@ -344,8 +344,19 @@ std::vector<ClassLaunch> plan_classes(ttcf_ctx *ctx, std::vector<BatchHost *> &b
     for (auto &c : cls) {
         c.smem = daughter_smem_bytes(mixed, c.nmax, c.ncellmax);
         c.grid = 0;
+        c.cpos = 0;
         if (c.smem > (size_t)ctx->smem_optin) continue;   // rejected by the caller
         int nb = daughter_occupancy(mixed, c.variant, c.threads, c.smem);
+        {   // the cell-ordered list build where its larger shared memory keeps
+            // the variant's resident CTAs per SM
+            const size_t s2 = daughter_smem_bytes(mixed, c.nmax, c.ncellmax, true);
+            if (s2 <= (size_t)ctx->smem_optin) {
+                const int nb2 = daughter_occupancy(mixed, c.variant, c.threads, s2);
+                if (nb2 >= 1 && nb2 >= std::min(nb, variant_of(c.variant).minb)) {
+                    c.cpos = 1; c.smem = s2; nb = nb2;
+                }
+            }
+        }
         if (nb < 1) nb = 1;
         c.grid = (int)std::min<long long>((long long)c.work.size(), (long long)nb * ctx->nsm);
         if (c.grid < 1) c.grid = 1;
@@ -440,6 +451,7 @@ ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &
             a.n_work = (int)cls[k].work.size();
             a.queue = d_q + k;
             a.nbr = d_nbr[k]; a.nmax = cls[k].nmax; a.ncellmax = cls[k].ncellmax;
+            a.cpos = cls[k].cpos;
             CK(launch_daughters(mixed, cls[k].variant, a, cls[k].threads, cls[k].grid, cls[k].smem, side[k]));
             launches++;
             ctx->stats.block_threads = std::max(ctx->stats.block_threads, cls[k].threads);

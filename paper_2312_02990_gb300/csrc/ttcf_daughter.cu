@@ -168,15 +168,21 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     if constexpr (MIXED) {
         pos4 = (float4 *)sp; sp += (size_t)nmax * 16;
         plo4 = (float4 *)sp; sp += (size_t)nmax * 16;
-    } else {
-        xd = (double *)sp; sp += (size_t)nmax * 8;
-        yd = (double *)sp; sp += (size_t)nmax * 8;
-        zd = (double *)sp; sp += (size_t)nmax * 8;
+    } else {   // each array padded to 16 bytes: ref4 below must stay float4-aligned
+        const size_t dn = ((size_t)nmax * 8 + 15) / 16 * 16;
+        xd = (double *)sp; sp += dn;
+        yd = (double *)sp; sp += dn;
+        zd = (double *)sp; sp += dn;
     }
     float4 *ref4 = (float4 *)sp; sp += (size_t)nmax * 16;
+    // cell-ordered copy of the wrapped positions (index in w), or the cell
+    // members' indices alone where shared memory is short
+    float4 *cpos = nullptr;
+    unsigned short *catom = nullptr;
+    if (a.cpos) { cpos = (float4 *)sp; sp += (size_t)nmax * 16; }
     int *cnt = (int *)sp; sp += (size_t)ncm * 4;
     int *start = (int *)sp; sp += (size_t)(ncm + 2) * 4;
-    unsigned short *catom = (unsigned short *)sp; sp += ((size_t)nmax * 2 + 15) / 16 * 16;
+    if (!a.cpos) { catom = (unsigned short *)sp; sp += ((size_t)nmax * 2 + 15) / 16 * 16; }
     Coef<S> *cf = (Coef<S> *)sp; sp += (sizeof(Coef<S>) + 15) / 16 * 16;
     Misc *m = (Misc *)sp;
 
@@ -331,7 +337,15 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         __syncthreads();
         for (int q = 0; q < APT; q++) {
             const int i = tid + q * T;
-            if (i < N) catom[start[mycell[q]] + myslot[q]] = (unsigned short)i;
+            if (i >= N) continue;
+            const int t = start[mycell[q]] + myslot[q];
+            if (cpos) {
+                float wx, wy, wz;
+                wrapped(i, wx, wy, wz);
+                cpos[t] = make_float4(wx, wy, wz, __int_as_float(i));
+            } else {
+                catom[t] = (unsigned short)i;
+            }
         }
         __syncthreads();
         const float rl = sqrtf(cf->rl2);
@@ -350,9 +364,16 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                 ncnt[q] = 0;
                 continue;
             }
+            // accepted neighbours are appended during the scan and sorted
+            // once after it: an insertion inside the divergent scan loops
+            // would be paid by every lane of the warp at nearly every
+            // candidate
             unsigned short lst[CAP];
             int k = 0;
-            bool ovf = false;
+            auto push = [&](int j) {
+                if (k < CAP) lst[k] = (unsigned short)j;
+                k++;
+            };
             // windows [w - r_l, w + r_l] in cell units; |w| <= L keeps them small
             const float hl0 = 0.5f * cf->Lf[0], hl1 = 0.5f * cf->Lf[1], hl2 = 0.5f * cf->Lf[2];
             const float s0 = (float)nc[0] * cf->invLf[0], s1 = (float)nc[1] * cf->invLf[1],
@@ -362,43 +383,65 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             const int y0 = ifloor((wy - rl + hl1) * s1);
             const int y1 = min(ifloor((wy + rl + hl1) * s1), y0 + nc[1] - 1);
             // window indices lie in [-nc, 2nc): wrap by one conditional add
+            const float rl2 = cf->rl2;
             for (int zu = z0; zu <= z1; zu++) {
-                const int zz = zu < 0 ? zu + nc[2] : (zu >= nc[2] ? zu - nc[2] : zu);
+                const int kz = zu < 0 ? -1 : (zu >= nc[2] ? 1 : 0);   // periodic image in z
+                const int zz = zu - kz * nc[2];
+                const float uz = wz - (float)kz * cf->Lf[2];
                 for (int yu = y0; yu <= y1; yu++) {
                     const int cross = yu < 0 ? -1 : (yu >= nc[1] ? 1 : 0);
                     const int yy = yu - cross * nc[1];
+                    const float uy = wy - (float)cross * cf->Lf[1];
                     // the row across the y face is seen shifted by cross*delta
                     const float xs = wx - (float)cross * cf->delta_f;
                     int x0 = ifloor((xs - rl + hl0) * s0);
                     int x1 = min(ifloor((xs + rl + hl0) * s0), x0 + nc[0] - 1);
                     const int row = (zz * nc[1] + yy) * nc[0];
-                    // the x window as one or two contiguous runs of cell-sorted atoms
-                    int ra[2], rb[2], nr = 0;
+                    // the x window as one or two contiguous runs of cell-sorted
+                    // atoms; run r holds the periodic image kx + r in x.
                     // x0 lies in [-2nc, 2nc): two conditional wraps
-                    int a0 = x0 < 0 ? x0 + nc[0] : (x0 >= nc[0] ? x0 - nc[0] : x0);
-                    a0 = a0 < 0 ? a0 + nc[0] : (a0 >= nc[0] ? a0 - nc[0] : a0);
+                    int a0 = x0, kx = 0;
+                    if (a0 < 0) { a0 += nc[0]; kx = -1; } else if (a0 >= nc[0]) { a0 -= nc[0]; kx = 1; }
+                    if (a0 < 0) { a0 += nc[0]; kx -= 1; } else if (a0 >= nc[0]) { a0 -= nc[0]; kx += 1; }
+                    int ra[2], rb[2], nr = 0;
                     const int b0 = a0 + (x1 - x0);
                     if (b0 < nc[0]) { ra[0] = a0; rb[0] = b0; nr = 1; }
                     else { ra[0] = a0; rb[0] = nc[0] - 1; ra[1] = 0; rb[1] = b0 - nc[0]; nr = 2; }
                     for (int r = 0; r < nr; r++) {
                         const int t1 = start[row + rb[r] + 1];
-                        for (int t = start[row + ra[r]]; t < t1; t++) {
-                            const int j = catom[t];
-                            if (j == i) continue;
-                            R dx, dy, dz;
-                            pair_vec(i, j, dx, dy, dz);
-                            const float r2 = (float)(dx * dx + dy * dy + dz * dz);
-                            if (r2 < cf->rl2) {
-                                if (k == CAP) { ovf = true; continue; }
-                                int pi = k++;
-                                while (pi > 0 && lst[pi - 1] > j) { lst[pi] = lst[pi - 1]; pi--; }
-                                lst[pi] = (unsigned short)j;
+                        if (cpos) {
+                            // i against the image of each member: one shared load
+                            // and the distance to a fixed shift, no rounding
+                            const float ux = xs - (float)(kx + r) * cf->Lf[0];
+                            for (int t = start[row + ra[r]]; t < t1; t++) {
+                                const float4 v = cpos[t];
+                                const float dx = ux - v.x, dy = uy - v.y, dz = uz - v.z;
+                                const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+                                if (r2 < rl2) {
+                                    const int j = __float_as_int(v.w);
+                                    if (j != i) push(j);
+                                }
+                            }
+                        } else {
+                            for (int t = start[row + ra[r]]; t < t1; t++) {
+                                const int j = catom[t];
+                                if (j == i) continue;
+                                R dx, dy, dz;
+                                pair_vec(i, j, dx, dy, dz);
+                                const float r2 = (float)(dx * dx + dy * dy + dz * dz);
+                                if (r2 < rl2) push(j);
                             }
                         }
                     }
                 }
             }
-            if (ovf) m->flag_ovf = 1;
+            if (k > CAP) { m->flag_ovf = 1; k = CAP; }
+            for (int e = 1; e < k; e++) {   // insertion sort by neighbour index
+                const unsigned short v = lst[e];
+                int pi = e;
+                while (pi > 0 && lst[pi - 1] > v) { lst[pi] = lst[pi - 1]; pi--; }
+                lst[pi] = v;
+            }
             // eight entries per 16-byte chunk, two per word; an odd tail is
             // padded with i itself (r = 0 is rejected by the force loop)
             for (int t = 0; t < k; t += 8) {

@@ -218,6 +218,9 @@ struct RunArgs {
     int snap_first, snap_every, n_snap;
     double *force_out;             // [D][3][N] forces at step0, or null
     double *wxy_out;               // [D] virial W_xy at step0, or null
+    int cpos;                      // shared-memory layout: 1 = cell-ordered wrapped
+                                   // positions for the list build, 0 = cell members'
+                                   // indices only (see daughter_smem_bytes)
 };
 
 // Launch variants of the daughter kernel: atoms per thread, maximum block
@@ -243,11 +246,14 @@ __host__ __device__ inline int default_variant(int N) {
 }
 
 // Shared-memory bytes of a daughter CTA (must match the carve-up in
-// ttcf_daughter.cu).
-__host__ __device__ inline size_t daughter_smem_bytes(bool mixed, int nmax, int ncellmax) {
-    size_t b = mixed ? (size_t)nmax * 48 : (size_t)nmax * (24 + 16);
+// ttcf_daughter.cu).  cpos: the list build reads a cell-ordered copy of the
+// wrapped positions (16 bytes per atom) instead of the cell members' indices
+// (2 bytes per atom).
+__host__ __device__ inline size_t daughter_smem_bytes(bool mixed, int nmax, int ncellmax,
+                                                      bool cpos = false) {
+    size_t b = mixed ? (size_t)nmax * 48 : 3 * (((size_t)nmax * 8 + 15) / 16 * 16) + (size_t)nmax * 16;
     b += (size_t)ncellmax * 4 + (size_t)(ncellmax + 2) * 4;
-    b += ((size_t)nmax * 2 + 15) / 16 * 16;
+    b += cpos ? (size_t)nmax * 16 : ((size_t)nmax * 2 + 15) / 16 * 16;
     b += 2048;   // coefficients, reduction slots and flags
     return b;
 }

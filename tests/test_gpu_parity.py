@@ -72,6 +72,34 @@ def test_forces_match_oracle(ttcf, precision, N):
             assert np.all(W[0, [0, 1, 2, 4, 5]] == pytest.approx(Wo[[0, 1, 2, 4, 5]], rel=1e-11))
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_odd_atom_count(ttcf, precision):
+    """N = 255 (one atom taken out of a 256-atom state): forces and a 30-step
+    run against the oracle.  With an odd N the FP64 position arrays end off
+    a 16-byte boundary, which the shared-memory layout pads for the float4
+    arrays behind them."""
+    N = 255
+    L = tuple(inputs.bulk_box(256))
+    b = oracle.Bulk(n=N, L=L)
+    st = np.ascontiguousarray(inputs.jittered_states(256, 2, seed=17, amp=0.1)[:, :, 1:])
+    with ctx(ttcf, precision=precision) as c:
+        F, W, U = c.forces(st[0], b.L, 0.0)
+    Fo, Wo, Uo = oracle.forces(b, st[0], 0.0)
+    err = np.linalg.norm(F[0] - Fo) / np.linalg.norm(Fo)
+    assert err < (1e-11 if precision == 0 else 1e-5), err
+    assert U[0] == pytest.approx(Uo, rel=1e-11)
+    gamma, n = 0.02, 30
+    with ctx(ttcf, precision=precision, n_steps=n) as c:
+        bid = c.spawn_daughters(st, None, gamma, box=b.L)
+        c.run()
+        B, _ = c.daughter_series(bid, 8)
+        stat = c.group_status(bid, 2)
+    assert np.all(stat == 0)
+    for d in range(8):
+        Bo = oracle.daughter(b, st[d // 4], 0.0, d % 4, gamma, n)[0]
+        assert np.abs(B[d] - Bo).max() < (1e-10 if precision == 0 else 1e-4) * np.abs(Bo).max()
+
+
 # -------------------------------------------------------------- spawn ----
 def test_spawn_matches_oracle_and_cancels_exactly(ttcf, eq_mothers_256):
     b, ms, al = eq_mothers_256
