@@ -1137,6 +1137,8 @@ ttcf_status ttcf_get_state(ttcf_ctx *ctx, int batch_id, int daughter, double *so
                   cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(sc, b->scal + (size_t)daughter * 4, sizeof(sc), cudaMemcpyDeviceToHost));
     const bool mixed = ctx->cfg.precision == TTCF_MIXED;
+    if (mixed)   // alpha, K2, e1, delta kept as float pairs in MIXED mode
+        for (int k = 0; k < 4; k++) { float2 v; memcpy(&v, &sc[k], 8); sc[k] = (double)v.x + (double)v.y; }
     auto val = [&](size_t k) {
         if (mixed) { float2 v; memcpy(&v, &sl[k], 8); return (double)v.x + (double)v.y; }
         double v; memcpy(&v, &sl[k], 8); return v;
@@ -1508,7 +1510,7 @@ extern "C++" {
 namespace {
 
 constexpr char CKPT_MAGIC[8] = {'T', 'T', 'C', 'F', 'C', 'K', 'P', '1'};
-constexpr int CKPT_VERSION = 1;
+constexpr int CKPT_VERSION = 2;   // 2: MIXED per-daughter scalars as float pairs
 
 struct FileW {
     FILE *f;

@@ -14,9 +14,10 @@
 //   phase B  WCA pair forces (Eq. 6) and virial W_xy over sorted lists
 //   phase C  p += (h/2) F, p_x -= gamma (h/2) p_y, per-warp partial sums
 //                                                              -> barrier 2
-//   lane 0   in IEEE double: the two Nose-Hoover half-steps of alpha, the
-//            factor exp(-alpha h/2) - 1, the sample B(s) = P_xy(s) of
-//            Eq. 7, the Lees-Edwards offset                    -> barrier 3
+//   lane 0   the two Nose-Hoover half-steps of alpha, the factor
+//            exp(-alpha h/2) - 1, the sample B(s) = P_xy(s) of Eq. 7, the
+//            Lees-Edwards offset (double-float in MIXED mode, IEEE double
+//            in FP64 mode; B(s) is stored as IEEE double)     -> barrier 3
 // Lists are sorted by neighbour index and only pairs with r < r_c
 // contribute, so forces are a function of the positions alone; positions
 // are wrapped into the box every WRAP_EVERY steps of absolute time; hence
@@ -44,6 +45,9 @@ __device__ __forceinline__ double sdbl(double a) { return a; }
 template <class S> __device__ __forceinline__ S sfrom(double x);
 template <> __device__ __forceinline__ df sfrom<df>(double x) { return df_from_double(x); }
 template <> __device__ __forceinline__ double sfrom<double>(double x) { return x; }
+template <class S> __device__ __forceinline__ S sfrom_df(df x);
+template <> __device__ __forceinline__ df sfrom_df<df>(df x) { return x; }
+template <> __device__ __forceinline__ double sfrom_df<double>(df x) { return df_to_double(x); }
 
 template <class S> __device__ __forceinline__ S load_slot(const unsigned long long *p);
 template <> __device__ __forceinline__ df load_slot<df>(const unsigned long long *p) {
@@ -77,6 +81,7 @@ struct Coef {
     int stop;
     int snap;              // snapshot index written after this step, or -1
     double fsnap;          // pending momentum factor for the snapshot
+    S f1;                  // (1 + e1)^2, the momentum factor still pending at the step end
 };
 
 struct Misc {
@@ -84,6 +89,12 @@ struct Misc {
     // IEEE-double scalars of the daughter, touched by thread 0 only
     double a_end, a_cur, K2_end, e1, delta, f1sq;
     double hhQ, invV, ddelta, halfLx;   // per-daughter constants
+    // MIXED mode: the same chain in double-float on the FP32 pipe (an IEEE-
+    // double instruction on one lane costs about a hundred cycles of latency
+    // on GB300, and this chain is on every step's critical path)
+    df a_endf, a_curf, K2f, e1f, f1f, deltaf;
+    df hhQf, ngTf, nhhf, sixthf, ddeltaf, halfLxf, Lxf;
+    float ddelta_abs;
     float dsince;                       // |change of delta| since the list build
     unsigned int n_rebuild;
     int warp_tmp[MAX_WARPS];
@@ -93,12 +104,39 @@ struct Misc {
     int flag_lost;
 };
 
+// daughter_smem_bytes reserves 2048 bytes for the two structures above
+static_assert(((sizeof(Coef<df>) + 15) / 16 * 16) + sizeof(Misc) <= 2048, "Coef + Misc exceed their reserve");
+static_assert(((sizeof(Coef<double>) + 15) / 16 * 16) + sizeof(Misc) <= 2048, "Coef + Misc exceed their reserve");
+
 // --------------------------------------------------------- reductions --
 __device__ __forceinline__ df shfl_df(df v, int o) {
     return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
 }
 __device__ __forceinline__ df warp_sum(df v) {
     for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_df(v, o));
+    return v;
+}
+// Two double-float sums at once on packed float pairs (each FADD2 lane is
+// IEEE round-to-nearest, so every lane gives what df_add gives).
+struct df2 { float2 hi, lo; };
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b) {
+    const float2 s = __fadd2_rn(a.hi, b.hi);          // TwoSum of the hi parts
+    const float2 bb = sub2(s, a.hi);
+    const float2 e = __fadd2_rn(sub2(a.hi, sub2(s, bb)), sub2(b.hi, bb));
+    const float2 lo = __fadd2_rn(e, __fadd2_rn(a.lo, b.lo));
+    const float2 h = __fadd2_rn(s, lo);               // Fast2Sum
+    return {h, sub2(lo, sub2(h, s))};
+}
+__device__ __forceinline__ df2 warp_sum(df2 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        df2 w;
+        w.hi.x = __shfl_down_sync(0xffffffffu, v.hi.x, o);
+        w.hi.y = __shfl_down_sync(0xffffffffu, v.hi.y, o);
+        w.lo.x = __shfl_down_sync(0xffffffffu, v.lo.x, o);
+        w.lo.y = __shfl_down_sync(0xffffffffu, v.lo.y, o);
+        v = df2_add(v, w);
+    }
     return v;
 }
 __device__ __forceinline__ double warp_sum(double v) {
@@ -141,6 +179,34 @@ __device__ __forceinline__ void cta_sum3(R a0, R a1, R a2, Misc *m, double out[3
             if (lane < nw) { t0 = m->slot[lane][0]; t1 = m->slot[lane][1]; t2 = m->slot[lane][2]; }
             t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2);
             if (lane == 0) { out[0] = t0; out[1] = t1; out[2] = t2; }
+        }
+    }
+}
+
+// CTA sums of two per-thread float partials as (normalised) double-float
+// pairs, in a fixed order (MIXED mode's per-step sums).  One __syncthreads; the result is
+// valid in lane 0 of warp 0 and of warp w2, which reduce identically.
+__device__ __forceinline__ void cta_sum2(float a0, float a1, Misc *m, df out[2], int w2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    df2 v = warp_sum(df2{make_float2(a0, a1), make_float2(0.f, 0.f)});
+    if (lane == 0) {
+        float2 *sl = reinterpret_cast<float2 *>(&m->slot[warp][0]);
+        sl[0] = v.hi;
+        sl[1] = v.lo;
+    }
+    __syncthreads();
+    if (warp == 0 || warp == w2) {
+        df2 t = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (lane < nw) {
+            const float2 *sl = reinterpret_cast<const float2 *>(&m->slot[lane][0]);
+            t.hi = sl[0];
+            t.lo = sl[1];
+        }
+        t = warp_sum(t);
+        if (lane == 0) {
+            out[0] = {t.hi.x, t.lo.x};
+            out[1] = {t.hi.y, t.lo.y};
         }
     }
 }
@@ -223,12 +289,40 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             a_end = a.reset_alpha ? 0.0 : sa * b.m_alpha[gl];
             e1 = 0.0;
             delta = a.delta0;
-        } else {
+        } else if constexpr (!MIXED) {
             const double *sc = b.scal + 4 * (size_t)dl;
             a_end = sc[0]; K2_end = sc[1]; e1 = sc[2]; delta = sc[3];
             f1sq = (1.0 + e1) * (1.0 + e1);
         }
-        cf->delta_d = delta; cf->delta_s = sfrom<S>(delta); cf->delta_f = (float)delta;
+        if constexpr (MIXED) {
+            if (a.fresh) {
+                m->a_endf = df_from_double(a_end);
+                m->K2f = df_make(0.f);
+                m->e1f = df_make(0.f);
+                m->deltaf = df_from_double(delta);
+            } else {   // saved as float pairs: the run continues bit for bit
+                const unsigned long long *sc = reinterpret_cast<const unsigned long long *>(b.scal) + 4 * (size_t)dl;
+                m->a_endf = load_slot<df>(sc); m->K2f = load_slot<df>(sc + 1);
+                m->e1f = load_slot<df>(sc + 2); m->deltaf = load_slot<df>(sc + 3);
+            }
+            m->a_curf = m->a_endf;
+            const df g = df_add_f(m->e1f, 1.0f);
+            m->f1f = df_mul(g, g);
+            m->hhQf = df_from_double(m->hhQ);
+            m->ngTf = df_from_double(-b.gT);
+            m->nhhf = df_from_double(-hh);
+            m->sixthf = df_from_double(1.0 / 6.0);
+            m->ddeltaf = df_from_double(m->ddelta);
+            m->halfLxf = df_from_double(m->halfLx);
+            m->Lxf = df_from_double(b.L[0]);
+            m->ddelta_abs = fabsf((float)m->ddelta);
+            delta = df_to_double(m->deltaf);
+            cf->delta_d = delta; cf->delta_s = m->deltaf; cf->delta_f = m->deltaf.hi;
+            cf->f1 = m->f1f;
+        } else {
+            cf->delta_d = delta; cf->delta_s = sfrom<S>(delta); cf->delta_f = (float)delta;
+            cf->f1 = sfrom<S>(f1sq);
+        }
     }
     __syncthreads();
 
@@ -544,8 +638,8 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     };
 
     // thread 0: coefficients of the next step from K2_end, a_end, e1, delta.
-    // IEEE double throughout; on GB300 each double instruction of this
-    // serial chain costs tens of cycles, so divisions and rint are avoided.
+    // FP64 mode: IEEE double; divisions and rint are avoided on this serial
+    // chain.
     auto next_alpha = [&]() {
         const double inc = m->hhQ * (K2_end - b.gT);
         a_cur = a_end + inc;                       // start-of-step alpha half-step
@@ -553,6 +647,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         const double ec = fma(e1, e3, e1 + e3);    // (1+e1)(1+e3) - 1
         e1 = e3;
         f1sq = (1.0 + e3) * (1.0 + e3);
+        cf->f1 = sfrom<S>(f1sq);
         cf->e = sfrom<S>(ec);
     };
     auto next_delta = [&]() {
@@ -564,7 +659,37 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         const float thr = 0.5f * (b.skin - dsince);
         cf->thr2 = thr > 0.f ? thr * thr : -1.f;
     };
-    auto next_step = [&]() { next_alpha(); next_delta(); };
+    // MIXED: the same two updates in double-float; inc = hhQ (K2_end - gT)
+    // is the increment of both alpha half-steps
+    auto next_alpha_f = [&](df inc) {
+        const df acur = df_add(m->a_endf, inc);    // start-of-step alpha half-step
+        m->a_curf = acur;
+        const df e3 = df_expm1_small(df_mul(m->nhhf, acur), m->sixthf);
+        const df ec = df_add(df_add(m->e1f, e3), df_mul(m->e1f, e3));   // (1+e1)(1+e3) - 1
+        m->e1f = e3;
+        const df g = df_add_f(e3, 1.0f);
+        m->f1f = df_mul(g, g);
+        cf->f1 = sfrom_df<S>(m->f1f);
+        cf->e = sfrom_df<S>(ec);
+    };
+    auto next_delta_f = [&]() {
+        df dl = df_add(m->deltaf, m->ddeltaf);     // sliding-brick offset advance
+        if (df_ge(dl, m->halfLxf)) dl = df_add(dl, df_neg(m->Lxf));
+        else if (df_lt(dl, df_neg(m->halfLxf))) dl = df_add(dl, m->Lxf);
+        m->deltaf = dl;
+        dsince += m->ddelta_abs;
+        cf->delta_s = sfrom_df<S>(dl); cf->delta_f = dl.hi;
+        const float thr = 0.5f * (b.skin - dsince);
+        cf->thr2 = thr > 0.f ? thr * thr : -1.f;
+    };
+    auto next_step = [&]() {
+        if constexpr (MIXED) {
+            next_alpha_f(df_mul(m->hhQf, df_add(m->K2f, m->ngTf)));
+            next_delta_f();
+        } else {
+            next_alpha(); next_delta();
+        }
+    };
 
     // ---- forces and sums of the initial state ----
     build_list();
@@ -591,7 +716,10 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         cta_sum3<MIXED, R>(s2, sxy, w0, m, sums);
         if (tid == 0) {
             if (a.wxy_out) a.wxy_out[d] = 0.5 * sums[2];
-            if (a.fresh) K2_end = sums[0];
+            if (a.fresh) {
+                K2_end = sums[0];
+                if constexpr (MIXED) m->K2f = df_from_double(sums[0]);
+            }
             if (m->flag_ovf) cf->stop = TTCF_D_NBR_OVERFLOW;
             if (m->flag_lost) cf->stop |= TTCF_D_NONFINITE;
             if (a.step1 > a.step0) next_step();
@@ -708,9 +836,22 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         const int nw = T >> 5;
         const int wo = nw > 1 ? 1 : 0, wd = nw > 2 ? 2 : 0;
         double f1sq_s = 0.0, e1_s = 0.0;
-        if (tid == 32 * wo) { f1sq_s = f1sq; e1_s = e1; }        // this step's values
+        df e1f_s = df_make(0.f);
+        if (tid == 32 * wo) {                                   // this step's values
+            if constexpr (MIXED) e1f_s = m->e1f;
+            else { f1sq_s = f1sq; e1_s = e1; }
+        }
         double sums[3];
-        cta_sum3<MIXED, R>(s2, sxy, wsum, m, sums, wo);         // barrier 2
+        df sumsf[2];
+        if constexpr (MIXED) {
+            // V P_xy = (1+e1)^2 sum p_x p_y + W_xy/2 formed per thread, so that
+            // two sums are reduced instead of three
+            const df f1 = cf->f1;
+            const float pv = __fmaf_rn(0.5f, wsum, mul_cf(f1, sxy));
+            cta_sum2(s2, pv, m, sumsf, wo);                    // barrier 2
+        } else {
+            cta_sum3<MIXED, R>(s2, sxy, wsum, m, sums, wo);     // barrier 2
+        }
         const bool last_save = s == a.step1 && a.save_state;
         int snap_k = -1;
         if (a.snap && s >= a.snap_first && (s - a.snap_first) % a.snap_every == 0 &&
@@ -719,27 +860,50 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         double *sc = last_save ? b.scal + 4 * (size_t)dl : nullptr;
         if (tid == 32 * wo) {
             // end of step s: pending factor (1+e1)^2 = f1sq from the scale half-step
-            const double pxy = fma(f1sq_s, sums[1], 0.5 * sums[2]) * m->invV;
+            double pxy;
             int st = 0;
-            if (!isfinite(sums[0] + sums[1] + sums[2])) st |= TTCF_D_NONFINITE;
+            if constexpr (MIXED) {
+                pxy = df_to_double(sumsf[1]) * m->invV;
+                if (!isfinite(sumsf[0].hi + sumsf[1].hi)) st |= TTCF_D_NONFINITE;
+            } else {
+                pxy = fma(f1sq_s, sums[1], 0.5 * sums[2]) * m->invV;
+                if (!isfinite(sums[0] + sums[1] + sums[2])) st |= TTCF_D_NONFINITE;
+            }
             if (m->flag_ovf) st |= TTCF_D_NBR_OVERFLOW;
             if (m->flag_lost) st |= TTCF_D_NONFINITE;
             if (a.abort_flag && (s & 63) == 0 && *a.abort_flag) st |= TTCF_D_ABORTED;
             if (st) atomicOr(&cf->stop, st);
             if (s % a.sample_every == 0) b.B[series + s / a.sample_every] = pxy;
             cf->snap = snap_k;
-            if (snap_k >= 0) cf->fsnap = 1.0 + e1_s;
+            if (snap_k >= 0) cf->fsnap = MIXED ? df_to_double(df_add_f(e1f_s, 1.0f)) : 1.0 + e1_s;
         }
+        unsigned long long *scu = reinterpret_cast<unsigned long long *>(sc);
         if (tid == 32 * wd) {
-            if (last_save) sc[3] = delta;
-            next_delta();
+            if constexpr (MIXED) {
+                if (last_save) store_slot(scu + 3, m->deltaf);
+                next_delta_f();
+            } else {
+                if (last_save) sc[3] = delta;
+                next_delta();
+            }
         }
         if (tid == 0) {
-            K2_end = f1sq * sums[0];
-            a_end = a_cur + m->hhQ * (K2_end - b.gT);           // end-of-step alpha half-step
-            if (snap_k >= 0) a.snap_alpha[(size_t)d * a.n_snap + snap_k] = a_end;
-            if (last_save) { sc[0] = a_end; sc[1] = K2_end; sc[2] = e1; }
-            next_alpha();
+            if constexpr (MIXED) {
+                const df K2 = df_mul(m->f1f, sumsf[0]);
+                m->K2f = K2;
+                const df inc = df_mul(m->hhQf, df_add(K2, m->ngTf));
+                const df aend = df_add(m->a_curf, inc);          // end-of-step alpha half-step
+                m->a_endf = aend;
+                if (snap_k >= 0) a.snap_alpha[(size_t)d * a.n_snap + snap_k] = df_to_double(aend);
+                if (last_save) { store_slot(scu, aend); store_slot(scu + 1, K2); store_slot(scu + 2, m->e1f); }
+                next_alpha_f(inc);
+            } else {
+                K2_end = f1sq * sums[0];
+                a_end = a_cur + m->hhQ * (K2_end - b.gT);       // end-of-step alpha half-step
+                if (snap_k >= 0) a.snap_alpha[(size_t)d * a.n_snap + snap_k] = a_end;
+                if (last_save) { sc[0] = a_end; sc[1] = K2_end; sc[2] = e1; }
+                next_alpha();
+            }
             m->flag_rebuild[fb ^ 1] = 0;
         }
         __syncthreads();                                        // barrier 3
@@ -785,7 +949,13 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         }
         if (tid == 0 && a.step1 == a.step0) {   // no step ran: state unchanged
             double *sc = b.scal + 4 * (size_t)dl;
-            sc[0] = a_end; sc[1] = K2_end; sc[2] = e1; sc[3] = delta;
+            if constexpr (MIXED) {
+                unsigned long long *scu = reinterpret_cast<unsigned long long *>(sc);
+                store_slot(scu, m->a_endf); store_slot(scu + 1, m->K2f);
+                store_slot(scu + 2, m->e1f); store_slot(scu + 3, m->deltaf);
+            } else {
+                sc[0] = a_end; sc[1] = K2_end; sc[2] = e1; sc[3] = delta;
+            }
         }
     }
     {

@@ -7,8 +7,12 @@
 //    error-free transformations TwoSum (Knuth) and FMA-based TwoProduct
 //    (Dekker 1971), all on the FP32 pipe;
 //  * pair forces and the virial are plain FP32, from the hi parts;
-//  * per-daughter scalars (Nose-Hoover alpha, Lees-Edwards offset, the
-//    pressure sample B(s), Omega(0)) are IEEE double, computed by one lane.
+//  * the per-step chain of per-daughter scalars (Nose-Hoover alpha, the
+//    momentum factor, the Lees-Edwards offset, the CTA sums behind B(s))
+//    is double-float too, computed by one lane each: an IEEE-double
+//    instruction costs about a hundred cycles of latency there;
+//  * Omega(0), B(s) as stored and every accumulation over daughters are
+//    IEEE double.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -83,6 +87,26 @@ __device__ __forceinline__ df df_from_double(double x) {
     return {h, __double2float_rn(x - (double)h)};
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+// Order of two normalised pairs (|lo| <= ulp(hi)/2): by hi, then by lo.
+__device__ __forceinline__ bool df_ge(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+__device__ __forceinline__ bool df_lt(df a, df b) { return !df_ge(a, b); }
+
+// exp(x) - 1 in double-float for the small arguments -alpha h/2, on the
+// FP32 pipe.  With e = x + x^2 q, q = 1/2 + x/6 + x^2 r and
+// r = 1/24 + x/120 + x^2/720 + x^3/5040: for |x| < 5e-3 the truncation is
+// below 1e-16 relative, x^2 and x/6 are formed as pairs, and x^2 r (at most
+// 1e-6 beside 1/2) in float, which keeps e within about 2^-48 relative.
+// `sixth` is 1/6 as a pair.  Larger |x| goes through the IEEE-double routine.
+__device__ __forceinline__ df df_expm1_small(df x, df sixth) {
+    const float xf = x.hi;
+    if (!(fabsf(xf) < 5e-3f)) return df_from_double(expm1(df_to_double(x)));
+    const float r = __fmaf_rn(xf, __fmaf_rn(xf, __fmaf_rn(xf, 1.f / 5040.f, 1.f / 720.f), 1.f / 120.f),
+                              1.f / 24.f);
+    const df x2 = df_mul(x, x);
+    df q = df_add_f(df_mul(x, sixth), __fmul_rn(x2.hi, r));
+    q = df_add_f(q, 0.5f);
+    return df_add(x, df_mul(x2, q));
+}
 
 // Round to nearest integer (ties to even) on the FP32 add pipe: valid for
 // |v| < 2^22.  1.5*2^23 has unit spacing, so v + M rounds v once.
