@@ -46,8 +46,8 @@ FLOPS_PER_PAIR_LJ = 25.0         # one unique LJ-c_ij pair of the confined syste
 # profiles/*.md), scaled to a launch by the units it processes:
 # daughter_kernel reads its mothers (per daughter) and writes the series (per
 # sample); conf_kernel streams its per-CTA scratch (per atom-step).
-BULK_READ_PER_DAUGHTER = 36.0e3
-BULK_WRITE_PER_SAMPLE = 6.75
+BULK_READ_PER_DAUGHTER = 31.1e3
+BULK_WRITE_PER_SAMPLE = 13.1
 CONF_BYTES_PER_ATOM_STEP = 391.0
 CONF_RATES = [1e-1, 1e-3, 1e-5, 1e-7]
 
@@ -303,8 +303,8 @@ def bench_gb300(args):
         "metric": "daughter atom-steps/s", "value": value, "unit": "atom-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "precision": "MIXED: FP32 pair forces; float-float positions and momenta; "
-                                     "FP64 alpha, delta, Omega(0), B(s) and accumulation",
+        "dtype": "f32", "precision": "MIXED: FP32 pair forces; float-float positions, momenta and the "
+                                     "per-step alpha/delta chain; FP64 Omega(0), B(s) and accumulation",
         "data": "synthetic (seeded FCC + Maxwell, GPU-thermalised mothers)",
         "config": {"workload": f"bulk WCA N={N}, {G} mother states x 4 mappings x {len(rates)} shear "
                                f"rates = {D} daughters x {args.daughter_steps} steps",
