@@ -116,18 +116,7 @@ __device__ __forceinline__ df warp_sum(df v) {
     for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_df(v, o));
     return v;
 }
-// Two double-float sums at once on packed float pairs (each FADD2 lane is
-// IEEE round-to-nearest, so every lane gives what df_add gives).
-struct df2 { float2 hi, lo; };
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
-__device__ __forceinline__ df2 df2_add(df2 a, df2 b) {
-    const float2 s = __fadd2_rn(a.hi, b.hi);          // TwoSum of the hi parts
-    const float2 bb = sub2(s, a.hi);
-    const float2 e = __fadd2_rn(sub2(a.hi, sub2(s, bb)), sub2(b.hi, bb));
-    const float2 lo = __fadd2_rn(e, __fadd2_rn(a.lo, b.lo));
-    const float2 h = __fadd2_rn(s, lo);               // Fast2Sum
-    return {h, sub2(lo, sub2(h, s))};
-}
+// Two double-float sums at once on packed float pairs (df2_add).
 __device__ __forceinline__ df2 warp_sum(df2 v) {
     for (int o = 16; o > 0; o >>= 1) {
         df2 w;
@@ -736,7 +725,62 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         const int fb = s & 1;
         const float thr2 = cf->thr2, fast2 = cf->fast2;
         // phase A
-        for (int q = 0; q < APT; q++) {
+        bool packed_a = false;
+        if constexpr (MIXED && APT % 2 == 0) {
+            // a thread's atoms q and q+1 side by side on packed FP32 pairs:
+            // the same operations as the scalar path below, lane by lane
+            // (that path runs the steps that re-wrap positions)
+            packed_a = !wrap_now;
+            if (packed_a) {
+                const float2 ef2 = f2(e.hi), ncf2 = f2(-chalf.hi);
+                for (int q = 0; q < APT; q += 2) {
+                    const int i0 = tid + q * T, i1 = i0 + T;
+                    if (i0 >= N) continue;
+                    const bool has1 = i1 < N;
+                    const int j1 = has1 ? i1 : i0;   // a missing second atom repeats the first
+                    df2 pp[3];
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        pp[c] = {make_float2(P[q][c].hi, P[q + 1][c].hi), make_float2(P[q][c].lo, P[q + 1][c].lo)};
+#pragma unroll
+                    for (int c = 0; c < 3; c++) acc_add2(pp[c], __fmul2_rn(pp[c].hi, ef2));
+                    acc_add2(pp[0], __fmul2_rn(ncf2, pp[1].hi));
+#pragma unroll
+                    for (int c = 0; c < 3; c++) acc_add2(pp[c], mul_cf2(hhS, make_float2(F[q][c], F[q + 1][c])));
+#pragma unroll
+                    for (int c = 0; c < 3; c++) renorm2(pp[c]);
+                    const float4 h0 = pos4[i0], h1 = pos4[j1], l0 = plo4[i0], l1 = plo4[j1];
+                    df2 x = {make_float2(h0.x, h1.x), make_float2(l0.x, l1.x)};
+                    df2 y = {make_float2(h0.y, h1.y), make_float2(l0.y, l1.y)};
+                    df2 z = {make_float2(h0.z, h1.z), make_float2(l0.z, l1.z)};
+                    const float2 ddx = mul_cd2(hS, pp[0]), ddy = mul_cd2(hS, pp[1]), ddz = mul_cd2(hS, pp[2]);
+                    const float2 ys = __fmul2_rn(f2(gh.hi), __ffma2_rn(f2(hhS.hi), pp[1].hi, y.hi));
+                    acc_add2(x, ddx); acc_add2(x, ys); acc_add2(y, ddy); acc_add2(z, ddz);
+                    renorm2(x); renorm2(y); renorm2(z);
+                    const float2 dxs = __fadd2_rn(ddx, ys);
+                    const float2 d2 = __ffma2_rn(ddz, ddz, __ffma2_rn(ddy, ddy, __fmul2_rn(dxs, dxs)));
+                    if (d2.x > fast2 || (has1 && d2.y > fast2)) m->flag_fast = 1;
+                    const float4 r0 = ref4[i0], r1 = ref4[j1];
+                    pos4[i0] = make_float4(x.hi.x, y.hi.x, z.hi.x, 0.f);
+                    plo4[i0] = make_float4(x.lo.x, y.lo.x, z.lo.x, 0.f);
+                    if (has1) {
+                        pos4[i1] = make_float4(x.hi.y, y.hi.y, z.hi.y, 0.f);
+                        plo4[i1] = make_float4(x.lo.y, y.lo.y, z.lo.y, 0.f);
+                    }
+                    const float2 ex = sub2(x.hi, make_float2(r0.x, r1.x));
+                    const float2 ey = sub2(y.hi, make_float2(r0.y, r1.y));
+                    const float2 ez = sub2(z.hi, make_float2(r0.z, r1.z));
+                    const float2 e2 = __ffma2_rn(ez, ez, __ffma2_rn(ey, ey, __fmul2_rn(ex, ex)));
+                    if (e2.x > thr2 || (has1 && e2.y > thr2)) m->flag_rebuild[fb] = 1;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        P[q][c] = {pp[c].hi.x, pp[c].lo.x};
+                        P[q + 1][c] = {pp[c].hi.y, pp[c].lo.y};
+                    }
+                }
+            }
+        }
+        for (int q = 0; q < APT && !packed_a; q++) {
             const int i = tid + q * T;
             if (i >= N) continue;
             S px = P[q][0], py = P[q][1], pz = P[q][2];
@@ -811,24 +855,59 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         const R wsum = forces();
         // phase C
         R s2 = 0, sxy = 0;
-        for (int q = 0; q < APT; q++) {
-            const int i = tid + q * T;
-            if (i >= N) continue;
-            S px = P[q][0], py = P[q][1], pz = P[q][2];
-            if constexpr (MIXED) {
-                acc_add(px, mul_cf(hhS, F[q][0]));
-                acc_add(py, mul_cf(hhS, F[q][1]));
-                acc_add(pz, mul_cf(hhS, F[q][2]));
-                acc_add(px, -chalf.hi * py.hi);
-                renorm(px); renorm(py); renorm(pz);
-            } else {
-                px += hhS * F[q][0]; py += hhS * F[q][1]; pz += hhS * F[q][2];
-                px = px - chalf * py;
+        if constexpr (MIXED && APT % 2 == 0) {   // atoms q and q+1 on packed pairs
+            const float2 ncf2 = f2(-chalf.hi);
+            for (int q = 0; q < APT; q += 2) {
+                const int i0 = tid + q * T;
+                if (i0 >= N) continue;
+                const bool has1 = i0 + T < N;
+                df2 pp[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    pp[c] = {make_float2(P[q][c].hi, P[q + 1][c].hi), make_float2(P[q][c].lo, P[q + 1][c].lo)};
+                    acc_add2(pp[c], mul_cf2(hhS, make_float2(F[q][c], F[q + 1][c])));
+                }
+                acc_add2(pp[0], __fmul2_rn(ncf2, pp[1].hi));
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    renorm2(pp[c]);
+                    P[q][c] = {pp[c].hi.x, pp[c].lo.x};
+                    P[q + 1][c] = {pp[c].hi.y, pp[c].lo.y};
+                }
+                const float2 hx = pp[0].hi, hy = pp[1].hi, hz = pp[2].hi;
+                const float2 t2 = __ffma2_rn(hz, hz, __ffma2_rn(hy, hy, __fmul2_rn(hx, hx)));
+                s2 = __fadd_rn(s2, t2.x);
+                sxy = __fmaf_rn(hx.x, hy.x, sxy);
+                if (has1) {
+                    s2 = __fadd_rn(s2, t2.y);
+                    sxy = __fmaf_rn(hx.y, hy.y, sxy);
+                }
             }
-            P[q][0] = px; P[q][1] = py; P[q][2] = pz;
-            const R hx = (R)shi(px), hy = (R)shi(py), hz = (R)shi(pz);
-            s2 += hx * hx + hy * hy + hz * hz;
-            sxy += hx * hy;
+        } else {
+            for (int q = 0; q < APT; q++) {
+                const int i = tid + q * T;
+                if (i >= N) continue;
+                S px = P[q][0], py = P[q][1], pz = P[q][2];
+                if constexpr (MIXED) {
+                    acc_add(px, mul_cf(hhS, F[q][0]));
+                    acc_add(py, mul_cf(hhS, F[q][1]));
+                    acc_add(pz, mul_cf(hhS, F[q][2]));
+                    acc_add(px, -chalf.hi * py.hi);
+                    renorm(px); renorm(py); renorm(pz);
+                } else {
+                    px += hhS * F[q][0]; py += hhS * F[q][1]; pz += hhS * F[q][2];
+                    px = px - chalf * py;
+                }
+                P[q][0] = px; P[q][1] = py; P[q][2] = pz;
+                const R hx = (R)shi(px), hy = (R)shi(py), hz = (R)shi(pz);
+                if constexpr (MIXED) {   // the packed path's operations, in order
+                    s2 = __fadd_rn(s2, __fmaf_rn(hz, hz, __fmaf_rn(hy, hy, __fmul_rn(hx, hx))));
+                    sxy = __fmaf_rn(hx, hy, sxy);
+                } else {
+                    s2 += hx * hx + hy * hy + hz * hz;
+                    sxy += hx * hy;
+                }
+            }
         }
         // step end, on three lanes at once (warp 0: the alpha chain; warp
         // wo: B(s), flags, snapshots; warp wd: the Lees-Edwards offset),

@@ -131,6 +131,41 @@ __device__ __forceinline__ float2 rint2(float2 v, float2 s) {
     return __fadd2_rn(__ffma2_rn(v, s, M), neg2(M));
 }
 
+// Two float pairs side by side (lane x: one atom, lane y: another), with the
+// float-pair operations above on packed FP32 instructions.  Each lane is
+// IEEE round-to-nearest, so every lane gives bit for bit what the scalar
+// helper gives.  a - b is formed as fma(b, -1, a), which is exact.
+struct df2 { float2 hi, lo; };
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b) {
+    const float2 s = __fadd2_rn(a.hi, b.hi);          // TwoSum of the hi parts
+    const float2 bb = sub2(s, a.hi);
+    const float2 e = __fadd2_rn(sub2(a.hi, sub2(s, bb)), sub2(b.hi, bb));
+    const float2 lo = __fadd2_rn(e, __fadd2_rn(a.lo, b.lo));
+    const float2 h = __fadd2_rn(s, lo);               // Fast2Sum
+    return {h, sub2(lo, sub2(h, s))};
+}
+__device__ __forceinline__ void acc_add2(df2 &a, float2 t) {   // acc_add on both lanes
+    const float2 s = __fadd2_rn(a.hi, t);
+    const float2 bb = sub2(s, a.hi);
+    const float2 e = __fadd2_rn(sub2(a.hi, sub2(s, bb)), sub2(t, bb));
+    a.hi = s;
+    a.lo = __fadd2_rn(a.lo, e);
+}
+__device__ __forceinline__ void renorm2(df2 &a) {
+    const float2 s = __fadd2_rn(a.hi, a.lo);
+    a = {s, sub2(a.lo, sub2(s, a.hi))};
+}
+__device__ __forceinline__ float2 mul_cf2(df c, float2 v) {
+    return __ffma2_rn(f2(c.hi), v, __fmul2_rn(f2(c.lo), v));
+}
+__device__ __forceinline__ float2 mul_cd2(df c, df2 a) {
+    return __ffma2_rn(f2(c.hi), a.hi, __ffma2_rn(f2(c.hi), a.lo, __fmul2_rn(f2(c.lo), a.hi)));
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
