@@ -291,13 +291,6 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             const int z1 = min(ifloor((wz + rl + hl2) * s2), z0 + nc2 - 1);
             const int y0 = max(ifloor((wy - rl + hl1) * s1), 0);
             const int y1 = min(ifloor((wy + rl + hl1) * s1), nc1 - 1);
-            const int x0 = ifloor((wx - rl + hl0) * s0);
-            const int x1 = min(ifloor((wx + rl + hl0) * s0), x0 + nc0 - 1);
-            const int a0 = x0 < 0 ? x0 + nc0 : (x0 >= nc0 ? x0 - nc0 : x0);
-            const int b0 = a0 + (x1 - x0);
-            int ra[2], rb[2], nr;
-            if (b0 < nc0) { ra[0] = a0; rb[0] = b0; ra[1] = rb[1] = 0; nr = 1; }
-            else { ra[0] = a0; rb[0] = nc0 - 1; ra[1] = 0; rb[1] = b0 - nc0; nr = 2; }
             // Entries enter a 128-bit shift register (w0 holds the oldest)
             // and leave as one 16-byte store per group of 8, from group 0 up.
             // A wall atom's wall neighbours go to the last groups instead
@@ -312,9 +305,34 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                 w2 = __byte_perm(w2, w3, 0x5432);
                 w3 = __byte_perm(w3, j, 0x5432);
             };
+            // cell widths, and r_l^2 with a margin for the rounding below
+            const float cw1 = Ly / (float)nc1, cw2 = Lz / (float)nc2, rl2m = rl2 * (1.f + 1e-5f);
             for (int zu = z0; zu <= z1; zu++) {
                 const int zz = zu < 0 ? zu + nc2 : (zu >= nc2 ? zu - nc2 : zu);
+                const float zlo = __fmaf_rn((float)zu, cw2, -hl2);
+                const float dz = fmaxf(0.f, fmaxf(zlo - wz, wz - (zlo + cw2)));
                 for (int yy = y0; yy <= y1; yy++) {
+                    // the row's cells lie at least (dy, dz) away: rows beyond
+                    // r_l are skipped and the x window is trimmed to
+                    // |dx| <= sqrt(r_l^2 - dy^2 - dz^2) (lists are unchanged).
+                    // The edge rows in y also hold the atoms clamped into
+                    // them, so they are open towards the outside.
+                    const float ylo = __fmaf_rn((float)yy, cw1, -hl1);
+                    const float below = yy > 0 ? ylo - wy : 0.f;
+                    const float above = yy < nc1 - 1 ? wy - (ylo + cw1) : 0.f;
+                    const float dy = fmaxf(0.f, fmaxf(below, above));
+                    const float h2 = rl2m - __fmaf_rn(dz, dz, dy * dy);
+                    if (h2 < 0.f) continue;
+                    const float hw = sqrtf(h2);
+                    const int xa = ifloor((wx - hw + hl0) * s0);
+                    const int xb = min(ifloor((wx + hw + hl0) * s0), xa + nc0 - 1);
+                    int ra[2], rb[2], nr;
+                    {
+                        const int a0 = xa < 0 ? xa + nc0 : (xa >= nc0 ? xa - nc0 : xa);
+                        const int b0 = a0 + (xb - xa);
+                        if (b0 < nc0) { ra[0] = a0; rb[0] = b0; ra[1] = rb[1] = 0; nr = 1; }
+                        else { ra[0] = a0; rb[0] = nc0 - 1; ra[1] = 0; rb[1] = b0 - nc0; nr = 2; }
+                    }
                     const int row = (zz * nc1 + yy) * nc0;
                     for (int r = 0; r < nr; r++) {
                         const int t1 = start[row + rb[r] + 1];
