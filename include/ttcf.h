@@ -256,6 +256,29 @@ ttcf_status ttcf_mother_acf(ttcf_ctx *ctx, int n_atoms, const double box[3], int
                             const double *init_soa, int n_eq, int n_steps, int max_lag,
                             double *acf_pxy, double *acf_pxy2, double *eta_gk, double *series);
 
+/* Further mother states from one thermalised state (the thermalisation
+ * workflow of the paper's computational section: further initial conditions
+ * from a single equilibrated state by a small random kick to the
+ * velocities; the dynamics is chaotic, so the copies decorrelate quickly).
+ * Writes n_copies copies of the phase point state_soa [6][N] (x y z px py
+ * pz) to out_soa [n_copies][6][N]: positions unchanged; copy c adds to
+ * momentum component k of atom i the kick  kick * sqrt(T) * g  (T of the
+ * context, unit masses), g standard normal from Philox-4x32-10 (Salmon et
+ * al., SC'11) keyed by seed (low word first) with counter (i, c, b, 0),
+ * b = 0, 1, and Box-Muller on the 53-bit uniforms of its word pairs (g0, g1
+ * from b = 0, g2 the cosine branch of b = 1).  Every group of atoms (types
+ * [N] with values 0, 1, 2, e.g. fluid and the two walls, or NULL for one
+ * group) keeps its net momentum: the group mean of the kicks is removed.
+ * keep_energy != 0: every group also keeps the kinetic energy of its
+ * momenta relative to the group mean (the kicked relative momenta are
+ * rescaled).  Inputs and outputs on the host (is_dev = 0) or on the
+ * context's device (is_dev = 1, stream of the context); caller-owned.
+ * IEEE double.  Errors: TTCF_E_INVALID (NULL, n_atoms or n_copies < 1,
+ * kick < 0 or not finite, a type outside 0..2), TTCF_E_OOM, TTCF_E_CUDA. */
+ttcf_status ttcf_kick_states(ttcf_ctx *ctx, int n_atoms, const double *state_soa, const int *types,
+                             int n_copies, double kick, unsigned long long seed, int keep_energy,
+                             double *out_soa, int is_dev);
+
 /* Pair forces of n_states phase points [n_states][6][N] (host; rows 0-2
  * used) at Lees-Edwards offset delta, with the context's precision and the
  * same device code the daughters use: F [n_states][3][N] and virial

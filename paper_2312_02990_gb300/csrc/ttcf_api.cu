@@ -1216,6 +1216,53 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
     return TTCF_OK;
 }
 
+// Copies of one phase point with small random momentum kicks (see
+// ttcf_kick.cu); host or device buffers.
+ttcf_status ttcf_kick_states(ttcf_ctx *ctx, int n_atoms, const double *state_soa, const int *types,
+                             int n_copies, double kick, unsigned long long seed, int keep_energy,
+                             double *out_soa, int is_dev) {
+    if (!ctx || !state_soa || !out_soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
+    if (n_atoms < 1 || n_copies < 1) return fail(ctx, TTCF_E_INVALID, "n_atoms and n_copies must be positive");
+    if (!(kick >= 0.0) || !isfinite(kick)) return fail(ctx, TTCF_E_INVALID, "kick must be finite and >= 0");
+    const int N = n_atoms;
+    std::vector<int> th;
+    if (types) {   // groups must be 0, 1 or 2
+        th.resize(N);
+        if (is_dev) CK(cudaMemcpy(th.data(), types, sizeof(int) * N, cudaMemcpyDeviceToHost));
+        else memcpy(th.data(), types, sizeof(int) * N);
+        for (int t : th)
+            if (t < 0 || t > 2) return fail(ctx, TTCF_E_INVALID, "types must be 0, 1 or 2");
+    }
+    Pool pool(ctx);
+    const double *d_src = state_soa;
+    const int *d_types = types;
+    double *d_out = out_soa;
+    if (!is_dev) {
+        double *s = pool.get<double>((size_t)6 * N);
+        int *t = types ? pool.get<int>(N) : nullptr;
+        d_out = pool.get<double>((size_t)n_copies * 6 * N);
+        if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (kicks)");
+        CK(cudaMemcpyAsync(s, state_soa, sizeof(double) * 6 * N, cudaMemcpyHostToDevice, ctx->st));
+        if (t) CK(cudaMemcpyAsync(t, th.data(), sizeof(int) * N, cudaMemcpyHostToDevice, ctx->st));
+        d_src = s;
+        d_types = t;
+    }
+    KickArgs ka;
+    ka.N = N;
+    ka.keep_energy = keep_energy ? 1 : 0;
+    ka.ks = kick * sqrt(ctx->cfg.T);
+    ka.seed = seed;
+    ka.src = d_src;
+    ka.types = d_types;
+    ka.out = d_out;
+    CK(launch_kick(ka, n_copies, ctx->st));
+    if (!is_dev)
+        CK(cudaMemcpyAsync(out_soa, d_out, sizeof(double) * (size_t)n_copies * 6 * N, cudaMemcpyDeviceToHost,
+                           ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return TTCF_OK;
+}
+
 ttcf_status ttcf_mother_acf(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_init,
                             const double *init_soa, int n_eq, int n_steps, int max_lag,
                             double *acf_pxy, double *acf_pxy2, double *eta_gk, double *series) {

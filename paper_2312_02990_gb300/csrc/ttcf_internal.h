@@ -13,6 +13,18 @@ cudaError_t launch_daughters(bool mixed, int variant, const RunArgs &a, int thre
                              size_t smem, cudaStream_t st);
 int daughter_occupancy(bool mixed, int variant, int threads, size_t smem);
 
+// momentum kicks of copies of one phase point (ttcf_kick.cu)
+struct KickArgs {
+    int N;
+    int keep_energy;
+    double ks;                    // kick * sqrt(T): standard deviation of a kick
+    unsigned long long seed;      // Philox key (low word k0)
+    const double *src;            // [6][N]
+    const int *types;             // [N] groups 0..2, or null (one group)
+    double *out;                  // [n_copies][6][N]
+};
+cudaError_t launch_kick(const KickArgs &a, int n_copies, cudaStream_t st);
+
 // spawn (ttcf_spawn.cu): per mother group, IEEE-double pressure tensor of
 // the mother, B(0) and Omega(0) of its mapped daughters, conversion of the
 // mother into the state format of the daughter kernel.

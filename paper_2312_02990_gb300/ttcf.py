@@ -29,6 +29,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_run",
            "ttcf_response", "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
            "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_mother_acf",
+           "ttcf_kick_states",
            "ttcf_forces", "ttcf_autotune",
            "ttcf_run_noalloc", "ttcf_cv_config_default", "ttcf_cv_data", "ttcf_cv_train",
            "ttcf_cv_apply", "ttcf_cv_get_model", "ttcf_cv_forward", "ttcf_cv_gradient",
@@ -135,6 +136,9 @@ def load(build_if_missing: bool = False):
     L.ttcf_mother_acf.argtypes = [vp, C.c_int, _dp, C.c_int, _dp, C.c_int, C.c_int, C.c_int,
                                   _dp, _dp, _dp, _dp]
     L.ttcf_mother_acf.restype = C.c_int
+    L.ttcf_kick_states.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_double, C.c_ulonglong, C.c_int,
+                                   vp, C.c_int]
+    L.ttcf_kick_states.restype = C.c_int
     L.ttcf_friction.argtypes = [vp, C.c_int, C.c_int] + [_dp] * 5 + [C.c_int, ip]
     L.ttcf_friction.restype = C.c_int
     L.ttcf_save.argtypes = [vp, C.c_char_p]
@@ -438,6 +442,33 @@ class Context:
                                             _ptr(ser) if ser is not None else None))
         if ser is not None:
             out["series"] = ser
+        return out
+
+    def kick_states(self, state_soa, n_copies: int, kick: float, seed: int, types=None,
+                    keep_energy: bool = True):
+        """n_copies copies [n, 6, N] of one phase point [6, N] with small random
+        momentum kicks (see ttcf_kick_states): numpy in and out, or a torch
+        CUDA tensor in and a torch CUDA tensor out."""
+        is_dev = hasattr(state_soa, "is_cuda") and state_soa.is_cuda
+        if is_dev:
+            import torch
+            st = state_soa.contiguous().to(torch.float64)
+            N = st.shape[1]
+            ty = None if types is None else torch.as_tensor(types, dtype=torch.int32, device=st.device).contiguous()
+            out = torch.empty((n_copies, 6, N), dtype=torch.float64, device=st.device)
+            p_st, p_ty, p_out = st.data_ptr(), (ty.data_ptr() if ty is not None else None), out.data_ptr()
+            keep = (st, ty)
+        else:
+            st = _f64(state_soa)
+            N = st.shape[1]
+            ty = None if types is None else np.ascontiguousarray(types, dtype=np.int32)
+            out = np.zeros((n_copies, 6, N))
+            p_st, p_ty, p_out = st.ctypes.data, (ty.ctypes.data if ty is not None else None), out.ctypes.data
+            keep = (st, ty)
+        self._check(self._L.ttcf_kick_states(self.h, int(N), p_st, p_ty, int(n_copies), float(kick),
+                                             int(seed) & 0xFFFFFFFFFFFFFFFF, 1 if keep_energy else 0, p_out,
+                                             1 if is_dev else 0))
+        del keep
         return out
 
     def autotune(self, soa, box, shear_rate: float = 1e-3, n_steps: int = 100):
