@@ -81,6 +81,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-floor", action="store_true", help="skip the precision-floor sweep")
     p.add_argument("--no-gk", action="store_true", help="skip the Green-Kubo cross-check")
+    p.add_argument("--no-kick", action="store_true", help="skip the momentum-kick mothers section")
     p.add_argument("--confined-only", action="store_true",
                    help="run only the confined-channel section and print its JSON")
     p.add_argument("--conf-chains", type=int, default=38, help="independent confined mother chains")
@@ -348,6 +349,8 @@ def bench_gb300(args):
         line["precision_floor"] = precision_floor_section(T, torch, args)
     if not args.no_gk and rank == 0:
         line["green_kubo"] = green_kubo_section(T, torch, args, N, L)
+    if not args.no_kick and rank == 0:
+        line["kick_mothers"] = kick_section(T, torch, args, N, L)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, N)
     if rank == 0:
@@ -448,6 +451,43 @@ def green_kubo_section(T, torch, args, N, L):
         per.append(V / Tt * float(np.sum(0.5 * (acf[1:] + acf[:-1])) * 10 * dt))
     return {"eta_gk_t_end": float(r["eta_gk"][-1]), "eta_gk_se": float(np.std(per, ddof=1) / np.sqrt(chains)),
             "t_end": lag * dt, "chains": chains, "steps_per_chain": n, "seconds": el}
+
+
+def kick_section(T, torch, args, N, L):
+    """Further mother states from one thermalised state by small momentum
+    kicks (ttcf_kick_states): device time of 152 kicked copies of one
+    thermalised N=2048 state (kick 1e-6 sqrt(T), device buffers), and the
+    number of steps after which the copies, run as GPU mother chains,
+    spread in P_xy like independent equilibrium samples (90 % of the
+    equilibrium spread, 20-step running mean)."""
+    from paper_2312_02990_gb300 import inputs
+    copies, kick, n_run = 152, 1e-6, 6000
+    cfg = T.config_default()
+    cfg.precision = T.TTCF_MIXED
+    with T.Context(cfg) as c:
+        st, _ = c.sample_mothers(inputs.initial_state(N, inputs.BASE_SEED + 90000), L, n_eq=4000,
+                                 n_states=1, spacing=1)
+        st = np.asarray(st).reshape(6, N)
+        dev = torch.from_numpy(st).cuda()
+        c.kick_states(dev, copies, kick, 1)            # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        cp = c.kick_states(dev, copies, kick, inputs.BASE_SEED)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = c.mother_acf(cp.cpu().numpy(), L, n_eq=0, n_steps=n_run, max_lag=10, want_series=True)
+    ser = r["series"]
+    eq = float(ser[:, -2000:].std())
+    spread = np.convolve(ser.std(axis=0), np.ones(20) / 20, mode="valid")
+    above = np.nonzero(spread >= 0.9 * eq)[0]
+    return {"copies": copies, "kick": kick, "n_atoms": N, "kick_ms": ms,
+            "bytes_written": copies * 6 * N * 8, "write_GB_per_s": copies * 6 * N * 8 / (ms * 1e-3) / 1e9,
+            "decorrelation_steps": int(above[0]) if above.size else None,
+            "decorrelation_time": float(above[0] * 0.0025) if above.size else None,
+            "spread_at_start": float(spread[0] / eq), "thermalisation_steps_of_the_source": 4000,
+            "note": "IEEE-double kernel (log, sin, cos per kick): bound by the FP64 pipe, not by HBM"}
 
 
 def precision_floor_section(T, torch, args):
