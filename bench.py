@@ -491,39 +491,69 @@ def kick_section(T, torch, args, N, L):
 
 
 def precision_floor_section(T, torch, args):
-    """TTCF viscosity of the N=256 system at shear rates 1e-3 ... 1e-15 in
-    MIXED and FP64 arithmetic on the same 256 mother states (64 GPU mother
-    chains x 4 states), 4 mappings, 500 steps: the estimate and its standard
-    error stay flat down to 1e-15 (Omega(0) is exactly proportional to the
-    rate and the products are accumulated in IEEE double), while the direct
-    average's error grows as 1/rate."""
+    """Signal, noise and precision floor across the shear rate (Eqs. 13-17):
+    the N=256 system at every decade from 1e-1 to 1e-15, MIXED and FP64, on
+    the same 256 mother states (64 GPU mother chains x 4 states), 4
+    mappings, 4000 steps, read at t = 1.25 (transient: the four mapped
+    daughters of a mother are still correlated, so the direct average's
+    noise is still small) and t = 10 (past the chaotic decorrelation, the
+    steady state the paper's analysis assumes).  Per rate and time:
+    <P_xy> by TTCF and by direct average (DAV) with their standard errors
+    over mother groups, the signal-to-noise ratios |<P_xy>|/SE,
+    sigma(Omega(0)) over daughters, the standard error of the integrand
+    <Omega(0) P_xy(t)>, the viscosities; and the log-log slopes against the
+    rate over the linear regime (rate <= 1e-3) of sigma(Omega(0)), the
+    integrand's SE and the SEs of <P_xy> by TTCF and DAV, which the paper's
+    analysis (steady state) predicts as 1, 1, 1 and 0: SNR_TTCF flat and
+    SNR_DAV proportional to the rate."""
     from paper_2312_02990_gb300 import inputs
-    N = 256
+    N, n_steps = 256, 4000
     L = inputs.bulk_box(N)
-    rates = [1e-3, 1e-7, 1e-11, 1e-15]
+    rates = [10.0 ** -k for k in range(1, 16)]
+    times = {"t1.25": 500, "t10": 4000}
     cfg = T.config_default()
     cfg.precision = T.TTCF_MIXED
     init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 90000 + k) for k in range(64)])
     with T.Context(cfg) as c:
         ms, al = c.sample_mothers(init, L, n_eq=4000, n_states=4, spacing=200)
     ms, al = ms.reshape(-1, 6, N), al.reshape(-1)
-    out = {}
+    D = 4 * ms.shape[0]
+    out, slopes = {}, {}
+    t0 = time.perf_counter()
     for name, prec in (("mixed", T.TTCF_MIXED), ("fp64", T.TTCF_FP64)):
         cfg = T.config_default()
-        cfg.precision, cfg.n_steps = prec, 500
+        cfg.precision, cfg.n_steps = prec, n_steps
         with T.Context(cfg) as c:
             ids = [c.spawn_daughters(ms, al, g, box=L) for g in rates]
             c.run()
-            res = {}
+            res = {tk: {} for tk in times}
             for g, b in zip(rates, ids):
                 v = c.viscosity(b)
-                res[f"{g:.0e}"] = {"eta_ttcf": float(v["eta_ttcf"][-1]),
-                                   "eta_ttcf_se": float(v["eta_ttcf_se"][-1]),
-                                   "eta_dav": float(v["eta_dav"][-1]),
-                                   "eta_dav_se": float(v["eta_dav_se"][-1])}
+                r = c.response(b)
+                _, om = c.daughter_series(b, D)
+                for tk, s in times.items():
+                    res[tk][f"{g:.0e}"] = {
+                        "eta_ttcf": float(v["eta_ttcf"][s]), "eta_ttcf_se": float(v["eta_ttcf_se"][s]),
+                        "eta_dav": float(v["eta_dav"][s]), "eta_dav_se": float(v["eta_dav_se"][s]),
+                        "pxy_ttcf": float(r["ttcf"][s]), "pxy_ttcf_se": float(r["ttcf_se"][s]),
+                        "pxy_dav": float(r["dav"][s]), "pxy_dav_se": float(r["dav_se"][s]),
+                        "snr_ttcf": float(abs(r["ttcf"][s]) / r["ttcf_se"][s]),
+                        "snr_dav": float(abs(r["dav"][s]) / r["dav_se"][s]),
+                        "sigma_omega0": float(np.std(om)), "integrand_se": float(r["corr_se"][s])}
             out[name] = res
-    return {"workload": "bulk WCA N=256, 256 mother states x 4 mappings, 500 steps, t_end = 1.25",
-            "results": out}
+        lin = [g for g in rates if g <= 1e-3]
+        lg = np.log10(lin)
+        slopes[name] = {}
+        for tk in times:
+            def slope(key):
+                y = np.array([res[tk][f"{g:.0e}"][key] for g in lin])
+                return float(np.polyfit(lg, np.log10(y), 1)[0]) if np.all(y > 0) else None
+            slopes[name][tk] = {k: slope(k) for k in ("sigma_omega0", "integrand_se", "pxy_ttcf_se", "pxy_dav_se")}
+    return {"workload": f"bulk WCA N=256, {ms.shape[0]} mother states x 4 mappings, {n_steps} steps, "
+                        "read at t = 1.25 and t = 10, rates 1e-1 ... 1e-15",
+            "snr": "|<P_xy(t)>| / its standard error over mother groups",
+            "seconds": time.perf_counter() - t0,
+            "slopes_rate_le_1e-3": slopes, "results": out}
 
 
 def confined_section(T, torch, args):
