@@ -82,6 +82,7 @@ def parse():
     p.add_argument("--no-floor", action="store_true", help="skip the precision-floor sweep")
     p.add_argument("--no-gk", action="store_true", help="skip the Green-Kubo cross-check")
     p.add_argument("--no-kick", action="store_true", help="skip the momentum-kick mothers section")
+    p.add_argument("--no-mapstudy", action="store_true", help="skip the mapping-set / Eq. 4 study")
     p.add_argument("--confined-only", action="store_true",
                    help="run only the confined-channel section and print its JSON")
     p.add_argument("--conf-chains", type=int, default=38, help="independent confined mother chains")
@@ -351,6 +352,8 @@ def bench_gb300(args):
         line["green_kubo"] = green_kubo_section(T, torch, args, N, L)
     if not args.no_kick and rank == 0:
         line["kick_mothers"] = kick_section(T, torch, args, N, L)
+    if not args.no_mapstudy and rank == 0:
+        line["mapping_study"] = mapping_study_section(T, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, N)
     if rank == 0:
@@ -451,6 +454,63 @@ def green_kubo_section(T, torch, args, N, L):
         per.append(V / Tt * float(np.sum(0.5 * (acf[1:] + acf[:-1])) * 10 * dt))
     return {"eta_gk_t_end": float(r["eta_gk"][-1]), "eta_gk_se": float(np.std(per, ddof=1) / np.sqrt(chains)),
             "t_end": lag * dt, "chains": chains, "steps_per_chain": n, "seconds": el}
+
+
+def mapping_study_section(T, torch, args):
+    """Mapping sets against the Eq. 4 correction: TTCF viscosity of the
+    N=256 system at t = 2.5 from the same 256 mother states with the four
+    mappings of Eq. 3 (<Omega(0)> = 0 in every group), identity plus
+    x-reflection (cancels Omega(0) too), identity plus time reversal (does
+    not: Omega(0) is even under p -> -p) and identity alone; each with the
+    plain TTCF integrand and the Eq. 4 form <Omega(0)B(s)> -
+    <Omega(0)><B(s)>, first with <B(0)> from the data (the library's
+    estimator: the mappings make it exactly 0), then with <B(0)> set to its
+    equilibrium value 0 (the integral alone; standard errors over mother
+    groups from the daughters' series).  The cost-normalised error is
+    SE x sqrt(daughters) (one daughter trajectory's worth of work)."""
+    from paper_2312_02990_gb300 import inputs
+    N, n_steps = 256, 1000
+    L = inputs.bulk_box(N)
+    rates = [1e-2, 1e-4, 1e-6]
+    sets = {"eq3_all4": 0xF, "id_xrefl": 0x5, "id_trev": 0x3, "id_only": 0x1}
+    cfg = T.config_default()
+    cfg.precision = T.TTCF_MIXED
+    init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 91000 + k) for k in range(64)])
+    with T.Context(cfg) as c:
+        ms, al = c.sample_mothers(init, L, n_eq=4000, n_states=4, spacing=200)
+    ms, al = ms.reshape(-1, 6, N), al.reshape(-1)
+    G = ms.shape[0]
+    out = {}
+    for sname, mask in sets.items():
+        cfg = T.config_default()
+        cfg.precision, cfg.n_steps, cfg.mapping_mask = T.TTCF_MIXED, n_steps, mask
+        M = bin(mask).count("1")
+        res = {}
+        with T.Context(cfg) as c:
+            ids = [c.spawn_daughters(ms, al, g, box=L) for g in rates]
+            c.run()
+            for g, b in zip(rates, ids):
+                B, om = c.daughter_series(b, G * M)
+                row = {"daughters": G * M, "omega0_mean_over_sd": float(abs(om.mean()) / om.std())}
+                for est, corr in (("plain", False), ("eq4", True)):
+                    r = c.response(b, corrected=corr)
+                    eta, se = -r["ttcf"][-1] / g, r["ttcf_se"][-1] / g
+                    row[est] = {"eta": float(eta), "se": float(se),
+                                "se_per_daughter": float(se * np.sqrt(G * M))}
+                # the integral alone (<B(0)> = 0 imposed), per mother group
+                dt = cfg.dt * cfg.sample_every
+                I = dt * (0.5 * (B[:, 0] + B[:, -1]) + B[:, 1:-1].sum(axis=1))
+                for est, corr in (("plain_b0_zero", False), ("eq4_b0_zero", True)):
+                    x = om * I
+                    if corr:
+                        x = x - om.mean() * I.mean()
+                    eg = -x.reshape(G, M).mean(axis=1) / g
+                    se = float(eg.std(ddof=1) / np.sqrt(G))
+                    row[est] = {"eta": float(eg.mean()), "se": se, "se_per_daughter": se * np.sqrt(G * M)}
+                res[f"{g:.0e}"] = row
+        out[sname] = res
+    return {"workload": f"bulk WCA N=256, {G} mother states, {n_steps} steps (t = 2.5), MIXED",
+            "results": out}
 
 
 def kick_section(T, torch, args, N, L):
