@@ -393,27 +393,32 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             const float m24c_fj = ti == 0 ? -24.f * (float)b.c_ff : m24cwf;
             float m24c_wj = m24cwf;
             float fx = 0.f, fy = 0.f, fz = 0.f;
-            auto pair = [&](unsigned int j) {
-                const float4 v = pos4[j];
-                const float dx = pbc_f(u.x - v.x, Lx, iLx);
-                const float dy = u.y - v.y;
-                const float dz = pbc_f(u.z - v.z, Lz, iLz);
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                const bool in = r2 < rc2;
-                const float m24c = v.w == 0.f ? m24c_fj : m24c_wj;
-                const float s = rcp_approx(r2), s3 = s * s * s;
-                const float f = in ? s3 * s * __fmaf_rn(48.f, s3, m24c) : 0.f;
-                fx = __fmaf_rn(f, dx, fx);
-                fy = __fmaf_rn(f, dy, fy);
-                fz = __fmaf_rn(f, dz, fz);
-                npairs += in ? 1u : 0u;
+            // the two entries of a word side by side on packed FP32 pairs
+            // (the scalar pair's operations lane by lane; the sums in list
+            // order, entry 0 then entry 1)
+            const float2 ux2 = f2(u.x), uy2 = f2(u.y), uz2 = f2(u.z);
+            auto pair2 = [&](unsigned int w) {
+                const float4 v0 = pos4[w & 0xffffu], v1 = pos4[w >> 16];
+                const float2 ddx = __fadd2_rn(ux2, make_float2(-v0.x, -v1.x));
+                const float2 dx = __ffma2_rn(neg2(rint2(ddx, f2(iLx))), f2(Lx), ddx);
+                const float2 dy = __fadd2_rn(uy2, make_float2(-v0.y, -v1.y));
+                const float2 ddz = __fadd2_rn(uz2, make_float2(-v0.z, -v1.z));
+                const float2 dz = __ffma2_rn(neg2(rint2(ddz, f2(iLz))), f2(Lz), ddz);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const bool in0 = r2.x < rc2, in1 = r2.y < rc2;
+                const float2 m24c = make_float2(v0.w == 0.f ? m24c_fj : m24c_wj, v1.w == 0.f ? m24c_fj : m24c_wj);
+                const float2 sv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+                const float2 s3 = __fmul2_rn(__fmul2_rn(sv, sv), sv);
+                float2 f = __fmul2_rn(__fmul2_rn(s3, sv), __ffma2_rn(f2(48.f), s3, m24c));
+                f.x = in0 ? f.x : 0.f;
+                f.y = in1 ? f.y : 0.f;
+                fx = __fmaf_rn(f.x, dx.x, fx); fy = __fmaf_rn(f.x, dy.x, fy); fz = __fmaf_rn(f.x, dz.x, fz);
+                fx = __fmaf_rn(f.y, dx.y, fx); fy = __fmaf_rn(f.y, dy.y, fy); fz = __fmaf_rn(f.y, dz.y, fz);
+                npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
             };
             auto group = [&](int t) {
                 const uint4 q = nbr[(size_t)t * nmax + i];
-                pair(q.x & 0xffffu); pair(q.x >> 16);
-                pair(q.y & 0xffffu); pair(q.y >> 16);
-                pair(q.z & 0xffffu); pair(q.z >> 16);
-                pair(q.w & 0xffffu); pair(q.w >> 16);
+                pair2(q.x); pair2(q.y); pair2(q.z); pair2(q.w);
             };
             for (int t = 0; t < kgf; t++) group(t);
             if (ti != 0) {
