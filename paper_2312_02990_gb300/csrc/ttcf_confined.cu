@@ -274,6 +274,7 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             const float4 u = pos4[i];
             ref[i] = u;
             const bool wall_i = u.w != 0.f;
+            const float2 ux2 = f2(u.x), uy2 = f2(u.y), uz2 = f2(u.z);
             const float wx = pbc_f(u.x, Lx, iLx);
             const float wy = u.y;
             const float wz = pbc_f(u.z, Lz, iLz);
@@ -336,27 +337,41 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                     const int row = (zz * nc1 + yy) * nc0;
                     for (int r = 0; r < nr; r++) {
                         const int t1 = start[row + rb[r] + 1];
-                        for (int j = start[row + ra[r]]; j < t1; j++) {
+                        auto accept = [&](int j, float r2, bool ww) {
+                            if (j == i || (ww && !ww_on) || !(r2 < rl2)) return;
+                            if (ww) {
+                                if (kw < CONF_CAP)
+                                    nbr16[((size_t)(CONF_GROUPS - 1 - (kw >> 3)) * nmax + i) * 8 + (kw & 7)] =
+                                        (unsigned short)j;
+                                kw++;
+                            } else {
+                                if (k < CONF_CAP) {
+                                    push((unsigned int)j);
+                                    if ((k & 7) == 7) nbr[(size_t)(k >> 3) * nmax + i] = make_uint4(w0, w1, w2, w3);
+                                }
+                                k++;
+                            }
+                        };
+                        // two consecutive candidates side by side on packed
+                        // FP32 pairs, accepted in order
+                        int j = start[row + ra[r]];
+                        for (; j + 1 < t1; j += 2) {
+                            const float4 v0 = pos4[j], v1 = pos4[j + 1];
+                            const float2 ddx = __fadd2_rn(ux2, make_float2(-v0.x, -v1.x));
+                            const float2 dx = __ffma2_rn(neg2(rint2(ddx, f2(iLx))), f2(Lx), ddx);
+                            const float2 dy = __fadd2_rn(uy2, make_float2(-v0.y, -v1.y));
+                            const float2 ddz = __fadd2_rn(uz2, make_float2(-v0.z, -v1.z));
+                            const float2 dz = __ffma2_rn(neg2(rint2(ddz, f2(iLz))), f2(Lz), ddz);
+                            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                            accept(j, r2.x, wall_i && v0.w != 0.f);
+                            accept(j + 1, r2.y, wall_i && v1.w != 0.f);
+                        }
+                        if (j < t1) {
                             const float4 v = pos4[j];
-                            const bool ww = wall_i && v.w != 0.f;
-                            if (j == i || (ww && !ww_on)) continue;
                             const float dx = pbc_f(u.x - v.x, Lx, iLx);
                             const float dy = u.y - v.y;
                             const float dz = pbc_f(u.z - v.z, Lz, iLz);
-                            if (dx * dx + dy * dy + dz * dz < rl2) {
-                                if (ww) {
-                                    if (kw < CONF_CAP)
-                                        nbr16[((size_t)(CONF_GROUPS - 1 - (kw >> 3)) * nmax + i) * 8 + (kw & 7)] =
-                                            (unsigned short)j;
-                                    kw++;
-                                } else {
-                                    if (k < CONF_CAP) {
-                                        push((unsigned int)j);
-                                        if ((k & 7) == 7) nbr[(size_t)(k >> 3) * nmax + i] = make_uint4(w0, w1, w2, w3);
-                                    }
-                                    k++;
-                                }
-                            }
+                            accept(j, __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))), wall_i && v.w != 0.f);
                         }
                     }
                 }
