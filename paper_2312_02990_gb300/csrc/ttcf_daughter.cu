@@ -496,10 +496,22 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                             // i against the image of each member: one shared load
                             // and the distance to a fixed shift, no rounding
                             const float ux = xs - (float)(kx + r) * cf->Lf[0];
-                            for (int t = start[row + ra[r]]; t < t1; t++) {
+                            // two consecutive members side by side on packed FP32
+                            // pairs, accepted in order
+                            int t = start[row + ra[r]];
+                            for (; t + 1 < t1; t += 2) {
+                                const float4 v0 = cpos[t], v1 = cpos[t + 1];
+                                const float2 dx = __fadd2_rn(f2(ux), make_float2(-v0.x, -v1.x));
+                                const float2 dy = __fadd2_rn(f2(uy), make_float2(-v0.y, -v1.y));
+                                const float2 dz = __fadd2_rn(f2(uz), make_float2(-v0.z, -v1.z));
+                                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                                if (r2.x < rl2) { const int j = __float_as_int(v0.w); if (j != i) push(j); }
+                                if (r2.y < rl2) { const int j = __float_as_int(v1.w); if (j != i) push(j); }
+                            }
+                            if (t < t1) {
                                 const float4 v = cpos[t];
                                 const float dx = ux - v.x, dy = uy - v.y, dz = uz - v.z;
-                                const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+                                const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
                                 if (r2 < rl2) {
                                     const int j = __float_as_int(v.w);
                                     if (j != i) push(j);
