@@ -46,9 +46,9 @@ FLOPS_PER_PAIR_LJ = 25.0         # one unique LJ-c_ij pair of the confined syste
 # profiles/*.md), scaled to a launch by the units it processes:
 # daughter_kernel reads its mothers (per daughter) and writes the series (per
 # sample); conf_kernel streams its per-CTA scratch (per atom-step).
-BULK_READ_PER_DAUGHTER = 31.0e3
-BULK_WRITE_PER_SAMPLE = 11.0
-CONF_BYTES_PER_ATOM_STEP = 394.0
+BULK_READ_PER_DAUGHTER = 31.1e3
+BULK_WRITE_PER_SAMPLE = 11.2
+CONF_BYTES_PER_ATOM_STEP = 397.0
 CONF_RATES = [1e-1, 1e-3, 1e-5, 1e-7]
 
 
