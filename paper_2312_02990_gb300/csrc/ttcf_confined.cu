@@ -3,8 +3,9 @@
 // A Lennard-Jones fluid between two walls of atoms tethered by springs of
 // stiffness k to lattice sites; during a daughter the bottom lattice slides
 // at -v and the top one at +v in x, v = gamma h / 2 (Eq. 10).  Pair
-// potential 4[r^-12 - c_ij r^-6] cut at r_c (Eq. 9); wall atoms do not
-// interact with each other.  Fluid: velocity Verlet.  Walls: the same plus a
+// potential 4[r^-12 - c_ij r^-6] cut at r_c (Eq. 9), c_ij = c_ff, c_wf or,
+// for wall-wall pairs, c_ww (switchable: with it off only the tethers hold
+// the walls).  Fluid: velocity Verlet.  Walls: the same plus a
 // Nose-Hoover multiplier on their momenta, alpha' = (sum_w p^2 - g T)/Q,
 // split symmetrically E B A B E around the velocity-Verlet step.  x and z
 // are periodic, y is bounded by the walls.

@@ -86,7 +86,8 @@ struct Coef {
 
 struct Misc {
     double slot[MAX_WARPS][3];   // per-warp partial sums (df packed or double)
-    // IEEE-double scalars of the daughter, touched by thread 0 only
+    // per-daughter scalars in IEEE double (the FP64 mode's step-end chain;
+    // in MIXED mode the set-up values), touched by thread 0 only
     double a_end, a_cur, K2_end, e1, delta, f1sq;
     double hhQ, invV, ddelta, halfLx;   // per-daughter constants
     // MIXED mode: the same chain in double-float on the FP32 pipe (an IEEE-
@@ -243,7 +244,8 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
 
     uint4 *nbr4 = reinterpret_cast<uint4 *>(a.nbr + (size_t)blockIdx.x * (CAP / 2) * nmax);
 
-    // thread 0 keeps the IEEE-double scalars of the daughter in shared memory
+    // thread 0 keeps the per-daughter scalars in shared memory (IEEE double;
+    // MIXED mode steps the double-float copies in Misc)
     double &a_end = m->a_end, &a_cur = m->a_cur, &K2_end = m->K2_end, &e1 = m->e1;
     double &delta = m->delta, &f1sq = m->f1sq;
     float &dsince = m->dsince;
@@ -396,7 +398,8 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         return min(max(c, 0), nc[k] - 1);
     };
 
-    // ---- Verlet list: cell binning (width >= r_c + skin), sorted lists ----
+    // ---- Verlet list: cell binning (cells cell_frac (r_c + skin) wide; the
+    //      window of cells covers r_l = r_c + skin), sorted lists ----
     auto build_list = [&]() {
         const int ncell = b.ncell;
         for (int c = tid; c < ncell; c += T) cnt[c] = 0;
