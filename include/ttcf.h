@@ -472,8 +472,11 @@ ttcf_status ttcf_cv_data(ttcf_ctx *ctx, int batch_id, float *X, double *z, size_
 
 /* Train the network on the daughters of a finished batch (all shear rates
  * allowed; targets are normalised by gamma).  The last `holdout` fraction
- * of its valid groups fits c instead.  Stores the network in the context;
- * loss_curve (may be NULL) receives the mean training loss per epoch.     */
+ * of its valid groups is held out: after every epoch the variance reduction
+ * of the group control variate on them is measured, the weights of the best
+ * epoch are kept (early stopping), and c is fitted on them.  Stores the
+ * network in the context; loss_curve (may be NULL) receives the mean
+ * training loss per epoch.                                                 */
 ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg,
                           double *loss_curve, int capacity);
 

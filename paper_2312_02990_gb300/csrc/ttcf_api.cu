@@ -1870,6 +1870,7 @@ ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg
     float *part = tmp.get<float>((size_t)tiles * CV_NP);
     double *lpart = tmp.get<double>(tiles), *loss = tmp.get<double>(1);
     double *yg = tmp.get<double>(nhold), *hg = tmp.get<double>(nhold), *est = tmp.get<double>(8);
+    float *wbest = tmp.get<float>(CV_NP);
     CvModel &cvm = ctx->cv;
     if (!cvm.w) {
         Pool keep(ctx);
@@ -1918,6 +1919,7 @@ ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg
     if (nb < 1) return fail(ctx, TTCF_E_INVALID, "fewer training daughters than one minibatch");
     std::vector<int> perm(rows);
     uint64_t sh = cfg->seed ^ 0xA5A5A5A5A5A5A5A5ull;
+    double best_gain = 0.0;
     for (int ep = 0; ep < cfg->epochs; ep++) {
         for (int k = nrows - 1; k > 0; k--) {
             const int j = (int)(splitmix64(sh) % (uint64_t)(k + 1));
@@ -1933,9 +1935,24 @@ ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg
         }
         double l = 0.0;
         CK(cudaMemcpyAsync(&l, loss, sizeof(double), cudaMemcpyDeviceToHost, sm));
+        // early stopping: the variance reduction 1/(1 - rho^2) of the group
+        // control variate on the held-out groups; the best epoch's weights
+        // are kept (the per-daughter target is mostly noise, and later
+        // epochs fit it)
+        CK(cv_launch_predict(cvm.wb, X, D, f, ctx->nsm, sm));
+        CK(cv_launch_group(z, f, cvm.zstats, b->M, d_hold, nhold, yg, hg, sm));
+        CK(cv_launch_estimate(yg, hg, nhold, nullptr, 0, 1, 0.0, est, sm));
+        double eh[8];
+        CK(cudaMemcpyAsync(eh, est, sizeof(eh), cudaMemcpyDeviceToHost, sm));
         CK(cudaStreamSynchronize(sm));
         if (loss_curve && ep < capacity) loss_curve[ep] = l / nb;
+        if (ep == 0 || eh[5] > best_gain) {
+            best_gain = eh[5];
+            CK(cudaMemcpyAsync(wbest, cvm.w, sizeof(float) * CV_NP, cudaMemcpyDeviceToDevice, sm));
+        }
     }
+    CK(cudaMemcpyAsync(cvm.w, wbest, sizeof(float) * CV_NP, cudaMemcpyDeviceToDevice, sm));
+    CK(cv_launch_to_bf16(cvm.w, cvm.wb, sm));
     // c from the held-out groups
     CK(cv_launch_predict(cvm.wb, X, D, f, ctx->nsm, sm));
     CK(cv_launch_group(z, f, cvm.zstats, b->M, d_hold, nhold, yg, hg, sm));
