@@ -276,6 +276,30 @@ def test_ragged_sizes_and_uneven_batch_in_one_run(ttcf):
                     assert Om[4 * g + m] == pytest.approx(omo, rel=1e-12, abs=1e-300)
 
 
+def test_uneven_batch_in_one_graph_launch(ttcf):
+    """The uneven-batch workload at its sizes: N = 256, 864 and 4000 mixed
+    with shear rates 1e-2 ... 1e-6 in one graph-captured run (MIXED), launch
+    shapes chosen by the autotuner per N (N = 4000 takes the index-only list
+    layout); two daughters of every (N, rate) batch against the oracle for
+    100 steps."""
+    sizes, rates, n = (256, 864, 4000), [1e-2, 1e-3, 1e-4, 1e-5, 1e-6], 100
+    states = {N: inputs.jittered_states(N, 2, seed=500 + N, amp=0.05) for N in sizes}
+    with ctx(ttcf, precision=1, n_steps=n, use_graph=1) as c:
+        for N in sizes:
+            c.autotune(states[N], bulk(N).L, n_steps=20)
+        ids = {(N, g): c.spawn_daughters(states[N], None, g, box=bulk(N).L) for N in sizes for g in rates}
+        c.run()
+        out = {k: c.daughter_series(b, 8) for k, b in ids.items()}
+        status = {k: c.group_status(b, 2) for k, b in ids.items()}
+    for (N, g), (B, Om) in out.items():
+        assert np.all(status[(N, g)] == 0), (N, g)
+        b = bulk(N)
+        for d in (0, 5):   # group 0 unmapped, group 1 time-reversed
+            Bo, omo, _, _ = oracle.daughter(b, states[N][d // 4], 0.0, d % 4, g, n)
+            assert Om[d] == pytest.approx(omo, rel=1e-10, abs=1e-300)
+            assert np.abs(B[d] - Bo).max() < 1e-4 * np.abs(Bo).max(), (N, g, d)
+
+
 def test_invalid_inputs_are_rejected(ttcf):
     T = ttcf
     with ctx(T, precision=1, n_steps=10) as c:
