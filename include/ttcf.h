@@ -481,8 +481,9 @@ ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg
                           double *loss_curve, int capacity);
 
 /* Control-variate estimate of eta(t_end) for a finished evaluation batch,
- * with n_aux auxiliary mother states [n_aux][6][N] (host, same N and box;
- * alpha may be NULL).  out[8]: eta_plain, se_plain, eta_cv, se_cv, c,
+ * with n_aux auxiliary mother states [n_aux][6][N] (same N and box; alpha
+ * may be NULL), host arrays or device arrays of the context's device (the
+ * kind is read from aux_soa; aux_alpha must be of the same kind).  out[8]: eta_plain, se_plain, eta_cv, se_cv, c,
  * gain = se_plain^2 / se_cv^2, n_groups, n_aux.                             */
 ttcf_status ttcf_cv_apply(ttcf_ctx *ctx, int batch_id, int n_aux, const double *aux_soa,
                           const double *aux_alpha, double out[8]);

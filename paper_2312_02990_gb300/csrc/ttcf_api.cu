@@ -1997,9 +1997,19 @@ ttcf_status ttcf_cv_apply(ttcf_ctx *ctx, int batch_id, int n_aux, const double *
     CK(cv_launch_standardize(X, D, cvm.fstats, nullptr, nullptr, nullptr, sm));
     CK(cv_launch_predict(cvm.wb, X, D, f, ctx->nsm, sm));
     CK(cv_launch_group(z, f, cvm.zstats, b->M, d_g, ng, yg, hg, sm));
-    // auxiliary mothers: spawn (features only), mapped features, predictions
+    // auxiliary mothers: spawn (features only), mapped features, predictions;
+    // they may be host or device arrays (both pointers of one kind)
+    int aux_dev = 0;
+    {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, aux_soa) == cudaSuccess &&
+            (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged))
+            aux_dev = 1;
+        cudaGetLastError();
+    }
     BatchHost ab;
-    s = make_batch(ctx, tmp, ab, b->N, b->L, n_aux, aux_soa, aux_alpha, nullptr, 0, b->maps, b->M, 1, 0.0);
+    s = make_batch(ctx, tmp, ab, b->N, b->L, n_aux, aux_soa, aux_alpha, nullptr, aux_dev, b->maps, b->M, 1,
+                   0.0);
     if (s != TTCF_OK) return s;
     const long long DA = ab.D();
     float *XA = tmp.get<float>((size_t)DA * CV_NF);

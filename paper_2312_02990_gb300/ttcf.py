@@ -499,11 +499,20 @@ class Context:
         return loss
 
     def cv_apply(self, batch: int, aux_soa, aux_alpha=None) -> dict:
-        a = _f64(aux_soa)
-        al = None if aux_alpha is None else _f64(aux_alpha)
+        """aux_soa [n, 6, N]: numpy host array or torch CUDA tensor (aux_alpha
+        of the same kind, or None)."""
         out = np.zeros(8)
-        self._check(self._L.ttcf_cv_apply(self.h, batch, int(a.shape[0]), _ptr(a),
-                                          None if al is None else _ptr(al), _ptr(out)))
+        if hasattr(aux_soa, "is_cuda") and aux_soa.is_cuda:
+            import torch
+            a = aux_soa.contiguous().to(torch.float64)
+            al = None if aux_alpha is None else torch.as_tensor(aux_alpha, dtype=torch.float64,
+                                                                device=a.device).contiguous()
+            pa, pal = C.cast(a.data_ptr(), _dp), (C.cast(al.data_ptr(), _dp) if al is not None else None)
+        else:
+            a = _f64(aux_soa)
+            al = None if aux_alpha is None else _f64(aux_alpha)
+            pa, pal = _ptr(a), (None if al is None else _ptr(al))
+        self._check(self._L.ttcf_cv_apply(self.h, batch, int(a.shape[0]), pa, pal, _ptr(out)))
         keys = ("eta_plain", "se_plain", "eta_cv", "se_cv", "c", "gain", "n_groups", "n_aux")
         return dict(zip(keys, out.tolist()))
 

@@ -89,7 +89,12 @@ def test_control_variate_is_unbiased_and_reduces_variance(T):
         cfg.epochs = 25
         loss = c.cv_train(bt, cfg)
         r = c.cv_apply(be, ms[aux], al[aux])
+        # the same auxiliary states from device memory give the same numbers
+        import torch
+        rd = c.cv_apply(be, torch.from_numpy(np.ascontiguousarray(ms[aux])).cuda(),
+                        torch.from_numpy(np.ascontiguousarray(al[aux])).cuda())
         v = c.viscosity(be)
+    assert rd == r
     assert loss[-1] < 0.9 * loss[0]
     assert r["n_groups"] == nD and r["n_aux"] == 16 * nD
     assert r["eta_plain"] == pytest.approx(v["eta_ttcf"][-1], rel=1e-9)
