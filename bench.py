@@ -4,17 +4,25 @@
 Workload (bulk WCA, Example 1 state point; the 16384-daughter configuration):
 N = 2048 atoms, rho = 0.8442, T = 0.722, dt = 0.0025; 4096 mother states
 (64 independent mothers x 64 states 200 steps apart after 20000
-thermalisation steps), x4 mappings = 16384 daughters of 1000 steps, at each
-shear rate 1e-1 ... 1e-7 (the rates reuse the same mothers).  One benchmark
-step = one full pass of the hot path over that batch: spawn (mapping,
-Omega(0), B(0)), the persistent daughter run of every daughter at every
-rate in one launch, and the on-device reduction of <Omega(0)B(s)>, its
-integral and the direct average.  Inputs are synthetic and seeded.
+thermalisation steps), x4 mappings = 16384 daughters of 1000 steps.  The
+shear rates 1e-1 ... 1e-7 reuse the same mothers.  One benchmark step = one
+full pass of the hot path over the 16384-daughter batch at one shear rate:
+spawn (mapping, Omega(0), B(0)), the persistent daughter launch and the
+on-device reduction of <Omega(0)B(s)>, its integral and the direct average;
+successive steps take the rates in turn (1e-1, 1e-2, ..., 1e-7, 1e-1, ...).
+Inputs are synthetic and seeded.
 
-value  = sum over daughters of N * steps / device time of the step, inputs
+value  = sum over daughters of N * steps / device time of the steps, inputs
          resident in HBM (mothers made on the GPU before timing);
 e2e    = the same through the C ABI with host buffers: mothers copied from
-         pinned host memory and responses read back inside the timed region.
+         pinned host memory and the viscosity read back inside the timed
+         region.
+
+The last stdout line is the compact result (one JSON object of < 2 KB).
+The long sections (confined channel, uneven batch, control variate,
+precision floor, Green-Kubo, momentum kicks, mapping study, plain GPU arm,
+oracle parity sample) are printed before it, one JSON line each, or written
+to the file given by --sections-out.
 
 Launch:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs the same per-GPU workload on its own mothers
@@ -26,8 +34,11 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
+import shutil
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -37,6 +48,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
 RATES = [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7]
+HEADLINE_RATES = (1e-1, 1e-3, 1e-7)
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (sm_103)
 N_SM = 152
 SM_MAX_MHZ = 2070.0
@@ -50,6 +62,9 @@ BULK_READ_PER_DAUGHTER = 31.1e3
 BULK_WRITE_PER_SAMPLE = 11.2
 CONF_BYTES_PER_ATOM_STEP = 397.0
 CONF_RATES = [1e-1, 1e-3, 1e-5, 1e-7]
+UNEVEN_SIZES = (256, 864, 4000)
+UNEVEN_RATES = [1e-2, 1e-3, 1e-4, 1e-5, 1e-6]
+PROBE_SRC = os.path.join(HERE, "paper_2312_02990_gb300", "microbench", "alu_rates.cu")
 
 
 def fp32_peak_tflops(mhz=SM_MAX_MHZ):
@@ -59,17 +74,22 @@ def fp32_peak_tflops(mhz=SM_MAX_MHZ):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=7)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n-atoms", type=int, default=2048)
     p.add_argument("--mothers", type=int, default=64)
     p.add_argument("--states", type=int, default=64)
     p.add_argument("--daughter-steps", type=int, default=1000)
-    p.add_argument("--rates", type=int, default=7, help="number of shear rates per step")
     p.add_argument("--n-eq", type=int, default=20000)
     p.add_argument("--spacing", type=int, default=200)
+    p.add_argument("--sections-out", default=None,
+                   help="write the long sections to this JSON file instead of stdout lines")
+    p.add_argument("--no-sections", action="store_true", help="headline only (with the CPU baseline)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--oracle-groups", type=int, default=16,
+                   help="mother groups of the oracle sample (CPU baseline and parity per rate)")
+    p.add_argument("--oracle-eq", type=int, default=2000)
     p.add_argument("--no-cv", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cv-train-groups", type=int, default=16384)
@@ -78,18 +98,23 @@ def parse():
     p.add_argument("--cv-steps", type=int, default=500)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-confined", action="store_true")
+    p.add_argument("--no-uneven", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-floor", action="store_true", help="skip the precision-floor sweep")
     p.add_argument("--no-gk", action="store_true", help="skip the Green-Kubo cross-check")
     p.add_argument("--no-kick", action="store_true", help="skip the momentum-kick mothers section")
     p.add_argument("--no-mapstudy", action="store_true", help="skip the mapping-set / Eq. 4 study")
-    p.add_argument("--confined-only", action="store_true",
-                   help="run only the confined-channel section and print its JSON")
-    p.add_argument("--conf-chains", type=int, default=38, help="independent confined mother chains")
+    p.add_argument("--no-probe", action="store_true", help="skip the FP32 throughput probe")
+    p.add_argument("--only", default=None,
+                   help="run one section alone and print its JSON (confined, uneven, cv, floor, "
+                        "gk, kick, mapstudy, probe)")
+    p.add_argument("--conf-chains", type=int, default=64, help="independent confined mother chains")
     p.add_argument("--conf-states", type=int, default=4, help="mother states per chain")
     p.add_argument("--conf-eq", type=int, default=4000)
     p.add_argument("--conf-spacing", type=int, default=200)
     p.add_argument("--conf-steps", type=int, default=2000)
+    p.add_argument("--uneven-chains", type=int, default=64)
+    p.add_argument("--uneven-states", type=int, default=4)
     return p.parse_args()
 
 
@@ -154,39 +179,65 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+class Sections:
+    """The long sections: one JSON line each on stdout (before the compact
+    result line), or collected into one JSON file."""
+
+    def __init__(self, path):
+        self.path = path
+        self.all = {}
+
+    def emit(self, name, d):
+        self.all[name] = d
+        if self.path is None:
+            print(json.dumps({"section": name, **d}), flush=True)
+
+    def close(self):
+        if self.path is not None:
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
+            with open(self.path, "w") as f:
+                json.dump(self.all, f, indent=1)
+
+
 # --------------------------------------------------------------- GB300 --
-def make_mothers(T, torch, args, rank, N, L):
-    """Equilibrium mothers on the GPU (untimed set-up)."""
+def make_mothers(T, args, rank, N, L, n_mothers=None, n_states=None, seed_off=0, n_eq=None):
+    """Equilibrium mothers on the GPU (untimed set-up): [G, 6, N], [G]."""
     from paper_2312_02990_gb300 import inputs
-    init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 1000 * rank + k)
-                     for k in range(args.mothers)])
+    nm = n_mothers or args.mothers
+    init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 1000 * rank + seed_off + k)
+                     for k in range(nm)])
     cfg = T.config_default()
     cfg.precision = T.TTCF_MIXED
     with T.Context(cfg) as c:
-        ms, al = c.sample_mothers(init, L, n_eq=args.n_eq, n_states=args.states,
-                                  spacing=args.spacing)
+        ms, al = c.sample_mothers(init, L, n_eq=args.n_eq if n_eq is None else n_eq,
+                                  n_states=n_states or args.states, spacing=args.spacing)
     return ms.reshape(-1, 6, N), al.reshape(-1)
 
 
-def one_step(T, torch, args, L, mothers_dev, alpha_dev, rates, host=None):
-    """One pass of the hot path.  Device inputs, or host (pinned) inputs."""
+def bench_config(T, args, precision=None):
     cfg = T.config_default()
-    cfg.precision = T.TTCF_MIXED
+    cfg.precision = T.TTCF_MIXED if precision is None else precision
     cfg.n_steps = args.daughter_steps
     if args.tuned:   # launch variant and skin chosen by the autotuner (set-up)
         cfg.kernel_variant, cfg.skin, cfg.cell_frac = args.tuned
-    c = T.Context(cfg)
-    ids = []
-    for g in rates:
-        if host is None:
-            ids.append(c.spawn_daughters(mothers_dev, alpha_dev, float(g), box=L))
-        else:
-            ids.append(c.spawn_daughters(host[0], host[1], float(g), box=L))
+    return cfg
+
+
+def one_step(T, args, L, rate, mothers, alpha, want_response=False):
+    """One pass of the hot path over the batch at one shear rate, through
+    the C ABI: create, spawn (device or host inputs), run, read back the
+    viscosity (and the response)."""
+    c = T.Context(bench_config(T, args))
+    bid = c.spawn_daughters(mothers, alpha, float(rate), box=L)
     c.run()
-    out = [(c.viscosity(bid), c.response(bid)) for bid in ids]
+    v = c.viscosity(bid)
+    r = None
+    if want_response:   # for the multi-rank merge (with <Omega(0)> for the Eq. 4 form)
+        r = c.response(bid)
+        r["omega_mean"], r["n_valid"] = c.omega_mean(bid)
     stats = c.get_stats()
     c.close()
-    return out, stats
+    return v, r, stats
 
 
 def bench_gb300(args):
@@ -196,25 +247,29 @@ def bench_gb300(args):
     from paper_2312_02990_gb300 import ttcf as T
 
     rank, world, local = dist_info()
+    torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    T.load(build_if_missing=(rank == 0))
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        T.load(build_if_missing=True)
+    if world > 1:   # the other ranks load the library rank 0 built
+        torch.distributed.barrier()
+        T.load(build_if_missing=False)
     N = args.n_atoms
     L = inputs.bulk_box(N)
-    rates = RATES[:args.rates]
+    sec = Sections(args.sections_out)
 
     t0 = time.time()
-    ms, al = make_mothers(T, torch, args, rank, N, L)
+    ms, al = make_mothers(T, args, rank, N, L)
     t_mothers = time.time() - t0
     G = ms.shape[0]
-    D = 4 * G * len(rates)
-    atom_steps = float(D) * N * args.daughter_steps
+    D = 4 * G
+    atom_steps = float(D) * N * args.daughter_steps     # per benchmark step
     ms_dev = torch.from_numpy(ms).cuda()
     al_dev = torch.from_numpy(al).cuda()
-    # the autotuner times every launch variant and Verlet skin on a sample of
-    # these mothers (untimed set-up) and the run uses its choice
+    # the autotuner times every launch variant, Verlet skin and list-cell
+    # width on a sample of these mothers (untimed set-up); the runs use it
     args.tuned = None
     if not args.no_autotune:
         cfg = T.config_default()
@@ -230,8 +285,8 @@ def bench_gb300(args):
         torch.cuda.synchronize()
 
     st = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        one_step(T, torch, args, L, ms_dev, al_dev, rates)
+    for k in range(args.warmup):
+        one_step(T, args, L, RATES[k % len(RATES)], ms_dev, al_dev)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -239,13 +294,15 @@ def bench_gb300(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(st)
     kernel_ms, pairs, rebuilds, launches = [], [], [], 0
-    results = None
-    for _ in range(args.steps):
-        results, s = one_step(T, torch, args, L, ms_dev, al_dev, rates)
+    per_rate = {}
+    for k in range(args.steps):
+        g = RATES[k % len(RATES)]
+        v, r, s = one_step(T, args, L, g, ms_dev, al_dev, want_response=world > 1)
+        per_rate[g] = (v, r)
         kernel_ms.append(s["ms_run"])
         pairs.append(s["pairs_interacting"])
         rebuilds.append(s["rebuilds"])
-        launches += s["launches"] + len(rates)   # + one spawn kernel per batch
+        launches += s["launches"] + 1            # + the spawn kernel
     ev1.record(st)
     barrier()
     clk = clocks.stop()
@@ -257,127 +314,242 @@ def bench_gb300(args):
     ms_step = ms_total / args.steps
     value = atom_steps * world / (ms_step * 1e-3)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers (pinned): the mothers
+    # go host -> device and the viscosity device -> host in every step
     e2e = None
     if not args.no_e2e:
         pin_ms = torch.from_numpy(ms).pin_memory()
         pin_al = torch.from_numpy(al).pin_memory()
         host = (pin_ms.numpy(), pin_al.numpy())
-        one_step(T, torch, args, L, None, None, rates, host=host)
+        one_step(T, args, L, RATES[0], *host)
         barrier()
         t1 = time.perf_counter()
-        for _ in range(args.steps):
-            one_step(T, torch, args, L, None, None, rates, host=host)
+        for k in range(args.steps):
+            one_step(T, args, L, RATES[k % len(RATES)], *host)
         barrier()
         e2e_s = (time.perf_counter() - t1) / args.steps
         if world > 1:
             tt = torch.tensor([e2e_s], device="cuda")
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             e2e_s = float(tt.item())
+        S = args.daughter_steps + 1
         e2e = {"value": atom_steps * world / e2e_s, "unit": "atom-steps/s",
-               "h2d_bytes_per_step": int(len(rates) * (ms.nbytes + al.nbytes + G * 8)),
-               "d2h_bytes_per_step": int(len(rates) * 5 * (args.daughter_steps + 1) * 8),
-               "ms_per_step": e2e_s * 1e3}
+               "h2d_bytes_per_step": int(ms.nbytes + al.nbytes + G * 8),
+               # viscosity (9 x S doubles of the reduction) + per-daughter status/counters
+               "d2h_bytes_per_step": int(9 * S * 8 + D * 16)}
 
-    # the dominant kernel: the persistent daughter launch
+    # the dominant kernel: the persistent daughter launch of one step
     k_ms = float(np.mean(kernel_ms))
     flops = float(np.mean(pairs)) / 2.0 * FLOPS_PER_PAIR
     achieved = flops / (k_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
     traffic = D * (BULK_READ_PER_DAUGHTER + BULK_WRITE_PER_SAMPLE * (args.daughter_steps + 1))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "daughter_kernel", "kernel_ms": k_ms,
-                "algorithmic": "unique interacting pairs x 36 FP32 flops",
-                "peak_note": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 5), "traffic": traffic,
+                "kernel": "daughter_kernel", "kernel_ms": round(k_ms, 2),
+                "peak_src": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
     # the one exchange of the weak-scaled job: per-rate ensemble statistics
     # merged over ranks (each rank's groups are independent)
-    if world > 1:
-        from paper_2312_02990_gb300 import merge
-        merged = [merge.merge_ranks(resp, G) for _, resp in results]
-    else:
-        merged = [resp for _, resp in results]
-    eta = {f"{g:.0e}": {"eta_ttcf": float(-m["ttcf"][-1] / g), "eta_ttcf_se": float(m["ttcf_se"][-1] / g),
-                        "eta_dav": float(-m["dav"][-1] / g), "eta_dav_se": float(m["dav_se"][-1] / g)}
-           for g, m in zip(rates, merged)}
-    results = [v for v, _ in results]
+    eta = {}
+    for g in RATES:
+        if g not in per_rate:
+            continue
+        v, r = per_rate[g]
+        if world > 1:
+            from paper_2312_02990_gb300 import merge
+            m = merge.merge_ranks(r, r["n_valid"], r["omega_mean"])
+            eta[g] = (float(-m["ttcf"][-1] / g), float(m["ttcf_se"][-1] / g),
+                      float(-m["dav"][-1] / g), float(m["dav_se"][-1] / g))
+        else:
+            eta[g] = (float(v["eta_ttcf"][-1]), float(v["eta_ttcf_se"][-1]),
+                      float(v["eta_dav"][-1]), float(v["eta_dav_se"][-1]))
+    sec.emit("viscosity_t_end", {f"{g:.0e}": {"eta_ttcf": e[0], "eta_ttcf_se": e[1], "eta_dav": e[2],
+                                              "eta_dav_se": e[3]} for g, e in eta.items()})
+
+    summary = {}
+    # the oracle on a bounded sample: CPU baseline and per-rate parity
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = guarded("oracle", lambda: oracle_leg(T, args, N, L))
+        if isinstance(res, tuple):
+            cpu, chk = res
+            summary["oracle_err"] = {k: [round(x["d_eta_over_se"], 4), float(f"{x['b_rel_max']:.2e}")]
+                                     for k, x in chk["rates"].items()}
+        else:
+            chk = res
+        sec.emit("oracle_check", chk)
+    if rank == 0 and not args.no_sections:
+        run_sections(T, torch, args, sec, summary, N, L, ms_dev, al_dev, eta, ms_step)
+    sec.close()
+
     line = {
         "metric": "daughter atom-steps/s", "value": value, "unit": "atom-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "precision": "MIXED: FP32 pair forces; float-float positions, momenta and the "
-                                     "per-step alpha/delta chain; FP64 Omega(0), B(s) and accumulation",
+        "dtype": "f32", "precision": "MIXED: FP32 pair forces, float-pair state, FP64 Omega/B/accumulation",
         "data": "synthetic (seeded FCC + Maxwell, GPU-thermalised mothers)",
-        "config": {"workload": f"bulk WCA N={N}, {G} mother states x 4 mappings x {len(rates)} shear "
-                               f"rates = {D} daughters x {args.daughter_steps} steps",
-                   "n_atoms": N, "mother_states": G, "daughters": D,
-                   "daughter_steps": args.daughter_steps, "shear_rates": rates,
-                   "rho": 0.8442, "T": 0.722, "dt": 0.0025,
-                   "autotuned": None if not args.tuned else {"kernel_variant": args.tuned[0],
-                                                             "skin": args.tuned[1],
-                                                             "cell_frac": args.tuned[2]},
-                   "l2": "inputs larger than L2 (mothers 403 MB, series 918 MB)"},
+        "config": {"workload": f"bulk WCA N={N}, {G} mother states x 4 mappings = {D} daughters x "
+                               f"{args.daughter_steps} steps per step, one shear rate per step cycling "
+                               "1e-1..1e-7",
+                   "autotuned": None if not args.tuned else [args.tuned[0], args.tuned[1],
+                                                             round(args.tuned[2], 4)],
+                   "l2": "inputs larger than L2 (mothers 403 MB, series 131 MB per step)"},
         "roofline": roofline,
+        "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
-        "clocks": clk,
-        "pairs_per_atom_step": float(np.mean(pairs)) / (atom_steps),
-        "rebuilds_per_daughter_step": float(np.mean(rebuilds)) / (D * args.daughter_steps),
-        "mother_setup_s": t_mothers,
-        "viscosity_t_end": eta,
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                   "reasons": clk.get("reasons")},
+        "eta_t_end": {f"{g:.0e}": [round(eta[g][0], 4), round(eta[g][1], 4)] for g in HEADLINE_RATES
+                      if g in eta},
+        "pairs_per_atom_step": round(float(np.mean(pairs)) / atom_steps, 4),
+        **summary,
     }
-    # viscosity variance per GPU-second against plain GPU TTCF
-    if not args.no_plain:
-        rate_plain, _ = plain_gpu_rate(T, torch, N, L, ms_dev, al_dev)
-        per_rate_s = ms_step * 1e-3 / len(rates)
-        eff = {}
-        for g, r in zip(rates, results):
-            var = float(r["eta_ttcf_se"][-1]) ** 2
-            t_plain = (atom_steps / len(rates)) / rate_plain
-            eff[f"{g:.0e}"] = {"per_gpu_second": 1.0 / (var * per_rate_s),
-                               "plain_per_gpu_second": 1.0 / (var * t_plain),
-                               "ratio": t_plain / per_rate_s}
-        line["plain_gpu_ttcf"] = {"value": rate_plain, "unit": "atom-steps/s",
-                                  "definition": "FP64 mode, one non-persistent launch per MD step, "
-                                                "no graph, no control variate",
-                                  "sample": "608 daughters x 29 steps, N=2048"}
-        line["viscosity_variance_per_gpu_second"] = eff
-    if not args.no_cv and rank == 0:
-        line["control_variate"] = cv_section(T, torch, args)
-    if not args.no_confined and rank == 0:
-        line["confined"] = confined_section(T, torch, args)
-    if not args.no_floor and rank == 0:
-        line["precision_floor"] = precision_floor_section(T, torch, args)
-    if not args.no_gk and rank == 0:
-        line["green_kubo"] = green_kubo_section(T, torch, args, N, L)
-    if not args.no_kick and rank == 0:
-        line["kick_mothers"] = kick_section(T, torch, args, N, L)
-    if not args.no_mapstudy and rank == 0:
-        line["mapping_study"] = mapping_study_section(T, torch, args)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, N)
     if rank == 0:
-        print(json.dumps(line))
+        out = json.dumps(line)
+        if len(out) > 2000:   # keep the last line short: drop the extras first
+            for k in ("pairs_per_atom_step", "cv", "uneven", "confined"):
+                line.pop(k, None)
+                out = json.dumps(line)
+                if len(out) <= 2000:
+                    break
+        print(out, flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def plain_gpu_rate(T, torch, N, L, ms_dev, al_dev, n_groups=152, n_steps=30):
+def guarded(name, fn):
+    """Run one section; a failure is reported in its place and does not
+    stop the benchmark (the result line is still printed)."""
+    try:
+        return fn()
+    except Exception as e:   # noqa: BLE001 -- reported in the section's JSON
+        return {"error": f"{type(e).__name__}: {e}"[:500], "section_failed": name}
+
+
+def run_sections(T, torch, args, sec, summary, N, L, ms_dev, al_dev, eta, ms_step):
+    """The long sections (rank 0), each emitted as it finishes; a compact
+    digest of each goes into the result line."""
+    try:
+        _run_sections(T, torch, args, sec, summary, N, L, ms_dev, al_dev, eta, ms_step)
+    except Exception as e:   # noqa: BLE001 -- the result line must still be printed
+        summary["sections_error"] = f"{type(e).__name__}: {e}"[:200]
+
+
+def _run_sections(T, torch, args, sec, summary, N, L, ms_dev, al_dev, eta, ms_step):
+    if not args.no_plain:
+        p = guarded("plain", lambda: plain_section(T, torch, args, N, L, ms_dev, al_dev))
+        g = p.get("rate")
+        if g in eta and "efficiency_plain_per_gpu_second" in p:   # efficiency 1/(Var(eta) T_GPU) of the benchmark step at that rate
+            e_new = 1.0 / (eta[g][1] ** 2 * ms_step * 1e-3)
+            p["efficiency_new_per_gpu_second"] = e_new
+            p["efficiency_ratio_new_vs_plain"] = e_new / p["efficiency_plain_per_gpu_second"]
+            summary["var_eff_vs_plain"] = round(p["efficiency_ratio_new_vs_plain"], 2)
+        sec.emit("plain_gpu_ttcf", p)
+    if not args.no_uneven:
+        u = guarded("uneven", lambda: uneven_section(T, torch, args))
+        if "value" in u:
+            summary["uneven"] = {"value": float(f"{u['value']:.4g}"), "frac": round(u["roofline"]["frac"], 4),
+                                 "daughters": u["daughters"]}
+        sec.emit("uneven_batch", u)
+    if not args.no_confined:
+        c = guarded("confined", lambda: confined_section(T, torch, args))
+        if "value" in c:
+            summary["confined"] = {"value": float(f"{c['value']:.4g}"), "frac": round(c["roofline"]["frac"], 4),
+                                   "daughters": c["daughters"]}
+        sec.emit("confined", c)
+    if not args.no_cv:
+        cv = guarded("cv", lambda: cv_section(T, torch, args))
+        if "variance_gain" in cv:
+            summary["cv"] = {"gain": round(cv["variance_gain"], 3),
+                             "eff": round(cv["efficiency_gain_cv_vs_same_kernels"], 3)}
+        sec.emit("control_variate", cv)
+    if not args.no_probe:
+        pr = guarded("probe", probe_section)
+        if pr.get("ffma_tflops_at_max_clock"):
+            summary["fp32_probe_tflops"] = round(pr["ffma_tflops_at_max_clock"], 2)
+        sec.emit("fp32_probe", pr)
+    if not args.no_floor:
+        sec.emit("precision_floor", guarded("floor", lambda: precision_floor_section(T, torch, args)))
+    if not args.no_gk:
+        sec.emit("green_kubo", guarded("gk", lambda: green_kubo_section(T, torch, args, N, L)))
+    if not args.no_kick:
+        sec.emit("kick_mothers", guarded("kick", lambda: kick_section(T, torch, args, N, L)))
+    if not args.no_mapstudy:
+        sec.emit("mapping_study", guarded("mapstudy", lambda: mapping_study_section(T, torch, args)))
+
+
+def plain_section(T, torch, args, N, L, ms_dev, al_dev, n_groups=152, rate=1e-3):
     """Plain GPU TTCF: the same kernels in FP64 mode, one non-persistent
     launch per MD step (chunked runs of one step: state saved and reloaded,
-    list rebuilt), no graph, no control variate.  Atom-steps/s."""
+    list rebuilt), no graph, no control variate, on n_groups of the
+    benchmark's mother states at one rate.  Its own variance and time give
+    its efficiency 1/(Var(eta_TTCF(t_end)) T_GPU), which does not depend on
+    the number of groups (Var ~ 1/G, T ~ G)."""
     cfg = T.config_default()
-    cfg.precision, cfg.n_steps, cfg.use_graph = T.TTCF_FP64, n_steps, 0
+    cfg.precision, cfg.n_steps, cfg.use_graph = T.TTCF_FP64, args.daughter_steps, 0
     with T.Context(cfg) as c:
-        c.spawn_daughters(ms_dev[:n_groups], al_dev[:n_groups], 1e-3, box=L)
-        c.run(1)
+        bid = c.spawn_daughters(ms_dev[:n_groups], al_dev[:n_groups], rate, box=L)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        for _ in range(n_steps - 1):
+        for _ in range(args.daughter_steps):
             c.run(1)
         torch.cuda.synchronize()
         el = time.perf_counter() - t
-    return 4 * n_groups * N * (n_steps - 1) / el, el
+        v = c.viscosity(bid)
+    se = float(v["eta_ttcf_se"][-1])
+    return {"rate": rate, "groups": n_groups, "daughter_steps": args.daughter_steps, "seconds": el,
+            "atom_steps_per_s": 4 * n_groups * N * args.daughter_steps / el,
+            "eta_ttcf": float(v["eta_ttcf"][-1]), "eta_ttcf_se": se,
+            "efficiency_plain_per_gpu_second": 1.0 / (se * se * el),
+            "definition": "FP64 mode, one non-persistent launch per MD step, no graph, no control variate"}
+
+
+def uneven_section(T, torch, args):
+    """The uneven batch: bulk WCA systems of N = 256, 864 and 4000 with
+    shear rates 1e-2 ... 1e-6, 256 mother states per N (64 GPU mother chains
+    x 4 states) x 4 mappings per (N, rate) cell = 15360 daughters of 1000
+    steps in one graph-captured run (one persistent launch per size class
+    on forked streams), launch shapes autotuned per N; MIXED."""
+    from paper_2312_02990_gb300 import inputs
+    moth = {}
+    t0 = time.perf_counter()
+    for N in UNEVEN_SIZES:
+        L = inputs.bulk_box(N)
+        moth[N] = make_mothers(T, args, 0, N, L, n_mothers=args.uneven_chains,
+                               n_states=args.uneven_states, seed_off=30000 + N, n_eq=4000)
+    t_moth = time.perf_counter() - t0
+    cfg = T.config_default()
+    cfg.precision, cfg.n_steps, cfg.use_graph = T.TTCF_MIXED, args.daughter_steps, 1
+    with T.Context(cfg) as c:
+        tuned = {}
+        for N in UNEVEN_SIZES:
+            ms = moth[N][0]
+            tuned[N] = c.autotune(ms[:min(len(ms), 152)], inputs.bulk_box(N), shear_rate=1e-3, n_steps=100)[:3]
+        dev = {N: (torch.from_numpy(moth[N][0]).cuda(), torch.from_numpy(moth[N][1]).cuda())
+               for N in UNEVEN_SIZES}
+        ids = {(N, g): c.spawn_daughters(*dev[N], g, box=inputs.bulk_box(N))
+               for N in UNEVEN_SIZES for g in UNEVEN_RATES}
+        c.run()
+        st = c.get_stats()
+        eta = {f"N{N}_{g:.0e}": float(c.viscosity(b)["eta_ttcf"][-1]) for (N, g), b in ids.items()}
+        bad = int(sum(np.count_nonzero(c.group_status(b, len(moth[N][0]))) for (N, g), b in ids.items()))
+    D = sum(4 * len(moth[N][0]) * len(UNEVEN_RATES) for N in UNEVEN_SIZES)
+    atom_steps = sum(4 * len(moth[N][0]) * len(UNEVEN_RATES) * N for N in UNEVEN_SIZES) * args.daughter_steps
+    k_ms = st["ms_run"]
+    flops = st["pairs_interacting"] / 2.0 * FLOPS_PER_PAIR
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    return {"value": atom_steps / (k_ms * 1e-3), "unit": "atom-steps/s", "daughters": D,
+            "workload": f"bulk WCA N = {list(UNEVEN_SIZES)} x rates {UNEVEN_RATES}, "
+                        f"{args.uneven_chains * args.uneven_states} mother states x 4 mappings per cell, "
+                        f"{args.daughter_steps} steps, one graph-captured run, MIXED",
+            "kernel_ms": k_ms, "launches": st["launches"],
+            "autotuned": {str(N): [t[0], t[1], round(t[2], 4)] for N, t in tuned.items()},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "kernel": "daughter_kernel (3 size classes)"},
+            "pairs_per_atom_step": st["pairs_interacting"] / atom_steps,
+            "flagged_groups": bad, "mother_setup_s": t_moth, "eta_ttcf_t_end": eta}
 
 
 def cv_section(T, torch, args):
@@ -435,7 +607,8 @@ def cv_section(T, torch, args):
             "efficiency_gain_cv_with_training": e_cv_train / e_plain,
             "train_loss_first_last": [float(loss[0]), float(loss[-1])],
             "groups": {"train": n_tr, "eval": n_ev, "aux": n_aux}, "daughter_steps": args.cv_steps,
-            "seconds": {"mothers": t_moth, "run": t_run, "train": t_train, "apply": t_apply}}
+            "seconds": {"mothers": t_moth, "run": t_run, "eval_run": t_eval_run, "train": t_train,
+                        "apply": t_apply}}
 
 
 def green_kubo_section(T, torch, args, N, L):
@@ -623,10 +796,11 @@ def precision_floor_section(T, torch, args):
 
 def confined_section(T, torch, args):
     """Confined channel of Example 2 (6048 fluid + 4200 tethered wall atoms,
-    dt = 0.005): GPU-thermalised mothers (lattices at rest), then every
-    mother x 4 mappings x 4 shear rates 1e-1 ... 1e-7 as daughters of
-    conf_steps steps in one persistent launch.  Reports daughter
-    atom-steps/s of that launch and the wall-stress and slab responses."""
+    dt = 0.005): GPU-thermalised mothers (lattices at rest; 64 chains x 4
+    states = 256 mother states), then every mother x 4 mappings x 4 shear
+    rates 1e-1 ... 1e-7 = 4096 daughters of conf_steps steps in one
+    persistent launch.  Reports daughter atom-steps/s of that launch and the
+    wall-stress responses."""
     from paper_2312_02990_gb300 import inputs
     sysd = inputs.confined_system()
     N, box = sysd["state"].shape[1], sysd["box"]
@@ -676,7 +850,7 @@ def confined_section(T, torch, args):
     flops = st["pairs_interacting"] / 2.0 * FLOPS_PER_PAIR_LJ
     achieved = flops / (k_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops()
-    return {"value": atom_steps / (k_ms * 1e-3), "unit": "atom-steps/s",
+    return {"value": atom_steps / (k_ms * 1e-3), "unit": "atom-steps/s", "daughters": D,
             "workload": f"confined LJ channel N={N} ({sysd['n_fluid']} fluid + {sysd['n_wall']} wall), "
                         f"{G} mother states x 4 mappings x {len(CONF_RATES)} shear rates = {D} daughters "
                         f"x {args.conf_steps} steps (dt 0.005), MIXED",
@@ -691,10 +865,37 @@ def confined_section(T, torch, args):
             "responses_t_end": resp}
 
 
+def probe_section():
+    """FP32 throughput measured on this GPU by the instruction-rate probe
+    (FFMA chains, clock64 per SM and CUDA events): a measured companion to
+    the derived FP32 peak of the roofline."""
+    cc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(PROBE_SRC) or not os.path.exists(cc):
+        return {"error": "probe source or nvcc missing"}
+    with tempfile.TemporaryDirectory() as td:
+        exe = os.path.join(td, "alu_rates")
+        r = subprocess.run([cc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, PROBE_SRC],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            return {"error": "probe build failed"}
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    out = {"raw": [ln for ln in r.stdout.splitlines() if ln.strip()][:20]}
+    for ln in r.stdout.splitlines():
+        m = re.match(r"(FFMA f32|FFMA2 \(2 FMA per instr\)|DFMA f64)\s+thread-ops/clk/SM=\s*([\d.]+).*"
+                     r"Gop/s=\s*([\d.]+).*MHz~(\d+)", ln)
+        if m:
+            key = {"FFMA f32": "ffma", "DFMA f64": "dfma"}.get(m.group(1), "ffma2")
+            out[f"{key}_per_clk_sm"] = float(m.group(2))
+            out[f"{key}_gops"] = float(m.group(3))
+            out[f"{key}_mhz"] = float(m.group(4))
+    if "ffma_per_clk_sm" in out:
+        out["ffma_tflops_at_max_clock"] = out["ffma_per_clk_sm"] * 2 * N_SM * SM_MAX_MHZ * 1e6 / 1e12
+    return out
+
+
 # -------------------------------------------------------------- oracle --
-def oracle_sample(N, n_groups, n_steps, gamma, threads):
-    """Bounded oracle workload: n_groups thermalised mothers (oracle-made,
-    untimed) x 4 mappings x n_steps daughter steps (timed)."""
+def oracle_mothers(N, n_groups, n_eq, threads, seed_off=0):
+    """Oracle-thermalised mother states (one chain each, untimed)."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
@@ -702,52 +903,86 @@ def oracle_sample(N, n_groups, n_steps, gamma, threads):
     b = oracle.Bulk(n=N, L=tuple(inputs.bulk_box(N)))
 
     def one(k):
-        return oracle.mother(b, inputs.initial_state(N, inputs.BASE_SEED + 7 * k), n_eq=600,
-                             n_states=1, spacing=200)
+        return oracle.mother(b, inputs.initial_state(N, inputs.BASE_SEED + 7 * k + seed_off), n_eq=n_eq,
+                             n_states=1, spacing=1)
 
     with ThreadPoolExecutor(threads) as ex:
         res = list(ex.map(one, range(n_groups)))
-    ms = np.concatenate([r[0] for r in res])
-    al = np.concatenate([r[1] for r in res])
-    t = time.perf_counter()
-    oracle.daughters(b, ms, al, gamma, n_steps, n_threads=threads)
-    el = time.perf_counter() - t
-    return 4 * n_groups * N * n_steps / el, el
+    return b, np.concatenate([r[0] for r in res]), np.concatenate([r[1] for r in res])
 
 
-def cpu_baseline(args, N):
+def oracle_leg(T, args, N, L):
+    """The FP64 CPU oracle on a bounded sample of the benchmark workload:
+    oracle-made mothers x 4 mappings x 1000 steps at the rates 1e-1, 1e-3
+    and 1e-7 (timed: the CPU baseline), then the GPU on the same inputs in
+    the benchmark's launch configuration, and the error of each GPU result
+    against the oracle (per rate: TTCF viscosity at t_end in units of the
+    sample's standard error, and the largest relative B(s) difference)."""
+    import oracle
     threads = os.cpu_count() or 1
-    groups = 2 * threads
-    steps = 1000
-    v, el = oracle_sample(N, groups, steps, 1e-3, threads)
-    return {"value": v, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"{4 * groups} daughters x {steps} steps, N={N}, gamma=1e-3 "
-                      f"({el:.1f} s; oracle-made mothers)"}
+    Go, n = args.oracle_groups, args.daughter_steps
+    rates = list(HEADLINE_RATES)
+    b, ms, al = oracle_mothers(N, Go, args.oracle_eq, threads)
+    msr = np.ascontiguousarray(np.concatenate([ms] * len(rates)))
+    alr = np.concatenate([al] * len(rates))
+    gm = np.repeat(rates, Go)
+    t = time.perf_counter()
+    Bo, Omo = oracle.daughters(b, msr, alr, gm, n, n_threads=threads)
+    el = time.perf_counter() - t
+    D = 4 * Go * len(rates)
+    cpu = {"value": D * N * n / el, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
+           "sample": f"{D} daughters x {n} steps, N={N}, rates 1e-1/1e-3/1e-7 ({el:.1f} s)"}
+    with T.Context(bench_config(T, args)) as c:
+        ids = [c.spawn_daughters(ms, al, g, box=L) for g in rates]
+        c.run()
+        gpu = [(c.daughter_series(bid, 4 * Go), c.viscosity(bid)) for bid in ids]
+    out = {}
+    for k, (g, ((B, Om), v)) in enumerate(zip(rates, gpu)):
+        sl = slice(4 * Go * k, 4 * Go * (k + 1))
+        ro = oracle.viscosity(oracle.responses(Bo[sl], Omo[sl], 4, b.dt), g)
+        d = abs(float(v["eta_ttcf"][-1]) - float(ro["eta_ttcf"][-1]))
+        se = float(ro["eta_ttcf_se"][-1])
+        out[f"{g:.0e}"] = {"eta_gpu": float(v["eta_ttcf"][-1]), "eta_oracle": float(ro["eta_ttcf"][-1]),
+                           "eta_se_sample": se, "d_eta": d, "d_eta_over_se": d / se,
+                           "b_rel_max": float(np.abs(B - Bo[sl]).max() / np.abs(Bo[sl]).max()),
+                           "omega_rel_max": float(np.abs(Om - Omo[sl]).max() / np.abs(Omo[sl]).max())}
+    chk = {"groups": Go, "daughters_per_rate": 4 * Go, "steps": n, "mother_eq_steps": args.oracle_eq,
+           "note": "same oracle-made inputs on both sides; GPU in the benchmark's launch configuration",
+           "rates": out}
+    return cpu, chk
 
 
 def bench_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host
+    cores, on a bounded sample of the same workload per step (rates in
+    turn, as in the GPU arm)."""
     rank, world, local = dist_info()
     if rank != 0:
         return
+    import oracle
     N = args.n_atoms
     threads = os.cpu_count() or 1
     groups = max(1, threads // 4)
     steps = 200
+    b, ms, al = oracle_mothers(N, groups, 600, threads, seed_off=5)
     vals = []
     for k in range(args.warmup + args.steps):
-        v, el = oracle_sample(N, groups, steps, RATES[k % len(RATES)], threads)
+        t = time.perf_counter()
+        oracle.daughters(b, ms, al, RATES[k % len(RATES)], steps, n_threads=threads)
+        el = time.perf_counter() - t
         if k >= args.warmup:
-            vals.append((v, el))
-    v = float(np.mean([x[0] for x in vals]))
-    ms = float(np.mean([x[1] for x in vals])) * 1e3
+            vals.append(el)
+    el = float(np.mean(vals))
+    v = 4 * groups * N * steps / el
     line = {"impl": "reference", "metric": "daughter atom-steps/s", "value": v,
             "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (seeded FCC + Maxwell, oracle-thermalised mothers)",
-            "config": {"workload": f"bulk WCA N={N}, bounded sample of {4 * groups} daughters x "
-                                   f"{steps} steps per step (FP64 CPU oracle)", "n_atoms": N},
+            "config": {"workload": f"bulk WCA N={N}, 4096 mother states x 4 mappings = 16384 daughters x "
+                                   f"{args.daughter_steps} steps per step, one shear rate per step cycling "
+                                   "1e-1..1e-7"},
             "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{4 * groups} daughters x {steps} steps per step"},
+                             "sample": f"bounded sample per step: {4 * groups} daughters x {steps} steps"},
             "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -757,12 +992,24 @@ def main():
     args = parse()
     if args.impl == "reference":
         bench_reference(args)
-    elif args.confined_only:
+    elif args.only:
         import torch
 
+        from paper_2312_02990_gb300 import inputs
         from paper_2312_02990_gb300 import ttcf as T
         T.load(build_if_missing=True)
-        print(json.dumps(confined_section(T, torch, args)))
+        args.tuned = None
+        N = args.n_atoms
+        L = inputs.bulk_box(N)
+        fn = {"confined": lambda: confined_section(T, torch, args),
+              "uneven": lambda: uneven_section(T, torch, args),
+              "cv": lambda: cv_section(T, torch, args),
+              "floor": lambda: precision_floor_section(T, torch, args),
+              "gk": lambda: green_kubo_section(T, torch, args, N, L),
+              "kick": lambda: kick_section(T, torch, args, N, L),
+              "mapstudy": lambda: mapping_study_section(T, torch, args),
+              "probe": probe_section}[args.only]
+        print(json.dumps(fn()))
     else:
         bench_gb300(args)
 
