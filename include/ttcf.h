@@ -197,6 +197,15 @@ ttcf_status ttcf_viscosity(ttcf_ctx *ctx, int batch_id, double *t, double *eta_t
                            double *eta_ttcf_se, double *eta_dav, double *eta_dav_se,
                            int capacity, int *n_samples);
 
+/* <Omega(0)> of a finished batch, the mean of the dissipation function at
+ * switch-on over the daughters of its valid mother groups, as used by the
+ * Eq. 4 form of ttcf_response (corrected = 1); exactly 0 with all four
+ * mappings of Eq. 3.  *n_valid receives the number of valid groups.  A
+ * multi-rank merge folds (n_valid, omega_mean) of each rank into the global
+ * <Omega(0)> that the Eq. 4 form of the merged ensemble needs.
+ * Errors: TTCF_E_INVALID (bad batch), TTCF_E_STATE (run not finished).    */
+ttcf_status ttcf_omega_mean(ttcf_ctx *ctx, int batch_id, double *omega_mean, double *n_valid);
+
 /* Raw per-daughter outputs of a batch: B [D][n_obs][S] and Omega [D]
  * (host arrays, D = n_mothers * M; n_obs = 1 for the bulk system, so B is
  * [D][S] there, TTCF_CONF_NOBS for the confined one).  capacity_B is the
@@ -415,8 +424,11 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path);
  *
  *  cfg            as for ttcf_create; stream, precision, dt, T, tau_T,
  *                 dof_mode, n_steps, sample_every, mapping_mask,
- *                 reset_alpha, skin, kernel_variant, block_threads are used;
- *                 allocator hooks, keep_state and timeout_s are ignored
+ *                 reset_alpha, skin, kernel_variant, block_threads,
+ *                 cell_frac are used (with the same defaults as a context
+ *                 without autotuning, so the results equal those of
+ *                 ttcf_spawn_daughters + ttcf_run bit for bit); allocator
+ *                 hooks, keep_state, use_graph and timeout_s are ignored
  *  mother_soa     DEVICE [n_mothers][6][N] float64 phase points
  *  mother_alpha   DEVICE [n_mothers] or NULL (zeros)
  *  shear_rates    DEVICE [n_mothers]
@@ -424,6 +436,9 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path);
  *                 sample_every + 1 (B(s) = P_xy(s) as in ttcf_daughter_series)
  *  Omega          DEVICE output [D]; status DEVICE output [D] (TTCF_D_*)
  *
+ * Every array must be device (or managed) memory of the current device: a
+ * host pointer is rejected with TTCF_E_INVALID (the library cannot check
+ * the arrays' sizes, which are the caller's responsibility).
  * All arrays are the caller's.  The call only enqueues work on cfg->stream
  * and returns; results are valid once that stream has completed it.  The
  * first call on each device looks up the array's device address with that

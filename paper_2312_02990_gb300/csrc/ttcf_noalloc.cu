@@ -15,6 +15,7 @@
 // cannot use the array's name as a device address (on the host it names a
 // stand-in), so the first call on each device, with that device current,
 // looks the address up with cudaGetSymbolAddress and caches it.
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -37,9 +38,23 @@ unsigned char *g_noalloc_ptr[MAX_DEVICES] = {nullptr};
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-__global__ void iota_kernel(int *w, int n) {
+// Writes the batch table (passed by value, so no host buffer has to outlive
+// the call) and the launch order 0..n-1 of the daughters.
+__global__ void noalloc_init_kernel(BatchDev bd, BatchDev *d_b, int *w, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *d_b = bd;
     if (i < n) w[i] = i;
+}
+
+// True if p is memory the current device can address as device memory
+// (device or managed allocations); a plain host pointer is rejected.
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 ttcf_status noalloc_fail(ttcf_status s, const std::string &m) {
@@ -59,12 +74,17 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
                                         double *B, double *Omega, int *status) {
     if (!cfg || !box || !mother_soa || !shear_rates || !B || !Omega || !status)
         return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: NULL argument");
+    if (!is_device_pointer(mother_soa) || !is_device_pointer(shear_rates) || !is_device_pointer(B) ||
+        !is_device_pointer(Omega) || !is_device_pointer(status) ||
+        (mother_alpha && !is_device_pointer(mother_alpha)))
+        return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: every array must be device memory");
     const ttcf_config &c = *cfg;
     if (c.system != TTCF_BULK_WCA || (c.precision != TTCF_FP64 && c.precision != TTCF_MIXED) ||
         !(c.dt > 0) || !(c.T > 0) || !(c.tau_T > 0) || c.n_steps < 1 || c.sample_every < 1 ||
         c.n_steps % c.sample_every || (c.mapping_mask & 0xF) == 0 || (c.mapping_mask & ~0xFu) ||
         c.kernel_variant < 0 || c.kernel_variant > N_VARIANTS || c.block_threads < 0 ||
-        c.block_threads % 32 || c.skin > 1.0)
+        c.block_threads % 32 || c.skin > 1.0 ||
+        (c.cell_frac != 0.0 && !(c.cell_frac >= 0.4 && c.cell_frac <= 1.0)))
         return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: invalid configuration");
     if (n_atoms < 4 || n_atoms > 4096 || n_mothers < 1)
         return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: n_atoms must be in [4, 4096], n_mothers >= 1");
@@ -91,14 +111,12 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     sa.N = bd.N = N; sa.M = bd.M = M; sa.G = bd.G = G; bd.S = sa.S = S;
     for (int k = 0; k < 4; k++) sa.maps[k] = bd.maps[k] = k < M ? maps[k] : 0;
     for (int k = 0; k < 3; k++) {
-        if (!(box[k] >= 3.0 * (rc + skin)))
-            return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: box edge shorter than 3*(r_c+skin)");
+        if (!isfinite(box[k]) || !(box[k] >= 3.0 * (rc + skin)))
+            return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: box edge not finite or shorter than 3*(r_c+skin)");
         sa.L[k] = bd.L[k] = box[k];
         sa.nc[k] = (int)(box[k] / rc);
-        bd.nc[k] = (int)(box[k] / (rc + skin));
     }
     sa.ncell = sa.nc[0] * sa.nc[1] * sa.nc[2];
-    bd.ncell = bd.nc[0] * bd.nc[1] * bd.nc[2];
     sa.V = bd.V = box[0] * box[1] * box[2];
     sa.T = bd.T = c.T;
     const double g = c.dof_mode == 1 ? 3.0 * N - 3.0 : 3.0 * N;
@@ -124,7 +142,6 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
         return noalloc_fail(TTCF_E_INVALID,
                             "ttcf_run_noalloc: batch needs more than the 32 MiB static scratch "
                             "(reduce n_mothers or n_atoms, or use ttcf_spawn_daughters)");
-    const size_t smem = daughter_smem_bytes(mixed, N, bd.ncell);
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
@@ -146,15 +163,45 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
         }
         base = g_noalloc_ptr[dev];
     }
-    int nsm = 0, optin = 0;
+    int nsm = 0, optin = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
         cudaGetLastError();
         return noalloc_fail(TTCF_E_CUDA, "ttcf_run_noalloc: device query failed");
     }
+    // list cells and list-build layout by the rule of ttcf_spawn_daughters +
+    // ttcf_run for a batch alone (cells cell_frac r_l wide, coarser where the
+    // variant's resident CTAs need the shared memory; the cell-ordered build
+    // where its larger shared memory keeps them), so both give the same bits
+    {
+        const double rl = rc + skin;
+        const double frac = c.cell_frac > 0 ? c.cell_frac : 2.0 / 3.0;
+        const double fracs[3] = {frac, std::max(frac, 2.0 / 3.0), 1.0};
+        for (int f = 0; f < 3; f++) {
+            int ncf[3];
+            for (int k = 0; k < 3; k++) ncf[k] = std::max(3, (int)floor(box[k] / (rl * fracs[f])));
+            const int ncell = ncf[0] * ncf[1] * ncf[2];
+            const size_t sm = daughter_smem_bytes(mixed, N, ncell);
+            if (f == 2 || (size_t)v.minb * (sm + 1024) <= (size_t)per_sm) {
+                for (int k = 0; k < 3; k++) bd.nc[k] = ncf[k];
+                bd.ncell = ncell;
+                break;
+            }
+        }
+    }
+    size_t smem = daughter_smem_bytes(mixed, N, bd.ncell);
     if (smem > (size_t)optin)
         return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: daughter needs more shared memory than a CTA has");
     int nb = daughter_occupancy(mixed, variant, threads, smem);
+    int cpos = 0;
+    {
+        const size_t s2 = daughter_smem_bytes(mixed, N, bd.ncell, true);
+        if (s2 <= (size_t)optin) {
+            const int nb2 = daughter_occupancy(mixed, variant, threads, s2);
+            if (nb2 >= 1 && nb2 >= std::min(nb, v.minb)) { cpos = 1; smem = s2; nb = nb2; }
+        }
+    }
     if (nb < 1) nb = 1;
     long long grid = std::min<long long>(D, (long long)nb * nsm);
     grid = std::min<long long>(grid, (long long)((NOALLOC_BYTES - off) / nbr_per_cta));
@@ -176,16 +223,17 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     bd.state = nullptr;
     bd.d0 = 0;
 
-    // the array keeps the previous call's contents: clear what starts at zero
-    cudaError_t e = cudaMemcpyAsync(d_b, &bd, sizeof(BatchDev), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_dbatch, 0, sizeof(int) * D, st);
+    // the array keeps the previous call's contents: clear what starts at
+    // zero.  Only kernels and memsets are queued: no host buffer is read
+    // after this function returns.
+    cudaError_t e = cudaMemsetAsync(d_dbatch, 0, sizeof(int) * D, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_queue, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_alpha, 0, sizeof(double) * G, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bd.pairs, 0, sizeof(unsigned long long) * D, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bd.rebuilds, 0, sizeof(unsigned int) * D, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int) * D, st);
     if (e == cudaSuccess) {
-        iota_kernel<<<(unsigned)((D + 255) / 256), 256, 0, st>>>(d_work, (int)D);
+        noalloc_init_kernel<<<(unsigned)((D + 255) / 256), 256, 0, st>>>(bd, d_b, d_work, (int)D);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -200,7 +248,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
         a.batches = d_b; a.work = d_work; a.dbatch = d_dbatch; a.n_work = (int)D;
         a.queue = d_queue;
         a.nbr = (unsigned int *)(base + off);
-        a.nmax = N; a.ncellmax = bd.ncell;
+        a.nmax = N; a.ncellmax = bd.ncell; a.cpos = cpos;
         a.step0 = 0; a.step1 = c.n_steps; a.sample_every = c.sample_every;
         a.fresh = 1; a.save_state = 0; a.reset_alpha = c.reset_alpha;
         a.dt = c.dt; a.delta0 = 0.0;

@@ -27,7 +27,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 # The C ABI exported by libttcf.so (kept in sync with include/ttcf.h).
 EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_run",
-           "ttcf_response", "ttcf_viscosity", "ttcf_daughter_series", "ttcf_group_status",
+           "ttcf_response", "ttcf_viscosity", "ttcf_omega_mean", "ttcf_daughter_series", "ttcf_group_status",
            "ttcf_get_state", "ttcf_get_stats", "ttcf_sample_mothers", "ttcf_mother_acf",
            "ttcf_kick_states",
            "ttcf_forces", "ttcf_autotune",
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = False):
     L.ttcf_run.argtypes = [vp, C.c_int]
     L.ttcf_response.argtypes = [vp, C.c_int, C.c_int] + [_dp] * 7 + [C.c_int, ip]
     L.ttcf_viscosity.argtypes = [vp, C.c_int] + [_dp] * 5 + [C.c_int, ip]
+    L.ttcf_omega_mean.argtypes = [vp, C.c_int, _dp, _dp]
     L.ttcf_daughter_series.argtypes = [vp, C.c_int, _dp, _dp, C.c_size_t]
     L.ttcf_group_status.argtypes = [vp, C.c_int, ip, C.c_int]
     L.ttcf_get_state.argtypes = [vp, C.c_int, C.c_int, _dp, _dp, _dp]
@@ -316,6 +317,12 @@ class Context:
                                            _ptr(arr["eta_ttcf_se"]), _ptr(arr["eta_dav"]),
                                            _ptr(arr["eta_dav_se"]), S, C.byref(n)))
         return arr
+
+    def omega_mean(self, batch: int):
+        """(<Omega(0)> over the valid groups' daughters, number of valid groups)."""
+        om, n = C.c_double(), C.c_double()
+        self._check(self._L.ttcf_omega_mean(self.h, batch, C.byref(om), C.byref(n)))
+        return om.value, int(n.value)
 
     def daughter_series(self, batch: int, n_daughters: int, n_obs: int = 1):
         """B [D, S] (n_obs = 1) or [D, n_obs, S], Omega [D]."""
@@ -576,9 +583,26 @@ def run_noalloc(cfg: Config, mother_soa, mother_alpha, shear_rates, box, B, Omeg
     caller (float64 mothers [G,6,N], alpha [G] or None, rates [G]; outputs
     B [D,S] float64, Omega [D] float64, status [D] int32).  Enqueues on
     cfg.stream and returns the status code."""
+    import torch
     L = load()
     bx = _box(box)
+
+    def need(name, t, dtype, shape):
+        if t is None or not t.is_cuda or not t.is_contiguous() or t.dtype != dtype or tuple(t.shape) != shape:
+            raise ValueError(f"run_noalloc: {name} must be a contiguous CUDA {dtype} tensor of shape {shape}")
+
+    if mother_soa is None or mother_soa.dim() != 3 or mother_soa.shape[1] != 6:
+        raise ValueError("run_noalloc: mother_soa must have shape [G, 6, N]")
     G, _, N = mother_soa.shape
+    D = G * bin(cfg.mapping_mask & 0xF).count("1")
+    S = cfg.n_steps // max(cfg.sample_every, 1) + 1
+    need("mother_soa", mother_soa, torch.float64, (G, 6, N))
+    if mother_alpha is not None:
+        need("mother_alpha", mother_alpha, torch.float64, (G,))
+    need("shear_rates", shear_rates, torch.float64, (G,))
+    need("B", B, torch.float64, (D, S))
+    need("Omega", Omega, torch.float64, (D,))
+    need("status", status, torch.int32, (D,))
     return L.ttcf_run_noalloc(C.byref(cfg), int(N), _ptr(bx), int(G), mother_soa.data_ptr(),
                               None if mother_alpha is None else mother_alpha.data_ptr(),
                               shear_rates.data_ptr(), B.data_ptr(), Omega.data_ptr(),
