@@ -11,8 +11,9 @@ control variate (not in the paper).
 """
 from .core import (Bulk, build, lib, wca, forces, pressure, apply_mapping,
                    trajectory, mother, daughter, daughters)
-from .reduce import responses, viscosity
+from .reduce import responses, viscosity, autocorrelation, green_kubo
 from . import cv
 
 __all__ = ["Bulk", "build", "lib", "wca", "forces", "pressure", "apply_mapping",
-           "trajectory", "mother", "daughter", "daughters", "responses", "viscosity", "cv"]
+           "trajectory", "mother", "daughter", "daughters", "responses", "viscosity",
+           "autocorrelation", "green_kubo", "cv"]

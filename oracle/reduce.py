@@ -9,6 +9,9 @@ mapped daughters per mother state g.
     corrected   <Omega(0)B(s)> - <Omega(0)><B(s)>                           Eq. 4
     DAV         <B(t)> = (1/D) sum_d B_d(t)                  direct average
     viscosity   eta(t) = -<P_xy(t)>/gamma                    Eq. 8
+    equilibrium <B(t)B(t+k)> over trajectories and time origins, and the
+                Green-Kubo integral (V/k_BT) int <P_xy(0)P_xy(t)> dt
+                (Eq. 8 at zero field; the mother-side correlations of Fig. 7)
 
 The integral is the trapezoid rule on the sample grid.  Standard errors are
 taken over mother groups (each group's mean over its M mapped daughters is
@@ -103,3 +106,30 @@ def friction(resp_obs, gamma: float, Ly: float, h: float, wall: int, nslab: int 
     with np.errstate(divide="ignore", invalid="ignore"):
         xi = sigma / slip
     return {"slip": slip, "xi": xi, "slabs": ks}
+
+
+def autocorrelation(B: np.ndarray, max_lag: int):
+    """Time correlations of the series B[G, n] (G independent trajectories,
+    one sample per step), averaged over trajectories and all time origins
+    t = 0 .. n-1-k:
+        acf[k]  = <B(t) B(t+k)>,
+        acf2[k] = <(B(t)^2 - m2)(B(t+k)^2 - m2)>,   m2 = <B^2>,
+    for lags k = 0 .. max_lag."""
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[None]
+    n = B.shape[1]
+    m2 = float(np.mean(B * B))
+    acf = np.zeros(max_lag + 1)
+    acf2 = np.zeros(max_lag + 1)
+    for k in range(max_lag + 1):
+        a, b = B[:, :n - k], B[:, k:]
+        acf[k] = np.mean(a * b)
+        acf2[k] = np.mean((a * a - m2) * (b * b - m2))
+    return acf, acf2
+
+
+def green_kubo(acf: np.ndarray, V: float, T: float, ds: float) -> np.ndarray:
+    """Running Green-Kubo viscosity (V / k_B T) int_0^{k ds} <P_xy(0)P_xy(t)> dt
+    by the trapezoid rule on the lag grid (Eq. 8 at zero field)."""
+    return (V / T) * _cumtrapz(np.asarray(acf, dtype=np.float64), ds)

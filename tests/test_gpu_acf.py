@@ -1,8 +1,8 @@
 """Equilibrium correlations along GPU mother trajectories (ttcf_mother_acf)
 through the C ABI: the recorded P_xy follows the oracle's zero-field
 trajectory for its first steps (MIXED tolerance as in test_gpu_parity), the
-device autocorrelations equal their definition on the device series, and
-the Green-Kubo integral is their trapezoid integral times V/T."""
+device autocorrelations equal the oracle's on the device series, and the
+Green-Kubo integral equals the oracle's trapezoid integral times V/T."""
 import numpy as np
 import pytest
 
@@ -40,14 +40,10 @@ def test_correlations_match_their_definition(T):
     with T.Context(T.config_default()) as c:
         r = c.mother_acf(init, L, n_eq=2000, n_steps=n, max_lag=lag, want_series=True)
     B = r["series"]
-    m2 = np.mean(B ** 2)
-    acf = np.array([np.mean(B[:, :n - k] * B[:, k:]) for k in range(lag + 1)])
-    acf2 = np.array([np.mean((B[:, :n - k] ** 2 - m2) * (B[:, k:] ** 2 - m2)) for k in range(lag + 1)])
+    acf, acf2 = oracle.autocorrelation(B, lag)
     assert np.allclose(r["acf_pxy"], acf, rtol=1e-10, atol=1e-14 * acf[0])
     assert np.allclose(r["acf_pxy2"], acf2, rtol=1e-9, atol=1e-12 * acf2[0])
-    V = float(np.prod(L))
-    dt = 0.0025
-    gk = V / 0.722 * np.concatenate([[0.0], np.cumsum(0.5 * dt * (acf[1:] + acf[:-1]))])
+    gk = oracle.green_kubo(acf, float(np.prod(L)), 0.722, 0.0025)
     assert np.allclose(r["eta_gk"], gk, rtol=1e-10, atol=1e-14)
     # an equilibrium stress correlation: largest at lag 0, decays within a
     # fraction of a time unit

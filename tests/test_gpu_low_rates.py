@@ -1,0 +1,156 @@
+"""GPU parity at the shear rates and launch shapes the benchmark runs.
+
+1. The TTCF response (Eq. 1) and viscosity (Eq. 8) down to gamma = 1e-7,
+   where the precision design has to earn its keep (the response is ~1e-7 of
+   the equilibrium noise): 64 oracle-thermalised mother groups of the N = 256
+   system x 4 mappings x 500 steps at gamma = 1e-3, 1e-5 and 1e-7, in FP64 and
+   MIXED, against the FP64 oracle on the same inputs.  Asserted at several
+   times: the ensemble TTCF response within 2 combined standard errors, and
+   the paired per-group TTCF estimates J_g(t) far below the standard error
+   (the daughters start from the same phase points on both sides and follow
+   the same trajectories through t = 1.25, apart from rounding):
+       FP64   |J_g,gpu - J_g,oracle| <= 1e-6 SE(t)
+       MIXED  |J_g,gpu - J_g,oracle| <= 2e-2 SE(t)
+   (MIXED positions differ from FP64 by ~1e-7 after one step; the chaotic
+   growth to t = 1.25 keeps the paired difference of a group's integral
+   well below 1 % of the ensemble's standard error.)
+2. 50-step daughter trajectories of the N = 2048 system in the benchmark's
+   launch shape (launch variant 3: two atoms per thread, 1024 threads; Verlet
+   skin 0.4; list cells 2/3 r_l; the cell-ordered list build), and in the
+   shape the autotuner picks on these states: positions 1e-6, momenta 1e-5,
+   B(s) 1e-4 relative.
+"""
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RATES = (1e-3, 1e-5, 1e-7)
+N_STEPS = 500
+
+
+@pytest.fixture(scope="module")
+def ttcf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2312_02990_gb300 import ttcf as T
+    T.load(build_if_missing=True)
+    return T
+
+
+def ctx(T, **kw):
+    c = T.config_default()
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return T.Context(c)
+
+
+@pytest.fixture(scope="module")
+def mothers_64():
+    """16 independent oracle mother chains, each thermalised 4000 steps, then
+    4 states 200 steps apart: 64 mother groups of the N = 256 system."""
+    N = 256
+    b = oracle.Bulk(n=N, L=tuple(inputs.bulk_box(N)))
+
+    def one(k):
+        return oracle.mother(b, inputs.initial_state(N, inputs.BASE_SEED + 300 + k), n_eq=4000,
+                             n_states=4, spacing=200)
+
+    with ThreadPoolExecutor(16) as ex:
+        res = list(ex.map(one, range(16)))
+    return b, np.concatenate([r[0] for r in res]), np.concatenate([r[1] for r in res])
+
+
+@pytest.fixture(scope="module")
+def oracle_low_rates(mothers_64):
+    """Oracle daughters of every mother group at each rate (one call)."""
+    b, ms, al = mothers_64
+    G = ms.shape[0]
+    Bo, Omo = oracle.daughters(b, np.concatenate([ms] * len(RATES)), np.concatenate([al] * len(RATES)),
+                               np.repeat(RATES, G), N_STEPS)
+    return {g: (Bo[4 * G * k:4 * G * (k + 1)], Omo[4 * G * k:4 * G * (k + 1)]) for k, g in enumerate(RATES)}
+
+
+def group_ttcf(B, Om, dt):
+    """Each mother group's own TTCF estimate J_g(t) (the oracle's Eq. 1 on
+    the group's four daughters alone)."""
+    G = B.shape[0] // 4
+    return np.stack([oracle.responses(B[4 * g:4 * g + 4], Om[4 * g:4 * g + 4], 4, dt)["ttcf"]
+                     for g in range(G)])
+
+
+@pytest.mark.parametrize("precision,paired_tol", [(0, 1e-6), (1, 2e-2)])
+def test_low_rate_ttcf_matches_the_oracle(ttcf, mothers_64, oracle_low_rates, precision, paired_tol):
+    b, ms, al = mothers_64
+    G = ms.shape[0]
+    with ctx(ttcf, precision=precision, n_steps=N_STEPS) as c:
+        ids = {g: c.spawn_daughters(ms, al, g, box=b.L) for g in RATES}
+        c.run()
+        gpu = {g: (c.daughter_series(bid, 4 * G), c.response(bid), c.viscosity(bid)) for g, bid in ids.items()}
+    for g in RATES:
+        (B, Om), r, v = gpu[g]
+        Bo, Omo = oracle_low_rates[g]
+        ro = oracle.responses(Bo, Omo, 4, b.dt)
+        vo = oracle.viscosity(ro, g)
+        # Omega(0) and B(0) are IEEE double on both sides
+        assert np.abs(Om - Omo).max() <= 1e-12 * np.abs(Omo).max(), g
+        Jg, Jo = group_ttcf(B, Om, b.dt), group_ttcf(Bo, Omo, b.dt)
+        for s in (100, 250, 500):
+            se = np.hypot(r["ttcf_se"][s], ro["ttcf_se"][s])
+            assert abs(r["ttcf"][s] - ro["ttcf"][s]) < 2.0 * se, (g, s)
+            assert abs(v["eta_ttcf"][s] - vo["eta_ttcf"][s]) < 2.0 * se / g, (g, s)
+            paired = np.abs(Jg[:, s] - Jo[:, s]).max()
+            assert paired <= paired_tol * ro["ttcf_se"][s], (g, s, paired / ro["ttcf_se"][s])
+            # the standard errors themselves agree (same groups, same trajectories)
+            assert r["ttcf_se"][s] == pytest.approx(ro["ttcf_se"][s], rel=1e-2), (g, s)
+
+
+@pytest.fixture(scope="module")
+def mothers_2048():
+    """Two oracle mother states of the N = 2048 system (thermalised 600 steps
+    from the lattice)."""
+    N = 2048
+    b = oracle.Bulk(n=N, L=tuple(inputs.bulk_box(N)))
+
+    def one(k):
+        return oracle.mother(b, inputs.initial_state(N, inputs.BASE_SEED + 400 + k), n_eq=600,
+                             n_states=1, spacing=1)
+
+    with ThreadPoolExecutor(2) as ex:
+        res = list(ex.map(one, range(2)))
+    return b, np.concatenate([r[0] for r in res]), np.concatenate([r[1] for r in res])
+
+
+@pytest.mark.parametrize("shape", ["bench", "autotuned"])
+def test_n2048_launch_shape_follows_the_oracle(ttcf, mothers_2048, shape):
+    b, ms, al = mothers_2048
+    gamma, n = 1e-3, 50
+    kw = dict(precision=1, n_steps=n, keep_state=1)
+    if shape == "bench":
+        kw.update(kernel_variant=3, skin=0.4, cell_frac=2.0 / 3.0)
+    with ctx(ttcf, **kw) as c:
+        if shape == "autotuned":
+            c.autotune(ms, b.L, shear_rate=gamma, n_steps=20)
+        bid = c.spawn_daughters(ms, al, gamma, box=b.L)
+        c.run()
+        B, Om = c.daughter_series(bid, 8)
+        states = [c.get_state(bid, d, b.n) for d in range(8)]
+        if shape == "bench":
+            assert c.get_stats()["skin"] == pytest.approx(0.4)
+    L = np.asarray(b.L)[:, None]
+    for d in range(8):
+        Bo, omo, fin, fa = oracle.daughter(b, ms[d // 4], al[d // 4], d % 4, gamma, n)
+        s, a, _ = states[d]
+        dx = s[:3] - fin[:3]
+        dx -= L * np.rint(dx / L)
+        assert np.abs(dx).max() < 1e-6, d
+        assert np.abs(s[3:] - fin[3:]).max() < 1e-5, d
+        assert a == pytest.approx(fa, abs=1e-5)
+        assert Om[d] == pytest.approx(omo, rel=1e-12)
+        assert np.abs(B[d] - Bo).max() < 1e-4 * np.abs(Bo).max(), d

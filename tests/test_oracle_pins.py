@@ -241,6 +241,72 @@ def test_reduce_closed_forms():
     assert np.allclose(r2["ttcf"], expect, atol=1e-13)
 
 
+def test_standard_errors_of_a_textbook_sample():
+    """The group standard error against a worked textbook example: the eight
+    values 2, 4, 4, 4, 5, 5, 7, 9 have mean 5, population standard deviation
+    2 and sample variance 32/7, so the standard error of their mean is
+    sqrt(32/7)/sqrt(8) = sqrt(4/7).  Eight mother groups take these values
+    as group means a_g of B; four mapped daughters per group add deviations
+    c_m(s) = w_m (1 + 0.3 s) that cancel within the group, w = (1, 1, -1, -1),
+    and Omega_{g,m} = a_g w_m, so each group's integrand is
+    Y_g(s) = a_g (1/4) sum_m w_m c_m(s) = a_g (1 + 0.3 s), hence
+        dav_se  = sqrt(4/7)                        (spread of D_g = a_g)
+        corr_se = sqrt(4/7) (1 + 0.3 s)            (spread of Y_g)
+        ttcf_se = sqrt(4/7) (1 + s ds + 0.15 s^2 ds)   (spread of J_g)
+    A standard error taken over daughters, with ddof = 0 or over 4G instead of
+    G samples gives another number."""
+    a = np.array([2.0, 4, 4, 4, 5, 5, 7, 9])
+    w = np.array([1.0, 1.0, -1.0, -1.0])
+    S, ds = 9, 0.25
+    s = np.arange(S)
+    G = a.size
+    B = np.zeros((4 * G, S))
+    Om = np.zeros(4 * G)
+    for g in range(G):
+        for m in range(4):
+            B[4 * g + m] = a[g] + w[m] * (1.0 + 0.3 * s)
+            Om[4 * g + m] = a[g] * w[m]
+    r = oracle.responses(B, Om, 4, ds)
+    se = np.sqrt(4.0 / 7.0)
+    assert np.allclose(r["dav"], 5.0, rtol=0, atol=1e-14)
+    assert np.allclose(r["dav_se"], se, rtol=1e-14, atol=0)
+    lin = 1.0 + 0.3 * s
+    assert np.allclose(r["corr"], 5.0 * lin, rtol=1e-14)
+    assert np.allclose(r["corr_se"], se * lin, rtol=1e-14)
+    # J_g(s) = a_g + a_g int_0^t (1 + 0.3 s') = a_g (1 + t + 0.15 t^2 / ds), t = s ds
+    # (the trapezoid rule is exact on a linear integrand)
+    J = 1.0 + s * ds + 0.15 * s * s * ds
+    assert np.allclose(r["ttcf"], 5.0 * J, rtol=1e-14)
+    assert np.allclose(r["ttcf_se"], se * J, rtol=1e-13)
+    # the paper's figure convention (over daughters) differs from the group SE
+    assert not np.allclose(r["dav_se_daughters"], se)
+
+
+def test_autocorrelation_closed_forms():
+    """The equilibrium correlation (over trajectories and time origins)
+    against series whose correlations are known exactly:
+      alternating +-1:  <B(t)B(t+k)> = (-1)^k, B^2 = 1 so acf2 = 0, and the
+                        trapezoid integral of (-1)^k vanishes at every lag;
+      ramp B(t) = t, n samples:  with m = n - k origins,
+                        <t (t+k)> = (m-1)(2m-1)/6 + k (m-1)/2;
+      constant c:       acf = c^2 and the Green-Kubo integral is
+                        (V/T) c^2 k ds."""
+    n, lag = 50, 7
+    alt = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    acf, acf2 = oracle.autocorrelation(np.stack([alt, -alt]), lag)
+    assert np.array_equal(acf, (-1.0) ** np.arange(lag + 1))
+    assert np.all(acf2 == 0.0)
+    assert np.allclose(oracle.green_kubo(acf, 2.0, 0.5, 0.1), 0.0, atol=1e-15)
+    ramp = np.arange(n, dtype=float)
+    acf, _ = oracle.autocorrelation(ramp[None], lag)
+    m = n - np.arange(lag + 1)
+    k = np.arange(lag + 1)
+    assert np.allclose(acf, (m - 1) * (2 * m - 1) / 6.0 + k * (m - 1) / 2.0, rtol=1e-14)
+    acf, acf2 = oracle.autocorrelation(np.full((3, n), 1.5), lag)
+    assert np.allclose(acf, 2.25) and np.allclose(acf2, 0.0)
+    assert np.allclose(oracle.green_kubo(acf, 3.0, 0.75, 0.01), 3.0 / 0.75 * 2.25 * k * 0.01, rtol=1e-14)
+
+
 def test_dav_standard_error_is_zero_at_t0(eq_mothers_256):
     b, ms, al = eq_mothers_256
     B, Om = oracle.daughters(b, ms[:8], al[:8], 1e-3, 40)
