@@ -515,7 +515,7 @@ ttcf_status ensure_reduce_buffers(ttcf_ctx *ctx, BatchHost &b) {
     b.Y = p.get<double>((size_t)b.n_obs * b.G * b.S);
     b.Dg = p.get<double>((size_t)b.n_obs * b.G * b.S);
     b.J = p.get<double>((size_t)b.n_obs * b.G * b.S);
-    b.Og = p.get<double>(b.G);
+    b.Og = p.get<double>(b.G + 2);   // + <Omega(0)> and the valid-group count
     b.valid = p.get<double>(b.G);
     b.out = p.get<double>((size_t)9 * b.n_obs * b.S);
     if (p.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (reduction)");
@@ -1093,6 +1093,18 @@ ttcf_status ttcf_viscosity(ttcf_ctx *ctx, int batch_id, double *t, double *eta_t
         if (eta_dav) eta_dav[k] = -dv[k] / g;
         if (eta_dav_se) eta_dav_se[k] = dse[k] / fabs(g);
     }
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_omega_mean(ttcf_ctx *ctx, int batch_id, double *omega_mean, double *n_valid) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (!b->reduced) return fail(ctx, TTCF_E_STATE, "run not finished");
+    double h[2];
+    CK(cudaMemcpyAsync(h, b->Og + b->G, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (omega_mean) *omega_mean = h[0];
+    if (n_valid) *n_valid = h[1];
     return TTCF_OK;
 }
 

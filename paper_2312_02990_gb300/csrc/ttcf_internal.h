@@ -62,7 +62,7 @@ struct ReduceArgs {
     const int *status;         // [G*M]
     double ds;                 // sample spacing in time
     double *Y, *Dg, *J;        // [n_obs][G][S] work arrays
-    double *Og;                // [G]
+    double *Og;                // [G + 2]: group means of Omega(0), then <Omega(0)> and the valid count
     double *valid;             // [G] 1 if every daughter of the group is OK
     double *out;               // [n_obs][9][S]: corr, corr_se, dav, dav_se,
                                //   ttcf, ttcf_se, corr_c, ttcf_c, n_valid

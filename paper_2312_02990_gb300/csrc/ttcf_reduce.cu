@@ -105,6 +105,7 @@ __global__ void reduce_correct_kernel(ReduceArgs a) {
     for (int g = 0; g < a.G; g++)
         if (a.valid[g] != 0.0) { n += 1.0; so += a.Og[g]; }
     const double om = so / n;
+    if (o == 0) { a.Og[a.G] = om; a.Og[a.G + 1] = n; }   // read by ttcf_omega_mean
     double *out = a.out + (size_t)o * 9 * S;
     const double *corr = out, *dav = out + 2 * S;
     double *cc = out + 6 * S, *tc = out + 7 * S;

@@ -20,15 +20,15 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, B, Om, out_q):
+def _worker(rank, world, port, B, Om, out_q, M=4):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    G = B.shape[0] // 4
+    G = B.shape[0] // M
     lo, hi = (0, G // 2 + 1) if rank == 0 else (G // 2 + 1, G)   # uneven split
-    r = oracle.responses(B[4 * lo:4 * hi], Om[4 * lo:4 * hi], 4, 0.0025)
-    m = merge.merge_ranks(r, hi - lo)
+    r = oracle.responses(B[M * lo:M * hi], Om[M * lo:M * hi], M, 0.0025)
+    m = merge.merge_ranks(r, hi - lo, r["omega_mean"])
     if rank == 0:
         out_q.put({k: np.asarray(v) for k, v in m.items()})
     dist.barrier()
@@ -66,3 +66,30 @@ def test_combine_is_exact_for_known_moments():
     m = merge.from_moments(merge.combine(a, b), np.array([0.0]))
     assert m["corr"][0] == pytest.approx(x.mean())
     assert m["corr_se"][0] == pytest.approx(x.std(ddof=1) / np.sqrt(10))
+
+
+def test_two_rank_merge_keeps_the_eq4_form():
+    """Two mappings per group (identity and time reversal: <Omega(0)> != 0),
+    so the Eq. 4 form needs the global <Omega(0)>: the merged corrected
+    response equals the corrected response of all groups reduced together,
+    and differs from the plain one."""
+    rng = np.random.default_rng(1)
+    G, S, M = 11, 30, 2
+    B = rng.standard_normal((M * G, S)).cumsum(axis=1) * 0.01 + 0.2
+    Om = np.repeat(rng.standard_normal(G), M) + 0.3
+    full_c = oracle.responses(B, Om, M, 0.0025, corrected=True)
+    full = oracle.responses(B, Om, M, 0.0025)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, B, Om, q, M)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res["omega_mean"] == pytest.approx(Om.mean(), rel=1e-13)
+    assert np.allclose(res["ttcf_c"], full_c["ttcf"], rtol=1e-12, atol=1e-15)
+    assert np.allclose(res["ttcf"], full["ttcf"], rtol=1e-12, atol=1e-15)
+    assert not np.allclose(res["ttcf_c"], res["ttcf"])
