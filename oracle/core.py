@@ -197,12 +197,13 @@ def daughter(b: Bulk, mother_state: np.ndarray, mother_alpha: float, m: int, gam
 def daughters(b: Bulk, mothers: np.ndarray, mother_alpha, gammas, n_steps: int,
               sample_every: int = 1, mapping_mask: int = 0xF, reset_alpha: bool = False,
               n_threads: int | None = None):
-    """The ensemble: B [G*M, S] and Omega [G*M], daughter d = g*M + k."""
+    """The ensemble: B [G*M, S] and Omega [G*M], daughter d = g*M + k for the
+    k-th set bit m of mapping_mask (mapping codes 0..31, see apply_mapping)."""
     mothers = np.ascontiguousarray(mothers, dtype=np.float64)
     G = mothers.shape[0]
     al = np.ascontiguousarray(np.broadcast_to(np.asarray(mother_alpha, np.float64), (G,)))
     gm = np.ascontiguousarray(np.broadcast_to(np.asarray(gammas, np.float64), (G,)))
-    M = bin(mapping_mask & 0xF).count("1")
+    M = bin(mapping_mask & 0xFFFFFFFF).count("1")
     S = n_steps // sample_every + 1
     B = np.zeros((G * M, S))
     Om = np.zeros(G * M)

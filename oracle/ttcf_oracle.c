@@ -379,31 +379,44 @@ int orc_state_forces(const orc_bulk *b, const double *soa, double delta,
     return orc_forces(b, delta, soa, soa + n, soa + 2 * n, F, F + n, F + 2 * n, W, U);
 }
 
-/* Eq. 3: mapping m of a phase point, with the Nose-Hoover multiplier      */
-/* carried and negated by the time-reversing mappings (1 and 3), or set    */
-/* to zero when reset_alpha is nonzero.                                    */
+/* Mappings of a phase point: Eq. 3 and the further choices listed after   */
+/* it (each position and momentum component mirrored, x and z exchanged in */
+/* a box with Lx = Lz).  Mapping code m, applied in this order:            */
+/*   bit 4  exchange of x and z, positions and momenta                     */
+/*   bit 1  x-reflection   x -> -x, px -> -px                              */
+/*   bit 2  y-reflection   y -> -y, py -> -py                              */
+/*   bit 3  z-reflection   z -> -z, pz -> -pz                              */
+/*   bit 0  time reversal  p -> -p, and the Nose-Hoover multiplier         */
+/*          alpha -> -alpha (set to zero instead when reset_alpha != 0)    */
+/* Codes 0..3 are the four mappings of Eq. 3:                              */
 /*   m = 0: identity                                                       */
 /*   m = 1: (x, y, z, -px, -py, -pz)                                       */
 /*   m = 2: (-x, y, z, -px, py, pz)                                        */
 /*   m = 3: (-x, y, z, px, -py, -pz)                                       */
+/* A reflected coordinate that lands on +L/2 is the periodic point -L/2.   */
 void orc_apply_mapping(const orc_bulk *b, int m, const double *in, double alpha_in,
                        int reset_alpha, double *out, double *alpha_out)
 {
     int n = b->n;
-    double sx = (m == 2 || m == 3) ? -1.0 : 1.0;
-    double spx = (m == 1 || m == 2) ? -1.0 : 1.0;
-    double spyz = (m == 1 || m == 3) ? -1.0 : 1.0;
-    for (int i = 0; i < n; i++) {
-        double x = sx * in[i];
-        if (x >= 0.5 * b->L[0]) x -= b->L[0];   /* -(-L/2) = L/2 maps back */
-        out[i] = x;
-        out[n + i] = in[n + i];
-        out[2 * n + i] = in[2 * n + i];
-        out[3 * n + i] = spx * in[3 * n + i];
-        out[4 * n + i] = spyz * in[4 * n + i];
-        out[5 * n + i] = spyz * in[5 * n + i];
+    for (int e = 0; e < 6 * n; e++) out[e] = in[e];
+    if (m & 16) {                                   /* x <-> z */
+        for (int i = 0; i < n; i++) {
+            double t = out[i]; out[i] = out[2 * n + i]; out[2 * n + i] = t;
+            t = out[3 * n + i]; out[3 * n + i] = out[5 * n + i]; out[5 * n + i] = t;
+        }
     }
-    double sa = (m == 1 || m == 3) ? -1.0 : 1.0;
+    for (int a = 0; a < 3; a++) {                   /* reflections */
+        if (!(m & (2 << a))) continue;
+        for (int i = 0; i < n; i++) {
+            double c = -out[a * n + i];
+            if (c >= 0.5 * b->L[a]) c -= b->L[a];
+            out[a * n + i] = c;
+            out[(3 + a) * n + i] = -out[(3 + a) * n + i];
+        }
+    }
+    if (m & 1)                                      /* time reversal */
+        for (int e = 3 * n; e < 6 * n; e++) out[e] = -out[e];
+    double sa = (m & 1) ? -1.0 : 1.0;
     *alpha_out = reset_alpha ? 0.0 : sa * alpha_in;
 }
 
@@ -498,9 +511,11 @@ int orc_daughters(const orc_bulk *b, int n_groups, const double *mothers,
                   unsigned mapping_mask, int reset_alpha, int n_steps,
                   int sample_every, double *B, double *Omega, int n_threads)
 {
-    int maps[4], M = 0;
-    for (int m = 0; m < 4; m++) if (mapping_mask & (1u << m)) maps[M++] = m;
+    int maps[32], M = 0;
+    for (int m = 0; m < 32; m++) if (mapping_mask & (1u << m)) maps[M++] = m;
     if (M == 0 || sample_every <= 0 || n_steps % sample_every) return -2;
+    for (int k = 0; k < M; k++)
+        if ((maps[k] & 16) && b->L[0] != b->L[2]) return -3;   /* x <-> z needs Lx = Lz */
     int S = n_steps / sample_every + 1;
     int D = n_groups * M;
     int err = 0;

@@ -276,7 +276,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         m->flag_rebuild[0] = m->flag_rebuild[1] = 0;
         m->flag_fast = 0; m->flag_ovf = 0; m->flag_lost = 0;
         if (a.fresh) {
-            const double sa = (map == 1 || map == 3) ? -1.0 : 1.0;
+            const double sa = map_reverses_time(map) ? -1.0 : 1.0;
             a_end = a.reset_alpha ? 0.0 : sa * b.m_alpha[gl];
             e1 = 0.0;
             delta = a.delta0;
@@ -322,12 +322,16 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     R F[APT][3];
     int ncnt[APT];
     {
-        const bool flipx = a.fresh && (map == 2 || map == 3);
-        const bool flippx = a.fresh && (map == 1 || map == 2);
-        const bool flippyz = a.fresh && (map == 1 || map == 3);
+        const int mp = a.fresh ? map : 0;   // mapping code applied at switch-on
         const unsigned long long *src = a.fresh ? b.mothers + (size_t)gl * 6 * N
                                                 : b.state + (size_t)dl * 6 * N;
-        const R Lhx = (R)(0.5 * b.L[0]);
+        const R Lh[3] = {(R)(0.5 * b.L[0]), (R)(0.5 * b.L[1]), (R)(0.5 * b.L[2])};
+        // c -> -c; -(-L/2) = +L/2 is the same periodic point
+        auto reflect = [&](S c, int k) {
+            c = sneg(c);
+            if (shi(c) >= Lh[k]) c = sadd(c, sneg(cf->L[k]));
+            return c;
+        };
         for (int q = 0; q < APT; q++) {
             const int i = tid + q * T;
             ncnt[q] = 0;
@@ -336,12 +340,11 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             if (i < N) {
                 S x = load_slot<S>(src + i), y = load_slot<S>(src + N + i), z = load_slot<S>(src + 2 * N + i);
                 S px = load_slot<S>(src + 3 * N + i), py = load_slot<S>(src + 4 * N + i), pz = load_slot<S>(src + 5 * N + i);
-                if (flipx) {   // x -> -x; -(-L/2) = +L/2 is the same periodic point
-                    x = sneg(x);
-                    if (shi(x) >= Lhx) x = sadd(x, sneg(cf->L[0]));
-                }
-                if (flippx) px = sneg(px);
-                if (flippyz) { py = sneg(py); pz = sneg(pz); }
+                if (map_swaps_xz(mp)) { S t = x; x = z; z = t; t = px; px = pz; pz = t; }
+                if (mp & 2) { x = reflect(x, 0); px = sneg(px); }
+                if (mp & 4) { y = reflect(y, 1); py = sneg(py); }
+                if (mp & 8) { z = reflect(z, 2); pz = sneg(pz); }
+                if (map_reverses_time(mp)) { px = sneg(px); py = sneg(py); pz = sneg(pz); }
                 P[q][0] = px; P[q][1] = py; P[q][2] = pz;
                 if constexpr (MIXED) {
                     pos4[i] = make_float4(x.hi, y.hi, z.hi, 0.f);

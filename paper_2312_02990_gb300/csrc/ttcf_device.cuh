@@ -23,6 +23,23 @@ constexpr int CAP = 32;          // Verlet neighbours kept per atom
 constexpr int WRAP_EVERY = 64;   // positions re-wrapped into the box every 64 steps
 constexpr int MAX_WARPS = 32;
 
+// Phase-space mappings of a mother state (Eq. 3 and the further choices the
+// paper lists after it).  Mapping code m: bit 0 time reversal (p -> -p,
+// alpha -> -alpha), bit 1 x-reflection (x -> -x, p_x -> -p_x), bit 2
+// y-reflection, bit 3 z-reflection, bit 4 exchange of the x and z
+// components of positions and momenta (needs L_x = L_z), applied in the
+// order exchange, reflections, time reversal.  Codes 0..3 are the four
+// mappings of Eq. 3 (identity, p -> -p, the x-reflection, and the two
+// combined).  Each is an isometry of the periodic box combined, for odd
+// codes, with the time reversal of the Nose-Hoover flow, so it preserves the
+// equilibrium measure.
+constexpr int MAX_MAPS = 32;
+__host__ __device__ inline bool map_reverses_time(int m) { return (m & 1) != 0; }
+// sign of P_xy of the mapped state relative to the source component
+// (P_xy, or P_zy = P_yz after the exchange): -1 for one reflection of x or y
+__host__ __device__ inline double map_pxy_sign(int m) { return (((m >> 1) ^ (m >> 2)) & 1) ? -1.0 : 1.0; }
+__host__ __device__ inline bool map_swaps_xz(int m) { return (m & 16) != 0; }
+
 // ----------------------------------------------------------------- df ---
 struct df { float hi, lo; };
 
@@ -235,7 +252,7 @@ __device__ inline void cta_exclusive_scan(const int *cnt, int *start, int n, int
 // One batch: the daughters spawned from mother states of one size N.
 struct BatchDev {
     int N, M, G, S;          // atoms, mappings per group, groups, samples
-    int maps[4];             // selected mappings (Eq. 3)
+    int maps[MAX_MAPS];      // selected mapping codes (Eq. 3 and its generalisations)
     int nc[3];               // cells per side for the neighbour build
     int ncell;
     double L[3];

@@ -30,7 +30,7 @@ cudaError_t launch_kick(const KickArgs &a, int n_copies, cudaStream_t st);
 // mother into the state format of the daughter kernel.
 struct SpawnArgs {
     int N, M, G;
-    int maps[4];
+    int maps[MAX_MAPS];        // mapping codes (see MAX_MAPS)
     int nc[3];                 // cells per side, width >= r_c
     int ncell;
     double L[3], V, T;
@@ -74,6 +74,24 @@ cudaError_t launch_reduce(const ReduceArgs &a, cudaStream_t st);
 // B^2 - <B^2>; m2 (device scalar) receives <B^2>.
 cudaError_t launch_acf(const double *B, int G, int S, int s0, int n, int max_lag, double *acf,
                        double *acf2, double *m2, cudaStream_t st);
+
+// Equilibrium friction (Eq. 12 by the equilibrium method): per confined
+// daughter d and sample s, the slip velocity dv = (inner wall layer p_x
+// sum) / n_layer - (adjacent slabs' p_x sum) / (their fluid count) and the
+// wall's force on the fluid F = -A sigma_w; then, for lags k = 0 .. max_lag,
+// the correlations <dv(t) F(t+k)> and <dv(t) dv(t+k)> over the valid
+// daughters (status 0) and all time origins, in a fixed summation order.
+constexpr int SLIP_MAX_SLABS = 8;
+struct SlipArgs {
+    const double *B;           // [D][n_obs][S]
+    const int *status;         // [D]
+    int D, n_obs, S, nslab, wall, n_slabs;
+    int slabs[SLIP_MAX_SLABS]; // slabs adjacent to the wall
+    double n_layer, area;
+    double *dv, *F;            // [D][S] out (zeros for invalid daughters)
+};
+cudaError_t launch_slip_correlations(const SlipArgs &a, int max_lag, double *c_dvf, double *c_dvdv,
+                                     cudaStream_t st);
 
 // Sets the text returned by ttcf_last_error(NULL) (calls without a context).
 void set_global_error(const char *msg);

@@ -81,7 +81,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     const ttcf_config &c = *cfg;
     if (c.system != TTCF_BULK_WCA || (c.precision != TTCF_FP64 && c.precision != TTCF_MIXED) ||
         !(c.dt > 0) || !(c.T > 0) || !(c.tau_T > 0) || c.n_steps < 1 || c.sample_every < 1 ||
-        c.n_steps % c.sample_every || (c.mapping_mask & 0xF) == 0 || (c.mapping_mask & ~0xFu) ||
+        c.n_steps % c.sample_every || c.mapping_mask == 0 ||
         c.kernel_variant < 0 || c.kernel_variant > N_VARIANTS || c.block_threads < 0 ||
         c.block_threads % 32 || c.skin > 1.0 ||
         (c.cell_frac != 0.0 && !(c.cell_frac >= 0.4 && c.cell_frac <= 1.0)))
@@ -91,8 +91,11 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     const double rc = 1.1224620483093730;
     const double skin = c.skin > 0 ? c.skin : DEFAULT_SKIN;
     const int N = n_atoms, G = n_mothers;
-    int maps[4], M = 0;
-    for (int m = 0; m < 4; m++) if (c.mapping_mask & (1u << m)) maps[M++] = m;
+    int maps[MAX_MAPS], M = 0;
+    for (int m = 0; m < MAX_MAPS; m++) if (c.mapping_mask & (1u << m)) maps[M++] = m;
+    for (int k = 0; k < M; k++)
+        if (map_swaps_xz(maps[k]) && !(fabs(box[0] - box[2]) <= 1e-12 * box[0]))
+            return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: the x <-> z exchange mappings need L_x = L_z");
     const long long D = (long long)G * M;
     const int S = c.n_steps / c.sample_every + 1;
 
@@ -109,7 +112,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     BatchDev bd;
     memset(&bd, 0, sizeof(bd));
     sa.N = bd.N = N; sa.M = bd.M = M; sa.G = bd.G = G; bd.S = sa.S = S;
-    for (int k = 0; k < 4; k++) sa.maps[k] = bd.maps[k] = k < M ? maps[k] : 0;
+    for (int k = 0; k < MAX_MAPS; k++) sa.maps[k] = bd.maps[k] = k < M ? maps[k] : 0;
     for (int k = 0; k < 3; k++) {
         if (!isfinite(box[k]) || !(box[k] >= 3.0 * (rc + skin)))
             return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: box edge not finite or shorter than 3*(r_c+skin)");

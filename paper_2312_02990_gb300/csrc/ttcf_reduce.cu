@@ -23,7 +23,7 @@ __global__ void reduce_groups_kernel(ReduceArgs a) {
     const size_t d0 = (size_t)g * M;
     int ok = 1;
     for (int k = 0; k < M; k++) ok &= (a.status[d0 + k] == 0);
-    double om[4];
+    double om[MAX_MAPS];
     for (int k = 0; k < M; k++) om[k] = a.Omega[d0 + k];
     const size_t w0 = ((size_t)o * a.G + g) * S;
     double *Y = a.Y + w0, *D = a.Dg + w0, *J = a.J + w0;
@@ -177,6 +177,60 @@ cudaError_t launch_acf(const double *B, int G, int S, int s0, int n, int max_lag
                        double *acf2, double *m2, cudaStream_t st) {
     acf_mean2_kernel<<<1, 256, 0, st>>>(B, G, S, s0, n, m2);
     acf_kernel<<<max_lag + 1, 256, 0, st>>>(B, G, S, s0, n, m2, acf, acf2);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------- equilibrium friction --
+__global__ void slip_force_kernel(SlipArgs a) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)a.D * a.S) return;
+    const int d = (int)(q / a.S), s = (int)(q % a.S);
+    double dv = 0.0, F = 0.0;
+    if (a.status[d] == 0) {
+        const double *b = a.B + (size_t)d * a.n_obs * a.S;
+        double P = 0.0, n = 0.0;
+        for (int j = 0; j < a.n_slabs; j++) {
+            P += b[(size_t)(2 + a.slabs[j]) * a.S + s];
+            n += b[(size_t)(2 + a.nslab + a.slabs[j]) * a.S + s];
+        }
+        dv = b[(size_t)(2 + 2 * a.nslab + a.wall) * a.S + s] / a.n_layer - (n > 0.0 ? P / n : 0.0);
+        F = -a.area * b[(size_t)a.wall * a.S + s];
+    }
+    a.dv[q] = dv;
+    a.F[q] = F;
+}
+
+// One CTA per lag k: sums over valid daughters and origins t = 0 .. S-1-k.
+__global__ void slip_xcorr_kernel(SlipArgs a, double *c_dvf, double *c_dvdv) {
+    __shared__ double sh[32];
+    __shared__ int nvalid_s;
+    const int k = blockIdx.x, m = a.S - k;
+    if (threadIdx.x == 0) {
+        int nv = 0;
+        for (int d = 0; d < a.D; d++) nv += a.status[d] == 0;
+        nvalid_s = nv;
+    }
+    double v1 = 0.0, v2 = 0.0;
+    for (long long q = threadIdx.x; q < (long long)a.D * m; q += blockDim.x) {
+        const size_t d = (size_t)(q / m), t = (size_t)(q % m);
+        const double x = a.dv[d * a.S + t];
+        v1 += x * a.F[d * a.S + t + k];
+        v2 += x * a.dv[d * a.S + t + k];
+    }
+    const double t1 = block_sum(v1, sh);
+    const double t2 = block_sum(v2, sh);
+    if (threadIdx.x == 0) {
+        const double cnt = (double)nvalid_s * m;
+        c_dvf[k] = cnt > 0 ? t1 / cnt : NAN;
+        c_dvdv[k] = cnt > 0 ? t2 / cnt : NAN;
+    }
+}
+
+cudaError_t launch_slip_correlations(const SlipArgs &a, int max_lag, double *c_dvf, double *c_dvdv,
+                                     cudaStream_t st) {
+    const long long n = (long long)a.D * a.S;
+    slip_force_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+    slip_xcorr_kernel<<<max_lag + 1, 256, 0, st>>>(a, c_dvf, c_dvdv);
     return cudaGetLastError();
 }
 

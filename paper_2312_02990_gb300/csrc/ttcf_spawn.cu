@@ -2,8 +2,9 @@
 // (Figure 1; Algorithm 2 "load system state", "apply mapping", "switch on
 // ext. field").  One CTA per mother state, all arithmetic IEEE double:
 //   P_ab(0) = (1/V)[sum_i p_a p_b + sum_{i<j} r_ij,a F_ij,b]   (WCA, Eq. 6)
-//   B(0)    = P_xy(0) of each mapped daughter: mappings 0, 1 keep P_xy,
-//             mappings 2, 3 (x-reflections) negate it exactly (Eq. 3)
+//   B(0)    = P_xy(0) of each mapped daughter: a reflection of x or of y
+//             negates it exactly, time reversal and the z-reflection keep
+//             it, the x <-> z exchange makes it the mother's P_zy (Eq. 3)
 //   Omega   = -gamma V B(0) / (k_B T)                        (Eq. 7)
 // so sum over the group of Omega(0) and of B(0) is exactly zero.
 #include "ttcf_internal.h"
@@ -144,11 +145,11 @@ __global__ void spawn_kernel(SpawnArgs a) {
             for (int w = 0; w < nw; w++) v += red[w * NACC + k];
             tot[k] = v;
         }
-        const double pxy = (tot[3] + tot[9]) / a.V;
+        const double pxy = (tot[3] + tot[9]) / a.V, pyz = (tot[5] + tot[11]) / a.V;
         const double gm = a.gamma[g];
         for (int k = 0; k < a.M; k++) {
             const int m = a.maps[k];
-            const double b0 = (m == 2 || m == 3) ? -pxy : pxy;
+            const double b0 = map_pxy_sign(m) * (map_swaps_xz(m) ? pyz : pxy);
             const size_t d = (size_t)g * a.M + k;
             a.B[d * a.S] = b0;
             a.Omega[d] = -gm * a.V * b0 / a.T;

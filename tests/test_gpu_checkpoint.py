@@ -130,7 +130,8 @@ def test_tampered_header_is_rejected(T, eq_mothers_256, tmp_path):
         c.run(10)
         c.save(str(path))
     raw = bytearray(path.read_bytes())
-    off = 8 + 4 + ctypes.sizeof(T.Config) + 4 + 8 + 4 + 6 * 4 + 16 + 24 + 24 + 12   # ncell
+    maps_bytes = 4 * 32   # the batch's table of mapping codes (32 int slots)
+    off = 8 + 4 + ctypes.sizeof(T.Config) + 4 + 8 + 4 + 6 * 4 + maps_bytes + 24 + 24 + 12   # ncell
     ncell = struct.unpack_from("<i", raw, off)[0]
     nc = struct.unpack_from("<3i", raw, off - 12)
     assert ncell == nc[0] * nc[1] * nc[2]

@@ -381,3 +381,79 @@ def test_mapping_keeps_positions_in_the_half_open_box():
         out, _ = oracle.apply_mapping(b, m, st)
         assert out[0, 0] == -0.5 * b.L[0]
         assert np.all(out[0] >= -0.5 * b.L[0]) and np.all(out[0] < 0.5 * b.L[0])
+
+
+# ------------------------------------------ mappings beyond Eq. 3 ----------
+def _pressure_tensor(b, s):
+    P, U, K2 = oracle.pressure(b, s)
+    # components xx yy zz xy xz yz
+    return P, U, K2
+
+
+@pytest.mark.parametrize("m", range(32))
+def test_every_mapping_is_an_isometry_with_the_tensor_law(m):
+    """Each mapping code (exchange x <-> z, then reflections, then time
+    reversal) keeps the kinetic and potential energy (an isometry of the
+    cubic periodic box) and transforms the pressure tensor as a tensor:
+    P'_xy = s_x s_y P_xy, or s_x s_y P_zy when x and z are exchanged, with
+    s_a = -1 for a reflected axis; time reversal leaves P unchanged and
+    negates alpha."""
+    N = 256
+    b = bulk(N)
+    st = inputs.jittered_states(N, 1, seed=40 + m, amp=0.1)[0]
+    st[3:] = np.random.default_rng(m).standard_normal((3, N))
+    P, U, K2 = _pressure_tensor(b, st)
+    out, a = oracle.apply_mapping(b, m, st, alpha=0.3)
+    P2, U2, K22 = _pressure_tensor(b, out)
+    assert U2 == pytest.approx(U, rel=1e-12)
+    assert K22 == pytest.approx(K2, rel=1e-14)
+    sx = -1.0 if m & 2 else 1.0
+    sy = -1.0 if m & 4 else 1.0
+    base = P[5] if m & 16 else P[3]      # P_zy = P_yz after the exchange
+    assert P2[3] == pytest.approx(sx * sy * base, rel=1e-11, abs=1e-13)
+    assert a == (-0.3 if m & 1 else 0.3)
+    # positions stay in the half-open box
+    L = np.asarray(b.L)[:, None]
+    assert np.all(out[:3] >= -L / 2) and np.all(out[:3] < L / 2)
+
+
+@pytest.mark.parametrize("m", [6, 8, 14])
+def test_shear_symmetric_mappings_commute_with_the_sheared_dynamics(m):
+    """(x, y) -> (-x, -y) and z -> -z are symmetries of planar shear in x
+    with gradient in y (SLLOD with Lees-Edwards images), so running the
+    mapped state gives the mapped trajectory: map(evolve(G)) =
+    evolve(map(G)) at gamma = 0.1 after 60 steps."""
+    N = 256
+    b = bulk(N)
+    st = inputs.jittered_states(N, 1, seed=7, amp=0.1)[0]
+    st[3:] = np.random.default_rng(3).standard_normal((3, N)) * np.sqrt(0.722)
+    mapped, am = oracle.apply_mapping(b, m, st, alpha=0.05)
+    s1, a1, d1, _ = oracle.trajectory(b, st, 60, gamma=0.1, alpha=0.05)
+    s2, a2, d2, _ = oracle.trajectory(b, mapped, 60, gamma=0.1, alpha=am)
+    ms1, _ = oracle.apply_mapping(b, m, s1, alpha=a1)
+    L = np.asarray(b.L)[:, None]
+    dx = s2[:3] - ms1[:3]
+    # positions are compared modulo the periodic (Lees-Edwards) images
+    dx[1] -= L[1] * np.rint(dx[1] / L[1])
+    dx[0] -= L[0] * np.rint(dx[0] / L[0])
+    dx[2] -= L[2] * np.rint(dx[2] / L[2])
+    assert np.abs(dx).max() < 1e-8
+    assert np.abs(s2[3:] - ms1[3:]).max() < 1e-8
+    assert a2 == pytest.approx(a1, abs=1e-10)
+
+
+def test_mapping_sets_closed_under_a_reflection_cancel_omega():
+    """Sets of mapping codes closed under the x-reflection (m -> m ^ 2), such
+    as all 32 codes or the 8 of Eq. 3 with and without the z-mirror, give
+    sum_m Omega(0) = 0 and sum_m B(0) = 0 in every group, to rounding."""
+    N = 256
+    b = bulk(N)
+    ms = inputs.jittered_states(N, 2, seed=21, amp=0.1)
+    ms[:, 3:] = np.random.default_rng(8).standard_normal((2, 3, N))
+    for mask in (0xFFFFFFFF, 0x0F0F, 0xFFFF):
+        B, Om = oracle.daughters(b, ms, np.zeros(2), 1e-2, 2, mapping_mask=mask)
+        M = bin(mask).count("1")
+        for g in range(2):
+            o = Om[g * M:(g + 1) * M]
+            assert abs(o.sum()) <= 1e-12 * np.abs(o).sum(), hex(mask)
+            assert abs(B[g * M:(g + 1) * M, 0].sum()) <= 1e-12 * np.abs(B[g * M:(g + 1) * M, 0]).sum()
