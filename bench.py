@@ -113,6 +113,8 @@ def parse():
     p.add_argument("--conf-eq", type=int, default=4000)
     p.add_argument("--conf-spacing", type=int, default=200)
     p.add_argument("--conf-steps", type=int, default=2000)
+    p.add_argument("--conf-eq-steps", type=int, default=20000,
+                   help="steps of the zero-shear chains of the equilibrium friction estimate")
     p.add_argument("--uneven-chains", type=int, default=64)
     p.add_argument("--uneven-states", type=int, default=4)
     return p.parse_args()
@@ -641,7 +643,9 @@ def mapping_study_section(T, torch, args):
     x-reflection (cancels Omega(0) too), identity plus time reversal (does
     not: Omega(0) is even under p -> -p) and identity alone; each with the
     plain TTCF integrand and the Eq. 4 form <Omega(0)B(s)> -
-    <Omega(0)><B(s)>, first with <B(0)> from the data (the library's
+    <Omega(0)><B(s)>; then the larger sets the paper lists after Eq. 3
+    (component mirrors: Eq. 3 with z -> -z, all 16 mirror combinations, and
+    all 32 with the x <-> z exchange), first with <B(0)> from the data (the library's
     estimator: the mappings make it exactly 0), then with <B(0)> set to its
     equilibrium value 0 (the integral alone; standard errors over mother
     groups from the daughters' series).  The cost-normalised error is
@@ -650,7 +654,11 @@ def mapping_study_section(T, torch, args):
     N, n_steps = 256, 1000
     L = inputs.bulk_box(N)
     rates = [1e-2, 1e-4, 1e-6]
-    sets = {"eq3_all4": 0xF, "id_xrefl": 0x5, "id_trev": 0x3, "id_only": 0x1}
+    sets = {"eq3_all4": 0xF, "id_xrefl": 0x5, "id_trev": 0x3, "id_only": 0x1,
+            # the further choices listed after Eq. 3: Eq. 3 with the z-mirror
+            # (8 codes), every component mirror (16), and with the x <-> z
+            # exchange (32); each set is closed under the x-reflection
+            "eq3_zmirror8": 0x0F0F, "mirrors16": 0xFFFF, "mirrors_swap32": 0xFFFFFFFF}
     cfg = T.config_default()
     cfg.precision = T.TTCF_MIXED
     init = np.stack([inputs.initial_state(N, inputs.BASE_SEED + 91000 + k) for k in range(64)])
@@ -799,8 +807,9 @@ def confined_section(T, torch, args):
     dt = 0.005): GPU-thermalised mothers (lattices at rest; 64 chains x 4
     states = 256 mother states), then every mother x 4 mappings x 4 shear
     rates 1e-1 ... 1e-7 = 4096 daughters of conf_steps steps in one
-    persistent launch.  Reports daughter atom-steps/s of that launch and the
-    wall-stress responses."""
+    persistent launch.  Reports daughter atom-steps/s of that launch, the
+    wall-stress responses and the slip velocity and friction coefficient of
+    Eq. 12 at t_end (TTCF and direct average)."""
     from paper_2312_02990_gb300 import inputs
     sysd = inputs.confined_system()
     N, box = sysd["state"].shape[1], sysd["box"]
@@ -836,7 +845,13 @@ def confined_section(T, torch, args):
             gs = c.group_status(b, G)
             top = c.response_obs(b, 1)
             bot = c.response_obs(b, 0)
-            resp[f"{g:.0e}"] = {"wall_stress_top_ttcf": float(top["ttcf"][-1]),
+            fr = [c.friction(b, w) for w in (0, 1)]
+            resp[f"{g:.0e}"] = {"slip_top_ttcf": float(fr[1]["slip_ttcf"][-1]),
+                                "slip_top_dav": float(fr[1]["slip_dav"][-1]),
+                                "xi_top_ttcf": float(fr[1]["xi_ttcf"][-1]),
+                                "xi_top_dav": float(fr[1]["xi_dav"][-1]),
+                                "xi_bottom_ttcf": float(fr[0]["xi_ttcf"][-1]),
+                                "wall_stress_top_ttcf": float(top["ttcf"][-1]),
                                 "wall_stress_top_ttcf_se": float(top["ttcf_se"][-1]),
                                 "wall_stress_top_dav": float(top["dav"][-1]),
                                 "wall_stress_top_dav_se": float(top["dav_se"][-1]),
@@ -844,6 +859,28 @@ def confined_section(T, torch, args):
                                 "wall_stress_bottom_ttcf_se": float(bot["ttcf_se"][-1]),
                                 "excluded_groups": int(np.count_nonzero(gs)),
                                 "status_flags": int(np.bitwise_or.reduce(gs))}
+    # the equilibrium friction coefficient xi_0 (Eq. 12 by the equilibrium
+    # method): the same mother states run at zero shear with one mapping are
+    # equilibrium trajectories; slip/force correlations over t = 10 (every
+    # 5th step), Maxwell fit of the friction kernel
+    eq_cfg = T.config_default()
+    eq_cfg.system, eq_cfg.precision = T.TTCF_CONFINED_LJ, T.TTCF_MIXED
+    eq_cfg.dt, eq_cfg.T, eq_cfg.tau_T = 0.005, 1.0, 0.25
+    eq_cfg.n_steps, eq_cfg.sample_every, eq_cfg.mapping_mask = args.conf_eq_steps, 5, 1
+    n_eq_ch = min(G, 152)
+    t0 = time.perf_counter()
+    with T.Context(eq_cfg) as c:
+        bid = c.spawn_confined(ms[:n_eq_ch], sysd["types"], sysd["lattice"], box, al[:n_eq_ch], 0.0)
+        c.run(allow_numeric=True)
+        lag = min(400, args.conf_eq_steps // 5 - 1)
+        svals = np.linspace(0.05, 1.0, 20)
+        eq = [c.friction_equilibrium(bid, w, lag, svals) for w in (0, 1)]
+    t_eq = time.perf_counter() - t0
+    friction_eq = {"xi0_bottom": float(eq[0]["xi0"]), "xi0_top": float(eq[1]["xi0"]),
+                   "tau_m": [float(eq[0]["tau_m"]), float(eq[1]["tau_m"])],
+                   "xi_ratio_unfitted": [float(eq[0]["xi_ratio"]), float(eq[1]["xi_ratio"])],
+                   "chains": n_eq_ch, "steps": args.conf_eq_steps, "max_lag_time": lag * 5 * 0.005,
+                   "laplace_s": [0.05, 1.0, 20], "seconds": t_eq}
     D = 4 * G * len(CONF_RATES)
     atom_steps = float(D) * N * args.conf_steps
     k_ms = st["ms_run"]
@@ -862,7 +899,7 @@ def confined_section(T, torch, args):
             "pairs_per_atom_step": st["pairs_interacting"] / atom_steps,
             "rebuilds_per_daughter_step": st["rebuilds"] / (D * args.conf_steps),
             "mother_setup_s": t_moth, "mother_chains_dropped": int(np.count_nonzero(~keep)),
-            "responses_t_end": resp}
+            "friction_equilibrium": friction_eq, "responses_t_end": resp}
 
 
 def probe_section():

@@ -67,8 +67,12 @@ enum { TTCF_BULK_WCA = 0, TTCF_CONFINED_LJ = 1 };
  *  2 + k          sum of fluid p_x in slab k (k < TTCF_CONF_NSLAB) of
  *                 equal slabs spanning y in [-Ly/2, Ly/2)
  *  2 + NSLAB + k  number of fluid atoms in slab k
+ *  2 + 2 NSLAB    sum of p_x over the innermost layer of the bottom wall
+ *                 (its atoms whose tether site lies within 0.1 sigma in y
+ *                 of the wall's site plane nearest the channel)
+ *  3 + 2 NSLAB    the same for the top wall
  * (slab velocity profile: response 2+k divided by response 2+NSLAB+k).  */
-enum { TTCF_CONF_NSLAB = 40, TTCF_CONF_NOBS = 2 + 2 * 40 };
+enum { TTCF_CONF_NSLAB = 40, TTCF_CONF_NOBS = 2 + 2 * 40 + 2 };
 
 /* Arithmetic of the daughter integrator.
  *  TTCF_FP64:  every per-atom quantity in IEEE double (slow on GB300).
@@ -104,9 +108,18 @@ typedef struct {
     int n_steps;            /* daughter length in steps                      */
     int sample_every;       /* B(s) recorded every sample_every steps;
                                n_steps must be a multiple of it              */
-    unsigned mapping_mask;  /* bit m selects mapping m of Eq. 3 (0xF = all)  */
+    unsigned mapping_mask;  /* bit m selects mapping code m (0xF = the four
+                               mappings of Eq. 3).  Code m, applied as:
+                               bit 4 exchange of x and z (positions and
+                               momenta; needs Lx = Lz), bit 1/2/3
+                               reflection of x/y/z with its momentum, bit 0
+                               time reversal p -> -p (the further choices
+                               listed after Eq. 3); codes 0..3 are Eq. 3.
+                               Bulk only beyond 0..3; a set closed under the
+                               x- or y-reflection keeps <Omega(0)> = 0 per
+                               group, other sets call for the Eq. 4 form    */
     int reset_alpha;        /* 0: daughters inherit the mother's alpha,
-                               negated by the time-reversing mappings 1, 3;
+                               negated by the time-reversing (odd) codes;
                                1: alpha = 0 at switch-on                     */
     int keep_state;         /* 1: keep every daughter's phase point on the
                                device after ttcf_run (ttcf_get_state)        */
@@ -380,14 +393,23 @@ ttcf_status ttcf_response_obs(ttcf_ctx *ctx, int batch_id, int observable, int c
                               int *n_samples);
 
 /* Slip velocity and friction coefficient at one wall of a confined batch
- * (Eq. 12, <F_x> = xi A <dv>), from its TTCF and direct-average responses:
- * v(t) = sum_k <P_k(t)> / sum_k <n_k(t)> over the slabs whose centres lie
- * within one sigma of the wall's innermost layer on the fluid side,
- * slip(t) = v(t) - s_w gamma h / 2 (s_w = -1 bottom, +1 top), and
- * xi(t) = <sigma_w(t)> / slip(t) with sigma_w the x force of the fluid on
- * the wall per area.  wall: 0 bottom, 1 top.  Arrays as in ttcf_response
- * (any may be NULL).  Errors: TTCF_E_INVALID (not a confined batch, shear
- * rate differing between groups, bad wall), TTCF_E_STATE (run not done). */
+ * (Eq. 12, <F_x> = xi A <dv>), from its TTCF and direct-average responses,
+ * with the slip velocity as the paper defines it (the velocity of the
+ * innermost wall layer minus that of the outermost fluid layer):
+ *   v_wall(t)  = <sum of p_x over the wall's innermost layer> / n_layer
+ *                (response 82 + wall; n_layer atoms: the wall's atoms whose
+ *                tether site lies within 0.1 sigma in y of its site plane
+ *                nearest the channel),
+ *   v_fluid(t) = sum_k <P_k(t)> / sum_k <n_k(t)> over the slabs whose
+ *                centres lie within one sigma of the wall on the fluid side,
+ *   slip(t) = v_wall(t) - v_fluid(t),
+ *   xi(t)   = -<sigma_w(t)> / slip(t), sigma_w being the x force of the
+ *             fluid on the wall per area (the wall's force on the fluid is
+ *             its negative).
+ * wall: 0 bottom, 1 top.  Arrays as in ttcf_response (any may be NULL).
+ * Errors: TTCF_E_INVALID (not a confined batch, shear rate differing
+ * between groups, bad wall, wall without atoms), TTCF_E_STATE (run not
+ * done).                                                                   */
 ttcf_status ttcf_friction(ttcf_ctx *ctx, int batch_id, int wall, double *t, double *slip_ttcf,
                           double *slip_dav, double *xi_ttcf, double *xi_dav, int capacity,
                           int *n_samples);
@@ -453,6 +475,32 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path);
 ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, const double box[3],
                              int n_mothers, const double *mother_soa, const double *mother_alpha,
                              const double *shear_rates, double *B, double *Omega, int *status);
+
+/* Equilibrium friction coefficient xi_0 of Eq. 12 by the equilibrium method
+ * the paper takes from its references (Hansen, Todd and Daivis 2011;
+ * Varghese, Hansen and Todd 2021), at one wall of a finished confined batch
+ * run at zero shear rate (its daughters are then equilibrium trajectories
+ * with the lattices at rest; a single mapping, mapping_mask = 1, makes them
+ * independent).  Per daughter and sample:
+ *   dv(t) = slip velocity as in ttcf_friction (inner wall layer velocity
+ *           minus the adjacent fluid slabs' velocity),
+ *   F(t)  = -A sigma_w(t), the wall's x force on the fluid;
+ * correlations over the valid daughters and all time origins, lags k =
+ * 0 .. max_lag samples:  c_dvf[k] = <dv(t) F(t+k)>, c_dvdv[k] = <dv(t)
+ * dv(t+k)>.  With F(t) = int_0^t zeta(t-u) dv(u) du + R(t), <dv(0)R(t)> = 0,
+ * the friction kernel in the Laplace domain is zeta~(s) = C~_dvF(s) /
+ * C~_dvdv(s) (trapezoid transforms over the lag window).  A Maxwell kernel
+ * zeta~(s) = zeta_0 / (1 + s tau_M) is fitted as the least-squares line
+ * 1/zeta~(s) = 1/zeta_0 + (tau_M/zeta_0) s over the n_s values s_grid.
+ *   out[0] = xi_0 = zeta_0 / A,  out[1] = zeta_0,  out[2] = tau_M,
+ *   out[3] = C~_dvF(0) / C~_dvdv(0) / A (the unfitted estimate).
+ * c_dvf, c_dvdv [max_lag + 1] and zeta_s [n_s] (host, may be NULL).
+ * Errors: TTCF_E_INVALID (not a confined batch, a nonzero shear rate, bad
+ * wall, max_lag outside [1, samples - 2], fewer than 2 Laplace variables),
+ * TTCF_E_STATE (run not finished), TTCF_E_OOM, TTCF_E_CUDA.                */
+ttcf_status ttcf_friction_equilibrium(ttcf_ctx *ctx, int batch_id, int wall, int max_lag, int n_s,
+                                      const double *s_grid, double out[4], double *c_dvf,
+                                      double *c_dvdv, double *zeta_s);
 
 /* ------------------------------------------------------------------------
  * Learned control variate.  The paper has no learned part; the estimator it

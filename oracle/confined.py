@@ -11,6 +11,9 @@ import numpy as np
 from .core import lib as _lib_bulk
 
 N_SLAB = 40
+# responses per sample: wall stress (bottom, top), 40 slab sums of fluid p_x,
+# 40 slab counts, inner-layer p_x sums (bottom, top)
+N_OBS = 2 + 2 * N_SLAB + 2
 _configured = False
 
 
@@ -160,11 +163,11 @@ def apply_mapping(sys: Confined, m: int, state, lattice, alpha: float = 0.0):
 
 
 def daughter(sys: Confined, mother_state, lattice, mother_alpha, m, n_steps, sample_every=1):
-    """(B [S, 2 + 2 nslab], Omega, final state)."""
+    """(B [S, 2 + 2 nslab + 2], Omega, final state)."""
     s = np.ascontiguousarray(mother_state, np.float64)
     lt = np.ascontiguousarray(lattice, np.float64)
     S = n_steps // sample_every + 1
-    B = np.zeros((S, 2 + 2 * sys.nslab))
+    B = np.zeros((S, 2 + 2 * sys.nslab + 2))
     om = C.c_double()
     fin = np.zeros((6, sys.n))
     if lib().orc_conf_daughter(C.byref(sys.c()), _ip(sys.t), _p(s), _p(lt), float(mother_alpha),
@@ -175,16 +178,28 @@ def daughter(sys: Confined, mother_state, lattice, mother_alpha, m, n_steps, sam
 
 
 def daughters(sys: Confined, mothers, lattice, alphas, n_steps, sample_every=1, n_threads=None):
-    """B [4G, S, 2 + 2 nslab], Omega [4G]; daughter d = 4 g + m."""
+    """B [4G, S, 2 + 2 nslab + 2], Omega [4G]; daughter d = 4 g + m."""
     ms = np.ascontiguousarray(mothers, np.float64)
     lt = np.ascontiguousarray(lattice, np.float64)
     al = np.ascontiguousarray(np.broadcast_to(np.asarray(alphas, np.float64), (ms.shape[0],)))
     G = ms.shape[0]
     S = n_steps // sample_every + 1
-    B = np.zeros((4 * G, S, 2 + 2 * sys.nslab))
+    B = np.zeros((4 * G, S, 2 + 2 * sys.nslab + 2))
     Om = np.zeros(4 * G)
     nt = n_threads or os.cpu_count() or 1
     if lib().orc_conf_daughters(C.byref(sys.c()), _ip(sys.t), G, _p(ms), _p(lt), _p(al), int(n_steps),
                                 int(sample_every), _p(B), _p(Om), int(nt)):
         raise RuntimeError("confined daughters failed")
     return B, Om
+
+
+def inner_layer(types, lattice, wall: int, tol: float = 0.1) -> np.ndarray:
+    """Indices of the innermost layer of wall 0 (bottom, type 1) or 1 (top,
+    type 2): the wall's atoms whose tether site lies within tol in y of the
+    wall's site plane nearest the channel."""
+    t = np.asarray(types)
+    yl = np.asarray(lattice)[1]
+    sel = t == (1 if wall == 0 else 2)
+    if wall == 0:
+        return np.nonzero(sel & (yl >= yl[sel].max() - tol))[0]
+    return np.nonzero(sel & (yl <= yl[sel].min() + tol))[0]

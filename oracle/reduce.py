@@ -90,21 +90,28 @@ def adjacent_slabs(Ly: float, h: float, wall: int, nslab: int = 40, width: float
     return np.nonzero(sel)[0]
 
 
-def friction(resp_obs, gamma: float, Ly: float, h: float, wall: int, nslab: int = 40,
+def friction(resp_obs, Ly: float, h: float, wall: int, n_layer: int, nslab: int = 40,
              estimator: str = "ttcf") -> dict:
     """Slip velocity and friction coefficient of Eq. 12 at one wall from the
-    confined responses (resp_obs[o] = responses of observable o):
-    v(t) = sum_k <P_k> / sum_k <n_k> over the slabs adjacent to the wall,
-    slip = v - s_w gamma h / 2, xi = <sigma_w> / slip (sigma_w: x force of
-    the fluid on the wall per area; s_w = -1 bottom, +1 top)."""
+    confined responses (resp_obs[o] = responses of observable o), with the
+    slip velocity as the paper defines it: the velocity of the innermost wall
+    layer minus that of the outermost fluid layer,
+        v_wall  = <sum of p_x over the wall's innermost layer> / n_layer
+                  (observable 2 + 2 nslab + wall),
+        v_fluid = sum_k <P_k> / sum_k <n_k> over the slabs adjacent to the
+                  wall (each average a TTCF-able linear response; the ratio
+                  is taken after averaging),
+        slip    = v_wall - v_fluid,
+        xi      = <F_x> / (A slip) = -<sigma_w> / slip,
+    sigma_w being the x force of the fluid on the wall per area (the force
+    of the wall on the fluid is its negative)."""
     ks = adjacent_slabs(Ly, h, wall, nslab)
     P = sum(resp_obs[2 + k][estimator] for k in ks)
     n = sum(resp_obs[2 + nslab + k][estimator] for k in ks)
-    sw = 1.0 if wall == 1 else -1.0
-    slip = P / n - sw * gamma * 0.5 * h
-    sigma = resp_obs[wall][estimator]
+    v_wall = resp_obs[2 + 2 * nslab + wall][estimator] / n_layer
     with np.errstate(divide="ignore", invalid="ignore"):
-        xi = sigma / slip
+        slip = v_wall - P / n
+        xi = -resp_obs[wall][estimator] / slip
     return {"slip": slip, "xi": xi, "slabs": ks}
 
 
@@ -133,3 +140,73 @@ def green_kubo(acf: np.ndarray, V: float, T: float, ds: float) -> np.ndarray:
     """Running Green-Kubo viscosity (V / k_B T) int_0^{k ds} <P_xy(0)P_xy(t)> dt
     by the trapezoid rule on the lag grid (Eq. 8 at zero field)."""
     return (V / T) * _cumtrapz(np.asarray(acf, dtype=np.float64), ds)
+
+
+# ----------------------------------------------------------------------------
+# Equilibrium friction coefficient xi_0 of Eq. 12 (<F_x> = xi_0 A <dv>), by
+# the equilibrium method the paper takes from its references (Hansen, Todd
+# and Daivis 2011; Varghese, Hansen and Todd 2021): along equilibrium
+# trajectories (walls at rest) the force F(t) of the wall on the fluid next
+# to it and the slip velocity dv(t) (innermost wall layer minus outermost
+# fluid layer) obey a generalised Langevin relation F(t) = int_0^t
+# zeta(t - u) dv(u) du + R(t) with a random force R uncorrelated with
+# dv(0), so that
+#     C_dvF(t) = <dv(0) F(t)> = int_0^t zeta(t - u) C_dvdv(u) du,
+# and in the Laplace domain zeta~(s) = C~_dvF(s) / C~_dvdv(s).  The friction
+# kernel is fitted with a Maxwell model zeta~(s) = zeta_0 / (1 + s tau_M),
+# i.e. the straight line 1/zeta~(s) = 1/zeta_0 + (tau_M/zeta_0) s, and
+# xi_0 = zeta_0 / A (the zero-frequency friction per wall area).
+# ----------------------------------------------------------------------------
+def cross_correlation(a: np.ndarray, b: np.ndarray, max_lag: int) -> np.ndarray:
+    """<a(t) b(t+k)> over trajectories (rows) and time origins t = 0 ..
+    n-1-k, for k = 0 .. max_lag."""
+    a = np.atleast_2d(np.asarray(a, dtype=np.float64))
+    b = np.atleast_2d(np.asarray(b, dtype=np.float64))
+    n = a.shape[1]
+    return np.array([np.mean(a[:, :n - k] * b[:, k:]) for k in range(max_lag + 1)])
+
+
+def laplace(c: np.ndarray, ds: float, s: float) -> float:
+    """int_0^{t_max} exp(-s t) c(t) dt by the trapezoid rule on the lag grid."""
+    t = np.arange(len(c)) * ds
+    f = np.exp(-s * t) * np.asarray(c, dtype=np.float64)
+    return float(ds * (f.sum() - 0.5 * (f[0] + f[-1])))
+
+
+def friction_from_correlations(c_dvf, c_dvdv, ds: float, area: float, s_grid) -> dict:
+    """xi_0 from the two equilibrium correlations: zeta~(s) on s_grid, the
+    least-squares line through 1/zeta~(s), zeta_0 = 1 / intercept,
+    tau_M = slope / intercept, xi_0 = zeta_0 / area; also the s = 0 ratio
+    of the integrals (the unfitted estimate) as xi_ratio."""
+    s_grid = np.asarray(s_grid, dtype=np.float64)
+    zeta = np.array([laplace(c_dvf, ds, s) / laplace(c_dvdv, ds, s) for s in s_grid])
+    slope, icpt = np.polyfit(s_grid, 1.0 / zeta, 1)
+    z0 = 1.0 / icpt
+    return {"xi0": z0 / area, "zeta0": z0, "tau_m": slope / icpt, "s": s_grid, "zeta_s": zeta,
+            "xi_ratio": laplace(c_dvf, ds, 0.0) / laplace(c_dvdv, ds, 0.0) / area}
+
+
+def slip_and_wall_force(series: np.ndarray, area: float, n_layer: int, slabs, wall: int,
+                        nslab: int = 40):
+    """dv(t) and F(t) of each trajectory from the confined responses
+    series[G, n_obs, S]: dv = (inner wall layer p_x sum) / n_layer - (sum
+    of the adjacent slabs' p_x) / (their fluid count), F = -A sigma_w (the
+    wall's force on the fluid; sigma_w is the fluid's x force on the wall
+    per area)."""
+    ser = np.asarray(series, dtype=np.float64)
+    P = ser[:, [2 + k for k in slabs]].sum(axis=1)
+    n = ser[:, [2 + nslab + k for k in slabs]].sum(axis=1)
+    dv = ser[:, 2 + 2 * nslab + wall] / n_layer - P / n
+    F = -area * ser[:, wall]
+    return dv, F
+
+
+def friction_equilibrium(series, area: float, n_layer: int, slabs, wall: int, ds: float,
+                         max_lag: int, s_grid, nslab: int = 40) -> dict:
+    """xi_0 of one wall from equilibrium confined trajectories (see above)."""
+    dv, F = slip_and_wall_force(series, area, n_layer, slabs, wall, nslab)
+    c_dvf = cross_correlation(dv, F, max_lag)
+    c_dvdv = cross_correlation(dv, dv, max_lag)
+    out = friction_from_correlations(c_dvf, c_dvdv, ds, area, s_grid)
+    out.update({"c_dvf": c_dvf, "c_dvdv": c_dvdv})
+    return out

@@ -17,7 +17,12 @@
  * dH^ad/dt): Omega = -(1/T_w) sum_w k (x_w - x_l) s_w v_wall.
  * Responses B per sample: the x force exerted by the fluid on the bottom and
  * on the top wall per unit area, then the fluid's sum of p_x and its atom
- * count in each of nslab slabs spanning y in [-Ly/2, Ly/2).
+ * count in each of nslab slabs spanning y in [-Ly/2, Ly/2), then the sum of
+ * p_x over the innermost layer of the bottom and of the top wall (the wall
+ * layer whose velocity enters the slip velocity of the friction study): the
+ * wall's atoms whose tether site lies within 0.1 sigma in y of the wall's
+ * site plane nearest the channel (sites slide in x only, so layers stay
+ * planar).
  *
  * Discretisation (the paper says "velocity Verlet"): the symmetric splitting
  * E D B A B D E, E = alpha flow, D = wall friction flow, B = kick with all
@@ -219,16 +224,30 @@ static void cs_load(const orc_conf *c, conf_state *s, const double *soa, const d
 }
 
 /* Responses at the current state: sw_bottom/A, sw_top/A, slab sums of     */
-/* fluid p_x, slab counts of fluid atoms.                                   */
+/* fluid p_x, slab counts of fluid atoms, inner-layer p_x sums of the       */
+/* bottom and top wall (2 + 2 nslab + 2 values).                            */
 static void cs_observe(const orc_conf *c, const int *type, const conf_state *s, double *B)
 {
     int ns = c->nslab;
     double A = c->L[0] * c->L[2];
     B[0] = s->sw[0] / A;
     B[1] = s->sw[1] / A;
-    for (int k = 0; k < 2 * ns; k++) B[2 + k] = 0.0;
+    for (int k = 0; k < 2 * ns + 2; k++) B[2 + k] = 0.0;
+    /* the site planes nearest the channel: highest bottom, lowest top     */
+    double ybot = -INFINITY, ytop = INFINITY;
     for (int i = 0; i < c->n; i++) {
-        if (type[i] != 0) continue;
+        if (type[i] == 1 && s->yl[i] > ybot) ybot = s->yl[i];
+        if (type[i] == 2 && s->yl[i] < ytop) ytop = s->yl[i];
+    }
+    for (int i = 0; i < c->n; i++) {
+        if (type[i] == 1) {
+            if (s->yl[i] >= ybot - 0.1) B[2 + 2 * ns] += s->px[i];
+            continue;
+        }
+        if (type[i] == 2) {
+            if (s->yl[i] <= ytop + 0.1) B[3 + 2 * ns] += s->px[i];
+            continue;
+        }
         int k = (int)floor((s->y[i] + 0.5 * c->L[1]) / c->L[1] * ns);
         k = k < 0 ? 0 : (k >= ns ? ns - 1 : k);
         B[2 + k] += s->px[i];
@@ -311,7 +330,7 @@ void orc_conf_map(const orc_conf *c, int m, const double *in, const double *lat,
 }
 
 /* One confined daughter: B has (n_steps/sample_every + 1) rows of         */
-/* 2 + 2 nslab responses; Omega as in the header.                          */
+/* 2 + 2 nslab + 2 responses; Omega as in the header.                      */
 int orc_conf_daughter(const orc_conf *c, const int *type, const double *mother, const double *lat,
                       double mother_alpha, int m, int reset_alpha, int n_steps, int sample_every,
                       double *B, double *Omega, double *final_state)
@@ -323,7 +342,7 @@ int orc_conf_daughter(const orc_conf *c, const int *type, const double *mother, 
     s.alpha = a0;
     if (cs_forces(c, type, &s)) { free(s.buf); return -1; }
     *Omega = lattice_power(c, type, &s) / c->Tw;
-    int nb = 2 + 2 * c->nslab;
+    int nb = 2 + 2 * c->nslab + 2;
     cs_observe(c, type, &s, B);
     for (int t = 1; t <= n_steps; t++) {
         if (cs_step(c, type, &s)) { free(s.buf); return -1; }
@@ -338,7 +357,7 @@ int orc_conf_daughters(const orc_conf *c, const int *type, int n_groups, const d
                        const double *lat, const double *alpha, int n_steps, int sample_every,
                        double *B, double *Omega, int n_threads)
 {
-    int S = n_steps / sample_every + 1, nb = 2 + 2 * c->nslab, D = 4 * n_groups, err = 0;
+    int S = n_steps / sample_every + 1, nb = 2 + 2 * c->nslab + 2, D = 4 * n_groups, err = 0;
     (void)n_threads;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(|:err)
     for (int d = 0; d < D; d++) {

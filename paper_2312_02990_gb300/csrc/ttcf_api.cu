@@ -27,7 +27,7 @@ struct BatchHost {
     int N = 0, M = 0, G = 0, S = 0;
     int n_obs = 1;                        // observables per sample
     bool confined = false;                // Example 2 batch (ttcf_confined.cu)
-    int maps[4] = {0, 0, 0, 0};
+    int maps[MAX_MAPS] = {};
     double L[3] = {0, 0, 0};
     double V = 0, Q = 0, gT = 0;
     int nc[3] = {0, 0, 0}, ncell = 0;     // list cells, width >= r_c + skin
@@ -49,6 +49,8 @@ struct BatchHost {
     double *lattice = nullptr;
     double A = 0, rc = 0, k_tether = 0, c_ff = 0, c_wf = 0, c_ww = 0, half_h = 0;
     int ww_on = 0;
+    double inner_y[2] = {0, 0};          // inner wall layers (see ConfBatchDev)
+    int n_inner[2] = {0, 0};              // atoms in each inner wall layer
     // reduction
     bool reduced = false;
     double *Y = nullptr, *Dg = nullptr, *J = nullptr, *Og = nullptr, *valid = nullptr, *out = nullptr;
@@ -229,6 +231,9 @@ ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const dou
         if (box[k] < 3.0 * rl)
             return fail(ctx, TTCF_E_INVALID, "box edge shorter than 3*(r_c+skin): system too small");
     }
+    for (int k = 0; k < M; k++)
+        if (map_swaps_xz(maps[k]) && !(fabs(box[0] - box[2]) <= 1e-12 * box[0]))
+            return fail(ctx, TTCF_E_INVALID, "the x <-> z exchange mappings need L_x = L_z");
     b.N = N; b.G = G; b.M = M; b.S = S;
     for (int k = 0; k < M; k++) b.maps[k] = maps[k];
     b.V = box[0] * box[1] * box[2];
@@ -296,7 +301,7 @@ ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const dou
     SpawnArgs sa;
     memset(&sa, 0, sizeof(sa));
     sa.N = N; sa.M = M; sa.G = G;
-    for (int k = 0; k < 4; k++) sa.maps[k] = b.maps[k];
+    for (int k = 0; k < MAX_MAPS; k++) sa.maps[k] = b.maps[k];
     for (int k = 0; k < 3; k++) { sa.nc[k] = b.snc[k]; sa.L[k] = b.L[k]; }
     sa.ncell = b.sncell;
     sa.V = b.V; sa.T = cf.T;
@@ -312,7 +317,7 @@ BatchDev to_dev(const BatchHost &b) {
     BatchDev d;
     memset(&d, 0, sizeof(d));
     d.N = b.N; d.M = b.M; d.G = b.G; d.S = b.S;
-    for (int k = 0; k < 4; k++) d.maps[k] = b.maps[k];
+    for (int k = 0; k < MAX_MAPS; k++) d.maps[k] = b.maps[k];
     for (int k = 0; k < 3; k++) { d.nc[k] = b.nc[k]; d.L[k] = b.L[k]; }
     d.ncell = b.ncell;
     d.V = b.V; d.Q = b.Q; d.gT = b.gT; d.d0 = b.d0;
@@ -626,6 +631,25 @@ ttcf_status make_conf_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, cons
         n_wall += t != 0;
     }
     if (n_wall == 0) return fail(ctx, TTCF_E_INVALID, "no wall atoms");
+    {   // the innermost layer of each wall: sites within CONF_LAYER_TOL in y of
+        // the wall's site plane nearest the channel
+        std::vector<double> ys(N);
+        if (is_dev) CK(cudaMemcpy(ys.data(), lattice + N, sizeof(double) * N, cudaMemcpyDeviceToHost));
+        else std::copy(lattice + N, lattice + 2 * (size_t)N, ys.begin());
+        double ybot = -INFINITY, ytop = INFINITY;
+        for (int i = 0; i < N; i++) {
+            if (!isfinite(ys[i])) return fail(ctx, TTCF_E_INVALID, "non-finite tether site");
+            if (types_h[i] == 1) ybot = std::max(ybot, ys[i]);
+            if (types_h[i] == 2) ytop = std::min(ytop, ys[i]);
+        }
+        b.inner_y[0] = ybot - CONF_LAYER_TOL;
+        b.inner_y[1] = ytop + CONF_LAYER_TOL;
+        b.n_inner[0] = b.n_inner[1] = 0;
+        for (int i = 0; i < N; i++) {
+            if (types_h[i] == 1 && ys[i] >= b.inner_y[0]) b.n_inner[0]++;
+            if (types_h[i] == 2 && ys[i] <= b.inner_y[1]) b.n_inner[1]++;
+        }
+    }
     for (int k = 0; k < G; k++)
         if (!isfinite(b.gamma[k]) || !isfinite(alpha_h[k]))
             return fail(ctx, TTCF_E_INVALID, "non-finite shear rate or alpha");
@@ -672,6 +696,7 @@ ttcf_status make_conf_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, cons
     for (int k = 0; k < 3; k++) { sa.nc[k] = b.snc[k]; sa.L[k] = b.L[k]; }
     sa.ncell = b.sncell;
     sa.A = b.A; sa.Tw = cf.T; sa.rc = b.rc; sa.k = b.k_tether; sa.c_wf = b.c_wf; sa.half_h = b.half_h;
+    sa.inner_y[0] = b.inner_y[0]; sa.inner_y[1] = b.inner_y[1];
     sa.src = src; sa.gamma = b.gamma_d; sa.types = b.types; sa.lattice = b.lattice;
     sa.mothers = b.mothers; sa.B = b.B; sa.Omega = b.Omega;
     CK(launch_conf_spawn(sa, st));
@@ -689,6 +714,7 @@ ConfBatchDev conf_to_dev(const BatchHost &b) {
     d.A = b.A; d.Q = b.Q; d.gT = b.gT;
     d.rc = b.rc; d.k = b.k_tether; d.c_ff = b.c_ff; d.c_wf = b.c_wf; d.c_ww = b.c_ww;
     d.ww_on = b.ww_on; d.half_h = b.half_h;
+    d.inner_y[0] = b.inner_y[0]; d.inner_y[1] = b.inner_y[1];
     d.skin = (float)b.skin;
     d.d0 = b.d0;
     d.mothers = b.mothers; d.m_alpha = b.m_alpha; d.gamma = b.gamma_d;
@@ -864,8 +890,10 @@ ttcf_status ttcf_create(const ttcf_config *cfg, ttcf_ctx **out) {
         return fail(nullptr, TTCF_E_INVALID, "dt, T and tau_T must be positive");
     if (c.n_steps < 1 || c.sample_every < 1 || c.n_steps % c.sample_every)
         return fail(nullptr, TTCF_E_INVALID, "n_steps must be a positive multiple of sample_every");
-    if ((c.mapping_mask & 0xF) == 0 || (c.mapping_mask & ~0xFu))
-        return fail(nullptr, TTCF_E_INVALID, "mapping_mask must select mappings 0..3");
+    if (c.mapping_mask == 0)
+        return fail(nullptr, TTCF_E_INVALID, "mapping_mask must select at least one mapping");
+    if (c.system == TTCF_CONFINED_LJ && (c.mapping_mask & ~0xFu))
+        return fail(nullptr, TTCF_E_INVALID, "the confined system takes the mappings 0..3 of Eq. 3 only");
     if (c.block_threads < 0 || c.block_threads % 32 || c.block_threads > 1024)
         return fail(nullptr, TTCF_E_INVALID, "block_threads must be 0 or a multiple of 32 <= 1024");
     if (c.kernel_variant < 0 || c.kernel_variant > N_VARIANTS)
@@ -917,8 +945,8 @@ ttcf_status ttcf_spawn_daughters(ttcf_ctx *ctx, int n_atoms, const double box[3]
     if (ctx->cfg.system != TTCF_BULK_WCA)
         return fail(ctx, TTCF_E_INVALID, "ttcf_spawn_daughters needs a TTCF_BULK_WCA context");
     if (ctx->ran) return fail(ctx, TTCF_E_STATE, "ttcf_spawn_daughters after ttcf_run");
-    int maps[4], M = 0;
-    for (int m = 0; m < 4; m++) if (ctx->cfg.mapping_mask & (1u << m)) maps[M++] = m;
+    int maps[MAX_MAPS], M = 0;
+    for (int m = 0; m < MAX_MAPS; m++) if (ctx->cfg.mapping_mask & (1u << m)) maps[M++] = m;
     const int S = ctx->cfg.n_steps / ctx->cfg.sample_every + 1;
     BatchHost b;
     Pool pool(ctx);
@@ -1520,6 +1548,22 @@ ttcf_status ttcf_sample_mothers_confined(ttcf_ctx *ctx, int n_atoms, const doubl
 }
 
 
+extern "C++" {
+namespace {
+// Slabs adjacent to a wall (0 bottom, 1 top): centres within 1 sigma of its
+// innermost layer, on the fluid side (the outermost fluid layer).
+std::vector<int> adjacent_slabs(const BatchHost &b, int wall) {
+    const double Ly = b.L[1], w = Ly / CONF_NSLAB, hh = b.half_h;
+    std::vector<int> ks;
+    for (int k = 0; k < CONF_NSLAB; k++) {
+        const double c = -0.5 * Ly + (k + 0.5) * w;
+        if (wall == 1 ? (c > hh - 1.0 && c < hh) : (c < -hh + 1.0 && c > -hh)) ks.push_back(k);
+    }
+    return ks;
+}
+}  // namespace
+}  // extern "C++"
+
 ttcf_status ttcf_friction(ttcf_ctx *ctx, int batch_id, int wall, double *t, double *slip_ttcf,
                           double *slip_dav, double *xi_ttcf, double *xi_dav, int capacity,
                           int *n_samples) {
@@ -1534,33 +1578,97 @@ ttcf_status ttcf_friction(ttcf_ctx *ctx, int batch_id, int wall, double *t, doub
     const int S = b->S;
     if (n_samples) *n_samples = S;
     if (capacity < S) return fail(ctx, TTCF_E_INVALID, "capacity smaller than the sample count");
-    // slabs adjacent to the wall: centres within 1 sigma of its innermost layer
-    const double Ly = b->L[1], w = Ly / CONF_NSLAB, hh = b->half_h;
-    std::vector<int> ks;
-    for (int k = 0; k < CONF_NSLAB; k++) {
-        const double c = -0.5 * Ly + (k + 0.5) * w;
-        if (wall == 1 ? (c > hh - 1.0 && c < hh) : (c < -hh + 1.0 && c > -hh)) ks.push_back(k);
-    }
+    const std::vector<int> ks = adjacent_slabs(*b, wall);
     if (ks.empty()) return fail(ctx, TTCF_E_INVALID, "no slab lies next to the wall");
     std::vector<double> h((size_t)b->n_obs * 9 * S);
     CK(cudaMemcpyAsync(h.data(), b->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    if (b->n_inner[wall] <= 0) return fail(ctx, TTCF_E_INVALID, "the wall has no inner layer");
     auto col = [&](int o, int q, int s) { return h[((size_t)o * 9 + q) * S + s]; };   // q: 2 dav, 4 ttcf
-    const double vw = (wall == 1 ? 1.0 : -1.0) * g * hh;
     const double ds = ctx->cfg.sample_every * ctx->cfg.dt;
+    const int o_wall = 2 + 2 * CONF_NSLAB + wall;   // sum of p_x over the inner wall layer
     for (int s = 0; s < S; s++) {
-        double P[2] = {0.0, 0.0}, n[2] = {0.0, 0.0};
+        double sl[2], sg[2];
         for (int e = 0; e < 2; e++) {
             const int q = e == 0 ? 4 : 2;
-            for (int k : ks) { P[e] += col(2 + k, q, s); n[e] += col(2 + CONF_NSLAB + k, q, s); }
+            double P = 0.0, n = 0.0;
+            for (int k : ks) { P += col(2 + k, q, s); n += col(2 + CONF_NSLAB + k, q, s); }
+            sl[e] = col(o_wall, q, s) / b->n_inner[wall] - P / n;
+            sg[e] = col(wall, q, s);
         }
-        const double sl_t = P[0] / n[0] - vw, sl_d = P[1] / n[1] - vw;
         if (t) t[s] = s * ds;
-        if (slip_ttcf) slip_ttcf[s] = sl_t;
-        if (slip_dav) slip_dav[s] = sl_d;
-        if (xi_ttcf) xi_ttcf[s] = col(wall, 4, s) / sl_t;
-        if (xi_dav) xi_dav[s] = col(wall, 2, s) / sl_d;
+        if (slip_ttcf) slip_ttcf[s] = sl[0];
+        if (slip_dav) slip_dav[s] = sl[1];
+        if (xi_ttcf) xi_ttcf[s] = -sg[0] / sl[0];
+        if (xi_dav) xi_dav[s] = -sg[1] / sl[1];
     }
+    return TTCF_OK;
+}
+
+ttcf_status ttcf_friction_equilibrium(ttcf_ctx *ctx, int batch_id, int wall, int max_lag, int n_s,
+                                      const double *s_grid, double out[4], double *c_dvf,
+                                      double *c_dvdv, double *zeta_s) {
+    BatchHost *b = get_batch(ctx, batch_id);
+    if (!b) return fail(ctx, TTCF_E_INVALID, "bad batch id");
+    if (!b->confined) return fail(ctx, TTCF_E_INVALID, "friction needs a confined batch");
+    if (wall != 0 && wall != 1) return fail(ctx, TTCF_E_INVALID, "wall must be 0 or 1");
+    for (double x : b->gamma)
+        if (x != 0.0) return fail(ctx, TTCF_E_INVALID, "the equilibrium method needs a zero-shear batch");
+    if (!b->reduced) return fail(ctx, TTCF_E_STATE, "run not finished");
+    const int S = b->S;
+    if (max_lag < 1 || max_lag > S - 2) return fail(ctx, TTCF_E_INVALID, "max_lag must be in [1, samples - 2]");
+    if (n_s < 2 || !s_grid || !out) return fail(ctx, TTCF_E_INVALID, "need >= 2 Laplace variables and out");
+    for (int j = 0; j < n_s; j++)
+        if (!(s_grid[j] >= 0.0) || !isfinite(s_grid[j])) return fail(ctx, TTCF_E_INVALID, "bad Laplace variable");
+    if (b->n_inner[wall] <= 0) return fail(ctx, TTCF_E_INVALID, "the wall has no inner layer");
+    const std::vector<int> ks = adjacent_slabs(*b, wall);
+    if (ks.empty() || ks.size() > (size_t)SLIP_MAX_SLABS)
+        return fail(ctx, TTCF_E_INVALID, "no (or too many) slabs next to the wall");
+    Pool pool(ctx);
+    const long long D = b->D();
+    double *dv = pool.get<double>((size_t)D * S), *F = pool.get<double>((size_t)D * S);
+    double *cf = pool.get<double>((size_t)max_lag + 1), *cv = pool.get<double>((size_t)max_lag + 1);
+    if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (friction)");
+    SlipArgs a;
+    memset(&a, 0, sizeof(a));
+    a.B = b->B; a.status = b->status;
+    a.D = (int)D; a.n_obs = b->n_obs; a.S = S; a.nslab = CONF_NSLAB; a.wall = wall;
+    a.n_slabs = (int)ks.size();
+    for (size_t j = 0; j < ks.size(); j++) a.slabs[j] = ks[j];
+    a.n_layer = (double)b->n_inner[wall];
+    a.area = b->A;
+    a.dv = dv; a.F = F;
+    CK(launch_slip_correlations(a, max_lag, cf, cv, ctx->st));
+    std::vector<double> hf((size_t)max_lag + 1), hv((size_t)max_lag + 1);
+    CK(cudaMemcpyAsync(hf.data(), cf, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hv.data(), cv, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (c_dvf) memcpy(c_dvf, hf.data(), sizeof(double) * hf.size());
+    if (c_dvdv) memcpy(c_dvdv, hv.data(), sizeof(double) * hv.size());
+    // Laplace transforms on the lag grid (trapezoid), zeta~(s) = C~_dvF / C~_dvdv,
+    // and the least-squares line 1/zeta~(s) = i + m s of the Maxwell kernel
+    const double ds = ctx->cfg.sample_every * ctx->cfg.dt;
+    auto lap = [&](const std::vector<double> &c, double sv) {
+        double acc = 0.0;
+        for (int k = 0; k <= max_lag; k++) acc += exp(-sv * k * ds) * c[k];
+        const double f0 = c[0], fl = exp(-sv * max_lag * ds) * c[max_lag];
+        return ds * (acc - 0.5 * (f0 + fl));
+    };
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (int j = 0; j < n_s; j++) {
+        const double z = lap(hf, s_grid[j]) / lap(hv, s_grid[j]);
+        if (zeta_s) zeta_s[j] = z;
+        const double x = s_grid[j], y = 1.0 / z;
+        sx += x; sy += y; sxx += x * x; sxy += x * y;
+    }
+    const double den = n_s * sxx - sx * sx;
+    if (!(den != 0.0)) return fail(ctx, TTCF_E_INVALID, "the Laplace variables must differ");
+    const double slope = (n_s * sxy - sx * sy) / den, icpt = (sy - slope * sx) / n_s;
+    const double z0 = 1.0 / icpt;
+    out[0] = z0 / b->A;                               // xi_0
+    out[1] = z0;                                      // zeta_0
+    out[2] = slope / icpt;                            // tau_M
+    out[3] = lap(hf, 0.0) / lap(hv, 0.0) / b->A;      // ratio of the integrals / A
     return TTCF_OK;
 }
 
@@ -1569,7 +1677,7 @@ extern "C++" {
 namespace {
 
 constexpr char CKPT_MAGIC[8] = {'T', 'T', 'C', 'F', 'C', 'K', 'P', '1'};
-constexpr int CKPT_VERSION = 2;   // 2: MIXED per-daughter scalars as float pairs
+constexpr int CKPT_VERSION = 3;   // 2: MIXED per-daughter scalars as float pairs; 3: 32 mapping codes, inner wall layers
 
 struct FileW {
     FILE *f;
@@ -1654,6 +1762,7 @@ ttcf_status ttcf_save(ttcf_ctx *ctx, const char *path) {
         w.bytes(b.gamma.data(), sizeof(double) * b.G);
         w.put(b.A); w.put(b.rc); w.put(b.k_tether); w.put(b.c_ff); w.put(b.c_wf); w.put(b.c_ww);
         w.put(b.ww_on); w.put(b.half_h);
+        w.bytes(b.inner_y, sizeof(b.inner_y)); w.bytes(b.n_inner, sizeof(b.n_inner));
         const size_t D = (size_t)b.D();
         if ((st = save_dev(ctx, w, b.mothers, sizeof(unsigned long long) * b.G * 6 * b.N)) != TTCF_OK) break;
         if ((st = save_dev(ctx, w, b.m_alpha, sizeof(double) * b.G)) != TTCF_OK) break;
@@ -1710,7 +1819,7 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path) {
         b.confined = conf != 0;
         // the kernels index shared arrays with these numbers: check that they
         // are the ones the spawn calls would have chosen
-        bool okh = r.ok && b.M >= 1 && b.M <= 4 && b.G >= 1 && b.S == c.n_steps / c.sample_every + 1 &&
+        bool okh = r.ok && b.M >= 1 && b.M <= MAX_MAPS && b.G >= 1 && b.S == c.n_steps / c.sample_every + 1 &&
                    b.d0 >= 0 && b.skin > 0 && b.skin <= 1.0 &&
                    b.n_obs == (b.confined ? CONF_NOBS : 1) && b.confined == (c.system == TTCF_CONFINED_LJ) &&
                    b.N >= 4 && b.N <= (b.confined ? CONF_NMAX : 4096);
@@ -1718,7 +1827,8 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path) {
             okh = isfinite(b.L[k]) && b.L[k] > 0 && b.nc[k] >= (b.confined ? 1 : 3) && b.nc[k] <= 4096 &&
                   b.snc[k] >= 1 && b.snc[k] <= 4096;
         okh = okh && b.ncell == b.nc[0] * b.nc[1] * b.nc[2] && b.sncell == b.snc[0] * b.snc[1] * b.snc[2];
-        for (int k = 0; k < b.M && okh; k++) okh = b.maps[k] >= 0 && b.maps[k] <= 3;
+        for (int k = 0; k < b.M && okh; k++)
+            okh = b.maps[k] >= 0 && b.maps[k] < (b.confined ? 4 : MAX_MAPS);
         if (okh && !b.confined) {
             okh = b.variant >= 0 && b.variant < N_VARIANTS;
             if (okh) {
@@ -1731,7 +1841,10 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path) {
         r.bytes(b.gamma.data(), sizeof(double) * b.G);
         r.get(b.A); r.get(b.rc); r.get(b.k_tether); r.get(b.c_ff); r.get(b.c_wf); r.get(b.c_ww);
         r.get(b.ww_on); r.get(b.half_h);
+        r.bytes(b.inner_y, sizeof(b.inner_y)); r.bytes(b.n_inner, sizeof(b.n_inner));
         if (!r.ok) return bad(TTCF_E_INVALID, "checkpoint truncated");
+        if (b.n_inner[0] < 0 || b.n_inner[1] < 0 || b.n_inner[0] + b.n_inner[1] > b.N)
+            return bad(TTCF_E_INVALID, "checkpoint batch header out of range");
         const size_t D = (size_t)b.D();
         ttcf_status s;
         if ((s = load_dev(ctx, r, pool, b.mothers, sizeof(unsigned long long) * b.G * 6 * b.N, false)) ||
@@ -1792,6 +1905,8 @@ bool batch_finished(ttcf_ctx *ctx, BatchHost *b) { return b && b->reduced; }
 // Features X [D][32] (device, unstandardised) and targets z [D] (device).
 ttcf_status cv_batch_data(ttcf_ctx *ctx, Pool &pool, BatchHost &b, float *&X, double *&z) {
     if (b.confined || !b.feat) return fail(ctx, TTCF_E_INVALID, "the control variate needs a bulk batch");
+    for (int k = 0; k < b.M; k++)
+        if (b.maps[k] > 3) return fail(ctx, TTCF_E_INVALID, "the control variate takes the mappings 0..3 of Eq. 3 only");
     const long long D = b.D();
     X = pool.get<float>((size_t)D * CV_NF);
     z = pool.get<double>((size_t)D);
@@ -1986,6 +2101,8 @@ ttcf_status ttcf_cv_apply(ttcf_ctx *ctx, int batch_id, int n_aux, const double *
     if (!ctx->cv.trained) return fail(ctx, TTCF_E_STATE, "control variate not trained");
     if (!batch_finished(ctx, b)) return fail(ctx, TTCF_E_STATE, "run not finished");
     if (b->N != ctx->cv.N) return fail(ctx, TTCF_E_INVALID, "evaluation batch N differs from training");
+    for (int k = 0; k < b->M; k++)
+        if (b->maps[k] > 3) return fail(ctx, TTCF_E_INVALID, "the control variate takes the mappings 0..3 of Eq. 3 only");
     if (n_aux < 2 || !aux_soa) return fail(ctx, TTCF_E_INVALID, "need >= 2 auxiliary mother states");
     for (double g : b->gamma)
         if (g == 0.0) return fail(ctx, TTCF_E_INVALID, "evaluation needs a nonzero shear rate");

@@ -15,7 +15,11 @@
 // IEEE double.  Each sample of a daughter records
 //   B[0], B[1]   x force of the fluid on the bottom / top wall per area
 //   B[2 + k]     sum of fluid p_x in slab k of 40 spanning y
-//   B[42 + k]    number of fluid atoms in slab k.
+//   B[42 + k]    number of fluid atoms in slab k
+//   B[82], B[83] sum of p_x over the innermost layer of the bottom / top
+//                wall (the wall's atoms whose tether site lies within 0.1
+//                sigma in y of its site plane nearest the channel): the wall
+//                velocity of the paper's slip velocity.
 //
 // One CTA of 1024 threads runs one daughter: the hi parts of the positions
 // and the atom type sit in shared memory (float4); lo parts, momenta, forces,
@@ -62,6 +66,7 @@ struct ConfMisc {
     int flag_fast, flag_ovf, flag_lost;
     unsigned long long slab_px[CONF_NSLAB];   // fixed point, units of 2^-40
     int slab_n[CONF_NSLAB];
+    unsigned long long wall_px[2];            // inner wall layers, fixed point
 };
 
 // Shared-memory carve-up of a daughter CTA; every region starts on a
@@ -175,9 +180,11 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
         pos4[nmax] = make_float4(0.f, 1.0e4f, 0.f, 0.f);
     }
     for (int k = tid; k < CONF_NSLAB; k += T) { m->slab_px[k] = 0ull; m->slab_n[k] = 0; }
+    if (tid < 2) m->wall_px[tid] = 0ull;
     __syncthreads();
 
     // ---- the mapped mother (Eq. 3 sign rules) and the tether sites ----
+    // (lath.w marks the atoms of the innermost wall layers)
     {
         const bool flipx = map == 2 || map == 3;
         const bool flippx = map == 1 || map == 2;
@@ -202,7 +209,10 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             plo[i] = make_float4(x.lo, y.lo, z.lo, __int_as_float(i));
             phi[i] = make_float4(px.hi, py.hi, pz.hi, 0.f);
             pml[i] = make_float4(px.lo, py.lo, pz.lo, 0.f);
-            lath[i] = make_float4(xl.hi, yl.hi, zl.hi, 0.f);
+            const int ty = b.types[i];
+            const double ys = b.lattice[(size_t)N + i];
+            const bool inner = (ty == 1 && ys >= b.inner_y[0]) || (ty == 2 && ys <= b.inner_y[1]);
+            lath[i] = make_float4(xl.hi, yl.hi, zl.hi, inner ? 1.f : 0.f);
             latl[i] = make_float4(xl.lo, yl.lo, zl.lo, 0.f);
         }
     }
@@ -567,6 +577,10 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
             pml[i] = make_float4(px.lo, py.lo, pz.lo, 0.f);
             if ((int)u.w != 0) {
                 k2 += px.hi * px.hi + py.hi * py.hi + pz.hi * pz.hi;
+                if (sample && lath[i].w != 0.f) {
+                    const long long q = __float2ll_rn(px.hi * FIX_SCALE) + __float2ll_rn(px.lo * FIX_SCALE);
+                    atomicAdd(&m->wall_px[(int)u.w - 1], (unsigned long long)q);
+                }
             } else if (sample) {
                 const int k = slab_of((double)u.y + (double)plo[i].y, Ly);
                 const long long q = __float2ll_rn(px.hi * FIX_SCALE) + __float2ll_rn(px.lo * FIX_SCALE);
@@ -593,6 +607,13 @@ __device__ void conf_daughter(const ConfRunArgs &a, int d, unsigned char *smem) 
                     Bo[(size_t)(2 + CONF_NSLAB + k) * b.S + si] = (double)m->slab_n[k];
                     m->slab_px[k] = 0ull;
                     m->slab_n[k] = 0;
+                }
+                // wall momenta still owe this step's closing thermostat
+                // factor 1 + e1 (applied in the next step's phase A)
+                for (int w = 0; w < 2; w++) {
+                    Bo[(size_t)(2 + 2 * CONF_NSLAB + w) * b.S + si] =
+                        (double)(long long)m->wall_px[w] * FIX_INV * (1.0 + m->e1);
+                    m->wall_px[w] = 0ull;
                 }
             }
             if (a.abort_flag && (s & 63) == 0 && *a.abort_flag) cf->stop |= TTCF_D_ABORTED;
@@ -656,13 +677,13 @@ __global__ void __launch_bounds__(CONF_THREADS, 1) conf_kernel(ConfRunArgs a) {
 // fluid p_x and counts (exact fixed point); then B(0) and Omega(0) of each
 // mapped daughter by the sign rules of the mappings, and the mother as
 // float-pair slots.
-__global__ void conf_spawn_kernel(ConfSpawnArgs a) {
+__global__ void __launch_bounds__(512) conf_spawn_kernel(ConfSpawnArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x, N = a.N;
     const double *src = a.src + (size_t)g * 6 * N;
     unsigned char *sp = smem;
     double *red = reinterpret_cast<double *>(sp); sp += 32 * 4 * sizeof(double);
-    unsigned long long *spx = reinterpret_cast<unsigned long long *>(sp); sp += CONF_NSLAB * 8;
+    unsigned long long *spx = reinterpret_cast<unsigned long long *>(sp); sp += (CONF_NSLAB + 2) * 8;
     int *sn = reinterpret_cast<int *>(sp); sp += CONF_NSLAB * 4;
     int *warp_tmp = reinterpret_cast<int *>(sp); sp += 32 * 4;
     int *cnt = reinterpret_cast<int *>(sp); sp += (size_t)a.ncell * 4;
@@ -694,6 +715,7 @@ __global__ void conf_spawn_kernel(ConfSpawnArgs a) {
     };
     for (int c = tid; c < a.ncell; c += T) cnt[c] = 0;
     for (int k = tid; k < CONF_NSLAB; k += T) { spx[k] = 0ull; sn[k] = 0; }
+    if (tid < 2) spx[CONF_NSLAB + tid] = 0ull;   // inner wall layers
     __syncthreads();
     for (int i = tid; i < N; i += T) atomicAdd(&cnt[cellid(i)], 1);
     __syncthreads();
@@ -725,6 +747,12 @@ __global__ void conf_spawn_kernel(ConfSpawnArgs a) {
             continue;
         }
         const double xi = src[i], yi = src[(size_t)N + i], zi = src[2 * (size_t)N + i];
+        {
+            const double ys = a.lattice[(size_t)N + i];
+            if ((ti == 1 && ys >= a.inner_y[0]) || (ti == 2 && ys <= a.inner_y[1]))
+                atomicAdd(&spx[CONF_NSLAB + ti - 1],
+                          (unsigned long long)llrint(src[3 * (size_t)N + i] * 1099511627776.0));
+        }
         double tx = xi - a.lattice[i];
         tx -= a.L[0] * rint(tx * iLx);
         acc[0] -= a.k * tx * (ti == 2 ? 1.0 : -1.0);
@@ -785,6 +813,15 @@ __global__ void conf_spawn_kernel(ConfSpawnArgs a) {
             }
         }
     }
+    // the inner wall layers' p_x sums, one thread per mapped daughter
+    // (p_x odd under mappings 1 and 2)
+    if (tid < a.M) {
+        const int mm = a.maps[tid];
+        const double sp_ = (mm == 1 || mm == 2) ? -1.0 : 1.0;
+        double *Bo = a.B + ((size_t)g * a.M + tid) * a.n_obs * a.S;
+        for (int w = 0; w < 2; w++)
+            Bo[(size_t)(2 + 2 * CONF_NSLAB + w) * a.S] = sp_ * ((double)(long long)spx[CONF_NSLAB + w] * FIX_INV);
+    }
 }
 
 }  // namespace
@@ -792,7 +829,7 @@ __global__ void conf_spawn_kernel(ConfSpawnArgs a) {
 size_t conf_smem_bytes(int nmax, int ncellmax) { return conf_layout(nmax, ncellmax).total; }
 
 size_t conf_spawn_smem_bytes(int N, int ncell) {
-    return 32 * 4 * sizeof(double) + CONF_NSLAB * 12 + 32 * 4 + (size_t)ncell * 4 + (size_t)(ncell + 2) * 4 +
+    return 32 * 4 * sizeof(double) + CONF_NSLAB * 12 + 16 + 32 * 4 + (size_t)ncell * 4 + (size_t)(ncell + 2) * 4 +
            (size_t)N * 2 + 16;
 }
 

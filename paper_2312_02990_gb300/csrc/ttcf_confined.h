@@ -10,7 +10,8 @@
 namespace ttcf {
 
 constexpr int CONF_NSLAB = 40;                     // slabs of the velocity profile
-constexpr int CONF_NOBS = 2 + 2 * CONF_NSLAB;      // responses per sample
+constexpr int CONF_NOBS = 2 + 2 * CONF_NSLAB + 2;  // responses per sample (see ttcf_confined.cu)
+constexpr double CONF_LAYER_TOL = 0.1;             // inner wall layer: sites within this of the plane
 constexpr int CONF_CAP = 128;                      // Verlet neighbours per atom
 constexpr int CONF_GROUPS = CONF_CAP / 8;          // 16-byte groups of 8 uint16 entries
 constexpr int CONF_THREADS = 1024;                 // one CTA per daughter
@@ -30,6 +31,8 @@ struct ConfBatchDev {
     int ww_on;                 // wall-wall pairs interact (c_ww)
     int pad2_;
     double half_h;             // v_wall = gamma * half_h
+    double inner_y[2];         // inner wall layers: bottom sites y >= inner_y[0],
+                               // top sites y <= inner_y[1]
     float skin;
     int pad_;
     long long d0;
@@ -72,6 +75,7 @@ struct ConfSpawnArgs {
     int maps[4];
     int nc[3], ncell;          // cells of width >= r_c
     double L[3], A, Tw, rc, k, c_wf, half_h;
+    double inner_y[2];         // as in ConfBatchDev
     const double *src;         // [G][6][N]
     const double *gamma;       // [G]
     const int *types;          // [N]

@@ -18,7 +18,7 @@ from . import build as _build
 TTCF_OK, TTCF_E_INVALID, TTCF_E_CUDA, TTCF_E_OOM, TTCF_E_NUMERIC, TTCF_E_TIMEOUT, TTCF_E_STATE = range(7)
 TTCF_BULK_WCA, TTCF_CONFINED_LJ = 0, 1
 CONF_NSLAB = 40
-CONF_NOBS = 2 + 2 * CONF_NSLAB
+CONF_NOBS = 2 + 2 * CONF_NSLAB + 2   # + the inner wall layers' p_x sums
 TTCF_FP64, TTCF_MIXED = 0, 1
 D_OK, D_NONFINITE, D_NBR_OVERFLOW, D_FAST_ATOM, D_ABORTED, D_ESCAPED = 0, 1, 2, 4, 8, 16
 
@@ -34,7 +34,7 @@ EXPORTS = ("ttcf_config_default", "ttcf_create", "ttcf_spawn_daughters", "ttcf_r
            "ttcf_run_noalloc", "ttcf_cv_config_default", "ttcf_cv_data", "ttcf_cv_train",
            "ttcf_cv_apply", "ttcf_cv_get_model", "ttcf_cv_forward", "ttcf_cv_gradient",
            "ttcf_confined_params_default", "ttcf_spawn_confined", "ttcf_sample_mothers_confined",
-           "ttcf_response_obs", "ttcf_friction", "ttcf_save", "ttcf_load", "ttcf_destroy",
+           "ttcf_response_obs", "ttcf_friction", "ttcf_friction_equilibrium", "ttcf_save", "ttcf_load", "ttcf_destroy",
            "ttcf_last_error",
            "ttcf_version")
 
@@ -105,6 +105,8 @@ def load(build_if_missing: bool = False):
     L.ttcf_response.argtypes = [vp, C.c_int, C.c_int] + [_dp] * 7 + [C.c_int, ip]
     L.ttcf_viscosity.argtypes = [vp, C.c_int] + [_dp] * 5 + [C.c_int, ip]
     L.ttcf_omega_mean.argtypes = [vp, C.c_int, _dp, _dp]
+    L.ttcf_friction_equilibrium.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp,
+                                            _dp, _dp]
     L.ttcf_daughter_series.argtypes = [vp, C.c_int, _dp, _dp, C.c_size_t]
     L.ttcf_group_status.argtypes = [vp, C.c_int, ip, C.c_int]
     L.ttcf_get_state.argtypes = [vp, C.c_int, C.c_int, _dp, _dp, _dp]
@@ -262,7 +264,7 @@ class Context:
 
     @property
     def n_maps(self) -> int:
-        return bin(self.cfg.mapping_mask & 0xF).count("1")
+        return bin(self.cfg.mapping_mask & 0xFFFFFFFF).count("1")
 
     # -- C ABI --
     def spawn_daughters(self, mother_soa, mother_alpha=None, shear_rates=0.0, box=None) -> int:
@@ -352,6 +354,18 @@ class Context:
                                           _ptr(arr["slip_ttcf"]), _ptr(arr["slip_dav"]),
                                           _ptr(arr["xi_ttcf"]), _ptr(arr["xi_dav"]), S, C.byref(n)))
         return arr
+
+    def friction_equilibrium(self, batch: int, wall: int, max_lag: int, s_grid) -> dict:
+        """Equilibrium friction coefficient xi_0 (Eq. 12) of a zero-shear
+        confined batch (see ttcf_friction_equilibrium)."""
+        s = _f64(s_grid).reshape(-1)
+        out = np.zeros(4)
+        cf, cv = np.zeros(max_lag + 1), np.zeros(max_lag + 1)
+        z = np.zeros(s.size)
+        self._check(self._L.ttcf_friction_equilibrium(self.h, batch, int(wall), int(max_lag), int(s.size),
+                                                      _ptr(s), _ptr(out), _ptr(cf), _ptr(cv), _ptr(z)))
+        return {"xi0": out[0], "zeta0": out[1], "tau_m": out[2], "xi_ratio": out[3],
+                "c_dvf": cf, "c_dvdv": cv, "zeta_s": z, "s": s}
 
     def save(self, path: str):
         self._check(self._L.ttcf_save(self.h, os.fsencode(path)))

@@ -43,8 +43,9 @@ def daughter_case():
 
 
 def confined_case():
-    """Small channel, 10 steps at gamma = 0.05: wall stresses and slab
-    totals of the four mapped daughters (Eq. 9, 10, 11)."""
+    """Small channel, 10 steps at gamma = 0.05: wall stresses, slab totals
+    and the inner wall layers' p_x sums of the four mapped daughters (Eq. 9,
+    10, 11)."""
     s = inputs.confined_system(nx=10, nz=10, layers=2, seed=11)
     sy = oc.Confined(types=s["types"], box=tuple(s["box"]), vwall=0.05 * 5.0)
     B, Om = oc.daughters(sy, s["state"][None], s["lattice"], np.zeros(1), 10, 5)
@@ -52,7 +53,8 @@ def confined_case():
     return {"cite": "Eq. 9 potential, Eq. 10 dynamics, Eq. 11 Omega; v = gamma h / 2", "seed": 11,
             "Omega": Om.tolist(), "wall_stress": B[:, :, :2].tolist(),
             "slab_px_total": B[:, :, 2:2 + ns].sum(axis=2).tolist(),
-            "slab_n": B[:, :, 2 + ns:].tolist()}
+            "slab_n": B[:, :, 2 + ns:2 + 2 * ns].tolist(),
+            "wall_layer_px": B[:, :, 2 + 2 * ns:].tolist()}
 
 
 def cv_case():

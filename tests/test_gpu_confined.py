@@ -30,7 +30,7 @@ from paper_2312_02990_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-NOBS = 2 + 2 * oc.N_SLAB
+NOBS = oc.N_OBS       # 2 wall stresses, 40 slab momenta, 40 slab counts, 2 inner wall layers
 H = 10.0     # channel width: v = gamma h / 2
 
 
@@ -67,7 +67,7 @@ def cctx(T, **kw):
 def assert_profiles_close(Bg, Bo, n_fluid, max_moves=6):
     """Bg, Bo [NOBS, S] of one daughter (device, oracle)."""
     ns = oc.N_SLAB
-    cg, co = Bg[2 + ns:], Bo[2 + ns:]
+    cg, co = Bg[2 + ns:2 + 2 * ns], Bo[2 + ns:2 + 2 * ns]
     assert np.all(cg.sum(axis=0) == n_fluid) and np.all(co.sum(axis=0) == n_fluid)
     dc = cg - co
     assert np.abs(dc).sum() <= 2 * max_moves, np.argwhere(dc != 0)
@@ -76,6 +76,8 @@ def assert_profiles_close(Bg, Bo, n_fluid, max_moves=6):
     assert dp[same].max() < 5e-4, dp[same].max()
     # the total fluid momentum does not depend on the slab assignment
     assert np.abs(Bg[2:2 + ns].sum(axis=0) - Bo[2:2 + ns].sum(axis=0)).max() < 5e-3
+    # the p_x sums of the innermost wall layers
+    assert np.abs(Bg[2 + 2 * ns:] - Bo[2 + 2 * ns:]).max() < 1e-3
 
 
 def oracle_daughters(sy, ms, lat, al, gamma, n_steps, sample_every=1):
@@ -101,12 +103,14 @@ def test_spawn_matches_oracle_and_cancels_exactly(ttcf, chan):
             assert Om[d] == pytest.approx(omo, rel=1e-10, abs=1e-12 * abs(omo) + 1e-300)
             assert Bg[d, :2, 0] == pytest.approx(Bo[0, :2], rel=1e-10, abs=1e-12)
             assert np.abs(Bg[d, 2:2 + oc.N_SLAB, 0] - Bo[0, 2:2 + oc.N_SLAB]).max() < 1e-9
-            assert np.array_equal(Bg[d, 2 + oc.N_SLAB:, 0], Bo[0, 2 + oc.N_SLAB:])
+            assert np.array_equal(Bg[d, 2 + oc.N_SLAB:2 + 2 * oc.N_SLAB, 0], Bo[0, 2 + oc.N_SLAB:2 + 2 * oc.N_SLAB])
+            assert np.abs(Bg[d, 2 + 2 * oc.N_SLAB:, 0] - Bo[0, 2 + 2 * oc.N_SLAB:]).max() < 1e-9
         # Eq. 3: the four mappings cancel Omega(0), the wall forces and the
         # slab momenta exactly within each group
         grp = slice(4 * g, 4 * g + 4)
         assert Om[grp].sum() == 0.0
         assert np.all(Bg[grp, :2 + oc.N_SLAB, 0].sum(axis=0) == 0.0)
+        assert np.all(Bg[grp, 2 + 2 * oc.N_SLAB:, 0].sum(axis=0) == 0.0)
 
 
 # -------------------------------------------------------- trajectories ---
@@ -266,8 +270,9 @@ def test_ensemble_responses_match_oracle(ttcf, chan):
 
 
 def test_friction_matches_the_oracle_formula(ttcf, chan):
-    """Eq. 12 from the device responses: slip velocity and friction at both
-    walls against oracle/reduce.friction on the same responses."""
+    """Eq. 12 from the device responses: slip velocity (innermost wall layer
+    minus outermost fluid layer) and friction at both walls against
+    oracle/reduce.friction on the same responses."""
     s, sy, ms, al = chan
     g = 0.05
     with cctx(ttcf, n_steps=100, sample_every=5) as c:
@@ -279,12 +284,14 @@ def test_friction_matches_the_oracle_formula(ttcf, chan):
             c.friction(bid, 2)
     for w in (0, 1):
         for est, key in (("ttcf", "ttcf"), ("dav", "dav")):
-            ref = orr.friction(resp, g, sy.box[1], H, w, estimator=key)
+            n_layer = len(oc.inner_layer(s["types"], s["lattice"], w))
+            assert n_layer == 100   # one FCC(111) layer of the 10 x 10 rows
+            ref = orr.friction(resp, sy.box[1], H, w, n_layer, estimator=key)
             assert np.allclose(got[w]["slip_" + est], ref["slip"], rtol=1e-12, atol=1e-15)
             ok = np.isfinite(ref["xi"])
             assert np.allclose(got[w]["xi_" + est][ok], ref["xi"][ok], rtol=1e-10)
-        # the fluid starts at rest: the slip is minus the wall velocity
-        assert got[w]["slip_dav"][0] == pytest.approx(-(1 if w else -1) * g * H / 2, rel=1e-9, abs=1e-12)
+        # at t = 0 the four mappings cancel every p_x sum: no slip
+        assert got[w]["slip_dav"][0] == 0.0
 
 
 # ------------------------------------------------------------- errors ----
@@ -319,3 +326,39 @@ def test_invalid_inputs_are_rejected(ttcf, chan):
             c.viscosity(bid)
         with pytest.raises(T.TTCFError):
             c.response_obs(bid, NOBS)
+
+
+def test_equilibrium_friction_matches_the_oracle(ttcf, chan):
+    """The equilibrium friction coefficient xi_0 (Eq. 12 by the equilibrium
+    method): zero-shear daughters of the oracle mothers with one mapping are
+    equilibrium trajectories; the device's slip/force correlations and the
+    Maxwell fit equal the oracle's estimator applied to the same device
+    series.  A sheared batch is refused."""
+    T = ttcf
+    s, sy, ms, al = chan
+    n, se, lag = 400, 2, 60
+    svals = np.linspace(0.2, 4.0, 12)
+    with cctx(T, n_steps=n, sample_every=se, mapping_mask=1) as c:
+        bid = c.spawn_confined(ms, s["types"], s["lattice"], sy.box, al, 0.0)
+        c.run()
+        Bg, _ = c.daughter_series(bid, ms.shape[0], NOBS)
+        got = [c.friction_equilibrium(bid, w, lag, svals) for w in (0, 1)]
+    ds = se * 0.005
+    area = sy.box[0] * sy.box[2]
+    for w in (0, 1):
+        n_layer = len(oc.inner_layer(s["types"], s["lattice"], w))
+        slabs = orr.adjacent_slabs(sy.box[1], H, w)
+        ref = orr.friction_equilibrium(Bg, area, n_layer, slabs, w, ds, lag, svals)
+        assert np.allclose(got[w]["c_dvf"], ref["c_dvf"], rtol=1e-9, atol=1e-12 * np.abs(ref["c_dvf"]).max())
+        assert np.allclose(got[w]["c_dvdv"], ref["c_dvdv"], rtol=1e-9, atol=1e-12 * np.abs(ref["c_dvdv"]).max())
+        assert np.allclose(got[w]["zeta_s"], ref["zeta_s"], rtol=1e-7)
+        for k in ("xi0", "zeta0", "tau_m", "xi_ratio"):
+            assert got[w][k] == pytest.approx(ref[k], rel=1e-6), k
+        # velocity and force uncorrelated at equal times (time reversal), to noise
+        assert abs(got[w]["c_dvf"][0]) < 0.2 * np.abs(got[w]["c_dvf"]).max()
+    with cctx(T, n_steps=20, mapping_mask=1) as c:
+        bid = c.spawn_confined(ms[:1], s["types"], s["lattice"], sy.box, al[:1], 0.05)
+        c.run()
+        with pytest.raises(T.TTCFError) as e:
+            c.friction_equilibrium(bid, 0, 5, svals)
+        assert e.value.status == T.TTCF_E_INVALID

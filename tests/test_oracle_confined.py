@@ -115,8 +115,9 @@ def test_mappings_cancel_omega_and_odd_responses(small):
         ns = sys2.nslab
         assert np.abs(B0[:, :2].sum(axis=0)).max() <= 1e-10 * np.abs(B0[:, :2]).max()   # wall stress
         assert np.abs(B0[:, 2:2 + ns].sum(axis=0)).max() < 1e-10                          # slab momenta
-        assert np.all(B0[:, 2 + ns:] == B0[0, 2 + ns:])                                    # slab counts
-        assert B0[0, 2 + ns:].sum() == np.sum(sy.types == 0)
+        assert np.all(B0[:, 2 + ns:2 + 2 * ns] == B0[0, 2 + ns:2 + 2 * ns])                # slab counts
+        assert np.abs(B0[:, 2 + 2 * ns:].sum(axis=0)).max() < 1e-10                        # wall layers
+        assert B0[0, 2 + ns:2 + 2 * ns].sum() == np.sum(sy.types == 0)
 
 
 def test_time_reversal_with_walls_at_rest(small):
@@ -155,24 +156,56 @@ def test_omega_is_beta_times_the_adiabatic_energy_rate(small):
 
 
 def test_friction_of_constructed_responses():
-    """Eq. 12 on responses built so that the slab velocity, slip and wall
-    stress are known: xi = sigma / (v - s_w gamma h / 2)."""
+    """Eq. 12 on responses built so that the wall-layer and fluid velocities
+    and the wall stress are known: slip = v_wall - v_fluid (the paper's slip
+    velocity: innermost wall layer minus outermost fluid layer) and
+    xi = -sigma / slip."""
     from oracle import reduce as orr
-    Ly, h, g, ns = 15.95, 10.0, 0.02, oc.N_SLAB
+    Ly, h, g, ns, n_layer = 15.95, 10.0, 0.02, oc.N_SLAB, 700
     t = np.linspace(0.0, 1.0, 11)
     for wall, sw in ((0, -1.0), (1, 1.0)):
         ks = orr.adjacent_slabs(Ly, h, wall, ns)
         centres = -0.5 * Ly + (ks + 0.5) * Ly / ns
         assert len(ks) >= 2 and np.all(np.abs(np.abs(centres) - 0.5 * h) < 1.0)
         v_fluid = 0.3 * sw * g * t            # fluid lags the wall
-        # the fluid drags the wall backwards: sigma has the sign of the slip
-        sigma = 2.5 * (v_fluid - sw * g * 0.5 * h)
-        resp = {o: {"ttcf": np.zeros_like(t)} for o in range(2 + 2 * ns)}
+        v_wall = sw * g * 0.5 * h * (1.0 + 0.1 * t)
+        # the fluid drags the wall backwards: sigma has the sign of -slip
+        sigma = 2.5 * (v_fluid - v_wall)
+        resp = {o: {"ttcf": np.zeros_like(t)} for o in range(oc.N_OBS)}
         resp[wall]["ttcf"] = sigma
+        resp[2 + 2 * ns + wall]["ttcf"] = n_layer * v_wall
         for j, k in enumerate(ks):
             n_k = 10.0 + j
             resp[2 + ns + k]["ttcf"] = np.full_like(t, n_k)
             resp[2 + k]["ttcf"] = n_k * v_fluid
-        f = orr.friction(resp, g, Ly, h, wall, ns)
-        assert np.allclose(f["slip"], v_fluid - sw * g * 0.5 * h, rtol=1e-14, atol=1e-16)
+        f = orr.friction(resp, Ly, h, wall, n_layer, ns)
+        assert np.allclose(f["slip"], v_wall - v_fluid, rtol=1e-14, atol=1e-16)
         assert np.allclose(f["xi"], 2.5, rtol=1e-13)
+
+
+def test_inner_wall_layer_observable():
+    """The inner-layer responses: the innermost FCC(111) layer of each wall
+    holds one layer's atoms (nx * nz), the response at t = 0 is the sum of
+    their p_x, and a layer tethered to a lattice sliding at +-v moves on
+    average at +-v: over a window of a few tether periods the layer velocity
+    x' = v (1 - cos w t) of an atom starting at rest on its site averages to
+    v (1 - sin(w T)/(w T)), w = sqrt(k), plus thermal noise of the layer
+    mean."""
+    s = inputs.confined_system(nx=10, nz=10, layers=2, seed=11)
+    ns = oc.N_SLAB
+    for w in (0, 1):
+        idx = oc.inner_layer(s["types"], s["lattice"], w)
+        assert len(idx) == 100
+        yl = s["lattice"][1, idx]
+        assert np.all(np.abs(yl - (1 if w else -1) * 0.5 * s["h"]) < 1e-12)
+    v = 0.5
+    sy = oc.Confined(types=s["types"], box=tuple(s["box"]), vwall=v)
+    B, om, _ = oc.daughter(sy, s["state"], s["lattice"], 0.0, 0, 400, 1)
+    for w, sgn in ((0, -1.0), (1, 1.0)):
+        idx = oc.inner_layer(s["types"], s["lattice"], w)
+        assert B[0, 2 + 2 * ns + w] == pytest.approx(s["state"][3, idx].sum(), rel=1e-12, abs=1e-12)
+        vel = B[:, 2 + 2 * ns + w] / len(idx)
+        T = 400 * sy.dt
+        om_t = np.sqrt(sy.k)
+        expect = sgn * v * (1.0 - np.sin(om_t * T) / (om_t * T))
+        assert abs(vel[1:].mean() - expect) < 0.1 * v, (w, vel[1:].mean(), expect)
