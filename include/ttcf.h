@@ -514,8 +514,12 @@ ttcf_status ttcf_friction_equilibrium(ttcf_ctx *ctx, int batch_id, int wall, int
  * states is unbiased for any network and c.  Features (in order): kinetic
  * and configurational pressure tensors P^K_ab, P^C_ab (xx yy zz xy xz yz),
  * U/N, K/N, alpha, P_xy^2, then for q = 1..4 the (cos, sin) modes over 40
- * slabs in y of the density and of the x momentum (each / N).  Weights are
- * FP32 masters used through their BF16 rounding; FP32 accumulation.
+ * slabs in y of the density and of the x momentum (each / N).  The features
+ * of every set of states (training, evaluation, auxiliary) come from one
+ * FP32 kernel over the states themselves (cell list of width >= r_c, FP64
+ * block sums), so the network is the same function on all sides of the
+ * estimator.  Weights are FP32 masters used through their BF16 rounding;
+ * FP32 accumulation.
  * ------------------------------------------------------------------------ */
 typedef struct {
     int epochs;             /* passes over the training daughters            */
@@ -546,7 +550,9 @@ ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg
 /* Control-variate estimate of eta(t_end) for a finished evaluation batch,
  * with n_aux auxiliary mother states [n_aux][6][N] (same N and box; alpha
  * may be NULL), host arrays or device arrays of the context's device (the
- * kind is read from aux_soa; aux_alpha must be of the same kind).  out[8]: eta_plain, se_plain, eta_cv, se_cv, c,
+ * kind is read from aux_soa; aux_alpha must be of the same kind).  The
+ * auxiliary states need their features only: no daughters are spawned for
+ * them.  out[8]: eta_plain, se_plain, eta_cv, se_cv, c,
  * gain = se_plain^2 / se_cv^2, n_groups, n_aux.                             */
 ttcf_status ttcf_cv_apply(ttcf_ctx *ctx, int batch_id, int n_aux, const double *aux_soa,
                           const double *aux_alpha, double out[8]);

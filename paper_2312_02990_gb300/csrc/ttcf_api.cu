@@ -1903,6 +1903,32 @@ double uniform01(uint64_t &x) { return (double)(splitmix64(x) >> 11) * (1.0 / 90
 bool batch_finished(ttcf_ctx *ctx, BatchHost *b) { return b && b->reduced; }
 
 // Features X [D][32] (device, unstandardised) and targets z [D] (device).
+// The network's forward pass (tensor cores) with its bounded waits checked.
+ttcf_status cv_predict(ttcf_ctx *ctx, const __nv_bfloat16 *wb, const float *X, long long n, float *out,
+                       cudaStream_t st) {
+    CK(cv_tc_reset(st));
+    CK(cv_launch_predict(wb, X, n, out, ctx->nsm, st));
+    int failed = 0;
+    CK(cv_tc_failed(st, &failed));
+    if (failed) return fail(ctx, TTCF_E_TIMEOUT, "tensor-core forward pass: a wait on the MMAs timed out");
+    return TTCF_OK;
+}
+
+// Raw features of G states of batch b's system from src ([G][6][N]: IEEE
+// doubles, kind 0, or float-pair slots, kind 1) with the FP32 features kernel.
+cudaError_t cv_raw_features(ttcf_ctx *ctx, const void *src, int kind, const BatchHost &b, int G, double *raw) {
+    CvRawArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.src = src; ra.kind = kind; ra.N = b.N; ra.G = G; ra.raw = raw;
+    for (int k = 0; k < 3; k++) {
+        ra.L[k] = b.L[k];
+        ra.nc[k] = std::max(3, (int)floor(b.L[k] / RC_WCA));
+    }
+    ra.ncell = ra.nc[0] * ra.nc[1] * ra.nc[2];
+    if (cv_raw_smem_bytes(b.N, ra.ncell) > (size_t)ctx->smem_optin) return cudaErrorInvalidValue;
+    return cv_launch_raw_features(ra, ctx->st);
+}
+
 ttcf_status cv_batch_data(ttcf_ctx *ctx, Pool &pool, BatchHost &b, float *&X, double *&z) {
     if (b.confined || !b.feat) return fail(ctx, TTCF_E_INVALID, "the control variate needs a bulk batch");
     for (int k = 0; k < b.M; k++)
@@ -1910,10 +1936,14 @@ ttcf_status cv_batch_data(ttcf_ctx *ctx, Pool &pool, BatchHost &b, float *&X, do
     const long long D = b.D();
     X = pool.get<float>((size_t)D * CV_NF);
     z = pool.get<double>((size_t)D);
+    double *raw = pool.get<double>((size_t)b.G * FEAT_RAW);
     if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (cv data)");
+    // the network's inputs come from the FP32 features kernel for every set
+    // of states (training, evaluation, auxiliary): one function on all sides
+    CK(cv_raw_features(ctx, b.mothers, ctx->cfg.precision == TTCF_MIXED ? 1 : 0, b, b.G, raw));
     CvFeatArgs fa;
     memset(&fa, 0, sizeof(fa));
-    fa.raw = b.feat; fa.alpha = b.m_alpha; fa.reset_alpha = ctx->cfg.reset_alpha;
+    fa.raw = raw; fa.alpha = b.m_alpha; fa.reset_alpha = ctx->cfg.reset_alpha;
     fa.M = b.M; for (int k = 0; k < 4; k++) fa.maps[k] = b.maps[k];
     fa.D = D; fa.N = b.N; fa.V = b.V; fa.X = X;
     CK(cv_launch_features(fa, ctx->st));
@@ -2066,7 +2096,7 @@ ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg
         // control variate on the held-out groups; the best epoch's weights
         // are kept (the per-daughter target is mostly noise, and later
         // epochs fit it)
-        CK(cv_launch_predict(cvm.wb, X, D, f, ctx->nsm, sm));
+        { const ttcf_status ps = cv_predict(ctx, cvm.wb, X, D, f, sm); if (ps != TTCF_OK) return ps; }
         CK(cv_launch_group(z, f, cvm.zstats, b->M, d_hold, nhold, yg, hg, sm));
         CK(cv_launch_estimate(yg, hg, nhold, nullptr, 0, 1, 0.0, est, sm));
         double eh[8];
@@ -2081,7 +2111,7 @@ ttcf_status ttcf_cv_train(ttcf_ctx *ctx, int batch_id, const ttcf_cv_config *cfg
     CK(cudaMemcpyAsync(cvm.w, wbest, sizeof(float) * CV_NP, cudaMemcpyDeviceToDevice, sm));
     CK(cv_launch_to_bf16(cvm.w, cvm.wb, sm));
     // c from the held-out groups
-    CK(cv_launch_predict(cvm.wb, X, D, f, ctx->nsm, sm));
+    { const ttcf_status ps = cv_predict(ctx, cvm.wb, X, D, f, sm); if (ps != TTCF_OK) return ps; }
     CK(cv_launch_group(z, f, cvm.zstats, b->M, d_hold, nhold, yg, hg, sm));
     CK(cv_launch_estimate(yg, hg, nhold, nullptr, 0, 1, 0.0, est, sm));
     double eh[8];
@@ -2124,10 +2154,10 @@ ttcf_status ttcf_cv_apply(ttcf_ctx *ctx, int batch_id, int n_aux, const double *
     if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (cv apply)");
     CK(cudaMemcpyAsync(d_g, groups.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, sm));
     CK(cv_launch_standardize(X, D, cvm.fstats, nullptr, nullptr, nullptr, sm));
-    CK(cv_launch_predict(cvm.wb, X, D, f, ctx->nsm, sm));
+    { const ttcf_status ps = cv_predict(ctx, cvm.wb, X, D, f, sm); if (ps != TTCF_OK) return ps; }
     CK(cv_launch_group(z, f, cvm.zstats, b->M, d_g, ng, yg, hg, sm));
-    // auxiliary mothers: spawn (features only), mapped features, predictions;
-    // they may be host or device arrays (both pointers of one kind)
+    // auxiliary mothers: features (FP32 kernel, no daughters), mapped
+    // features, predictions; host or device arrays (both pointers of one kind)
     int aux_dev = 0;
     {
         cudaPointerAttributes pa;
@@ -2136,29 +2166,41 @@ ttcf_status ttcf_cv_apply(ttcf_ctx *ctx, int batch_id, int n_aux, const double *
             aux_dev = 1;
         cudaGetLastError();
     }
-    BatchHost ab;
-    s = make_batch(ctx, tmp, ab, b->N, b->L, n_aux, aux_soa, aux_alpha, nullptr, aux_dev, b->maps, b->M, 1,
-                   0.0);
-    if (s != TTCF_OK) return s;
-    const long long DA = ab.D();
+    // the auxiliary states need features only: no daughters are spawned
+    const long long DA = (long long)n_aux * b->M;
+    const size_t aslots = (size_t)n_aux * 6 * b->N;
     float *XA = tmp.get<float>((size_t)DA * CV_NF);
     float *fA = tmp.get<float>(DA);
     int *d_ga = tmp.get<int>(n_aux);
     double *hA = tmp.get<double>(n_aux);
+    double *rawA = tmp.get<double>((size_t)n_aux * FEAT_RAW);
+    double *alA = tmp.get<double>(n_aux);
+    const double *srcA = aux_soa;
+    if (!aux_dev) {
+        double *d = tmp.get<double>(aslots);
+        if (d) CK(cudaMemcpyAsync(d, aux_soa, sizeof(double) * aslots, cudaMemcpyHostToDevice, sm));
+        srcA = d;
+    }
     if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (cv auxiliary)");
+    if (aux_alpha)
+        CK(cudaMemcpyAsync(alA, aux_alpha, sizeof(double) * n_aux,
+                           aux_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sm));
+    else
+        CK(cudaMemsetAsync(alA, 0, sizeof(double) * n_aux, sm));
+    CK(cv_raw_features(ctx, srcA, 0, *b, n_aux, rawA));
     CvFeatArgs fa;
     memset(&fa, 0, sizeof(fa));
-    fa.raw = ab.feat; fa.alpha = ab.m_alpha; fa.reset_alpha = ctx->cfg.reset_alpha;
-    fa.M = ab.M; for (int k = 0; k < 4; k++) fa.maps[k] = ab.maps[k];
-    fa.D = DA; fa.N = ab.N; fa.V = ab.V; fa.X = XA;
+    fa.raw = rawA; fa.alpha = alA; fa.reset_alpha = ctx->cfg.reset_alpha;
+    fa.M = b->M; for (int k = 0; k < 4; k++) fa.maps[k] = b->maps[k];
+    fa.D = DA; fa.N = b->N; fa.V = b->V; fa.X = XA;
     CK(cv_launch_features(fa, sm));
     CK(cv_launch_standardize(XA, DA, cvm.fstats, nullptr, nullptr, nullptr, sm));
-    CK(cv_launch_predict(cvm.wb, XA, DA, fA, ctx->nsm, sm));
+    { const ttcf_status ps = cv_predict(ctx, cvm.wb, XA, DA, fA, sm); if (ps != TTCF_OK) return ps; }
     {
         std::vector<int> ga(n_aux);
         for (int k = 0; k < n_aux; k++) ga[k] = k;
         CK(cudaMemcpyAsync(d_ga, ga.data(), sizeof(int) * n_aux, cudaMemcpyHostToDevice, sm));
-        CK(cv_launch_group(nullptr, fA, cvm.zstats, ab.M, d_ga, n_aux, nullptr, hA, sm));
+        CK(cv_launch_group(nullptr, fA, cvm.zstats, b->M, d_ga, n_aux, nullptr, hA, sm));
         CK(cv_launch_estimate(yg, hg, ng, hA, n_aux, 0, cvm.c, est, sm));
         CK(cudaMemcpyAsync(out, est, sizeof(double) * 8, cudaMemcpyDeviceToHost, sm));
         CK(cudaStreamSynchronize(sm));
@@ -2196,7 +2238,7 @@ ttcf_status ttcf_cv_forward(ttcf_ctx *ctx, const float *params, int n, const flo
     float *dX = tmp.get<float>((size_t)n * CV_NF), *df = tmp.get<float>(n);
     if (tmp.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (forward)");
     CK(cudaMemcpyAsync(dX, X, sizeof(float) * n * CV_NF, cudaMemcpyHostToDevice, ctx->st));
-    CK(cv_launch_predict(wb, dX, n, df, ctx->nsm, ctx->st));
+    { const ttcf_status ps = cv_predict(ctx, wb, dX, n, df, ctx->st); if (ps != TTCF_OK) return ps; }
     CK(cudaMemcpyAsync(out, df, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return TTCF_OK;

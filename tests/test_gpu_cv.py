@@ -1,10 +1,12 @@
 """GPU control variate (not in the paper; the estimator it improves is
 Eq. 1) against the FP64 oracle of oracle/cv.py.
 
-Tolerances: features 1e-5 relative (FP32 outputs of FP64 sums); targets
-1e-12 relative (FP64 on both sides); network outputs and gradients with the
-BF16-rounded weights on both sides, FP32 accumulation on the GPU: 1e-4
-relative to the largest entry."""
+Tolerances: features 1e-5 relative (FP32 features kernel against FP64
+sums); targets 1e-12 relative (FP64 on both sides); network outputs and
+gradients with the BF16-rounded weights on both sides, FP32 accumulation on
+the GPU (the forward pass on the tensor cores with the activations as two
+BF16 terms, about 2^-17 relative per product): 1e-4 relative to the
+largest entry."""
 import numpy as np
 import pytest
 
@@ -63,6 +65,23 @@ def test_forward_and_gradient_match_the_oracle(T):
     assert np.abs(f - fo).max() < 1e-4 * np.abs(fo).max()
     assert loss == pytest.approx(lo, rel=1e-4)
     assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
+
+
+def test_tensor_core_forward_over_many_tiles(T):
+    """The forward pass runs on the tensor cores (tcgen05, 128 samples per
+    tile, activations as two BF16 terms, FP32 accumulation in tensor memory):
+    40001 samples (many tiles per CTA and a ragged last tile) against the
+    FP64 oracle with the same BF16 weights, 1e-4 of the largest output."""
+    rng = np.random.default_rng(17)
+    th = rng.normal(0, 0.12, ocv.N_PARAMS).astype(np.float32)
+    X = rng.normal(size=(40001, 32)).astype(np.float32)
+    with ctx(T) as c:
+        f = c.cv_forward(th, X)
+    fo, _ = ocv.forward(ocv.bf16(th), X.astype(np.float64))
+    assert np.all(np.isfinite(f))
+    assert np.abs(f - fo).max() < 1e-4 * np.abs(fo).max()
+    # the outputs also follow the inputs row by row (no tile or row mix-up)
+    assert np.corrcoef(f, fo)[0, 1] > 0.999999
 
 
 def test_control_variate_is_unbiased_and_reduces_variance(T):
