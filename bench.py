@@ -58,9 +58,9 @@ FLOPS_PER_PAIR_LJ = 25.0         # one unique LJ-c_ij pair of the confined syste
 # profiles/*.md), scaled to a launch by the units it processes:
 # daughter_kernel reads its mothers (per daughter) and writes the series (per
 # sample); conf_kernel streams its per-CTA scratch (per atom-step).
-BULK_READ_PER_DAUGHTER = 31.1e3
-BULK_WRITE_PER_SAMPLE = 11.2
-CONF_BYTES_PER_ATOM_STEP = 397.0
+BULK_READ_PER_DAUGHTER = 31.3e3
+BULK_WRITE_PER_SAMPLE = 10.9
+CONF_BYTES_PER_ATOM_STEP = 399.0
 CONF_RATES = [1e-1, 1e-3, 1e-5, 1e-7]
 UNEVEN_SIZES = (256, 864, 4000)
 UNEVEN_RATES = [1e-2, 1e-3, 1e-4, 1e-5, 1e-6]
