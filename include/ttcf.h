@@ -242,7 +242,9 @@ ttcf_status ttcf_get_state(ttcf_ctx *ctx, int batch_id, int daughter, double *so
  * rebuilds, atom-steps, and kernel launches issued.                        */
 typedef struct {
     double ms_run, ms_spawn, ms_reduce;
-    double pairs_interacting;   /* ordered pairs (i,j), r_ij < r_c, summed  */
+    double pairs_interacting;   /* ordered pairs (i,j), r_ij < r_c, summed
+                                   over daughter steps (bulk: counted on the
+                                   first of every 16 steps and scaled)      */
     double rebuilds;            /* neighbour-list builds, summed over daughters */
     double atom_steps;          /* sum over daughters of N * steps run       */
     int launches;               /* kernels launched by the last ttcf_run     */

@@ -1048,9 +1048,12 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
         CK(cudaMemcpy(stv.data(), b.status, sizeof(int) * b.D(), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(pr.data(), b.pairs, sizeof(unsigned long long) * b.D(), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(rb.data(), b.rebuilds, sizeof(unsigned int) * b.D(), cudaMemcpyDeviceToHost));
+        // the daughter kernel counts pairs on the first of every 16 steps
+        const int nrun = step1 - step0, counted = (nrun + 15) / 16;
+        const double pscale = counted > 0 ? (double)nrun / counted : 0.0;
         for (long long d = 0; d < b.D(); d++) {
             any_fail |= stv[d] != 0;
-            ctx->stats.pairs_interacting += (double)pr[d];
+            ctx->stats.pairs_interacting += (double)pr[d] * pscale;
             ctx->stats.rebuilds += (double)rb[d];
         }
         ctx->stats.atom_steps += (double)b.D() * b.N * (step1 - step0);

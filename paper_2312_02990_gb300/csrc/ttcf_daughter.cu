@@ -561,8 +561,12 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     };
 
     // ---- WCA forces (Eq. 6) and virial of own atoms ----
+    // Interacting pairs are counted on the first of every 16 steps of a run
+    // (the library scales the count to all steps): a second instantiation
+    // of the pair loop, so the other steps carry no counting instructions.
     unsigned int npairs = 0;
-    auto forces = [&]() -> R {
+    auto forces = [&](auto count_pairs) -> R {
+        constexpr bool COUNT = decltype(count_pairs)::value;
         const R rc2 = (R)1.2599210498948732;   // r_c^2 = 2^(1/3)
         R wsum = 0;
         for (int q = 0; q < APT; q++) {
@@ -615,7 +619,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                         w = __fmaf_rn(fdx.x, dy.x, w);
                         fx = __fmaf_rn(f.y, dx.y, fx); fy = __fmaf_rn(f.y, dy.y, fy); fz = __fmaf_rn(f.y, dz.y, fz);
                         w = __fmaf_rn(fdx.y, dy.y, w);
-                        npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
+                        if constexpr (COUNT) npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
                       }
                     }
                 } else {
@@ -633,7 +637,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                             const R f = s3 * s * ((R)48 * s3 - (R)24);   // |F|/r
                             fx += f * dx; fy += f * dy; fz += f * dz;
                             w += f * dx * dy;
-                            npairs++;
+                            if constexpr (COUNT) npairs++;
                         }
                     }
                 }
@@ -701,7 +705,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     // ---- forces and sums of the initial state ----
     build_list();
     if (tid == 0) m->n_rebuild++;
-    R w0 = forces();
+    R w0 = forces(std::false_type{});
     if (a.force_out) {
         double *fo = a.force_out + (size_t)d * 3 * N;
         for (int q = 0; q < APT; q++) {
@@ -870,7 +874,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             if (tid == 0) { dsince = 0.f; m->n_rebuild++; }
         }
         // phase B
-        const R wsum = forces();
+        const R wsum = ((s - a.step0) & 15) == 1 ? forces(std::true_type{}) : forces(std::false_type{});
         // phase C
         R s2 = 0, sxy = 0;
         if constexpr (MIXED && APT % 2 == 0) {   // atoms q and q+1 on packed pairs

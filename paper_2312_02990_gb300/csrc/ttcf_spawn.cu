@@ -1,6 +1,10 @@
 // ttcf_spawn.cu -- switch-on of the field for one batch of daughters
 // (Figure 1; Algorithm 2 "load system state", "apply mapping", "switch on
-// ext. field").  One CTA per mother state, all arithmetic IEEE double:
+// ext. field").  One CTA per mother state.  Kinetic sums, slab modes and
+// the results are IEEE double; the pair sums (virial, U) are IEEE double in
+// FP64 mode, and in MIXED mode double-float pairs on the FP32 pipe (about
+// 48 significand bits; GB300 runs IEEE double at 1/72 of the FP32 rate),
+// each candidate first screened in FP32 on the hi parts with a margin:
 //   P_ab(0) = (1/V)[sum_i p_a p_b + sum_{i<j} r_ij,a F_ij,b]   (WCA, Eq. 6)
 //   B(0)    = P_xy(0) of each mapped daughter: a reflection of x or of y
 //             negates it exactly, time reversal and the z-reflection keep
@@ -18,27 +22,46 @@ size_t spawn_smem_bytes(int N, int ncell) {
            32 * NACC * 8 + 256;
 }
 
+// Reciprocal of a double-float: the float reciprocal and one Newton step
+// in double-float (about 2^-44 relative).
+__device__ __forceinline__ df df_rcp(df a) {
+    const float y = __frcp_rn(a.hi);
+    const df e = df_add_f(df_neg(df_mul_f(a, y)), 1.0f);   // 1 - a y
+    return df_add_f(df_mul_f(e, y), y);                      // y + y (1 - a y)
+}
+
 __global__ void spawn_kernel(SpawnArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
     const int N = a.N;
     const double *src = a.src + (size_t)g * 6 * N;
+    // positions, 24 bytes per atom: IEEE doubles (FP64 mode) or double-float
+    // pairs as hi and lo rows (MIXED)
     double *xd = (double *)smem, *yd = xd + N, *zd = yd + N;
-    int *cnt = (int *)(zd + N);
+    float *xh = (float *)smem, *yh = xh + N, *zh = yh + N, *xl = zh + N, *yl = xl + N, *zl = yl + N;
+    int *cnt = (int *)(zl + N);
     int *start = cnt + a.ncell;
     unsigned short *catom = (unsigned short *)(start + a.ncell + 2);
     double *red = (double *)((unsigned char *)catom + ((size_t)N * 2 + 15) / 16 * 16);
     int *warp_tmp = (int *)(red + 32 * NACC);
 
     const double invL[3] = {1.0 / a.L[0], 1.0 / a.L[1], 1.0 / a.L[2]};
-    for (int i = tid; i < N; i += T) { xd[i] = src[i]; yd[i] = src[N + i]; zd[i] = src[2 * N + i]; }
+    for (int i = tid; i < N; i += T) {
+        if (a.mixed) {
+            const df x = df_from_double(src[i]), y = df_from_double(src[N + i]), z = df_from_double(src[2 * N + i]);
+            xh[i] = x.hi; xl[i] = x.lo; yh[i] = y.hi; yl[i] = y.lo; zh[i] = z.hi; zl[i] = z.lo;
+        } else {
+            xd[i] = src[i]; yd[i] = src[N + i]; zd[i] = src[2 * N + i];
+        }
+    }
     for (int c = tid; c < a.ncell; c += T) cnt[c] = 0;
     __syncthreads();
-    auto cell3 = [&](int i, int &cx, int &cy, int &cz) {
-        double y = yd[i] - a.L[1] * rint(yd[i] * invL[1]);
-        double x = xd[i] - rint(yd[i] * invL[1]) * a.delta;
+    auto cell3 = [&](int i, int &cx, int &cy, int &cz) {   // binning in IEEE double
+        const double xi = src[i], yi = src[N + i], zi = src[2 * N + i];
+        double y = yi - a.L[1] * rint(yi * invL[1]);
+        double x = xi - rint(yi * invL[1]) * a.delta;
         x -= a.L[0] * rint(x * invL[0]);
-        double z = zd[i] - a.L[2] * rint(zd[i] * invL[2]);
+        double z = zi - a.L[2] * rint(zi * invL[2]);
         cx = min(max((int)floor((x + 0.5 * a.L[0]) * a.nc[0] * invL[0]), 0), a.nc[0] - 1);
         cy = min(max((int)floor((y + 0.5 * a.L[1]) * a.nc[1] * invL[1]), 0), a.nc[1] - 1);
         cz = min(max((int)floor((z + 0.5 * a.L[2]) * a.nc[2] * invL[2]), 0), a.nc[2] - 1);
@@ -83,12 +106,19 @@ __global__ void spawn_kernel(SpawnArgs a) {
     double acc[NACC];
     for (int k = 0; k < NACC; k++) acc[k] = 0.0;
     const double rc2 = 1.2599210498948732;
+    const float rc2_screen = 1.2599210498948732f * (1.0f + 1e-4f);   // hi parts: |error| << 1e-4 r_c^2
+    const float Lf[3] = {(float)a.L[0], (float)a.L[1], (float)a.L[2]};
+    const float invLf[3] = {(float)invL[0], (float)invL[1], (float)invL[2]};
+    const float deltaf = (float)a.delta;
+    const df Ld[3] = {df_from_double(a.L[0]), df_from_double(a.L[1]), df_from_double(a.L[2])};
+    const df deltad = df_from_double(a.delta);
+    const df rc2d = df_from_double(rc2);
     for (int i = tid; i < N; i += T) {
         const double px = src[3 * N + i], py = src[4 * N + i], pz = src[5 * N + i];
         acc[0] += px * px; acc[1] += py * py; acc[2] += pz * pz;
         acc[3] += px * py; acc[4] += px * pz; acc[5] += py * pz;
         {
-            int k = (int)floor((yd[i] + 0.5 * a.L[1]) * invL[1] * NSLAB);
+            int k = (int)floor((src[N + i] + 0.5 * a.L[1]) * invL[1] * NSLAB);
             k = min(max(k, 0), NSLAB - 1);
             for (int u = 0; u < 2 * NMODE; u++) {
                 acc[13 + u] += cs_tab[k][u];
@@ -97,6 +127,44 @@ __global__ void spawn_kernel(SpawnArgs a) {
         }
         int cx, cy, cz;
         cell3(i, cx, cy, cz);
+        if (!a.mixed) {   // FP64 mode: the pair sums in IEEE double
+            for (int oy = -1; oy <= 1; oy++) {
+                int yy = cy + oy;
+                const int cross = yy < 0 ? -1 : (yy >= a.nc[1] ? 1 : 0);
+                yy = (yy + a.nc[1]) % a.nc[1];
+                const int x0 = cross ? 0 : cx - 1, x1 = cross ? a.nc[0] - 1 : cx + 1;
+                for (int oz = -1; oz <= 1; oz++) {
+                    const int zz = (cz + oz + a.nc[2]) % a.nc[2];
+                    for (int xc = x0; xc <= x1; xc++) {
+                        const int xx = ((xc % a.nc[0]) + a.nc[0]) % a.nc[0];
+                        const int c = (zz * a.nc[1] + yy) * a.nc[0] + xx;
+                        for (int t = start[c]; t < start[c + 1]; t++) {
+                            const int j = catom[t];
+                            if (j == i) continue;
+                            double dx = xd[i] - xd[j], dy = yd[i] - yd[j], dz = zd[i] - zd[j];
+                            const double ny = rint(dy * invL[1]);
+                            dy -= ny * a.L[1]; dx -= ny * a.delta;
+                            dx -= rint(dx * invL[0]) * a.L[0];
+                            dz -= rint(dz * invL[2]) * a.L[2];
+                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < rc2) {
+                                const double sv = 1.0 / r2, s3 = sv * sv * sv;
+                                const double f = s3 * sv * (48.0 * s3 - 24.0);
+                                acc[6] += 0.5 * f * dx * dx; acc[7] += 0.5 * f * dy * dy;
+                                acc[8] += 0.5 * f * dz * dz; acc[9] += 0.5 * f * dx * dy;
+                                acc[10] += 0.5 * f * dx * dz; acc[11] += 0.5 * f * dy * dz;
+                                acc[12] += 0.5 * (4.0 * s3 * (s3 - 1.0) + 1.0);
+                            }
+                        }
+                    }
+                }
+            }
+            continue;
+        }
+        // pair sums of atom i as double-float pairs: 0.5 f d_a d_b, 0.5 U
+        df pw[7];
+        for (int k = 0; k < 7; k++) pw[k] = df_make(0.f);
+        const df xi = {xh[i], xl[i]}, yi = {yh[i], yl[i]}, zi = {zh[i], zl[i]};
         for (int oy = -1; oy <= 1; oy++) {
             int yy = cy + oy;
             const int cross = yy < 0 ? -1 : (yy >= a.nc[1] ? 1 : 0);
@@ -111,24 +179,40 @@ __global__ void spawn_kernel(SpawnArgs a) {
                     for (int t = start[c]; t < start[c + 1]; t++) {
                         const int j = catom[t];
                         if (j == i) continue;
-                        double dx = xd[i] - xd[j], dy = yd[i] - yd[j], dz = zd[i] - zd[j];
-                        const double ny = rint(dy * invL[1]);
-                        dy -= ny * a.L[1]; dx -= ny * a.delta;
-                        dx -= rint(dx * invL[0]) * a.L[0];
-                        dz -= rint(dz * invL[2]) * a.L[2];
-                        const double r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rc2) {
-                            const double s = 1.0 / r2, s3 = s * s * s;
-                            const double f = s3 * s * (48.0 * s3 - 24.0);
-                            acc[6] += 0.5 * f * dx * dx; acc[7] += 0.5 * f * dy * dy;
-                            acc[8] += 0.5 * f * dz * dz; acc[9] += 0.5 * f * dx * dy;
-                            acc[10] += 0.5 * f * dx * dz; acc[11] += 0.5 * f * dy * dz;
-                            acc[12] += 0.5 * (4.0 * s3 * (s3 - 1.0) + 1.0);
-                        }
+                        // FP32 screen on the hi parts: the periodic and
+                        // Lees-Edwards images, and r^2 with a margin
+                        float dyf = yh[i] - yh[j];
+                        const float ny = rintf(dyf * invLf[1]);
+                        dyf = __fmaf_rn(-ny, Lf[1], dyf);
+                        float dxf = __fmaf_rn(-ny, deltaf, xh[i] - xh[j]);
+                        const float nx = rintf(dxf * invLf[0]);
+                        dxf = __fmaf_rn(-nx, Lf[0], dxf);
+                        float dzf = zh[i] - zh[j];
+                        const float nz = rintf(dzf * invLf[2]);
+                        dzf = __fmaf_rn(-nz, Lf[2], dzf);
+                        if (dxf * dxf + dyf * dyf + dzf * dzf >= rc2_screen) continue;
+                        // the pair in double-float with the same images
+                        const df dy = df_add(df_add(yi, df_neg({yh[j], yl[j]})), df_mul_f(Ld[1], -ny));
+                        const df dx = df_add(df_add(df_add(xi, df_neg({xh[j], xl[j]})), df_mul_f(deltad, -ny)),
+                                             df_mul_f(Ld[0], -nx));
+                        const df dz = df_add(df_add(zi, df_neg({zh[j], zl[j]})), df_mul_f(Ld[2], -nz));
+                        const df r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+                        if (!df_lt(r2, rc2d)) continue;
+                        const df sv = df_rcp(r2);
+                        const df s3 = df_mul(df_mul(sv, sv), sv);
+                        const df hf = df_mul_f(df_mul(df_mul(s3, sv), df_add_f(df_mul_f(s3, 48.0f), -24.0f)), 0.5f);
+                        const df hx = df_mul(hf, dx), hy = df_mul(hf, dy);
+                        pw[0] = df_add(pw[0], df_mul(hx, dx)); pw[1] = df_add(pw[1], df_mul(hy, dy));
+                        pw[2] = df_add(pw[2], df_mul(df_mul(hf, dz), dz)); pw[3] = df_add(pw[3], df_mul(hx, dy));
+                        pw[4] = df_add(pw[4], df_mul(hx, dz)); pw[5] = df_add(pw[5], df_mul(hy, dz));
+                        // 0.5 (4 s3 (s3 - 1) + 1)
+                        pw[6] = df_add(pw[6], df_mul_f(df_add_f(df_mul_f(df_mul(s3, df_add_f(s3, -1.0f)), 4.0f), 1.0f),
+                                                       0.5f));
                     }
                 }
             }
         }
+        for (int k = 0; k < 7; k++) acc[6 + k] += df_to_double(pw[k]);
     }
     // fixed-order CTA reduction
     const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
