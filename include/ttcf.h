@@ -244,7 +244,8 @@ typedef struct {
     double ms_run, ms_spawn, ms_reduce;
     double pairs_interacting;   /* ordered pairs (i,j), r_ij < r_c, summed
                                    over daughter steps (bulk: counted on the
-                                   first of every 16 steps and scaled)      */
+                                   force passes that refresh the active
+                                   lists, their mean times the steps run)   */
     double rebuilds;            /* neighbour-list builds, summed over daughters */
     double atom_steps;          /* sum over daughters of N * steps run       */
     int launches;               /* kernels launched by the last ttcf_run     */

@@ -402,7 +402,7 @@ ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &
     std::vector<unsigned int *> d_nbr(cls.size());
     for (size_t k = 0; k < cls.size(); k++) {
         d_work[k] = pool.get<int>(cls[k].work.size());
-        d_nbr[k] = pool.get<unsigned int>((size_t)cls[k].grid * (CAP / 2) * cls[k].nmax);
+        d_nbr[k] = pool.get<unsigned int>((size_t)cls[k].grid * NBR_WORDS * cls[k].nmax);
         if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (work lists)");
         CK(cudaMemcpyAsync(d_work[k], cls[k].work.data(), sizeof(int) * cls[k].work.size(),
                            cudaMemcpyHostToDevice, st));
@@ -1048,12 +1048,9 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
         CK(cudaMemcpy(stv.data(), b.status, sizeof(int) * b.D(), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(pr.data(), b.pairs, sizeof(unsigned long long) * b.D(), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(rb.data(), b.rebuilds, sizeof(unsigned int) * b.D(), cudaMemcpyDeviceToHost));
-        // the daughter kernel counts pairs on the first of every 16 steps
-        const int nrun = step1 - step0, counted = (nrun + 15) / 16;
-        const double pscale = counted > 0 ? (double)nrun / counted : 0.0;
         for (long long d = 0; d < b.D(); d++) {
             any_fail |= stv[d] != 0;
-            ctx->stats.pairs_interacting += (double)pr[d] * pscale;
+            ctx->stats.pairs_interacting += (double)pr[d];
             ctx->stats.rebuilds += (double)rb[d];
         }
         ctx->stats.atom_steps += (double)b.D() * b.N * (step1 - step0);

@@ -78,6 +78,8 @@ struct Coef {
     float thr2;            // rebuild threshold, squared; < 0 forces a rebuild
     float fast2;           // fatal single-step displacement, squared
     float rl2;             // list radius squared
+    float ra2;             // active-list radius squared, (r_c + ACTIVE_SKIN)^2
+    float thr_a;           // active-list refresh threshold on the path length; < 0 forces one
     int stop;
     int snap;              // snapshot index written after this step, or -1
     double fsnap;          // pending momentum factor for the snapshot
@@ -97,7 +99,11 @@ struct Misc {
     df hhQf, ngTf, nhhf, sixthf, ddeltaf, halfLxf, Lxf;
     float ddelta_abs;
     float dsince;                       // |change of delta| since the list build
+    float dsince_a;                     // |change of delta| since the active-list refresh
     unsigned int n_rebuild;
+    unsigned int n_filter;              // force passes over the Verlet lists (refreshes)
+    unsigned long long np;              // interacting pairs counted on those passes
+    int flag_filter[2];
     int warp_tmp[MAX_WARPS];
     int flag_rebuild[2];
     int flag_fast;
@@ -242,7 +248,11 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     Coef<S> *cf = (Coef<S> *)sp; sp += (sizeof(Coef<S>) + 15) / 16 * 16;
     Misc *m = (Misc *)sp;
 
+    // Verlet lists of all CTAs, then the active lists of all CTAs
     uint4 *nbr4 = reinterpret_cast<uint4 *>(a.nbr + (size_t)blockIdx.x * (CAP / 2) * nmax);
+    uint4 *nbra4 = reinterpret_cast<uint4 *>(a.nbr + (size_t)gridDim.x * (CAP / 2) * nmax +
+                                             (size_t)blockIdx.x * (CAP_A / 2) * nmax);
+    unsigned short *nbra16 = reinterpret_cast<unsigned short *>(nbra4);
 
     // thread 0 keeps the per-daughter scalars in shared memory (IEEE double;
     // MIXED mode steps the double-float copies in Misc)
@@ -254,7 +264,11 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         a_end = a_cur = K2_end = e1 = delta = 0.0;
         f1sq = 1.0;
         dsince = 0.f;
+        m->dsince_a = 0.f;
         m->n_rebuild = 0;
+        m->n_filter = 0;
+        m->np = 0ull;
+        m->flag_filter[0] = m->flag_filter[1] = 0;
         // constants of the per-step lane-0 chain (no division in the loop)
         m->hhQ = hh / b.Q;
         m->invV = 1.0 / b.V;
@@ -270,6 +284,9 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         }
         const float rl = (float)(1.1224620483093730 + (double)b.skin);
         cf->rl2 = rl * rl;
+        const float ra = (float)1.1224620483093730 + fminf(ACTIVE_SKIN, b.skin);
+        cf->ra2 = ra * ra;
+        cf->thr_a = -1.f;
         cf->fast2 = 0.25f * b.skin * b.skin;
         cf->thr2 = -1.f;
         cf->stop = 0; cf->snap = -1; cf->fsnap = 1.0;
@@ -561,19 +578,36 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     };
 
     // ---- WCA forces (Eq. 6) and virial of own atoms ----
-    // Interacting pairs are counted on the first of every 16 steps of a run
-    // (the library scales the count to all steps): a second instantiation
-    // of the pair loop, so the other steps carry no counting instructions.
+    // Two passes share the pair arithmetic.  FILTER: over the Verlet list,
+    // counting the interacting pairs; in FP64 mode it also refreshes the
+    // atom's active list (the entries within r_c + ACTIVE_SKIN, kept in list
+    // order).  Otherwise over the active list (FP64) or again the Verlet list
+    // (MIXED).  Both lists are sorted by neighbour index and out-of-range
+    // entries add exact zeros, so the two passes give the same sums bit for
+    // bit.  ncnt: Verlet count in the low 16 bits, the active count in the
+    // high 16 (0xffff: more than CAP_A, use the Verlet list).
+    // MIXED mode keeps to the Verlet lists: there the pass is cheap beside
+    // its fixed costs, and the active-list bookkeeping (path sums in phase
+    // A, appends in the filter pass) raised register spills by more than
+    // the shorter lists saved (0.90x on the N = 2048 launch, results equal);
+    // the FP64 pass pays for it (1.28x at N = 256).
+    constexpr bool ACTIVE = !MIXED;
     unsigned int npairs = 0;
-    auto forces = [&](auto count_pairs) -> R {
-        constexpr bool COUNT = decltype(count_pairs)::value;
+    auto forces = [&](auto filter) -> R {
+        constexpr bool FILTER = decltype(filter)::value;
         const R rc2 = (R)1.2599210498948732;   // r_c^2 = 2^(1/3)
         R wsum = 0;
         for (int q = 0; q < APT; q++) {
             const int i = tid + q * T;
             R fx = 0, fy = 0, fz = 0, w = 0;
             if (i < N) {
-                const int kk = ncnt[q];
+                const int kv = ACTIVE ? ncnt[q] & 0xffff : ncnt[q], kac = (unsigned int)ncnt[q] >> 16;
+                const bool verlet = !ACTIVE || FILTER || kac == 0xffff;
+                const int kk = verlet ? kv : kac;
+                const uint4 *lst = verlet ? nbr4 : nbra4;
+                int ka = 0;
+                // entry e of atom i's active list
+                auto aslot = [&](int e) { return ((size_t)(e >> 3) * nmax + i) * 8 + (e & 7); };
                 if constexpr (MIXED) {
                     const float4 u = pos4[i];
                     const float Lx = cf->Lf[0], Ly = cf->Lf[1], Lz = cf->Lf[2];
@@ -586,7 +620,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                     const float2 dl2 = make_float2(dl, dl);
                     const float2 c48 = make_float2(48.f, 48.f), cm24 = make_float2(-24.f, -24.f);
                     for (int t8 = 0; t8 < kk; t8 += 8) {
-                      const uint4 ch = nbr4[(size_t)(t8 >> 3) * nmax + i];
+                      const uint4 ch = lst[(size_t)(t8 >> 3) * nmax + i];
                       const unsigned int wv[4] = {ch.x, ch.y, ch.z, ch.w};
 #pragma unroll
                       for (int wq = 0; wq < 4; wq++) {
@@ -619,27 +653,40 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                         w = __fmaf_rn(fdx.x, dy.x, w);
                         fx = __fmaf_rn(f.y, dx.y, fx); fy = __fmaf_rn(f.y, dy.y, fy); fz = __fmaf_rn(f.y, dz.y, fz);
                         w = __fmaf_rn(fdx.y, dy.y, w);
-                        if constexpr (COUNT) npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
+                        if constexpr (FILTER) npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
                       }
                     }
                 } else {
+                    const R ra2 = (R)cf->ra2;
                     for (int t = 0; t < kk; t++) {
-                        const uint4 ch = nbr4[(size_t)(t >> 3) * nmax + i];
+                        const uint4 ch = lst[(size_t)(t >> 3) * nmax + i];
                         const int u = (t >> 1) & 3;
                         const unsigned int word = u == 0 ? ch.x : u == 1 ? ch.y : u == 2 ? ch.z : ch.w;
                         const int j = (t & 1) ? (int)(word >> 16) : (int)(word & 0xffffu);
                         R dx, dy, dz;
                         pair_vec(i, j, dx, dy, dz);
                         const R r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rc2) {
+                        if (r2 < rc2 && r2 > (R)0) {
                             const R s = 1.0 / r2;
                             const R s3 = s * s * s;
                             const R f = s3 * s * ((R)48 * s3 - (R)24);   // |F|/r
                             fx += f * dx; fy += f * dy; fz += f * dz;
                             w += f * dx * dy;
-                            if constexpr (COUNT) npairs++;
+                            if constexpr (FILTER) npairs++;
+                        }
+                        if constexpr (FILTER && ACTIVE) {
+                            if (r2 < ra2 && r2 > (R)0) {
+                                if (ka < CAP_A) nbra16[aslot(ka)] = (unsigned short)j;
+                                ka++;
+                            }
                         }
                     }
+                }
+                if constexpr (FILTER && ACTIVE) {
+                    // an odd count is padded with i itself (r = 0 adds nothing)
+                    if (ka <= CAP_A && (ka & 1)) nbra16[aslot(ka)] = (unsigned short)i;
+                    ncnt[q] = kv | ((ka > CAP_A ? 0xffff : ka) << 16);
+                    reinterpret_cast<float *>(ref4 + i)[3] = 0.f;   // path length since the refresh
                 }
             }
             F[q][0] = fx; F[q][1] = fy; F[q][2] = fz;
@@ -661,14 +708,24 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         cf->f1 = sfrom<S>(f1sq);
         cf->e = sfrom<S>(ec);
     };
+    // Active lists stay complete while every atom's path length since the
+    // refresh is at most (s_a - |change of delta|) / 2: a pair then moved
+    // together by at most s_a.  1e-4 sigma of margin covers the FP32
+    // rounding of the path sums and of r^2.
+    auto set_thr_a = [&]() {
+        const float tha = 0.5f * (fminf(ACTIVE_SKIN, b.skin) - m->dsince_a) - 1e-4f;
+        cf->thr_a = tha > 0.f ? tha : -1.f;
+    };
     auto next_delta = [&]() {
         delta += m->ddelta;                        // sliding-brick offset advance
         if (delta >= m->halfLx) delta -= b.L[0];
         else if (delta < -m->halfLx) delta += b.L[0];
         dsince += fabsf((float)m->ddelta);
+        m->dsince_a += fabsf((float)m->ddelta);
         cf->delta_d = delta; cf->delta_s = sfrom<S>(delta); cf->delta_f = (float)delta;
         const float thr = 0.5f * (b.skin - dsince);
         cf->thr2 = thr > 0.f ? thr * thr : -1.f;
+        set_thr_a();
     };
     // MIXED: the same two updates in double-float; inc = hhQ (K2_end - gT)
     // is the increment of both alpha half-steps
@@ -705,7 +762,13 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     // ---- forces and sums of the initial state ----
     build_list();
     if (tid == 0) m->n_rebuild++;
-    R w0 = forces(std::false_type{});
+    R w0;
+    if constexpr (ACTIVE) {   // the first Verlet pass also builds the active lists
+        w0 = forces(std::true_type{});
+        if (tid == 0) m->n_filter++;
+    } else {
+        w0 = forces(std::false_type{});
+    }
     if (a.force_out) {
         double *fo = a.force_out + (size_t)d * 3 * N;
         for (int q = 0; q < APT; q++) {
@@ -745,7 +808,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         const S e = cf->e, chalf = cf->chalf, hS = cf->h, hhS = cf->hh, gh = cf->gh;
         const bool wrap_now = (s % WRAP_EVERY) == 0;
         const int fb = s & 1;
-        const float thr2 = cf->thr2, fast2 = cf->fast2;
+        const float thr2 = cf->thr2, fast2 = cf->fast2, thr_a = cf->thr_a;
         // phase A
         bool packed_a = false;
         if constexpr (MIXED && APT % 2 == 0) {
@@ -837,8 +900,13 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                 x += dxs; y += dys; z += dzs;
                 ddx = (float)dxs; ddy = (float)dys; ddz = (float)dzs;
             }
-            if (ddx * ddx + ddy * ddy + ddz * ddz > fast2) m->flag_fast = 1;
+            const float dd2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (dd2 > fast2) m->flag_fast = 1;
             float4 r = ref4[i];
+            if constexpr (ACTIVE) {   // path length since the active-list refresh
+                r.w += sqrtf(dd2);
+                if (r.w > thr_a) m->flag_filter[fb] = 1;
+            }
             if (wrap_now) {   // back into [-L/2, L/2) with the sliding-brick x shift;
                               // the reference moves with it (same periodic image)
                 R ny, nx, nz;
@@ -856,6 +924,8 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                 r.y -= (float)ny * cf->Lf[1];
                 r.z -= (float)nz * cf->Lf[2];
                 ref4[i] = r;
+            } else if constexpr (ACTIVE) {
+                reinterpret_cast<float *>(ref4 + i)[3] = r.w;
             }
             if constexpr (MIXED) {
                 pos4[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
@@ -869,12 +939,21 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
         }
         __syncthreads();                                        // barrier 1
         if (m->flag_fast) break;
-        if (m->flag_rebuild[fb] || thr2 < 0.f) {
+        const bool rebuild = m->flag_rebuild[fb] || thr2 < 0.f;
+        if (rebuild) {
             build_list();
             if (tid == 0) { dsince = 0.f; m->n_rebuild++; }
         }
-        // phase B
-        const R wsum = ((s - a.step0) & 15) == 1 ? forces(std::true_type{}) : forces(std::false_type{});
+        // FP64: refresh the active lists when due; MIXED: count the pairs on
+        // the first of every 16 steps
+        const bool refresh = ACTIVE ? (rebuild || m->flag_filter[fb] || thr_a < 0.f)
+                                    : ((s - a.step0) & 15) == 1;
+        if constexpr (ACTIVE) {   // (MIXED keeps these off thread 0's per-step chain)
+            if (refresh && tid == 0) { m->dsince_a = 0.f; m->n_filter++; }
+        }
+        // phase B: over the Verlet lists (refreshing the active lists) or
+        // over the active lists
+        const R wsum = refresh ? forces(std::true_type{}) : forces(std::false_type{});
         // phase C
         R s2 = 0, sxy = 0;
         if constexpr (MIXED && APT % 2 == 0) {   // atoms q and q+1 on packed pairs
@@ -1006,6 +1085,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                 next_alpha();
             }
             m->flag_rebuild[fb ^ 1] = 0;
+            if constexpr (ACTIVE) m->flag_filter[fb ^ 1] = 0;
         }
         __syncthreads();                                        // barrier 3
         if (cf->snap >= 0) {   // mother mode: store the clean phase point
@@ -1062,9 +1142,17 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     {
         unsigned long long np = npairs;
         for (int o = 16; o > 0; o >>= 1) np += __shfl_down_sync(0xffffffffu, np, o);
-        if ((tid & 31) == 0 && np) atomicAdd(&b.pairs[dl], np);
+        if ((tid & 31) == 0 && np) atomicAdd(&m->np, np);
     }
+    __syncthreads();
     if (tid == 0) {
+        // pairs were counted on the Verlet-list passes (FP64: the initial
+        // pass and the refreshes; MIXED: the first of every 16 steps): their
+        // mean per pass times the steps of this run
+        const int nrun = a.step1 - a.step0;
+        const unsigned int passes = ACTIVE ? m->n_filter : (unsigned int)((nrun + 15) / 16);
+        if (passes && nrun > 0)
+            atomicAdd(&b.pairs[dl], (unsigned long long)llrint((double)m->np * (double)nrun / (double)passes));
         int st = cf->stop;
         if (m->flag_fast) st |= TTCF_D_FAST_ATOM;
         if (m->flag_ovf) st |= TTCF_D_NBR_OVERFLOW;

@@ -20,6 +20,13 @@
 namespace ttcf {
 
 constexpr int CAP = 32;          // Verlet neighbours kept per atom
+// Active list: the Verlet entries within r_c + ACTIVE_SKIN, refreshed from
+// the (index-sorted) Verlet list whenever an atom's path length since the
+// last refresh could close the gap; the force loop walks it on the other
+// steps.  Up to CAP_A entries; an atom with more uses its Verlet list.
+constexpr int CAP_A = 24;
+constexpr float ACTIVE_SKIN = 0.1f;
+constexpr int NBR_WORDS = (CAP + CAP_A) / 2;   // uint32 words per atom, both lists
 constexpr int WRAP_EVERY = 64;   // positions re-wrapped into the box every 64 steps
 constexpr int MAX_WARPS = 32;
 
@@ -279,7 +286,9 @@ struct RunArgs {
     const int *dbatch;             // batch of each global daughter
     int n_work;
     int *queue;                    // persistent work counter
-    unsigned int *nbr;             // [grid][CAP/2][nmax], two uint16 entries per word
+    unsigned int *nbr;             // [grid][CAP/2][nmax] Verlet lists, then
+                                   // [grid][CAP_A/2][nmax] active lists; two uint16
+                                   // entries per word (NBR_WORDS words per atom)
     int nmax, ncellmax;
     int step0, step1;              // run absolute steps step0+1 .. step1
     int sample_every;

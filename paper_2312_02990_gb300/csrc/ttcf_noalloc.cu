@@ -140,7 +140,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     const size_t o_pairs = off; off += align256(sizeof(unsigned long long) * D);
     const size_t o_reb = off; off += align256(sizeof(unsigned int) * D);
     const size_t o_scal = off; off += align256(sizeof(double) * D * 4);
-    const size_t nbr_per_cta = sizeof(unsigned int) * (CAP / 2) * (size_t)N;
+    const size_t nbr_per_cta = sizeof(unsigned int) * NBR_WORDS * (size_t)N;
     if (off + nbr_per_cta > NOALLOC_BYTES)
         return noalloc_fail(TTCF_E_INVALID,
                             "ttcf_run_noalloc: batch needs more than the 32 MiB static scratch "

@@ -141,6 +141,38 @@ def test_first_50_steps_follow_the_oracle(ttcf, eq_mothers_256, precision, tol_x
                 assert np.abs(B[4 * g + m] - Bo).max() < (1e-10 if precision == 0 else 1e-4) * scale
 
 
+def test_fp64_active_lists_under_strong_shear_follow_the_oracle(ttcf, eq_mothers_256):
+    """FP64 force passes walk each atom's active list (the Verlet entries
+    within r_c + 0.1 sigma, refreshed from the sorted Verlet list when an
+    atom's path length or the Lees-Edwards offset could close the gap).  At
+    gamma = 1 the offset alone forces a refresh every few steps and the
+    Verlet lists are rebuilt often: 300 steps of 8 daughters against the
+    oracle, positions and momenta to 1e-9."""
+    b, ms, al = eq_mothers_256
+    G, n, gamma = 2, 300, 1.0
+    with ctx(ttcf, precision=0, n_steps=n, keep_state=1) as c:
+        bid = c.spawn_daughters(ms[:G], al[:G], gamma, box=b.L)
+        c.run()
+        st = c.get_stats()
+        B, _ = c.daughter_series(bid, 4 * G)
+        states = [c.get_state(bid, d, b.n) for d in range(4 * G)]
+    assert st["rebuilds"] > 4 * G * 3
+    Lx, Ly, Lz = b.L
+    for d in range(4 * G):
+        Bo, _, fin, fa = oracle.daughter(b, ms[d // 4], al[d // 4], d % 4, gamma, n)
+        s, a, delta = states[d]
+        # Lees-Edwards minimum image: a y image carries the x offset delta
+        dx, dy, dz = s[:3] - fin[:3]
+        ny = np.rint(dy / Ly)
+        dy, dx = dy - ny * Ly, dx - ny * delta
+        dx -= Lx * np.rint(dx / Lx)
+        dz -= Lz * np.rint(dz / Lz)
+        assert max(np.abs(dx).max(), np.abs(dy).max(), np.abs(dz).max()) < 1e-9, d
+        assert np.abs(s[3:] - fin[3:]).max() < 1e-9, d
+        assert a == pytest.approx(fa, abs=1e-9)
+        assert np.abs(B[d] - Bo).max() < 1e-9 * np.abs(Bo).max(), d
+
+
 def test_config1_fp64_ensemble_matches_oracle(ttcf):
     """N=256, 10 mother states 200 steps apart, x4 mappings, 500 steps at
     gamma = 1e-3, FP64 (the smallest configuration, in full)."""
