@@ -295,13 +295,14 @@ def bench_gb300(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(st)
-    kernel_ms, pairs, rebuilds, launches = [], [], [], 0
+    kernel_ms, spawn_ms, pairs, rebuilds, launches = [], [], [], [], 0
     per_rate = {}
     for k in range(args.steps):
         g = RATES[k % len(RATES)]
         v, r, s = one_step(T, args, L, g, ms_dev, al_dev, want_response=world > 1)
         per_rate[g] = (v, r)
         kernel_ms.append(s["ms_run"])
+        spawn_ms.append(s["ms_spawn"])
         pairs.append(s["pairs_interacting"])
         rebuilds.append(s["rebuilds"])
         launches += s["launches"] + 1            # + the spawn kernel
@@ -349,6 +350,7 @@ def bench_gb300(args):
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 5), "traffic": traffic,
                 "kernel": "daughter_kernel", "kernel_ms": round(k_ms, 2),
+                "spawn_ms": round(float(np.mean(spawn_ms)), 2),
                 "peak_src": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
     # the one exchange of the weak-scaled job: per-rate ensemble statistics
     # merged over ranks (each rank's groups are independent)

@@ -237,7 +237,8 @@ ttcf_status ttcf_get_state(ttcf_ctx *ctx, int batch_id, int daughter, double *so
 
 /* Work counters of the last ttcf_run: device time of the persistent
  * launch(es) measured with CUDA events on the context's stream (ms), the
- * spawn and reduce times (ms), the number of interacting ordered pairs
+ * device time of the spawn kernels of the batches this run is the first
+ * to cover and of the reductions (ms), the number of interacting ordered pairs
  * (r < r_c) summed over all atoms and steps, the number of Verlet-list
  * rebuilds, atom-steps, and kernel launches issued.                        */
 typedef struct {

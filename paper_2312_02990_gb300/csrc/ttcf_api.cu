@@ -93,6 +93,7 @@ struct ttcf_ctx {
     int *h_abort = nullptr, *d_abort = nullptr;
     cudaStream_t cap_st = nullptr;   // private stream for CUDA-graph capture
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double ms_spawn_pending = 0.0;   // spawn-kernel time not yet reported by a ttcf_run
     ttcf_stats stats;
     // launch tables, rebuilt when batches change
     bool tables_ok = false;
@@ -308,8 +309,13 @@ ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const dou
     sa.mixed = cf.precision == TTCF_MIXED;
     sa.src = src; sa.gamma = b.gamma_d; sa.mothers = b.mothers;
     sa.B = b.B; sa.S = S; sa.Omega = b.Omega; sa.feat = b.feat; sa.delta = delta0;
+    CK(cudaEventRecord(ctx->ev[2], st));
     CK(launch_spawn(sa, st));
+    CK(cudaEventRecord(ctx->ev[3], st));
     CK(cudaStreamSynchronize(st));   // before the temporary copy is released
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    ctx->ms_spawn_pending += ms;
     return TTCF_OK;
 }
 
@@ -699,8 +705,13 @@ ttcf_status make_conf_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, cons
     sa.inner_y[0] = b.inner_y[0]; sa.inner_y[1] = b.inner_y[1];
     sa.src = src; sa.gamma = b.gamma_d; sa.types = b.types; sa.lattice = b.lattice;
     sa.mothers = b.mothers; sa.B = b.B; sa.Omega = b.Omega;
+    CK(cudaEventRecord(ctx->ev[2], st));
     CK(launch_conf_spawn(sa, st));
+    CK(cudaEventRecord(ctx->ev[3], st));
     CK(cudaStreamSynchronize(st));   // before the temporary copy is released
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    ctx->ms_spawn_pending += ms;
     return TTCF_OK;
 }
 
@@ -780,6 +791,8 @@ ttcf_status run_confined(ttcf_ctx *ctx, int n_steps) {
     ctx->ran = true;
     *(volatile int *)ctx->h_abort = 0;
     memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.ms_spawn = ctx->ms_spawn_pending;
+    ctx->ms_spawn_pending = 0.0;
     for (auto &b : ctx->batches) {
         ttcf_status r = ensure_reduce_buffers(ctx, b);
         if (r != TTCF_OK) return r;
@@ -987,6 +1000,8 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
     ctx->ran = true;
     *(volatile int *)ctx->h_abort = 0;
     memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.ms_spawn = ctx->ms_spawn_pending;   // the spawns this run is the first to cover
+    ctx->ms_spawn_pending = 0.0;
 
     RunArgs a;
     memset(&a, 0, sizeof(a));

@@ -152,8 +152,10 @@ def test_n2048_launch_shape_follows_the_oracle(ttcf, mothers_2048, shape):
         c.run()
         B, Om = c.daughter_series(bid, 8)
         states = [c.get_state(bid, d, b.n) for d in range(8)]
+        st = c.get_stats()
+        assert st["ms_spawn"] > 0.0 and st["ms_run"] > 0.0
         if shape == "bench":
-            assert c.get_stats()["skin"] == pytest.approx(0.4)
+            assert st["skin"] == pytest.approx(0.4)
     L = np.asarray(b.L)[:, None]
     for d in range(8):
         Bo, omo, fin, fa = oracle.daughter(b, ms[d // 4], al[d // 4], d % 4, gamma, n)
