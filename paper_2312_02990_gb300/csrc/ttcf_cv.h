@@ -12,7 +12,7 @@ constexpr int CV_H = 128;    // hidden units per layer
 constexpr int CV_NP = CV_H * CV_NF + CV_H + CV_H * CV_H + CV_H + CV_H + 1;   // 20865
 
 struct CvFeatArgs {
-    const double *raw;      // [G][FEAT_RAW] from the spawn kernel
+    const double *raw;      // [G][FEAT_RAW] from the features kernel
     const double *alpha;    // [G] mother alpha, or null
     int reset_alpha;
     int M;
@@ -25,8 +25,8 @@ struct CvFeatArgs {
 
 cudaError_t cv_launch_features(const CvFeatArgs &a, cudaStream_t st);
 
-// Raw features (FEAT_RAW doubles per state, the layout the spawn kernel
-// writes) of G phase points of one bulk system, in FP32 arithmetic with
+// Raw features (FEAT_RAW doubles per state, the layout of FEAT_RAW) of G
+// phase points of one bulk system, in FP32 arithmetic with
 // FP64 block sums: kinetic sums, WCA virial and energy, sum p^2, slab modes.
 // src holds [G][6][N] values: IEEE doubles (kind 0) or float-pair slots
 // (kind 1, hi part used); both give the same FP32 inputs.

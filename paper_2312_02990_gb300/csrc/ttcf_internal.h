@@ -46,10 +46,12 @@ struct SpawnArgs {
 };
 cudaError_t launch_spawn(const SpawnArgs &a, cudaStream_t st);
 
-// Raw per-mother features written by the spawn kernel: K_ab = sum p_a p_b
-// (6: xx yy zz xy xz yz), W_ab virial sums (6), U, sum p^2, then for
-// q = 1..4 (cos, sin) modes over 40 slabs in y of the density (8) and of the
-// x momentum (8), each divided by N; two unused slots.
+// Raw per-state features: K_ab = sum p_a p_b (6: xx yy zz xy xz yz), W_ab
+// virial sums (6), U, sum p^2, then for q = 1..4 (cos, sin) modes over 40
+// slabs in y of the density (8) and of the x momentum (8), each divided by
+// N; two unused slots.  The spawn kernel writes the first 14 (its pressure
+// tensor pass) and zeros; the FP32 features kernel of the control variate
+// writes all of them.
 constexpr int FEAT_RAW = 32;
 size_t spawn_smem_bytes(int N, int ncell);
 

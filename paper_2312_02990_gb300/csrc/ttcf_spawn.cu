@@ -15,7 +15,7 @@
 
 namespace ttcf {
 
-constexpr int NSLAB = 40, NMODE = 4, NACC = 13 + 4 * NMODE;
+constexpr int NACC = 13;   // K_ab (6), W_ab (6), U
 
 size_t spawn_smem_bytes(int N, int ncell) {
     return (size_t)N * 24 + (size_t)(2 * ncell + 2) * 4 + ((size_t)N * 2 + 15) / 16 * 16 +
@@ -46,12 +46,18 @@ __global__ void spawn_kernel(SpawnArgs a) {
     int *warp_tmp = (int *)(red + 32 * NACC);
 
     const double invL[3] = {1.0 / a.L[0], 1.0 / a.L[1], 1.0 / a.L[2]};
-    for (int i = tid; i < N; i += T) {
+    // the mother into the daughter kernel's state format; in MIXED the same
+    // float pairs are this pass's positions (one conversion per value)
+    unsigned long long *dst = a.mothers + (size_t)g * 6 * N;
+    for (int e = tid; e < 6 * N; e += T) {
+        const double v = src[e];
         if (a.mixed) {
-            const df x = df_from_double(src[i]), y = df_from_double(src[N + i]), z = df_from_double(src[2 * N + i]);
-            xh[i] = x.hi; xl[i] = x.lo; yh[i] = y.hi; yl[i] = y.lo; zh[i] = z.hi; zl[i] = z.lo;
+            const df q = df_from_double(v);
+            reinterpret_cast<float2 *>(dst)[e] = make_float2(q.hi, q.lo);
+            if (e < 3 * N) { xh[e] = q.hi; xh[3 * N + e] = q.lo; }   // rows x, y, z: hi, then lo
         } else {
-            xd[i] = src[i]; yd[i] = src[N + i]; zd[i] = src[2 * N + i];
+            reinterpret_cast<double *>(dst)[e] = v;
+            if (e < 3 * N) xd[e] = v;
         }
     }
     for (int c = tid; c < a.ncell; c += T) cnt[c] = 0;
@@ -91,20 +97,15 @@ __global__ void spawn_kernel(SpawnArgs a) {
     }
     __syncthreads();
 
-    // cosine/sine of 2 pi q (k + 1/2) / 40 for the 40 slabs in y, q = 1..4
-    __shared__ double cs_tab[NSLAB][2 * NMODE];
-    for (int e = tid; e < NSLAB * NMODE; e += T) {
-        const int k = e / NMODE, q = e % NMODE + 1;
-        double sn, c;
-        sincospi(2.0 * q * (k + 0.5) / NSLAB, &sn, &c);
-        cs_tab[k][2 * (q - 1)] = c;
-        cs_tab[k][2 * (q - 1) + 1] = sn;
-    }
-    __syncthreads();
-    // partial sums: kinetic K_ab (6), virial W_ab (6), U, then the density
-    // modes (8) and x-momentum modes (8) over the slabs
+    // partial sums: kinetic K_ab (6), virial W_ab (6), U in IEEE double;
+    // in MIXED the pair sums of a thread's atoms run in double-float pairs
+    // on the FP32 pipe (pwt) and are converted once (on GB300 the FP64 pipe,
+    // conversions included, is the bound of this pass).  The CTA reduction
+    // is IEEE double in both modes.
     double acc[NACC];
     for (int k = 0; k < NACC; k++) acc[k] = 0.0;
+    df pwt[7];
+    for (int k = 0; k < 7; k++) pwt[k] = df_make(0.f);
     const double rc2 = 1.2599210498948732;
     const float rc2_screen = 1.2599210498948732f * (1.0f + 1e-4f);   // hi parts: |error| << 1e-4 r_c^2
     const float Lf[3] = {(float)a.L[0], (float)a.L[1], (float)a.L[2]};
@@ -113,20 +114,12 @@ __global__ void spawn_kernel(SpawnArgs a) {
     const df Ld[3] = {df_from_double(a.L[0]), df_from_double(a.L[1]), df_from_double(a.L[2])};
     const df deltad = df_from_double(a.delta);
     const df rc2d = df_from_double(rc2);
-    for (int i = tid; i < N; i += T) {
+    for (int q = 0, i = tid; i < N; i += T, q++) {
         const double px = src[3 * N + i], py = src[4 * N + i], pz = src[5 * N + i];
         acc[0] += px * px; acc[1] += py * py; acc[2] += pz * pz;
         acc[3] += px * py; acc[4] += px * pz; acc[5] += py * pz;
-        {
-            int k = (int)floor((src[N + i] + 0.5 * a.L[1]) * invL[1] * NSLAB);
-            k = min(max(k, 0), NSLAB - 1);
-            for (int u = 0; u < 2 * NMODE; u++) {
-                acc[13 + u] += cs_tab[k][u];
-                acc[13 + 2 * NMODE + u] += px * cs_tab[k][u];
-            }
-        }
-        int cx, cy, cz;
-        cell3(i, cx, cy, cz);
+        // the cell from the binning pass (same atoms, same order)
+        const int cx = cid[q] % a.nc[0], cy = (cid[q] / a.nc[0]) % a.nc[1], cz = cid[q] / (a.nc[0] * a.nc[1]);
         if (!a.mixed) {   // FP64 mode: the pair sums in IEEE double
             for (int oy = -1; oy <= 1; oy++) {
                 int yy = cy + oy;
@@ -161,9 +154,7 @@ __global__ void spawn_kernel(SpawnArgs a) {
             }
             continue;
         }
-        // pair sums of atom i as double-float pairs: 0.5 f d_a d_b, 0.5 U
-        df pw[7];
-        for (int k = 0; k < 7; k++) pw[k] = df_make(0.f);
+        // pair sums as double-float pairs: 0.5 f d_a d_b, 0.5 U
         const df xi = {xh[i], xl[i]}, yi = {yh[i], yl[i]}, zi = {zh[i], zl[i]};
         for (int oy = -1; oy <= 1; oy++) {
             int yy = cy + oy;
@@ -202,18 +193,19 @@ __global__ void spawn_kernel(SpawnArgs a) {
                         const df s3 = df_mul(df_mul(sv, sv), sv);
                         const df hf = df_mul_f(df_mul(df_mul(s3, sv), df_add_f(df_mul_f(s3, 48.0f), -24.0f)), 0.5f);
                         const df hx = df_mul(hf, dx), hy = df_mul(hf, dy);
-                        pw[0] = df_add(pw[0], df_mul(hx, dx)); pw[1] = df_add(pw[1], df_mul(hy, dy));
-                        pw[2] = df_add(pw[2], df_mul(df_mul(hf, dz), dz)); pw[3] = df_add(pw[3], df_mul(hx, dy));
-                        pw[4] = df_add(pw[4], df_mul(hx, dz)); pw[5] = df_add(pw[5], df_mul(hy, dz));
+                        pwt[0] = df_add(pwt[0], df_mul(hx, dx)); pwt[1] = df_add(pwt[1], df_mul(hy, dy));
+                        pwt[2] = df_add(pwt[2], df_mul(df_mul(hf, dz), dz)); pwt[3] = df_add(pwt[3], df_mul(hx, dy));
+                        pwt[4] = df_add(pwt[4], df_mul(hx, dz)); pwt[5] = df_add(pwt[5], df_mul(hy, dz));
                         // 0.5 (4 s3 (s3 - 1) + 1)
-                        pw[6] = df_add(pw[6], df_mul_f(df_add_f(df_mul_f(df_mul(s3, df_add_f(s3, -1.0f)), 4.0f), 1.0f),
+                        pwt[6] = df_add(pwt[6], df_mul_f(df_add_f(df_mul_f(df_mul(s3, df_add_f(s3, -1.0f)), 4.0f), 1.0f),
                                                        0.5f));
                     }
                 }
             }
         }
-        for (int k = 0; k < 7; k++) acc[6 + k] += df_to_double(pw[k]);
     }
+    if (a.mixed)
+        for (int k = 0; k < 7; k++) acc[6 + k] = df_to_double(pwt[k]);
     // fixed-order CTA reduction
     const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     for (int k = 0; k < NACC; k++) {
@@ -243,20 +235,7 @@ __global__ void spawn_kernel(SpawnArgs a) {
             for (int k = 0; k < 12; k++) f[k] = tot[k];          // K_ab, W_ab
             f[12] = tot[12];                                      // U
             f[13] = tot[0] + tot[1] + tot[2];                     // sum p^2
-            for (int u = 0; u < 4 * NMODE; u++) f[14 + u] = tot[13 + u] / N;   // modes
-            f[30] = f[31] = 0.0;
-        }
-    }
-    // mother into the daughter kernel's state format
-    unsigned long long *dst = a.mothers + (size_t)g * 6 * N;
-    for (int e = tid; e < 6 * N; e += T) {
-        const double v = src[e];
-        if (a.mixed) {
-            const float h = __double2float_rn(v);
-            const float l = __double2float_rn(v - (double)h);
-            reinterpret_cast<float2 *>(dst)[e] = make_float2(h, l);
-        } else {
-            reinterpret_cast<double *>(dst)[e] = v;
+            for (int u = 14; u < FEAT_RAW; u++) f[u] = 0.0;   // (the slab modes: features kernel)
         }
     }
 }
