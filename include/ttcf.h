@@ -316,8 +316,8 @@ ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_s
 /* Autotuner (launch shape, Verlet skin and list-cell width).  Times
  * n_steps of the daughter kernel on n_states phase points [n_states][6][N]
  * (host; all four mappings, shear rate gamma) for every launch variant that
- * holds n_atoms, Verlet skins {0.3, 0.4, 0.5, 0.6} and cell widths
- * {1/2, 2/3} (r_c + skin), with CUDA events on the context's stream, and
+ * holds n_atoms, Verlet skins {0.3, 0.35, 0.4, 0.5, 0.6} and cell widths
+ * {1/2, 2/3, 1} (r_c + skin), with CUDA events on the context's stream, and
  * remembers the fastest for batches of n_atoms spawned later on this
  * context (explicit kernel_variant / skin / cell_frac in the config still
  * win).  Returns the choice (1-based variant as in

@@ -1429,13 +1429,13 @@ ttcf_status ttcf_autotune(ttcf_ctx *ctx, int n_atoms, const double box[3], int n
         return fail(ctx, TTCF_E_INVALID, "bad autotune arguments");
     if (ctx->cfg.system != TTCF_BULK_WCA)
         return fail(ctx, TTCF_E_INVALID, "ttcf_autotune needs a TTCF_BULK_WCA context");
-    const double skins[4] = {0.3, 0.4, 0.5, 0.6};
+    const double skins[5] = {0.3, 0.35, 0.4, 0.5, 0.6};
     const int maps[4] = {0, 1, 2, 3};
     std::vector<double> gam(n_states, shear_rate);
     double best = 1e300;
     int bv = -1;
     double bskin = DEFAULT_SKIN, bfrac = DEFAULT_CELL_FRAC;
-    const double fracs[2] = {0.5, 2.0 / 3.0};
+    const double fracs[3] = {0.5, 2.0 / 3.0, 1.0};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
