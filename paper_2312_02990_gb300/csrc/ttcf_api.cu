@@ -203,7 +203,7 @@ void pick_cells(ttcf_ctx *ctx, BatchHost &b, double rl, double frac) {
         int nc[3];
         for (int k = 0; k < 3; k++) nc[k] = std::max(3, (int)floor(b.L[k] / (rl * fracs[f])));
         const int ncell = nc[0] * nc[1] * nc[2];
-        const size_t sm = daughter_smem_bytes(mixed, b.N, ncell);
+        const size_t sm = daughter_smem_bytes(mixed, b.N, ncell, false, !plo_global(mixed, b.variant));
         if (f == 2 || (size_t)v.minb * (sm + 1024) <= (size_t)ctx->smem_per_sm) {
             for (int k = 0; k < 3; k++) b.nc[k] = nc[k];
             b.ncell = ncell;
@@ -353,14 +353,15 @@ std::vector<ClassLaunch> plan_classes(ttcf_ctx *ctx, std::vector<BatchHost *> &b
     }
     const bool mixed = ctx->cfg.precision == TTCF_MIXED;
     for (auto &c : cls) {
-        c.smem = daughter_smem_bytes(mixed, c.nmax, c.ncellmax);
+        const bool plo_smem = !plo_global(mixed, c.variant);
+        c.smem = daughter_smem_bytes(mixed, c.nmax, c.ncellmax, false, plo_smem);
         c.grid = 0;
         c.cpos = 0;
         if (c.smem > (size_t)ctx->smem_optin) continue;   // rejected by the caller
         int nb = daughter_occupancy(mixed, c.variant, c.threads, c.smem);
         {   // the cell-ordered list build where its larger shared memory keeps
             // the variant's resident CTAs per SM
-            const size_t s2 = daughter_smem_bytes(mixed, c.nmax, c.ncellmax, true);
+            const size_t s2 = daughter_smem_bytes(mixed, c.nmax, c.ncellmax, true, plo_smem);
             if (s2 <= (size_t)ctx->smem_optin) {
                 const int nb2 = daughter_occupancy(mixed, c.variant, c.threads, s2);
                 if (nb2 >= 1 && nb2 >= std::min(nb, variant_of(c.variant).minb)) {
@@ -406,9 +407,13 @@ ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &
     CK(cudaMemsetAsync(d_q, 0, sizeof(int) * cls.size(), st));
     std::vector<int *> d_work(cls.size());
     std::vector<unsigned int *> d_nbr(cls.size());
+    std::vector<float4 *> d_plo(cls.size(), nullptr);
+    const bool mixed_run = ctx->cfg.precision == TTCF_MIXED;
     for (size_t k = 0; k < cls.size(); k++) {
         d_work[k] = pool.get<int>(cls[k].work.size());
         d_nbr[k] = pool.get<unsigned int>((size_t)cls[k].grid * NBR_WORDS * cls[k].nmax);
+        if (plo_global(mixed_run, cls[k].variant))
+            d_plo[k] = pool.get<float4>((size_t)cls[k].grid * cls[k].nmax);
         if (pool.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (work lists)");
         CK(cudaMemcpyAsync(d_work[k], cls[k].work.data(), sizeof(int) * cls[k].work.size(),
                            cudaMemcpyHostToDevice, st));
@@ -462,6 +467,7 @@ ttcf_status launch_batches(ttcf_ctx *ctx, Pool &pool, std::vector<BatchHost *> &
             a.n_work = (int)cls[k].work.size();
             a.queue = d_q + k;
             a.nbr = d_nbr[k]; a.nmax = cls[k].nmax; a.ncellmax = cls[k].ncellmax;
+            a.plo_g = d_plo[k];
             a.cpos = cls[k].cpos;
             CK(launch_daughters(mixed, cls[k].variant, a, cls[k].threads, cls[k].grid, cls[k].smem, side[k]));
             launches++;

@@ -223,7 +223,11 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
     double *xd = nullptr, *yd = nullptr, *zd = nullptr;
     if constexpr (MIXED) {
         pos4 = (float4 *)sp; sp += (size_t)nmax * 16;
-        plo4 = (float4 *)sp; sp += (size_t)nmax * 16;
+        if constexpr (APT >= 8) {   // plo_global: lo parts in the per-CTA global scratch
+            plo4 = a.plo_g + (size_t)blockIdx.x * nmax;
+        } else {
+            plo4 = (float4 *)sp; sp += (size_t)nmax * 16;
+        }
     } else {   // each array padded to 16 bytes: ref4 below must stay float4-aligned
         const size_t dn = ((size_t)nmax * 8 + 15) / 16 * 16;
         xd = (double *)sp; sp += dn;

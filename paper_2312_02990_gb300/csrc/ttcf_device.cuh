@@ -303,6 +303,7 @@ struct RunArgs {
     int snap_first, snap_every, n_snap;
     double *force_out;             // [D][3][N] forces at step0, or null
     double *wxy_out;               // [D] virial W_xy at step0, or null
+    float4 *plo_g;                 // [grid][nmax] position lo parts (plo_global variants)
     int cpos;                      // shared-memory layout: 1 = cell-ordered wrapped
                                    // positions for the list build, 0 = cell members'
                                    // indices only (see daughter_smem_bytes)
@@ -334,9 +335,17 @@ __host__ __device__ inline int default_variant(int N) {
 // ttcf_daughter.cu).  cpos: the list build reads a cell-ordered copy of the
 // wrapped positions (16 bytes per atom) instead of the cell members' indices
 // (2 bytes per atom).
+// The MIXED variant of 8 atoms per thread keeps the lo parts of its
+// positions in a per-CTA global scratch ([grid][nmax] float4, read and
+// written by the owner thread in phase A only) rather than in shared
+// memory; the 16 bytes per atom it frees let its N ~ 4000 daughters use the
+// cell-ordered list build.
+__host__ __device__ inline bool plo_global(bool mixed, int variant) { return mixed && variant >= 5; }
+
 __host__ __device__ inline size_t daughter_smem_bytes(bool mixed, int nmax, int ncellmax,
-                                                      bool cpos = false) {
-    size_t b = mixed ? (size_t)nmax * 48 : 3 * (((size_t)nmax * 8 + 15) / 16 * 16) + (size_t)nmax * 16;
+                                                      bool cpos = false, bool plo_smem = true) {
+    size_t b = mixed ? (size_t)nmax * (plo_smem ? 48 : 32)
+                     : 3 * (((size_t)nmax * 8 + 15) / 16 * 16) + (size_t)nmax * 16;
     b += (size_t)ncellmax * 4 + (size_t)(ncellmax + 2) * 4;
     b += cpos ? (size_t)nmax * 16 : ((size_t)nmax * 2 + 15) / 16 * 16;
     b += 2048;   // coefficients, reduction slots and flags

@@ -141,7 +141,10 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     const size_t o_reb = off; off += align256(sizeof(unsigned int) * D);
     const size_t o_scal = off; off += align256(sizeof(double) * D * 4);
     const size_t nbr_per_cta = sizeof(unsigned int) * NBR_WORDS * (size_t)N;
-    if (off + nbr_per_cta > NOALLOC_BYTES)
+    // per CTA: its neighbour lists and, for the plo_global variant, the lo
+    // parts of its daughter's positions
+    const size_t plo_per_cta = plo_global(mixed, variant) ? sizeof(float4) * (size_t)N : 0;
+    if (off + nbr_per_cta + plo_per_cta > NOALLOC_BYTES)
         return noalloc_fail(TTCF_E_INVALID,
                             "ttcf_run_noalloc: batch needs more than the 32 MiB static scratch "
                             "(reduce n_mothers or n_atoms, or use ttcf_spawn_daughters)");
@@ -185,7 +188,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
             int ncf[3];
             for (int k = 0; k < 3; k++) ncf[k] = std::max(3, (int)floor(box[k] / (rl * fracs[f])));
             const int ncell = ncf[0] * ncf[1] * ncf[2];
-            const size_t sm = daughter_smem_bytes(mixed, N, ncell);
+            const size_t sm = daughter_smem_bytes(mixed, N, ncell, false, !plo_global(mixed, variant));
             if (f == 2 || (size_t)v.minb * (sm + 1024) <= (size_t)per_sm) {
                 for (int k = 0; k < 3; k++) bd.nc[k] = ncf[k];
                 bd.ncell = ncell;
@@ -193,13 +196,14 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
             }
         }
     }
-    size_t smem = daughter_smem_bytes(mixed, N, bd.ncell);
+    const bool plo_smem = !plo_global(mixed, variant);
+    size_t smem = daughter_smem_bytes(mixed, N, bd.ncell, false, plo_smem);
     if (smem > (size_t)optin)
         return noalloc_fail(TTCF_E_INVALID, "ttcf_run_noalloc: daughter needs more shared memory than a CTA has");
     int nb = daughter_occupancy(mixed, variant, threads, smem);
     int cpos = 0;
     {
-        const size_t s2 = daughter_smem_bytes(mixed, N, bd.ncell, true);
+        const size_t s2 = daughter_smem_bytes(mixed, N, bd.ncell, true, plo_smem);
         if (s2 <= (size_t)optin) {
             const int nb2 = daughter_occupancy(mixed, variant, threads, s2);
             if (nb2 >= 1 && nb2 >= std::min(nb, v.minb)) { cpos = 1; smem = s2; nb = nb2; }
@@ -207,7 +211,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
     }
     if (nb < 1) nb = 1;
     long long grid = std::min<long long>(D, (long long)nb * nsm);
-    grid = std::min<long long>(grid, (long long)((NOALLOC_BYTES - off) / nbr_per_cta));
+    grid = std::min<long long>(grid, (long long)((NOALLOC_BYTES - off) / (nbr_per_cta + plo_per_cta)));
     if (grid < 1) grid = 1;
 
     cudaStream_t st = (cudaStream_t)c.stream;
@@ -251,6 +255,7 @@ extern "C" ttcf_status ttcf_run_noalloc(const ttcf_config *cfg, int n_atoms, con
         a.batches = d_b; a.work = d_work; a.dbatch = d_dbatch; a.n_work = (int)D;
         a.queue = d_queue;
         a.nbr = (unsigned int *)(base + off);
+        a.plo_g = plo_per_cta ? (float4 *)(base + off + (size_t)grid * nbr_per_cta) : nullptr;
         a.nmax = N; a.ncellmax = bd.ncell; a.cpos = cpos;
         a.step0 = 0; a.step1 = c.n_steps; a.sample_every = c.sample_every;
         a.fresh = 1; a.save_state = 0; a.reset_alpha = c.reset_alpha;
