@@ -30,12 +30,14 @@ def env():
     return torch, T, b, ms, al
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_noalloc_matches_the_allocating_path_twice(env, precision):
+# variant 6 (8 atoms per thread) keeps the lo parts of its positions in the
+# per-CTA scratch the no-allocation path carves from its static array
+@pytest.mark.parametrize("precision,variant", [(0, 0), (1, 0), (1, 6)])
+def test_noalloc_matches_the_allocating_path_twice(env, precision, variant):
     torch, T, b, ms, al = env
     G, n, gamma = ms.shape[0], 60, 1e-3
     cfg = T.config_default()
-    cfg.precision, cfg.n_steps = precision, n
+    cfg.precision, cfg.n_steps, cfg.kernel_variant = precision, n, variant
     with T.Context(cfg) as c:
         bid = c.spawn_daughters(ms, al, gamma, box=b.L)
         c.run()
@@ -45,7 +47,7 @@ def test_noalloc_matches_the_allocating_path_twice(env, precision):
     a_t = torch.from_numpy(al).to(dev)
     g_t = torch.full((G,), gamma, dtype=torch.float64, device=dev)
     cfg2 = T.config_default()
-    cfg2.precision, cfg2.n_steps = precision, n
+    cfg2.precision, cfg2.n_steps, cfg2.kernel_variant = precision, n, variant
     cfg2.stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         B = torch.full((4 * G, n + 1), np.nan, dtype=torch.float64, device=dev)
