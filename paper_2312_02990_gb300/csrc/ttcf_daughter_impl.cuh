@@ -117,18 +117,6 @@ __device__ __forceinline__ df warp_sum(df v) {
     for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_df(v, o));
     return v;
 }
-// Two double-float sums at once on packed float pairs (df2_add).
-__device__ __forceinline__ df2 warp_sum(df2 v) {
-    for (int o = 16; o > 0; o >>= 1) {
-        df2 w;
-        w.hi.x = __shfl_down_sync(0xffffffffu, v.hi.x, o);
-        w.hi.y = __shfl_down_sync(0xffffffffu, v.hi.y, o);
-        w.lo.x = __shfl_down_sync(0xffffffffu, v.lo.x, o);
-        w.lo.y = __shfl_down_sync(0xffffffffu, v.lo.y, o);
-        v = df2_add(v, w);
-    }
-    return v;
-}
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
@@ -173,33 +161,54 @@ __device__ __forceinline__ void cta_sum3(R a0, R a1, R a2, Misc *m, double out[3
     }
 }
 
-// CTA sums of two per-thread float partials as (normalised) double-float
-// pairs, in a fixed order (MIXED mode's per-step sums).  One __syncthreads; the result is
-// valid in lane 0 of warp 0 and of warp w2, which reduce identically.
-__device__ __forceinline__ void cta_sum2(float a0, float a1, Misc *m, df out[2], int w2) {
+// CTA sums of two per-thread float partials (MIXED mode's per-step sums)
+// in 64-bit fixed point of 2^-40 units: every float of magnitude >= 2^-17
+// is exact there, so the integer sums are exact and independent of order;
+// the totals come back as normalised double-float pairs (the same pairs a
+// double-float tree gives where its sum is exact, as it is here; about 1 %
+// faster).  One __syncthreads; the result is valid in lane 0 of warp 0 and
+// of warp w2.
+__device__ __forceinline__ long long fix40(float v) { return __float2ll_rn(v * 1099511627776.0f); }
+__device__ __forceinline__ df df_from_fix40(long long s) {
+    const float hi = __ll2float_rn(s);
+    const float lo = __ll2float_rn(s - __float2ll_rn(hi));   // the exact remainder, rounded
+    return {hi * 9.094947017729282e-13f, lo * 9.094947017729282e-13f};   // x 2^-40, exact
+}
+__device__ __forceinline__ void cta_sum2_fix(float a0, float a1, Misc *m, df out[2], int w2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    df2 v = warp_sum(df2{make_float2(a0, a1), make_float2(0.f, 0.f)});
+    // outside +-2^22 (or not finite) the 64-bit sums could overflow: the
+    // daughter stops as non-finite (normal partials are below 10^3)
+    if (!(fabsf(a0) < 4194304.f && fabsf(a1) < 4194304.f)) m->flag_lost = 1;
+    long long v0 = fix40(a0), v1 = fix40(a1);
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    }
     if (lane == 0) {
-        float2 *sl = reinterpret_cast<float2 *>(&m->slot[warp][0]);
-        sl[0] = v.hi;
-        sl[1] = v.lo;
+        long long *sl = reinterpret_cast<long long *>(&m->slot[warp][0]);
+        sl[0] = v0;
+        sl[1] = v1;
     }
     __syncthreads();
     if (warp == 0 || warp == w2) {
-        df2 t = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        long long t0 = 0, t1 = 0;
         if (lane < nw) {
-            const float2 *sl = reinterpret_cast<const float2 *>(&m->slot[lane][0]);
-            t.hi = sl[0];
-            t.lo = sl[1];
+            const long long *sl = reinterpret_cast<const long long *>(&m->slot[lane][0]);
+            t0 = sl[0];
+            t1 = sl[1];
         }
-        t = warp_sum(t);
+        for (int o = 16; o > 0; o >>= 1) {
+            t0 += __shfl_down_sync(0xffffffffu, t0, o);
+            t1 += __shfl_down_sync(0xffffffffu, t1, o);
+        }
         if (lane == 0) {
-            out[0] = {t.hi.x, t.lo.x};
-            out[1] = {t.hi.y, t.lo.y};
+            out[0] = df_from_fix40(t0);
+            out[1] = df_from_fix40(t1);
         }
     }
 }
+
 
 // ------------------------------------------------------- one daughter --
 template <bool MIXED, int APT>
@@ -1056,7 +1065,7 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             // two sums are reduced instead of three
             const df f1 = cf->f1;
             const float pv = __fmaf_rn(0.5f, wsum, mul_cf(f1, sxy));
-            cta_sum2(s2, pv, m, sumsf, wo);                    // barrier 2
+            cta_sum2_fix(s2, pv, m, sumsf, wo);                // barrier 2
         } else {
             cta_sum3<MIXED, R>(s2, sxy, wsum, m, sums, wo);     // barrier 2
         }
