@@ -210,6 +210,39 @@ __device__ __forceinline__ void cta_sum2_fix(float a0, float a1, Misc *m, df out
 }
 
 
+// ------------------------------------------------ sorting a Verlet list --
+// Compare-exchange of the uint16 halves of two registers (both halves in
+// the same direction), and of the two halves of one register.
+__device__ __forceinline__ void ce_reg(unsigned int &a, unsigned int &b, bool asc) {
+    const unsigned int lo = __vminu2(a, b), hi = __vmaxu2(a, b);
+    a = asc ? lo : hi;
+    b = asc ? hi : lo;
+}
+__device__ __forceinline__ unsigned int ce_half(unsigned int x, bool asc) {
+    const unsigned int s = __byte_perm(x, 0u, 0x1032);   // halves swapped
+    const unsigned int mn = __vminu2(x, s), mx = __vmaxu2(x, s);
+    return asc ? __byte_perm(mn, mx, 0x7610) : __byte_perm(mx, mn, 0x7610);
+}
+// Bitonic sort of 32 uint16 keys, key e in half (e & 1) of r[e / 2],
+// ascending: merges of sizes 2, 4, ..., 32, compare distances j halving;
+// distances >= 2 pair two registers, distance 1 the halves of one.
+static_assert(CAP == 32, "sort32_u16 sorts the 32 slots of a Verlet list");
+__device__ __forceinline__ void sort32_u16(unsigned int r[16]) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j >= 2; j >>= 1) {
+#pragma unroll
+            for (int m = 0; m < 16; m++) {
+                const int mp = m ^ (j >> 1);
+                if (mp > m) ce_reg(r[m], r[mp], ((2 * m) & k) == 0);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 16; m++) r[m] = ce_half(r[m], ((2 * m) & k) == 0);
+    }
+}
+
 // ------------------------------------------------------- one daughter --
 template <bool MIXED, int APT>
 __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned char *smem) {
@@ -485,10 +518,13 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
             // once after it: an insertion inside the divergent scan loops
             // would be paid by every lane of the warp at nearly every
             // candidate
-            unsigned short lst[CAP];
+            // entries as uint16, entry e in half e % 2 of word e / 2 (the
+            // network's layout) or, one atom per thread, a plain array
+            using LstT = typename std::conditional<(APT >= 2), unsigned int, unsigned short>::type;
+            LstT lstw[APT >= 2 ? CAP / 2 : CAP];
             int k = 0;
             auto push = [&](int j) {
-                if (k < CAP) lst[k] = (unsigned short)j;
+                if (k < CAP) reinterpret_cast<unsigned short *>(lstw)[k] = (unsigned short)j;
                 k++;
             };
             // windows [w - r_l, w + r_l] in cell units; |w| <= L keeps them small
@@ -565,24 +601,58 @@ __device__ __forceinline__ void run_daughter(const RunArgs &a, int d, unsigned c
                 }
             }
             if (k > CAP) { m->flag_ovf = 1; k = CAP; }
-            for (int e = 1; e < k; e++) {   // insertion sort by neighbour index
-                const unsigned short v = lst[e];
-                int pi = e;
-                while (pi > 0 && lst[pi - 1] > v) { lst[pi] = lst[pi - 1]; pi--; }
-                lst[pi] = v;
-            }
-            // eight entries per 16-byte chunk, two per word; an odd tail is
-            // padded with i itself (r = 0 is rejected by the force loop)
-            for (int t = 0; t < k; t += 8) {
-                unsigned int wv[4];
+            // sorted by neighbour index with a bitonic network over the 32
+            // slots held as 16 packed uint16 pairs in registers (the same
+            // steps on every lane: no divergent insertion loop; free slots
+            // hold 0xffff and sort last).  One atom per thread (256-thread
+            // CTAs of small daughters) keeps the insertion sort, which is
+            // cheaper there.
+            if constexpr (APT >= 2) {
+                unsigned int r[CAP / 2];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int e = t + 2 * u;
-                    const unsigned int lo = e < k ? lst[e] : (unsigned int)i;
-                    const unsigned int hi = e + 1 < k ? lst[e + 1] : (unsigned int)i;
-                    wv[u] = lo | (hi << 16);
+                for (int w = 0; w < CAP / 2; w++) {
+                    const unsigned int v = 2 * w < k ? lstw[w] : 0xffffffffu;
+                    r[w] = v | (2 * w + 1 < k ? 0u : 0xffff0000u);
                 }
-                nbr4[(size_t)(t >> 3) * nmax + i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                sort32_u16(r);
+                // eight entries per 16-byte chunk, two per word; slots from
+                // k on become i itself (r = 0 is rejected by the force loop)
+                const unsigned int ii = (unsigned int)i;
+#pragma unroll
+                for (int c = 0; c < CAP / 8; c++) {
+                    if (8 * c < k) {
+                        unsigned int wv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            unsigned int w = r[4 * c + u];
+                            if ((w & 0xffffu) == 0xffffu) w = (w & 0xffff0000u) | ii;
+                            if ((w >> 16) == 0xffffu) w = (w & 0xffffu) | (ii << 16);
+                            wv[u] = w;
+                        }
+                        nbr4[(size_t)c * nmax + i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                    }
+                }
+            } else {
+                unsigned short *lst = lstw;
+                for (int e = 1; e < k; e++) {   // insertion sort by neighbour index
+                    const unsigned short v = lst[e];
+                    int pi = e;
+                    while (pi > 0 && lst[pi - 1] > v) { lst[pi] = lst[pi - 1]; pi--; }
+                    lst[pi] = v;
+                }
+                // eight entries per 16-byte chunk, two per word; an odd tail
+                // is padded with i itself (r = 0 is rejected by the force loop)
+                for (int t = 0; t < k; t += 8) {
+                    unsigned int wv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int e = t + 2 * u;
+                        const unsigned int lo = e < k ? lst[e] : (unsigned int)i;
+                        const unsigned int hi = e + 1 < k ? lst[e + 1] : (unsigned int)i;
+                        wv[u] = lo | (hi << 16);
+                    }
+                    nbr4[(size_t)(t >> 3) * nmax + i] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                }
             }
             ncnt[q] = k;
         }
