@@ -94,7 +94,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cv-train-groups", type=int, default=16384)
     p.add_argument("--cv-eval-groups", type=int, default=4096)
-    p.add_argument("--cv-aux", type=int, default=65536)
+    p.add_argument("--cv-aux", type=int, default=16384)
     p.add_argument("--cv-steps", type=int, default=500)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-confined", action="store_true")

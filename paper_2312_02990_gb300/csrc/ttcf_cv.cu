@@ -61,7 +61,7 @@ __global__ void cv_features_kernel(CvFeatArgs a) {
 //   q = 1..4 of the density over 40 slabs in y, [22..29] the same of p_x.
 constexpr int CV_NSLAB = 40, CV_NACC = 30;
 
-__global__ void cv_raw_features_kernel(CvRawArgs a) {
+__global__ void __launch_bounds__(256, 4) cv_raw_features_kernel(CvRawArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x, N = a.N;
     float *xf = reinterpret_cast<float *>(smem), *yf = xf + N, *zf = yf + N;
@@ -164,19 +164,44 @@ __global__ void cv_raw_features_kernel(CvRawArgs a) {
             }
         }
     }
-    // fixed-order block sums in FP64
+    // block sums in 64-bit fixed point of 2^-40 units (integer shuffles:
+    // a float partial of magnitude >= 2^-17 is exact there, so the sums
+    // are exact and order-free; GB300's FP64 pipe, on which a shuffle tree
+    // of 30 doubles per warp took a quarter of this kernel, stays idle)
+    // The 64-bit sums hold |total| < 2^23: a state with a thread partial of
+    // 2^15 or more (or not finite) takes the FP64 tree instead (normal
+    // partials are below 10^3).
     const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-    for (int k = 0; k < CV_NACC; k++) {
-        double v = (double)acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp * CV_NACC + k] = v;
-    }
-    __syncthreads();
-    if (tid < CV_NACC) {
-        double v = 0.0;
-        for (int w = 0; w < nw; w++) v += red[w * CV_NACC + tid];
-        if (tid >= 14) v /= N;   // modes per atom
-        a.raw[(size_t)g * FEAT_RAW + tid] = v;
+    bool big = false;
+    for (int k = 0; k < CV_NACC; k++) big |= !(fabsf(acc[k]) < 32768.f);
+    if (!__syncthreads_or(big)) {
+        long long *redl = reinterpret_cast<long long *>(red);
+        for (int k = 0; k < CV_NACC; k++) {
+            long long v = __float2ll_rn(acc[k] * 1099511627776.0f);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) redl[warp * CV_NACC + k] = v;
+        }
+        __syncthreads();
+        if (tid < CV_NACC) {
+            long long v = 0;
+            for (int w = 0; w < nw; w++) v += redl[w * CV_NACC + tid];
+            double x = (double)v * 9.094947017729282e-13;   // x 2^-40
+            if (tid >= 14) x /= N;   // modes per atom
+            a.raw[(size_t)g * FEAT_RAW + tid] = x;
+        }
+    } else {
+        for (int k = 0; k < CV_NACC; k++) {
+            double v = (double)acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp * CV_NACC + k] = v;
+        }
+        __syncthreads();
+        if (tid < CV_NACC) {
+            double v = 0.0;
+            for (int w = 0; w < nw; w++) v += red[w * CV_NACC + tid];
+            if (tid >= 14) v /= N;   // modes per atom
+            a.raw[(size_t)g * FEAT_RAW + tid] = v;
+        }
     }
     if (tid == 0) { a.raw[(size_t)g * FEAT_RAW + 30] = 0.0; a.raw[(size_t)g * FEAT_RAW + 31] = 0.0; }
 }

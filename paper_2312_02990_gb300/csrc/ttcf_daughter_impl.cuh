@@ -177,9 +177,11 @@ __device__ __forceinline__ df df_from_fix40(long long s) {
 __device__ __forceinline__ void cta_sum2_fix(float a0, float a1, Misc *m, df out[2], int w2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    // outside +-2^22 (or not finite) the 64-bit sums could overflow: the
-    // daughter stops as non-finite (normal partials are below 10^3)
-    if (!(fabsf(a0) < 4194304.f && fabsf(a1) < 4194304.f)) m->flag_lost = 1;
+    // the 64-bit sums hold |total| < 2^23; with at most 1024 threads a
+    // thread partial of 2^13 or more (or one not finite) stops the daughter
+    // as non-finite (normal partials are below 10^2; 2^13 takes a WCA pair
+    // nearer than 0.6 sigma, about 1800 kT above contact)
+    if (!(fabsf(a0) < 8192.f && fabsf(a1) < 8192.f)) m->flag_lost = 1;
     long long v0 = fix40(a0), v1 = fix40(a1);
     for (int o = 16; o > 0; o >>= 1) {
         v0 += __shfl_down_sync(0xffffffffu, v0, o);
