@@ -66,6 +66,14 @@ def lib():
         L.orc_daughters.restype = C.c_int
         L.orc_daughters.argtypes = [bp, C.c_int, dp, dp, dp, C.c_uint, C.c_int, C.c_int,
                                     C.c_int, dp, dp, C.c_int]
+        L.orc_trajectory_elong.restype = C.c_int
+        L.orc_trajectory_elong.argtypes = [bp, C.c_double, dp, dp, C.c_int, dp]
+        L.orc_daughter_elong.restype = C.c_int
+        L.orc_daughter_elong.argtypes = [bp, dp, C.c_double, C.c_int, C.c_int, C.c_double,
+                                         C.c_int, C.c_int, dp, dp, dp, dp]
+        L.orc_daughters_elong.restype = C.c_int
+        L.orc_daughters_elong.argtypes = [bp, C.c_int, dp, dp, dp, C.c_uint, C.c_int, C.c_int,
+                                          C.c_int, dp, dp, C.c_int]
         _lib = L
     return _lib
 
@@ -213,4 +221,60 @@ def daughters(b: Bulk, mothers: np.ndarray, mother_alpha, gammas, n_steps: int,
                              int(sample_every), _p(B), _p(Om), int(nt))
     if rc:
         raise RuntimeError(f"oracle daughters failed ({rc})")
+    return B, Om
+
+
+# ------------------------------------------------- planar elongational flow --
+
+def trajectory_elong(b: Bulk, state: np.ndarray, n_steps: int, eps: float,
+                     alpha: float = 0.0):
+    """Run n_steps under planar elongation grad u = diag(eps, 0, -eps) from
+    the switch-on box b.L; returns (final state, alpha, obs[n_steps+1, 9])
+    with obs columns K2, U, alpha, xi, Pxx-Pzz, Wxx-Wzz, Lx, Lz, H_ext."""
+    s = np.array(state, dtype=np.float64, order="C")
+    a = C.c_double(alpha)
+    obs = np.zeros((n_steps + 1, 9))
+    if lib().orc_trajectory_elong(C.byref(b.c()), float(eps), _p(s), C.byref(a),
+                                  int(n_steps), _p(obs)):
+        raise RuntimeError("oracle elongational trajectory failed")
+    return s, a.value, obs
+
+
+def daughter_elong(b: Bulk, mother_state: np.ndarray, mother_alpha: float, m: int,
+                   eps: float, n_steps: int, sample_every: int = 1,
+                   reset_alpha: bool = False):
+    """One elongational daughter: (B[S] = P_xx - P_zz, Omega, final state, alpha)."""
+    s = np.ascontiguousarray(mother_state, dtype=np.float64)
+    S = n_steps // sample_every + 1
+    B = np.zeros(S)
+    om = C.c_double()
+    fin = np.zeros((6, b.n))
+    fa = C.c_double()
+    if lib().orc_daughter_elong(C.byref(b.c()), _p(s), float(mother_alpha), int(m),
+                                1 if reset_alpha else 0, float(eps), int(n_steps),
+                                int(sample_every), _p(B), C.byref(om), _p(fin),
+                                C.byref(fa)):
+        raise RuntimeError("oracle elongational daughter failed")
+    return B, om.value, fin, fa.value
+
+
+def daughters_elong(b: Bulk, mothers: np.ndarray, mother_alpha, rates, n_steps: int,
+                    sample_every: int = 1, mapping_mask: int = 0x30003,
+                    reset_alpha: bool = False, n_threads: int | None = None):
+    """The elongational ensemble, laid out as daughters(); the default set
+    {identity, p -> -p, x <-> z, x <-> z with p -> -p} cancels Omega(0)."""
+    mothers = np.ascontiguousarray(mothers, dtype=np.float64)
+    G = mothers.shape[0]
+    al = np.ascontiguousarray(np.broadcast_to(np.asarray(mother_alpha, np.float64), (G,)))
+    er = np.ascontiguousarray(np.broadcast_to(np.asarray(rates, np.float64), (G,)))
+    M = bin(mapping_mask & 0xFFFFFFFF).count("1")
+    S = n_steps // sample_every + 1
+    B = np.zeros((G * M, S))
+    Om = np.zeros(G * M)
+    nt = n_threads or os.cpu_count() or 1
+    rc = lib().orc_daughters_elong(C.byref(b.c()), G, _p(mothers), _p(al), _p(er),
+                                   int(mapping_mask), 1 if reset_alpha else 0,
+                                   int(n_steps), int(sample_every), _p(B), _p(Om), int(nt))
+    if rc:
+        raise RuntimeError(f"oracle elongational daughters failed ({rc})")
     return B, Om

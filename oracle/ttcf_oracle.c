@@ -21,6 +21,8 @@
  *   - the four phase-space mappings .................................. Eq. 3
  *   - mother sampling and daughter runs .......... Algorithm 2, Figure 1
  *   - responses B(s) and dissipation Omega(0) per daughter ..... Eq. 1-2
+ *   - the same dynamics under planar elongational flow, the other
+ *     homogeneous field the introduction lists beside shear (end of file)
  *
  * The time discretisation is not stated in the paper beyond "velocity
  * Verlet".  The oracle uses the symmetric splitting (Strang) of the Eq. 5
@@ -526,6 +528,178 @@ int orc_daughters(const orc_bulk *b, int n_groups, const double *mothers,
         err |= orc_daughter(b, mothers + (size_t)g * 6 * b->n, mother_alpha[g], m,
                             reset_alpha, gammas[g], n_steps, sample_every,
                             B + (size_t)d * S, Omega + d, NULL, NULL) ? 1 : 0;
+    }
+    return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Planar elongational flow (the other homogeneous field the paper's    */
+/* introduction lists beside shear).  The streaming velocity is          */
+/* u(r) = r . grad u with grad u = diag(eps, 0, -eps): stretching along  */
+/* x, compression along z, y neutral, so the volume is constant.  The    */
+/* Eq. 5 vector field with this grad u:                                  */
+/*     r' = p/m + (eps x, 0, -eps z)                                     */
+/*     p' = F - (eps px, 0, -eps pz) - alpha p                           */
+/* The periodic box deforms with the flow, Lx(t) = Lx(0) exp(eps t),     */
+/* Lz(t) = Lz(0) exp(-eps t) (no Kraynik-Reinelt remapping: a daughter   */
+/* is short enough that the compressed edge stays above 2 r_c, which the */
+/* callers check).  The dissipation function (Omega = beta dH^ad/dt with  */
+/* dH^ad/dt = -V grad u : P) is                                          */
+/*     Omega = -eps V (P_xx - P_zz) / (k_B T)                            */
+/* and the response B = P_xx - P_zz; the planar elongational viscosity  */
+/* is eta_1 = -<P_xx - P_zz> / (4 eps), the shear viscosity in the       */
+/* Newtonian limit.  The x <-> z exchange (mapping bit 4) negates Omega  */
+/* and time reversal keeps it, so the set {0, 1, 16, 17} cancels          */
+/* <Omega(0)> per group, as Eq. 3's set does for shear.                  */
+/* Splitting as for shear, with the shear flows replaced by:             */
+/*     C': px <- px exp(-eps tau), pz <- pz exp(eps tau)                 */
+/*     A': the exact drift with p frozen,                                */
+/*         x <- x exp(eps h) + px (exp(eps h) - 1)/eps                   */
+/*         z <- z exp(-eps h) + pz (1 - exp(-eps h))/eps                 */
+/*         y <- y + py h,                                                 */
+/*         then the box edges at the new time and one periodic wrap.    */
+/* ------------------------------------------------------------------ */
+
+/* Flow C' for a time tau. */
+static void flow_elong(const orc_bulk *b, orc_state *s, double eps, double tau)
+{
+    double cx = exp(-eps * tau), cz = exp(eps * tau);
+    for (int i = 0; i < b->n; i++) { s->px[i] *= cx; s->pz[i] *= cz; }
+}
+
+/* One periodic wrap into [-L/2, L/2) (a step moves an atom far less     */
+/* than L/2).                                                             */
+static double wrap_once(double v, double L)
+{
+    if (v >= 0.5 * L) return v - L;
+    if (v < -0.5 * L) return v + L;
+    return v;
+}
+
+/* Flow A' for a time h; bt->L holds the box at the start and is set to  */
+/* the box at time t_new = (step number) h from the switch-on box L0.     */
+static void flow_drift_elong(orc_bulk *bt, orc_state *s, double eps, double h,
+                             const double L0[3], double t_new)
+{
+    double ex = exp(eps * h), ez = exp(-eps * h);
+    double phx = eps != 0.0 ? expm1(eps * h) / eps : h;
+    double phz = eps != 0.0 ? expm1(-eps * h) / (-eps) : h;
+    bt->L[0] = L0[0] * exp(eps * t_new);
+    bt->L[1] = L0[1];
+    bt->L[2] = L0[2] * exp(-eps * t_new);
+    for (int i = 0; i < bt->n; i++) {
+        s->x[i] = wrap_once(s->x[i] * ex + s->px[i] * phx, bt->L[0]);
+        s->y[i] = wrap_once(s->y[i] + s->py[i] * h, bt->L[1]);
+        s->z[i] = wrap_once(s->z[i] * ez + s->pz[i] * phz, bt->L[2]);
+    }
+}
+
+/* B = P_xx - P_zz of the current state in the current box. */
+static double pxx_pzz(const orc_bulk *bt, const orc_state *s)
+{
+    double k = 0.0;
+    for (int i = 0; i < bt->n; i++) k += s->px[i] * s->px[i] - s->pz[i] * s->pz[i];
+    return (k + s->W[0] - s->W[2]) / (bt->L[0] * bt->L[1] * bt->L[2]);
+}
+
+/* One step E D C' B A' B C' D E taking the box from step n-1 to step n.  */
+static int orc_step_elong(orc_bulk *bt, orc_state *s, double eps, const double L0[3], int n)
+{
+    double hh = 0.5 * bt->dt;
+    flow_alpha(bt, s, hh);
+    flow_scale(bt, s, hh);
+    flow_elong(bt, s, eps, hh);
+    flow_kick(bt, s, hh);
+    flow_drift_elong(bt, s, eps, bt->dt, L0, n * bt->dt);
+    if (compute_forces(bt, s)) return -1;   /* minimum image in the new box */
+    flow_kick(bt, s, hh);
+    flow_elong(bt, s, eps, hh);
+    flow_scale(bt, s, hh);
+    flow_alpha(bt, s, hh);
+    return 0;
+}
+
+/* Run n_steps under elongation rate eps from a state [6][n] (in/out) at  */
+/* the switch-on box b->L, recording per step s = 0..n_steps              */
+/*   obs[s] = {K2, U, alpha, xi, Pxx - Pzz, Wxx - Wzz, Lx, Lz, H_ext}      */
+/* with H_ext = K2/2 + U + Q alpha^2/2 + g T xi, whose rate of change is  */
+/* -V eps (P_xx - P_zz).  The final state is in the final box.            */
+int orc_trajectory_elong(const orc_bulk *b, double eps, double *soa, double *alpha_io,
+                         int n_steps, double *obs)
+{
+    orc_bulk bt = *b;
+    orc_state s;
+    if (state_alloc(&s, b->n)) return -1;
+    load_state(b, &s, soa);
+    s.alpha = *alpha_io;
+    if (compute_forces(&bt, &s)) { state_free(&s); return -1; }
+    for (int t = 0; t <= n_steps; t++) {
+        if (t > 0 && orc_step_elong(&bt, &s, eps, b->L, t)) { state_free(&s); return -1; }
+        if (obs) {
+            double K2 = kin2(&bt, &s);
+            double *o = obs + 9 * t;
+            o[0] = K2; o[1] = s.U; o[2] = s.alpha; o[3] = s.xi;
+            o[4] = pxx_pzz(&bt, &s); o[5] = s.W[0] - s.W[2];
+            o[6] = bt.L[0]; o[7] = bt.L[2];
+            o[8] = 0.5 * K2 + s.U + 0.5 * b->Q * s.alpha * s.alpha + b->g * b->T * s.xi;
+        }
+    }
+    store_state(b, &s, soa);
+    *alpha_io = s.alpha;
+    state_free(&s);
+    return 0;
+}
+
+/* One daughter under elongation: map the mother (codes as for shear, in  */
+/* the switch-on box), B(0) = P_xx - P_zz, Omega(0) = -eps V B(0) / T,    */
+/* then B(s) every sample_every steps.                                     */
+int orc_daughter_elong(const orc_bulk *b, const double *mother, double mother_alpha,
+                       int m, int reset_alpha, double eps, int n_steps, int sample_every,
+                       double *B, double *Omega, double *final_state, double *final_alpha)
+{
+    orc_bulk bt = *b;
+    orc_state s;
+    if (state_alloc(&s, b->n)) return -1;
+    double a0;
+    orc_apply_mapping(b, m, mother, mother_alpha, reset_alpha, s.x, &a0);
+    s.alpha = a0;
+    if (compute_forces(&bt, &s)) { state_free(&s); return -1; }
+    double V = b->L[0] * b->L[1] * b->L[2];
+    double b0 = pxx_pzz(&bt, &s);
+    *Omega = -eps * V * b0 / b->T;
+    B[0] = b0;
+    for (int t = 1; t <= n_steps; t++) {
+        if (orc_step_elong(&bt, &s, eps, b->L, t)) { state_free(&s); return -1; }
+        if (t % sample_every == 0) B[t / sample_every] = pxx_pzz(&bt, &s);
+    }
+    if (final_state) store_state(b, &s, final_state);
+    if (final_alpha) *final_alpha = s.alpha;
+    state_free(&s);
+    return 0;
+}
+
+/* The elongational ensemble, laid out as orc_daughters (gammas are the    */
+/* elongation rates of the groups).                                        */
+int orc_daughters_elong(const orc_bulk *b, int n_groups, const double *mothers,
+                        const double *mother_alpha, const double *rates,
+                        unsigned mapping_mask, int reset_alpha, int n_steps,
+                        int sample_every, double *B, double *Omega, int n_threads)
+{
+    int maps[32], M = 0;
+    for (int m = 0; m < 32; m++) if (mapping_mask & (1u << m)) maps[M++] = m;
+    if (M == 0 || sample_every <= 0 || n_steps % sample_every) return -2;
+    for (int k = 0; k < M; k++)
+        if ((maps[k] & 16) && b->L[0] != b->L[2]) return -3;
+    int S = n_steps / sample_every + 1;
+    int D = n_groups * M;
+    int err = 0;
+    (void)n_threads;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(|:err)
+    for (int d = 0; d < D; d++) {
+        int g = d / M, m = maps[d % M];
+        err |= orc_daughter_elong(b, mothers + (size_t)g * 6 * b->n, mother_alpha[g], m,
+                                  reset_alpha, rates[g], n_steps, sample_every,
+                                  B + (size_t)d * S, Omega + d, NULL, NULL) ? 1 : 0;
     }
     return err ? -1 : 0;
 }
