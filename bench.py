@@ -105,9 +105,12 @@ def parse():
     p.add_argument("--no-kick", action="store_true", help="skip the momentum-kick mothers section")
     p.add_argument("--no-mapstudy", action="store_true", help="skip the mapping-set / Eq. 4 study")
     p.add_argument("--no-probe", action="store_true", help="skip the FP32 throughput probe")
+    p.add_argument("--no-elong", action="store_true", help="skip the planar elongational flow section")
+    p.add_argument("--elong-chains", type=int, default=256)
+    p.add_argument("--elong-states", type=int, default=16)
     p.add_argument("--only", default=None,
                    help="run one section alone and print its JSON (confined, uneven, cv, floor, "
-                        "gk, kick, mapstudy, probe)")
+                        "gk, kick, mapstudy, probe, elong)")
     p.add_argument("--conf-chains", type=int, default=64, help="independent confined mother chains")
     p.add_argument("--conf-states", type=int, default=4, help="mother states per chain")
     p.add_argument("--conf-eq", type=int, default=4000)
@@ -462,6 +465,14 @@ def _run_sections(T, torch, args, sec, summary, N, L, ms_dev, al_dev, eta, ms_st
             summary["confined"] = {"value": float(f"{c['value']:.4g}"), "frac": round(c["roofline"]["frac"], 4),
                                    "daughters": c["daughters"]}
         sec.emit("confined", c)
+    if not args.no_elong:
+        el = guarded("elong", lambda: elong_section(T, torch, args))
+        if "value" in el:
+            summary["elong"] = {"value": float(f"{el['value']:.4g}"), "frac": round(el["roofline"]["frac"], 4),
+                                "eta1_t_end": {k: [round(v[0], 3), round(v[1], 3)]
+                                               for k, v in el["eta1_t_end"].items()},
+                                "eta_shear_t_end": [round(x, 3) for x in el["eta_shear_t_end"]]}
+        sec.emit("elongational", el)
     if not args.no_cv:
         cv = guarded("cv", lambda: cv_section(T, torch, args))
         if "variance_gain" in cv:
@@ -554,6 +565,64 @@ def uneven_section(T, torch, args):
                          "frac": achieved / peak, "kernel": "daughter_kernel (3 size classes)"},
             "pairs_per_atom_step": st["pairs_interacting"] / atom_steps,
             "flagged_groups": bad, "mother_setup_s": t_moth, "eta_ttcf_t_end": eta}
+
+
+ELONG_RATES = [1e-1, 1e-3, 1e-5]
+
+
+def elong_section(T, torch, args):
+    """Planar elongational flow (grad u = diag(eps, 0, -eps), deforming box)
+    on the N=256 system: elong_chains x elong_states GPU mother states x the
+    four mappings {identity, p -> -p, x <-> z, both} x daughter_steps steps
+    at each rate of ELONG_RATES (one batch per rate, one run, MIXED); the
+    same mothers sheared at 1e-3 give the shear viscosity, which the
+    elongational viscosity eta_1 = -<P_xx - P_zz>/(4 eps) equals in the
+    linear regime (an isotropic fluid: P_xx - P_zz is the shear stress of
+    axes turned by 45 degrees)."""
+    from paper_2312_02990_gb300 import inputs
+    N = 256
+    L = inputs.bulk_box(N)
+    t0 = time.perf_counter()
+    ms, al = make_mothers(T, args, 0, N, L, n_mothers=args.elong_chains, n_states=args.elong_states,
+                          seed_off=50000, n_eq=4000)
+    t_moth = time.perf_counter() - t0
+    msd, ald = torch.from_numpy(ms).cuda(), torch.from_numpy(al).cuda()
+    G = len(ms)
+    cfg = T.config_default()
+    cfg.system, cfg.precision = T.TTCF_BULK_WCA_ELONG, T.TTCF_MIXED
+    cfg.n_steps, cfg.mapping_mask = args.daughter_steps, 0x30003
+    with T.Context(cfg) as c:
+        ids = {g: c.spawn_daughters(msd, ald, g, box=L) for g in ELONG_RATES}
+        c.run()
+        st = c.get_stats()
+        eta = {}
+        for g, b in ids.items():
+            v = c.viscosity(b)
+            eta[f"{g:.0e}"] = [float(v["eta_ttcf"][-1]), float(v["eta_ttcf_se"][-1]),
+                               float(v["eta_dav"][-1]), float(v["eta_dav_se"][-1])]
+        bad = int(sum(np.count_nonzero(c.group_status(b, G)) for b in ids.values()))
+    scfg = T.config_default()
+    scfg.precision, scfg.n_steps = T.TTCF_MIXED, args.daughter_steps
+    with T.Context(scfg) as c:
+        b = c.spawn_daughters(msd, ald, 1e-3, box=L)
+        c.run()
+        vs = c.viscosity(b)
+    D = 4 * G * len(ELONG_RATES)
+    atom_steps = D * N * args.daughter_steps
+    k_ms = st["ms_run"]
+    achieved = st["pairs_interacting"] / 2.0 * FLOPS_PER_PAIR / (k_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    return {"value": atom_steps / (k_ms * 1e-3), "unit": "atom-steps/s", "daughters": D,
+            "workload": f"bulk WCA N = {N}, planar elongation at rates {ELONG_RATES}, {G} mother states "
+                        f"x 4 mappings per rate, {args.daughter_steps} steps, one run, MIXED",
+            "kernel_ms": k_ms, "launches": st["launches"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "kernel": "elong_kernel"},
+            "pairs_per_atom_step": st["pairs_interacting"] / atom_steps,
+            "eta1_t_end": {k: v[:2] for k, v in eta.items()},
+            "eta1_dav_t_end": {k: v[2:] for k, v in eta.items()},
+            "eta_shear_t_end": [float(vs["eta_ttcf"][-1]), float(vs["eta_ttcf_se"][-1])],
+            "flagged_groups": bad, "mother_setup_s": t_moth}
 
 
 def cv_section(T, torch, args):
@@ -1047,7 +1116,8 @@ def main():
               "gk": lambda: green_kubo_section(T, torch, args, N, L),
               "kick": lambda: kick_section(T, torch, args, N, L),
               "mapstudy": lambda: mapping_study_section(T, torch, args),
-              "probe": probe_section}[args.only]
+              "probe": probe_section,
+              "elong": lambda: elong_section(T, torch, args)}[args.only]
         print(json.dumps(fn()))
     else:
         bench_gb300(args)

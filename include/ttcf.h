@@ -58,8 +58,33 @@ typedef enum {
  *                    Lees-Edwards boundaries and a Nose-Hoover thermostat.
  *  TTCF_CONFINED_LJ  Example 2: Lennard-Jones fluid between two walls of
  *                    tethered atoms whose lattices slide at +-v in x
- *                    (Eq. 9, 10); MIXED precision only.                  */
-enum { TTCF_BULK_WCA = 0, TTCF_CONFINED_LJ = 1 };
+ *                    (Eq. 9, 10); MIXED precision only.
+ *  TTCF_BULK_WCA_ELONG  the WCA fluid of Example 1 under planar
+ *                    elongational flow, the other homogeneous field the
+ *                    paper's introduction lists beside shear: the Eq. 5
+ *                    equations with grad u = diag(eps, 0, -eps)
+ *                    (stretching along x, compression along z) in a box
+ *                    that deforms with the flow, Lx(t) = Lx e^{eps t},
+ *                    Lz(t) = Lz e^{-eps t} (no periodic remapping: every
+ *                    compressed edge must stay above 2 r_c up to the
+ *                    daughter's end, which ttcf_spawn_daughters checks).
+ *                    The per-group rates passed as shear_rates are the
+ *                    elongation rates eps; the response is B = P_xx - P_zz,
+ *                    Omega = -eps V B(0) / (k_B T), and ttcf_viscosity
+ *                    returns eta_1 = -<P_xx - P_zz> / (4 eps), the shear
+ *                    viscosity in the Newtonian limit.  Mapping codes as
+ *                    for shear; the x <-> z exchange (bit 4) negates
+ *                    Omega and time reversal keeps it, so the set
+ *                    {0, 1, 16, 17} (mapping_mask 0x30003) cancels
+ *                    <Omega(0)> per group.  One CTA per daughter with the
+ *                    whole daughter in shared memory (N up to about 2200
+ *                    in MIXED, 1500 in FP64); use_graph, skin,
+ *                    kernel_variant, block_threads and cell_frac do not
+ *                    apply; the control variate is not available.  The
+ *                    equilibrium tools (ttcf_sample_mothers,
+ *                    ttcf_mother_acf, ttcf_forces) work as in
+ *                    TTCF_BULK_WCA.                                     */
+enum { TTCF_BULK_WCA = 0, TTCF_CONFINED_LJ = 1, TTCF_BULK_WCA_ELONG = 2 };
 
 /* Responses per sample of a confined daughter (TTCF_CONFINED_LJ):
  *  0              x force of the fluid on the bottom wall per wall area
@@ -99,7 +124,8 @@ typedef void (*ttcf_free_fn)(void *ptr, void *stream, void *user);
 
 /* Plain-old-data configuration; copied by ttcf_create. */
 typedef struct {
-    int system;             /* TTCF_BULK_WCA or TTCF_CONFINED_LJ             */
+    int system;             /* TTCF_BULK_WCA, TTCF_CONFINED_LJ or
+                               TTCF_BULK_WCA_ELONG                           */
     int precision;          /* TTCF_FP64 or TTCF_MIXED                       */
     double dt;              /* time step h (Example 1: 0.0025)               */
     double T;               /* thermostat k_B T (Example 1: 0.722)           */
@@ -203,9 +229,11 @@ ttcf_status ttcf_response(ttcf_ctx *ctx, int batch_id, int corrected, double *t,
 
 /* Shear viscosity of a batch whose groups share one shear rate gamma
  * (Eq. 8 with the standard pressure tensor): eta(t) = -<P_xy(t)>/gamma
- * from the TTCF and the direct averages, with standard errors.  Arrays as
- * in ttcf_response.  Errors: as ttcf_response; TTCF_E_INVALID if gamma
- * differs between groups or is 0.                                          */
+ * from the TTCF and the direct averages, with standard errors.  For a
+ * TTCF_BULK_WCA_ELONG batch, the planar elongational viscosity
+ * eta_1(t) = -<P_xx(t) - P_zz(t)>/(4 eps).  Arrays as in ttcf_response.
+ * Errors: as ttcf_response; TTCF_E_INVALID if the rate differs between
+ * groups or is 0.                                                          */
 ttcf_status ttcf_viscosity(ttcf_ctx *ctx, int batch_id, double *t, double *eta_ttcf,
                            double *eta_ttcf_se, double *eta_dav, double *eta_dav_se,
                            int capacity, int *n_samples);
@@ -231,7 +259,9 @@ ttcf_status ttcf_group_status(ttcf_ctx *ctx, int batch_id, int *status, int capa
 
 /* Phase point [6][N], alpha and Lees-Edwards offset of daughter d of a
  * batch after the last ttcf_run; requires keep_state = 1.  Positions are
- * wrapped into the box.                                                    */
+ * wrapped into the box; for a TTCF_BULK_WCA_ELONG batch that is the box
+ * of the last step run (Lx e^{eps t}, Ly, Lz e^{-eps t}) and the offset
+ * is 0.                                                                    */
 ttcf_status ttcf_get_state(ttcf_ctx *ctx, int batch_id, int daughter, double *soa,
                            double *alpha, double *delta);
 

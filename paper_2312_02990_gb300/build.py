@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libttcf.so")
 SOURCES = ["ttcf_daughter.cu", "ttcf_daughter_u8.cu", "ttcf_spawn.cu", "ttcf_reduce.cu", "ttcf_api.cu", "ttcf_noalloc.cu",
-           "ttcf_cv.cu", "ttcf_confined.cu", "ttcf_kick.cu"]
+           "ttcf_cv.cu", "ttcf_confined.cu", "ttcf_kick.cu", "ttcf_elong.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--diag-suppress", "177",
          "-I", INCLUDE, "-I", CSRC]

@@ -27,6 +27,8 @@ struct BatchHost {
     int N = 0, M = 0, G = 0, S = 0;
     int n_obs = 1;                        // observables per sample
     bool confined = false;                // Example 2 batch (ttcf_confined.cu)
+    bool elong = false;                   // planar elongational flow (ttcf_elong.cu)
+    int ncmax[3] = {0, 0, 0};             // elongational cell-grid bound per axis
     int maps[MAX_MAPS] = {};
     double L[3] = {0, 0, 0};
     double V = 0, Q = 0, gT = 0;
@@ -309,6 +311,7 @@ ttcf_status make_batch(ttcf_ctx *ctx, Pool &pool, BatchHost &b, int N, const dou
     sa.mixed = cf.precision == TTCF_MIXED;
     sa.src = src; sa.gamma = b.gamma_d; sa.mothers = b.mothers;
     sa.B = b.B; sa.S = S; sa.Omega = b.Omega; sa.feat = b.feat; sa.delta = delta0;
+    sa.elong = b.elong ? 1 : 0;
     CK(cudaEventRecord(ctx->ev[2], st));
     CK(launch_spawn(sa, st));
     CK(cudaEventRecord(ctx->ev[3], st));
@@ -863,6 +866,138 @@ ttcf_confined_params conf_params_or_default(const ttcf_confined_params *p) {
     return q;
 }
 
+// ======================================================= elongational flow ==
+// Checks an elongational batch against the daughter length and sizes its
+// cell grid: the box deforms as Lx(t) = Lx e^{eps t}, Lz(t) = Lz e^{-eps t},
+// so every compressed edge must stay above 2 r_c up to t = n_steps dt, and
+// the grid (cells at least r_c (1 + 1e-4) wide) is bounded per axis by the
+// largest edge the run reaches.
+ttcf_status elong_plan(ttcf_ctx *ctx, int N, const double box[3], const std::vector<double> &rates,
+                       BatchHost &b) {
+    const ttcf_config &cf = ctx->cfg;
+    const double t_end = cf.n_steps * cf.dt;
+    double emax = 0.0, emin = 0.0;
+    for (double r : rates) {
+        if (!isfinite(r)) return fail(ctx, TTCF_E_INVALID, "non-finite elongation rate");
+        emax = std::max(emax, r);
+        emin = std::min(emin, r);
+    }
+    const double lo_x = box[0] * exp(emin * t_end), lo_z = box[2] * exp(-emax * t_end);
+    if (!(lo_x > 2.002 * RC_WCA) || !(lo_z > 2.002 * RC_WCA) || !(box[1] > 2.002 * RC_WCA))
+        return fail(ctx, TTCF_E_INVALID, "elongation too strong for the daughter length: a compressed "
+                                         "box edge would fall below 2 r_c");
+    const double hi[3] = {box[0] * exp(emax * t_end), box[1], box[2] * exp(-emin * t_end)};
+    for (int k = 0; k < 3; k++) {
+        const double n = floor(hi[k] / (RC_WCA * (1.0 + 1e-4))) + 1.0;
+        if (!(n >= 1.0 && n <= 4096.0)) return fail(ctx, TTCF_E_INVALID, "elongational box too large");
+        b.ncmax[k] = (int)n;
+    }
+    const size_t smem = elong_smem_bytes(cf.precision == TTCF_MIXED, N,
+                                         b.ncmax[0] * b.ncmax[1] * b.ncmax[2]);
+    if (smem > (size_t)ctx->smem_optin)
+        return fail(ctx, TTCF_E_INVALID, "n_atoms too large for an elongational daughter in one CTA's "
+                                         "shared memory");
+    b.elong = true;
+    return TTCF_OK;
+}
+
+// One persistent launch per elongational batch, then the reductions.
+ttcf_status run_elong(ttcf_ctx *ctx, int n_steps) {
+    const ttcf_config &cf = ctx->cfg;
+    const int step0 = ctx->steps_done;
+    if (step0 >= cf.n_steps) return TTCF_OK;
+    const int step1 = (n_steps <= 0 || step0 + n_steps > cf.n_steps) ? cf.n_steps : step0 + n_steps;
+    const bool save = step1 < cf.n_steps || cf.keep_state;
+    if (save) {
+        for (auto &b : ctx->batches) {
+            if (b.state) continue;
+            Pool p(ctx);
+            b.state = p.get<unsigned long long>((size_t)b.D() * 6 * b.N);
+            if (p.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (state)");
+            p.keep();
+        }
+    }
+    if (step0 > 0)
+        for (auto &b : ctx->batches)
+            if (!b.state) return fail(ctx, TTCF_E_STATE, "resume without saved state");
+    const bool finishing = step1 >= cf.n_steps;
+    if (finishing) {
+        for (auto &b : ctx->batches) {
+            ttcf_status r = ensure_reduce_buffers(ctx, b);
+            if (r != TTCF_OK) return r;
+        }
+    }
+    ctx->ran = true;
+    *(volatile int *)ctx->h_abort = 0;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.ms_spawn = ctx->ms_spawn_pending;
+    ctx->ms_spawn_pending = 0.0;
+    const bool mixed = cf.precision == TTCF_MIXED;
+    int launches = 0;
+    CK(cudaEventRecord(ctx->ev[0], ctx->st));
+    for (auto &b : ctx->batches) {
+        ElongArgs a;
+        memset(&a, 0, sizeof(a));
+        a.b = to_dev(b);
+        a.step0 = step0; a.step1 = step1;
+        a.sample_every = cf.sample_every;
+        a.fresh = step0 == 0;
+        a.save_state = save ? 1 : 0;
+        a.reset_alpha = cf.reset_alpha;
+        for (int k = 0; k < 3; k++) a.ncmax[k] = b.ncmax[k];
+        a.dt = cf.dt;
+        a.abort_flag = ctx->d_abort;
+        int grid = 0;
+        CK(launch_elong(mixed, a, ctx->nsm, ctx->st, &grid));
+        launches++;
+        ctx->stats.block_threads = std::max(ctx->stats.block_threads, elong_threads(b.N));
+    }
+    CK(cudaEventRecord(ctx->ev[1], ctx->st));
+    if (finishing) {
+        CK(cudaEventRecord(ctx->ev[2], ctx->st));
+        for (auto &b : ctx->batches) {
+            b.reduced = false;
+            ttcf_status r = reduce_batch(ctx, b);
+            if (r != TTCF_OK) return r;
+            launches += 3;
+        }
+        CK(cudaEventRecord(ctx->ev[3], ctx->st));
+    }
+    ttcf_status s = wait_with_timeout(ctx, finishing ? ctx->ev[3] : ctx->ev[1]);
+    if (s != TTCF_OK && s != TTCF_E_TIMEOUT) return s;
+    const bool timed_out = s == TTCF_E_TIMEOUT;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    ctx->stats.ms_run = ms;
+    if (finishing) {
+        float msr = 0.f;
+        cudaEventElapsedTime(&msr, ctx->ev[2], ctx->ev[3]);
+        ctx->stats.ms_reduce = msr;
+    }
+    ctx->steps_done = step1;
+    bool any_fail = false;
+    for (auto &b : ctx->batches) {
+        std::vector<int> stv(b.D());
+        std::vector<unsigned long long> pr(b.D());
+        std::vector<unsigned int> rb(b.D());
+        CK(cudaMemcpy(stv.data(), b.status, sizeof(int) * b.D(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(pr.data(), b.pairs, sizeof(unsigned long long) * b.D(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(rb.data(), b.rebuilds, sizeof(unsigned int) * b.D(), cudaMemcpyDeviceToHost));
+        for (long long d = 0; d < b.D(); d++) {
+            any_fail |= stv[d] != 0;
+            ctx->stats.pairs_interacting += (double)pr[d];
+            ctx->stats.rebuilds += (double)rb[d];
+        }
+        ctx->stats.atom_steps += (double)b.D() * b.N * (step1 - step0);
+        CK(cudaMemsetAsync(b.pairs, 0, sizeof(unsigned long long) * b.D(), ctx->st));
+        CK(cudaMemsetAsync(b.rebuilds, 0, sizeof(unsigned int) * b.D(), ctx->st));
+    }
+    ctx->stats.launches = launches;
+    if (timed_out) return fail(ctx, TTCF_E_TIMEOUT, "ttcf_run exceeded timeout_s; daughters aborted");
+    if (any_fail) return fail(ctx, TTCF_E_NUMERIC, "some daughters failed; see ttcf_group_status");
+    return TTCF_OK;
+}
+
 }  // namespace
 
 // =================================================================== ABI ==
@@ -899,7 +1034,7 @@ ttcf_status ttcf_create(const ttcf_config *cfg, ttcf_ctx **out) {
     if (!cfg || !out) return fail(nullptr, TTCF_E_INVALID, "NULL argument");
     *out = nullptr;
     const ttcf_config &c = *cfg;
-    if (c.system != TTCF_BULK_WCA && c.system != TTCF_CONFINED_LJ)
+    if (c.system != TTCF_BULK_WCA && c.system != TTCF_CONFINED_LJ && c.system != TTCF_BULK_WCA_ELONG)
         return fail(nullptr, TTCF_E_INVALID, "unknown system");
     if (c.system == TTCF_CONFINED_LJ && c.precision != TTCF_MIXED)
         return fail(nullptr, TTCF_E_INVALID, "the confined system runs in TTCF_MIXED precision only");
@@ -961,13 +1096,26 @@ ttcf_status ttcf_spawn_daughters(ttcf_ctx *ctx, int n_atoms, const double box[3]
                                  const double *mother_soa, const double *mother_alpha,
                                  const double *shear_rates, int ptr_is_device, int *batch_id) {
     if (!ctx || !box) return fail(ctx, TTCF_E_INVALID, "NULL argument");
-    if (ctx->cfg.system != TTCF_BULK_WCA)
-        return fail(ctx, TTCF_E_INVALID, "ttcf_spawn_daughters needs a TTCF_BULK_WCA context");
+    if (ctx->cfg.system != TTCF_BULK_WCA && ctx->cfg.system != TTCF_BULK_WCA_ELONG)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_spawn_daughters needs a bulk (TTCF_BULK_WCA or "
+                                         "TTCF_BULK_WCA_ELONG) context");
     if (ctx->ran) return fail(ctx, TTCF_E_STATE, "ttcf_spawn_daughters after ttcf_run");
     int maps[MAX_MAPS], M = 0;
     for (int m = 0; m < MAX_MAPS; m++) if (ctx->cfg.mapping_mask & (1u << m)) maps[M++] = m;
     const int S = ctx->cfg.n_steps / ctx->cfg.sample_every + 1;
     BatchHost b;
+    if (ctx->cfg.system == TTCF_BULK_WCA_ELONG) {   // checked before any work is queued
+        if (n_mothers <= 0 || !shear_rates)
+            return fail(ctx, TTCF_E_INVALID, "an elongational batch needs its elongation rates");
+        if (n_atoms < 4 || n_atoms > 4096) return fail(ctx, TTCF_E_INVALID, "n_atoms must be in [4, 4096]");
+        std::vector<double> rates(n_mothers);
+        if (ptr_is_device)
+            CK(cudaMemcpy(rates.data(), shear_rates, sizeof(double) * n_mothers, cudaMemcpyDeviceToHost));
+        else
+            for (int k = 0; k < n_mothers; k++) rates[k] = shear_rates[k];
+        ttcf_status ps = elong_plan(ctx, n_atoms, box, rates, b);
+        if (ps != TTCF_OK) return ps;
+    }
     Pool pool(ctx);
     ttcf_status s = make_batch(ctx, pool, b, n_atoms, box, n_mothers, mother_soa, mother_alpha,
                                shear_rates, ptr_is_device, maps, M, S, 0.0);
@@ -986,6 +1134,7 @@ ttcf_status ttcf_run(ttcf_ctx *ctx, int n_steps) {
     if (!ctx) return fail(ctx, TTCF_E_INVALID, "NULL context");
     if (ctx->batches.empty()) return fail(ctx, TTCF_E_STATE, "ttcf_run before ttcf_spawn_daughters");
     if (ctx->cfg.system == TTCF_CONFINED_LJ) return run_confined(ctx, n_steps);
+    if (ctx->cfg.system == TTCF_BULK_WCA_ELONG) return run_elong(ctx, n_steps);
     const ttcf_config &cf = ctx->cfg;
     const int step0 = ctx->steps_done;
     if (step0 >= cf.n_steps) return TTCF_OK;
@@ -1135,12 +1284,14 @@ ttcf_status ttcf_viscosity(ttcf_ctx *ctx, int batch_id, double *t, double *eta_t
                                   nullptr, tc.data(), tse.data(), (int)b->S, n_samples);
     if (s != TTCF_OK) return s;
     if (capacity < b->S) return fail(ctx, TTCF_E_INVALID, "capacity smaller than the sample count");
+    // shear: eta = -P_xy / gamma; planar elongation: eta_1 = -(P_xx - P_zz) / (4 eps)
+    const double sc = b->elong ? 4.0 * g : g;
     for (int k = 0; k < b->S; k++) {
         if (t) t[k] = tt[k];
-        if (eta_ttcf) eta_ttcf[k] = -tc[k] / g;
-        if (eta_ttcf_se) eta_ttcf_se[k] = tse[k] / fabs(g);
-        if (eta_dav) eta_dav[k] = -dv[k] / g;
-        if (eta_dav_se) eta_dav_se[k] = dse[k] / fabs(g);
+        if (eta_ttcf) eta_ttcf[k] = -tc[k] / sc;
+        if (eta_ttcf_se) eta_ttcf_se[k] = tse[k] / fabs(sc);
+        if (eta_dav) eta_dav[k] = -dv[k] / sc;
+        if (eta_dav_se) eta_dav_se[k] = dse[k] / fabs(sc);
     }
     return TTCF_OK;
 }
@@ -1204,6 +1355,12 @@ ttcf_status ttcf_get_state(ttcf_ctx *ctx, int batch_id, int daughter, double *so
         if (mixed) { float2 v; memcpy(&v, &sl[k], 8); return (double)v.x + (double)v.y; }
         double v; memcpy(&v, &sl[k], 8); return v;
     };
+    if (b->elong) {   // wrapped into the box of the last step; alpha, Lx, Lz kept
+        for (int e = 0; e < 6 * N && soa; e++) soa[e] = val(e);
+        if (alpha) *alpha = sc[0];
+        if (delta) *delta = 0.0;
+        return TTCF_OK;
+    }
     const double f = 1.0 + sc[2];
     const double dl = sc[3];
     for (int i = 0; i < N; i++) {
@@ -1237,8 +1394,8 @@ ttcf_status ttcf_sample_mothers(ttcf_ctx *ctx, int n_atoms, const double box[3],
                                 const double *init_soa, int n_eq, int n_states, int spacing,
                                 double *out_soa, double *out_alpha) {
     if (!ctx || !box || !init_soa || !out_soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
-    if (ctx->cfg.system != TTCF_BULK_WCA)
-        return fail(ctx, TTCF_E_INVALID, "ttcf_sample_mothers needs a TTCF_BULK_WCA context");
+    if (ctx->cfg.system != TTCF_BULK_WCA && ctx->cfg.system != TTCF_BULK_WCA_ELONG)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_sample_mothers needs a bulk context");
     if (n_eq < 0 || n_states < 1 || spacing < 1) return fail(ctx, TTCF_E_INVALID, "bad sampling schedule");
     const long long total = (long long)n_eq + (long long)n_states * spacing;
     if (total > 2000000000LL) return fail(ctx, TTCF_E_INVALID, "trajectory too long");
@@ -1328,8 +1485,8 @@ ttcf_status ttcf_mother_acf(ttcf_ctx *ctx, int n_atoms, const double box[3], int
                             const double *init_soa, int n_eq, int n_steps, int max_lag,
                             double *acf_pxy, double *acf_pxy2, double *eta_gk, double *series) {
     if (!ctx || !box || !init_soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
-    if (ctx->cfg.system != TTCF_BULK_WCA)
-        return fail(ctx, TTCF_E_INVALID, "ttcf_mother_acf needs a TTCF_BULK_WCA context");
+    if (ctx->cfg.system != TTCF_BULK_WCA && ctx->cfg.system != TTCF_BULK_WCA_ELONG)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_mother_acf needs a bulk context");
     if (n_eq < 0 || n_steps < 2 || max_lag < 0 || max_lag >= n_steps || n_init < 1 ||
         (long long)n_eq + n_steps > 2000000000LL)
         return fail(ctx, TTCF_E_INVALID, "bad correlation schedule");
@@ -1389,8 +1546,8 @@ ttcf_status ttcf_mother_acf(ttcf_ctx *ctx, int n_atoms, const double box[3], int
 ttcf_status ttcf_forces(ttcf_ctx *ctx, int n_atoms, const double box[3], int n_states,
                         double delta, const double *soa, double *F, double *W, double *U) {
     if (!ctx || !box || !soa) return fail(ctx, TTCF_E_INVALID, "NULL argument");
-    if (ctx->cfg.system != TTCF_BULK_WCA)
-        return fail(ctx, TTCF_E_INVALID, "ttcf_forces needs a TTCF_BULK_WCA context");
+    if (ctx->cfg.system != TTCF_BULK_WCA && ctx->cfg.system != TTCF_BULK_WCA_ELONG)
+        return fail(ctx, TTCF_E_INVALID, "ttcf_forces needs a bulk context");
     const int maps[1] = {0};
     BatchHost b;
     Pool pool(ctx);
@@ -1886,6 +2043,10 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path) {
             return bad(TTCF_E_INVALID, "checkpoint batch is inconsistent");
         if (steps_done > 0 && steps_done < c.n_steps && !b.confined && !b.state)
             return bad(TTCF_E_INVALID, "checkpoint of a partial run lacks the loop state");
+        if (c.system == TTCF_BULK_WCA_ELONG) {   // the grid bound, as the spawn planned it
+            ttcf_status ps = elong_plan(ctx, b.N, b.L, b.gamma, b);
+            if (ps != TTCF_OK) { fclose(f); return ps; }
+        }
         b.pairs = pool.get<unsigned long long>(D);
         b.rebuilds = pool.get<unsigned int>(D);
         if (pool.oom) return bad(TTCF_E_OOM, "device allocation failed (checkpoint)");
@@ -1951,7 +2112,8 @@ cudaError_t cv_raw_features(ttcf_ctx *ctx, const void *src, int kind, const Batc
 }
 
 ttcf_status cv_batch_data(ttcf_ctx *ctx, Pool &pool, BatchHost &b, float *&X, double *&z) {
-    if (b.confined || !b.feat) return fail(ctx, TTCF_E_INVALID, "the control variate needs a bulk batch");
+    if (b.confined || b.elong || !b.feat)
+        return fail(ctx, TTCF_E_INVALID, "the control variate needs a sheared bulk batch");
     for (int k = 0; k < b.M; k++)
         if (b.maps[k] > 3) return fail(ctx, TTCF_E_INVALID, "the control variate takes the mappings 0..3 of Eq. 3 only");
     const long long D = b.D();

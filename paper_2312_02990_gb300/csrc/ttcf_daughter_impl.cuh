@@ -23,41 +23,6 @@
 
 namespace ttcf {
 
-// ------------------------------------------------ generic state algebra --
-__device__ __forceinline__ df sadd(df a, df b) { return df_add(a, b); }
-__device__ __forceinline__ double sadd(double a, double b) { return a + b; }
-__device__ __forceinline__ df smul(df a, df b) { return df_mul(a, b); }
-__device__ __forceinline__ double smul(double a, double b) { return a * b; }
-__device__ __forceinline__ df smulf(df a, float b) { return df_mul_f(a, b); }
-__device__ __forceinline__ double smulf(double a, double b) { return a * b; }
-__device__ __forceinline__ df sneg(df a) { return df_neg(a); }
-__device__ __forceinline__ double sneg(double a) { return -a; }
-__device__ __forceinline__ float shi(df a) { return a.hi; }
-__device__ __forceinline__ double shi(double a) { return a; }
-__device__ __forceinline__ double sdbl(df a) { return df_to_double(a); }
-__device__ __forceinline__ double sdbl(double a) { return a; }
-template <class S> __device__ __forceinline__ S sfrom(double x);
-template <> __device__ __forceinline__ df sfrom<df>(double x) { return df_from_double(x); }
-template <> __device__ __forceinline__ double sfrom<double>(double x) { return x; }
-template <class S> __device__ __forceinline__ S sfrom_df(df x);
-template <> __device__ __forceinline__ df sfrom_df<df>(df x) { return x; }
-template <> __device__ __forceinline__ double sfrom_df<double>(df x) { return df_to_double(x); }
-
-template <class S> __device__ __forceinline__ S load_slot(const unsigned long long *p);
-template <> __device__ __forceinline__ df load_slot<df>(const unsigned long long *p) {
-    float2 v = *reinterpret_cast<const float2 *>(p);
-    return {v.x, v.y};
-}
-template <> __device__ __forceinline__ double load_slot<double>(const unsigned long long *p) {
-    return *reinterpret_cast<const double *>(p);
-}
-__device__ __forceinline__ void store_slot(unsigned long long *p, df v) {
-    *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo);
-}
-__device__ __forceinline__ void store_slot(unsigned long long *p, double v) {
-    *reinterpret_cast<double *>(p) = v;
-}
-
 // Per-daughter constants and per-step coefficients, written by thread 0.
 template <class S>
 struct Coef {
@@ -110,17 +75,6 @@ static_assert(((sizeof(Coef<df>) + 15) / 16 * 16) + sizeof(Misc) <= 2048, "Coef 
 static_assert(((sizeof(Coef<double>) + 15) / 16 * 16) + sizeof(Misc) <= 2048, "Coef + Misc exceed their reserve");
 
 // --------------------------------------------------------- reductions --
-__device__ __forceinline__ df shfl_df(df v, int o) {
-    return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
-}
-__device__ __forceinline__ df warp_sum(df v) {
-    for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_df(v, o));
-    return v;
-}
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // CTA sums of three per-thread partials in a fixed order (float partials
 // summed as double-float in MIXED mode).  Contains one __syncthreads; the

@@ -214,6 +214,54 @@ __device__ __forceinline__ double expm1_small(double x) {
     return expm1(x);
 }
 
+// ------------------------------------------------ generic state algebra --
+__device__ __forceinline__ df sadd(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ double sadd(double a, double b) { return a + b; }
+__device__ __forceinline__ df smul(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ double smul(double a, double b) { return a * b; }
+__device__ __forceinline__ df smulf(df a, float b) { return df_mul_f(a, b); }
+__device__ __forceinline__ double smulf(double a, double b) { return a * b; }
+__device__ __forceinline__ df sneg(df a) { return df_neg(a); }
+__device__ __forceinline__ double sneg(double a) { return -a; }
+__device__ __forceinline__ float shi(df a) { return a.hi; }
+__device__ __forceinline__ double shi(double a) { return a; }
+__device__ __forceinline__ double sdbl(df a) { return df_to_double(a); }
+__device__ __forceinline__ double sdbl(double a) { return a; }
+template <class S> __device__ __forceinline__ S sfrom(double x);
+template <> __device__ __forceinline__ df sfrom<df>(double x) { return df_from_double(x); }
+template <> __device__ __forceinline__ double sfrom<double>(double x) { return x; }
+template <class S> __device__ __forceinline__ S sfrom_df(df x);
+template <> __device__ __forceinline__ df sfrom_df<df>(df x) { return x; }
+template <> __device__ __forceinline__ double sfrom_df<double>(df x) { return df_to_double(x); }
+
+template <class S> __device__ __forceinline__ S load_slot(const unsigned long long *p);
+template <> __device__ __forceinline__ df load_slot<df>(const unsigned long long *p) {
+    float2 v = *reinterpret_cast<const float2 *>(p);
+    return {v.x, v.y};
+}
+template <> __device__ __forceinline__ double load_slot<double>(const unsigned long long *p) {
+    return *reinterpret_cast<const double *>(p);
+}
+__device__ __forceinline__ void store_slot(unsigned long long *p, df v) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo);
+}
+__device__ __forceinline__ void store_slot(unsigned long long *p, double v) {
+    *reinterpret_cast<double *>(p) = v;
+}
+
+// Warp sums (lane 0 holds the total).
+__device__ __forceinline__ df shfl_df(df v, int o) {
+    return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ df warp_sum(df v) {
+    for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_df(v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // ----------------------------------------------------- warp/CTA helpers --
 __device__ __forceinline__ int warp_incl_scan(int v) {
     const int lane = threadIdx.x & 31;

@@ -13,6 +13,25 @@ cudaError_t launch_daughters(bool mixed, int variant, const RunArgs &a, int thre
                              size_t smem, cudaStream_t st);
 int daughter_occupancy(bool mixed, int variant, int threads, size_t smem);
 
+// daughters under planar elongational flow (ttcf_elong.cu): one CTA per
+// daughter of one batch (gamma holds the elongation rates), persistent over
+// the batch; the cell grid of each step has at most ncmax[k] cells along
+// axis k (the bound of the largest box the run reaches).
+struct ElongArgs {
+    BatchDev b;
+    int step0, step1;              // run absolute steps step0+1 .. step1
+    int sample_every;
+    int fresh;                     // start from the mapped mother state
+    int save_state;                // write the loop state at step1
+    int reset_alpha;
+    int ncmax[3];
+    double dt;
+    const volatile int *abort_flag;  // host-mapped, may be null
+};
+size_t elong_smem_bytes(bool mixed, int N, int ncellmax);
+int elong_threads(int N);
+cudaError_t launch_elong(bool mixed, const ElongArgs &a, int nsm, cudaStream_t st, int *grid_out);
+
 // momentum kicks of copies of one phase point (ttcf_kick.cu)
 struct KickArgs {
     int N;
@@ -43,6 +62,8 @@ struct SpawnArgs {
     double *Omega;             // [D]
     double *feat;              // [G][FEAT_RAW] raw features, or null
     double delta;              // Lees-Edwards offset of the phase points
+    int elong;                 // 1: B(0) = P_xx - P_zz (planar elongational
+                               // flow; the x <-> z exchange negates it)
 };
 cudaError_t launch_spawn(const SpawnArgs &a, cudaStream_t st);
 

@@ -10,7 +10,10 @@
 //             negates it exactly, time reversal and the z-reflection keep
 //             it, the x <-> z exchange makes it the mother's P_zy (Eq. 3)
 //   Omega   = -gamma V B(0) / (k_B T)                        (Eq. 7)
-// so sum over the group of Omega(0) and of B(0) is exactly zero.
+// so sum over the group of Omega(0) and of B(0) is exactly zero.  Under
+// planar elongational flow (grad u = diag(eps, 0, -eps)) B(0) = P_xx(0) -
+// P_zz(0) instead: reflections and time reversal keep it, the x <-> z
+// exchange negates it, and Omega = -eps V B(0) / (k_B T).
 #include "ttcf_internal.h"
 
 namespace ttcf {
@@ -222,10 +225,12 @@ __global__ void spawn_kernel(SpawnArgs a) {
             tot[k] = v;
         }
         const double pxy = (tot[3] + tot[9]) / a.V, pyz = (tot[5] + tot[11]) / a.V;
+        const double pxz = ((tot[0] + tot[6]) - (tot[2] + tot[8])) / a.V;   // P_xx - P_zz
         const double gm = a.gamma[g];
         for (int k = 0; k < a.M; k++) {
             const int m = a.maps[k];
-            const double b0 = map_pxy_sign(m) * (map_swaps_xz(m) ? pyz : pxy);
+            const double b0 = a.elong ? (map_swaps_xz(m) ? -pxz : pxz)
+                                      : map_pxy_sign(m) * (map_swaps_xz(m) ? pyz : pxy);
             const size_t d = (size_t)g * a.M + k;
             a.B[d * a.S] = b0;
             a.Omega[d] = -gm * a.V * b0 / a.T;

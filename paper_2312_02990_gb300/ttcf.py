@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 TTCF_OK, TTCF_E_INVALID, TTCF_E_CUDA, TTCF_E_OOM, TTCF_E_NUMERIC, TTCF_E_TIMEOUT, TTCF_E_STATE = range(7)
-TTCF_BULK_WCA, TTCF_CONFINED_LJ = 0, 1
+TTCF_BULK_WCA, TTCF_CONFINED_LJ, TTCF_BULK_WCA_ELONG = 0, 1, 2
 CONF_NSLAB = 40
 CONF_NOBS = 2 + 2 * CONF_NSLAB + 2   # + the inner wall layers' p_x sums
 TTCF_FP64, TTCF_MIXED = 0, 1

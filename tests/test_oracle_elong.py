@@ -4,12 +4,11 @@ affinely deformed crystal, the extended-energy balance of Eq. 5 with
 grad u = diag(eps, 0, -eps), the reduction to the zero-field dynamics, the
 x <-> z exchange symmetry of the flow, and the mapping set's cancellation of
 Omega(0)."""
-import itertools
-
 import numpy as np
 import pytest
 
 import oracle
+from elong_lattice import fcc_vectors, lattice_sums
 from paper_2312_02990_gb300 import inputs
 
 RC = 2.0 ** (1.0 / 6.0)
@@ -27,34 +26,6 @@ def _eq_state(N=256, seed=7, n_eq=3000):
     return b, ms[0], al[0]
 
 
-def _fcc_vectors(a, reach):
-    """FCC lattice vectors (a/2)(n1, n2, n3), n1 + n2 + n3 even, nonzero,
-    with every component below `reach` in magnitude."""
-    m = int(np.ceil(2 * reach / a)) + 1
-    out = []
-    for n in itertools.product(range(-m, m + 1), repeat=3):
-        if n != (0, 0, 0) and sum(n) % 2 == 0:
-            v = 0.5 * a * np.array(n, dtype=float)
-            if np.all(np.abs(v) < reach):
-                out.append(v)
-    return np.array(out)
-
-
-def _lattice_sums(R0, N, V, t, eps):
-    """B = P_xx - P_zz and U of the perfect lattice deformed by
-    diag(e^{eps t}, 1, e^{-eps t}) with zero momenta: every atom sees the
-    same neighbour shell, so W_ab = (N/2) sum_R R_a R_b f(|R|)/|R|."""
-    E = np.array([np.exp(eps * t), 1.0, np.exp(-eps * t)])
-    R = R0 * E
-    r2 = np.sum(R * R, axis=1)
-    R, r2 = R[r2 < RC * RC], r2[r2 < RC * RC]
-    s3 = r2 ** -3
-    f_over_r = (48.0 * s3 * s3 - 24.0 * s3) / r2
-    U = 0.5 * N * np.sum(4.0 * (s3 * s3 - s3) + 1.0)
-    B = 0.5 * N * np.sum(f_over_r * (R[:, 0] ** 2 - R[:, 2] ** 2)) / V
-    return B, U
-
-
 def test_affine_lattice_follows_the_closed_form():
     """A perfect FCC crystal at rest stays a perfect (deformed) crystal: every
     site is an inversion centre, so all forces vanish, momenta stay zero,
@@ -68,11 +39,11 @@ def test_affine_lattice_follows_the_closed_form():
     st[:3] = inputs.fcc_lattice(N)
     fin, a_end, obs = oracle.trajectory_elong(b, st, n, eps, alpha=0.0)
     a = L / inputs.fcc_cells_for(N)
-    R0 = _fcc_vectors(a, 2.0 * RC)
+    R0 = fcc_vectors(a, 2.0 * RC)
     h = b.dt
     interacting = 0
     for k in range(0, n + 1, 25):
-        B, U = _lattice_sums(R0, N, b.V, k * h, eps)
+        B, U = lattice_sums(R0, N, b.V, k * h, eps)
         interacting += U > 0
         assert obs[k, 4] == pytest.approx(B, rel=1e-10, abs=1e-12)
         assert obs[k, 1] == pytest.approx(U, rel=1e-10, abs=1e-12)
