@@ -28,7 +28,8 @@ struct BatchHost {
     int n_obs = 1;                        // observables per sample
     bool confined = false;                // Example 2 batch (ttcf_confined.cu)
     bool elong = false;                   // planar elongational flow (ttcf_elong.cu)
-    int ncmax[3] = {0, 0, 0};             // elongational cell-grid bound per axis
+    int ncmax[3] = {0, 0, 0};             // elongational list-cell bound per axis
+    double eskin = 0.0;                   // elongational Verlet skin
     int maps[MAX_MAPS] = {};
     double L[3] = {0, 0, 0};
     double V = 0, Q = 0, gT = 0;
@@ -868,10 +869,12 @@ ttcf_confined_params conf_params_or_default(const ttcf_confined_params *p) {
 
 // ======================================================= elongational flow ==
 // Checks an elongational batch against the daughter length and sizes its
-// cell grid: the box deforms as Lx(t) = Lx e^{eps t}, Lz(t) = Lz e^{-eps t},
-// so every compressed edge must stay above 2 r_c up to t = n_steps dt, and
-// the grid (cells at least r_c (1 + 1e-4) wide) is bounded per axis by the
-// largest edge the run reaches.
+// Verlet lists and their cell grid: the box deforms as Lx(t) = Lx e^{eps t},
+// Lz(t) = Lz e^{-eps t}, and the minimum image of a listed pair is unique
+// while every edge stays above 2 r_l, r_l = r_c + skin; the skin is
+// ELONG_SKIN, or less where the most compressed edge of the run needs it
+// (at least 0.05).  The grid (cells at least r_l (1 + 1e-4) wide) is
+// bounded per axis by the largest edge the run reaches.
 ttcf_status elong_plan(ttcf_ctx *ctx, int N, const double box[3], const std::vector<double> &rates,
                        BatchHost &b) {
     const ttcf_config &cf = ctx->cfg;
@@ -882,14 +885,16 @@ ttcf_status elong_plan(ttcf_ctx *ctx, int N, const double box[3], const std::vec
         emax = std::max(emax, r);
         emin = std::min(emin, r);
     }
-    const double lo_x = box[0] * exp(emin * t_end), lo_z = box[2] * exp(-emax * t_end);
-    if (!(lo_x > 2.002 * RC_WCA) || !(lo_z > 2.002 * RC_WCA) || !(box[1] > 2.002 * RC_WCA))
+    const double lo = std::min({box[0] * exp(emin * t_end), box[1], box[2] * exp(-emax * t_end)});
+    const double skin = std::min(ELONG_SKIN, 0.5 * lo - RC_WCA - 0.01);
+    if (!(skin >= 0.05))
         return fail(ctx, TTCF_E_INVALID, "elongation too strong for the daughter length: a compressed "
-                                         "box edge would fall below 2 r_c");
+                                         "box edge would fall below 2 (r_c + 0.06)");
+    const double w = (RC_WCA + skin) * (1.0 + 1e-4);
     const double hi[3] = {box[0] * exp(emax * t_end), box[1], box[2] * exp(-emin * t_end)};
     for (int k = 0; k < 3; k++) {
-        const double n = floor(hi[k] / (RC_WCA * (1.0 + 1e-4))) + 1.0;
-        if (!(n >= 1.0 && n <= 4096.0)) return fail(ctx, TTCF_E_INVALID, "elongational box too large");
+        const double n = floor(hi[k] / w) + 1.0;
+        if (!(n >= 1.0 && n <= 40.0)) return fail(ctx, TTCF_E_INVALID, "elongational box too large");
         b.ncmax[k] = (int)n;
     }
     const size_t smem = elong_smem_bytes(cf.precision == TTCF_MIXED, N,
@@ -897,6 +902,7 @@ ttcf_status elong_plan(ttcf_ctx *ctx, int N, const double box[3], const std::vec
     if (smem > (size_t)ctx->smem_optin)
         return fail(ctx, TTCF_E_INVALID, "n_atoms too large for an elongational daughter in one CTA's "
                                          "shared memory");
+    b.eskin = skin;
     b.elong = true;
     return TTCF_OK;
 }
@@ -934,11 +940,24 @@ ttcf_status run_elong(ttcf_ctx *ctx, int n_steps) {
     ctx->ms_spawn_pending = 0.0;
     const bool mixed = cf.precision == TTCF_MIXED;
     int launches = 0;
+    Pool scratch(ctx);
+    std::vector<int> grids;
+    std::vector<unsigned short *> lists;
+    for (auto &b : ctx->batches) {   // Verlet list scratch of each launch
+        const int g = elong_grid(mixed, b.N, b.ncmax[0] * b.ncmax[1] * b.ncmax[2], ctx->nsm, b.D());
+        if (g <= 0) return fail(ctx, TTCF_E_INVALID, "an elongational daughter does not fit one CTA");
+        grids.push_back(g);
+        lists.push_back(scratch.get<unsigned short>((size_t)g * ELONG_CAP * b.N));
+        if (scratch.oom) return fail(ctx, TTCF_E_OOM, "device allocation failed (Verlet lists)");
+    }
     CK(cudaEventRecord(ctx->ev[0], ctx->st));
-    for (auto &b : ctx->batches) {
+    for (size_t q = 0; q < ctx->batches.size(); q++) {
+        BatchHost &b = ctx->batches[q];
         ElongArgs a;
         memset(&a, 0, sizeof(a));
         a.b = to_dev(b);
+        a.skin = (float)b.eskin;
+        a.nbr = lists[q];
         a.step0 = step0; a.step1 = step1;
         a.sample_every = cf.sample_every;
         a.fresh = step0 == 0;
@@ -947,8 +966,7 @@ ttcf_status run_elong(ttcf_ctx *ctx, int n_steps) {
         for (int k = 0; k < 3; k++) a.ncmax[k] = b.ncmax[k];
         a.dt = cf.dt;
         a.abort_flag = ctx->d_abort;
-        int grid = 0;
-        CK(launch_elong(mixed, a, ctx->nsm, ctx->st, &grid));
+        CK(launch_elong(mixed, a, grids[q], ctx->st));
         launches++;
         ctx->stats.block_threads = std::max(ctx->stats.block_threads, elong_threads(b.N));
     }
@@ -969,6 +987,7 @@ ttcf_status run_elong(ttcf_ctx *ctx, int n_steps) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
     ctx->stats.ms_run = ms;
+    ctx->stats.skin = ctx->batches[0].eskin;
     if (finishing) {
         float msr = 0.f;
         cudaEventElapsedTime(&msr, ctx->ev[2], ctx->ev[3]);

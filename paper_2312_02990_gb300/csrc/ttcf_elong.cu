@@ -19,18 +19,23 @@
 // Omega = -eps V B(0) / (k_B T) in IEEE double (Omega = beta dH^ad/dt with
 // dH^ad/dt = -V grad u : P).
 //
-// Layout: one CTA per daughter, the whole daughter in shared memory (the
-// phase point as 8-byte slots, forces, a cell-ordered copy of the
-// positions).  The box changes every step, so the cell grid (cells at
-// least r_c wide) is rebuilt from the new box every step: a counting sort
-// of the atoms into cells, each cell put in index order (atomic slots
-// depend on scheduling; the order fixes the force sums bit for bit), and a
-// force pass over the 27 neighbour cells with one periodic image shift per
-// cell.  The force pass takes atoms in cell order, so that neighbouring
-// lanes scan nearly the same cells; the integrator passes take them in
-// index order.  A grid with fewer than three cells along an axis visits the
-// same cell under two or three shifts, each a distinct image: with every box
-// edge above 2 r_c at most one of them lies within r_c.
+// Layout: one CTA per daughter, the whole daughter in shared memory (hi and
+// lo parts of the positions, momenta as 8-byte slots, forces, list
+// references) except its Verlet lists, which sit in a per-CTA global
+// scratch (L2-resident).  The lists hold each atom's neighbours within
+// r_l = r_c + skin in index order; the force pass takes every pair at its
+// minimum image in the current box, so a list built at any time gives the
+// same force sums bit for bit (chunked runs equal uninterrupted ones).
+// Because the box deforms, a pair's separation follows the affine flow plus
+// the atoms' own displacements u = r - diag(e^{eps dt}, 1, e^{-eps dt}) r0
+// since the build; the lists are rebuilt when 2 max|u| reaches
+// e^{-|eps| dt} r_l - r_c (the affine flow shrinks distances by at most that
+// factor).  Builds bin the atoms into cells at least r_l wide (distinct
+// cells only, so an axis with fewer than three cells is scanned once) and
+// leave the atoms in cell order, which is the order of the force pass
+// (neighbouring lanes then read nearby atoms); the integrator passes take
+// atoms in index order, and the per-atom virial terms are summed in index
+// order too.
 // MIXED: double-float phase point, FP32 pairs, the per-step sums in exact
 // 64-bit fixed point; FP64: IEEE double throughout.
 #include <algorithm>
@@ -43,17 +48,9 @@ namespace ttcf {
 namespace {
 
 constexpr double RC = 1.1224620483093730;          // 2^(1/6)
-constexpr double CELL_MIN = RC * (1.0 + 1e-4);     // smallest cell width
 
-// A cell-ordered position of the FP64 mode (index in w).
+// A position (or force and virial term) of the FP64 mode.
 struct alignas(16) Pd { double x, y, z, w; };
-
-__device__ __forceinline__ int idx_of(const float4 &p) { return __float_as_int(p.w); }
-__device__ __forceinline__ int idx_of(const Pd &p) { return (int)p.w; }
-__device__ __forceinline__ float4 make_p4(float x, float y, float z, int i) {
-    return make_float4(x, y, z, __int_as_float(i));
-}
-__device__ __forceinline__ Pd make_p4(double x, double y, double z, int i) { return {x, y, z, (double)i}; }
 
 __device__ __forceinline__ df sexpm1(df x, df sixth) { return df_expm1_small(x, sixth); }
 __device__ __forceinline__ double sexpm1(double x, double) { return expm1_small(x); }
@@ -105,11 +102,23 @@ struct ElongScal {
     S ex, ez, phx, phz;      // drift factors e^{+-eps h} and (e^{+-eps h} - 1)/(+-eps)
     S cxh, czh;              // C' factors e^{-eps h/2}, e^{eps h/2}
     S h, hh, hhQ, ngT, nhh, sixth;
+    S Lg[3];                 // box edges of the grid (image shifts of the pair distances)
     double invV;
-    S Lg[3];                 // box edges of the grid (image shifts of the force pass)
-    float Lf[3];             // the same in float (binning)
-    float sf[3];             // cells per unit length
+    float Lf[3], invLf[3];   // the same box in float (binning, image choice)
+    float sf[3];             // list cells per unit length
     int nc[3], ncell;
+    // Verlet lists: radius r_l = r_c + skin, built from positions r0 at time
+    // t0; a pair outside r_l at t0 stays outside r_c while
+    // 2 max|u| < e^{-|eps| (t - t0)} r_l - r_c, with u = r - diag(e^{eps(t - t0)},
+    // 1, e^{-eps(t - t0)}) r0 (minimum image) the displacement beyond the
+    // affine flow
+    float rl, rl2;
+    float fxa, fza, ea;      // e^{eps (t - t0)}, e^{-eps (t - t0)}, e^{-|eps| (t - t0)} for the next step
+    float exf, ezf, eaf;     // their one-step factors
+    float thr2;              // rebuild when max |u|^2 >= thr2 (negative: at once)
+    unsigned int umax2;      // float bits of this step's max |u|^2
+    int rebuild;             // build before the next force pass
+    int n_build;
     int stop;                // TTCF_D_* flags of the daughter
     int flag_lost;           // a per-step sum out of the fixed-point range
     unsigned long long pairs;
@@ -117,11 +126,11 @@ struct ElongScal {
 };
 
 size_t elong_smem_bytes(bool mixed, int N, int ncellmax) {
-    const size_t rsz = mixed ? 4 : 8;
-    size_t b = (size_t)6 * N * 8;                 // phase point slots
-    b += align16((size_t)3 * N * rsz);            // forces
-    b += (size_t)N * (mixed ? 16 : 32);           // cell-ordered positions
-    b += 2 * align16((size_t)N * 4);              // cell and slot of each atom
+    size_t b = (size_t)N * 32;                    // positions (hi and lo float4, or double)
+    b += align16((size_t)N * 24);                 // momenta (16-byte regions: odd N)
+    b += (size_t)N * (mixed ? 16 : 32);           // forces and per-atom virial
+    b += (size_t)N * 16;                          // reference positions of the lists
+    b += 3 * align16((size_t)N * 2) + align16((size_t)N);   // cell order, cell, slot; list lengths
     b += align16((size_t)ncellmax * 4) + align16((size_t)(ncellmax + 2) * 4);
     b += align16(mixed ? sizeof(ElongScal<df>) : sizeof(ElongScal<double>));
     b += 32 * 4 + 16;                             // scan scratch
@@ -139,7 +148,7 @@ template <bool MIXED>
 __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
     using S = typename std::conditional<MIXED, df, double>::type;    // state scalar
     using R = typename std::conditional<MIXED, float, double>::type; // pair arithmetic
-    using P4 = typename std::conditional<MIXED, float4, Pd>::type;
+    using R4 = typename std::conditional<MIXED, float4, Pd>::type;
     const int tid = threadIdx.x, T = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     const BatchDev &b = a.b;
@@ -148,30 +157,64 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
     const int map = b.maps[d % b.M];
     const double eps = b.gamma[gl];
     const int ncm = a.ncmax[0] * a.ncmax[1] * a.ncmax[2];
+    unsigned short *nb = a.nbr + (size_t)blockIdx.x * ELONG_CAP * N;   // [ELONG_CAP][N] lists
 
     // shared-memory carve-up (elong_smem_bytes mirrors it)
     unsigned char *sp = smem;
-    unsigned long long *st = (unsigned long long *)sp; sp += (size_t)6 * N * 8;
-    R *F = (R *)sp; sp += align16((size_t)3 * N * sizeof(R));
-    P4 *cpos = (P4 *)sp; sp += (size_t)N * sizeof(P4);
-    int *cellof = (int *)sp; sp += align16((size_t)N * 4);
-    int *rank = (int *)sp; sp += align16((size_t)N * 4);
+    float4 *pos4 = nullptr, *plo4 = nullptr;   // MIXED: hi and lo parts of the positions
+    Pd *posd = nullptr;                        // FP64
+    if constexpr (MIXED) {
+        pos4 = (float4 *)sp; plo4 = pos4 + N;
+    } else {
+        posd = (Pd *)sp;
+    }
+    sp += (size_t)N * 32;
+    unsigned long long *mom = (unsigned long long *)sp; sp += align16((size_t)N * 24);   // [3][N] slots
+    R4 *F4 = (R4 *)sp; sp += (size_t)N * sizeof(R4);          // force and per-atom virial
+    float4 *ref4 = (float4 *)sp; sp += (size_t)N * 16;
+    unsigned short *catom = (unsigned short *)sp; sp += align16((size_t)N * 2);   // atoms in cell order
+    unsigned short *cellof = (unsigned short *)sp; sp += align16((size_t)N * 2);
+    unsigned short *rank = (unsigned short *)sp; sp += align16((size_t)N * 2);
+    unsigned char *cntl = (unsigned char *)sp; sp += align16((size_t)N);       // list lengths (cell order)
     int *cnt = (int *)sp; sp += align16((size_t)ncm * 4);
     int *start = (int *)sp; sp += align16((size_t)(ncm + 2) * 4);
     ElongScal<S> *m = (ElongScal<S> *)sp; sp += align16(sizeof(ElongScal<S>));
     int *warp_tmp = (int *)sp;
 
-    // the cell grid of a box (thread 0): cells at least CELL_MIN wide, at
-    // most the planned bound per axis (fewer cells are wider, still valid)
+    auto ld_pos = [&](int i, S &x, S &y, S &z) {
+        if constexpr (MIXED) {
+            const float4 h = pos4[i], l = plo4[i];
+            x = {h.x, l.x}; y = {h.y, l.y}; z = {h.z, l.z};
+        } else {
+            const Pd p = posd[i];
+            x = p.x; y = p.y; z = p.z;
+        }
+    };
+    auto st_pos = [&](int i, S x, S y, S z) {
+        if constexpr (MIXED) {
+            pos4[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
+            plo4[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
+        } else {
+            posd[i] = {x, y, z, 0.0};
+        }
+    };
+    auto pos_r = [&](int i) -> R4 {   // the pair-arithmetic positions (hi parts in MIXED)
+        if constexpr (MIXED) return pos4[i]; else return posd[i];
+    };
+
+    // the list-cell grid of a box (thread 0): cells at least r_l (1 + 1e-4)
+    // wide, at most the planned bound per axis (fewer cells are wider)
     auto set_grid = [&](S Lx, S Lz) {
         m->Lg[0] = Lx; m->Lg[1] = m->Ly; m->Lg[2] = Lz;
         m->Lf[0] = (float)shi(Lx); m->Lf[1] = (float)b.L[1]; m->Lf[2] = (float)shi(Lz);
+        const float inv_w = 1.0f / (m->rl * 1.0001f);
         int nct = 1;
         for (int k = 0; k < 3; k++) {
-            int n = (int)(m->Lf[k] * (float)(1.0 / CELL_MIN));
+            int n = (int)(m->Lf[k] * inv_w);
             n = n < 1 ? 1 : (n > a.ncmax[k] ? a.ncmax[k] : n);
             m->nc[k] = n;
             m->sf[k] = (float)n / m->Lf[k];
+            m->invLf[k] = 1.0f / m->Lf[k];
             nct *= n;
         }
         m->ncell = nct;
@@ -191,6 +234,11 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
         m->nhh = sfrom<S>(-hh); m->sixth = sfrom<S>(1.0 / 6.0);
         m->Ly = sfrom<S>(b.L[1]); m->hLy = sfrom<S>(0.5 * b.L[1]);
         m->invV = 1.0 / b.V;
+        m->rl = (float)(RC + (double)a.skin);
+        m->rl2 = m->rl * m->rl;
+        m->exf = (float)exp(eps * h); m->ezf = (float)exp(-eps * h); m->eaf = (float)exp(-fabs(eps) * h);
+        m->fxa = m->fza = m->ea = 1.f;
+        m->thr2 = -1.f; m->umax2 = 0u; m->rebuild = 1; m->n_build = 0;
         if (a.fresh) {
             const double sa = map_reverses_time(map) ? -1.0 : 1.0;
             m->alpha = sfrom<S>(a.reset_alpha ? 0.0 : sa * b.m_alpha[gl]);
@@ -204,7 +252,6 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
         }
         set_grid(m->Lx, m->Lz);
     }
-    for (int c = tid; c < ncm; c += T) cnt[c] = 0;
     __syncthreads();
 
     // ---- the phase point: the mapped mother (codes as for shear), or the
@@ -217,7 +264,7 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
         const R Lh[3] = {(R)(0.5 * b.L[0]), (R)(0.5 * b.L[1]), (R)(0.5 * b.L[2])};
         auto reflect = [&](S c, int k) {   // -(-L/2) = +L/2 is the periodic point -L/2
             c = sneg(c);
-            if (shi(c) >= Lh[k]) c = sadd(c, sneg(L0[k]));
+            if (shi(c) >= Lh[k]) c = xadd(c, sneg(L0[k]));
             return c;
         };
         for (int i = tid; i < N; i += T) {
@@ -229,34 +276,29 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
             if (mp & 4) { y = reflect(y, 1); py = sneg(py); }
             if (mp & 8) { z = reflect(z, 2); pz = sneg(pz); }
             if (map_reverses_time(mp)) { px = sneg(px); py = sneg(py); pz = sneg(pz); }
-            store_slot(st + i, x); store_slot(st + N + i, y); store_slot(st + 2 * N + i, z);
-            store_slot(st + 3 * N + i, px); store_slot(st + 4 * N + i, py); store_slot(st + 5 * N + i, pz);
+            st_pos(i, x, y, z);
+            store_slot(mom + i, px); store_slot(mom + N + i, py); store_slot(mom + 2 * N + i, pz);
         }
     }
 
     // ---- building blocks ----
-    // cell of atom i from its position (hi parts), atomic slot in the cell
-    auto bin_atom = [&](int i, R x, R y, R z) {
-        const float p[3] = {(float)x, (float)y, (float)z};
-        int cc[3];
-        for (int k = 0; k < 3; k++) {
-            int c = __float2int_rd(__fmul_rn(__fmaf_rn(0.5f, m->Lf[k], p[k]), m->sf[k]));
-            cc[k] = c < 0 ? 0 : (c >= m->nc[k] ? m->nc[k] - 1 : c);
-        }
-        const int c = (cc[2] * m->nc[1] + cc[1]) * m->nc[0] + cc[0];
-        cellof[i] = c;
-        rank[i] = atomicAdd(&cnt[c], 1);
+    // minimum image of a coordinate difference: the image chosen in float
+    // (relevant pairs lie far inside half a box edge), applied at R
+    auto mimg = [](R dd, float il, R L) -> R {
+        const float n = rintf(__fmul_rn((float)dd, il));
+        return rfma(-(R)n, L, dd);
     };
     // kinetic partials of a thread's atoms (index order): sum p^2 and
-    // sum (px^2 - pz^2), from the hi parts in MIXED
-    auto kin_partial = [&](R &k2, R &bk) {
+    // sum (px^2 - pz^2) (+ half the atoms' virial terms), hi parts in MIXED
+    auto kin_partial = [&](R &k2, R &bk, bool virial) {
         k2 = (R)0; bk = (R)0;
         for (int i = tid; i < N; i += T) {
-            const R qx = (R)shi(load_slot<S>(st + 3 * N + i));
-            const R qy = (R)shi(load_slot<S>(st + 4 * N + i));
-            const R qz = (R)shi(load_slot<S>(st + 5 * N + i));
+            const R qx = (R)shi(load_slot<S>(mom + i));
+            const R qy = (R)shi(load_slot<S>(mom + N + i));
+            const R qz = (R)shi(load_slot<S>(mom + 2 * N + i));
             k2 = radd(k2, rfma(qz, qz, rfma(qy, qy, rmul(qx, qx))));
             bk = radd(bk, rsub(rmul(qx, qx), rmul(qz, qz)));
+            if (virial) bk = rfma((R)0.5, F4[i].w, bk);
         }
     };
     // CTA sums of two per-thread partials, valid in thread 0.  MIXED: 64-bit
@@ -304,75 +346,111 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
             }
         }
     };
-    // cell sort, cell-ordered copy, forces into F (the cell counts must be
-    // complete); returns the thread's partial of sum over ordered pairs of
-    // f (dx^2 - dz^2) and counts the interacting ordered pairs.
-    const R rc2 = (R)1.2599210498948732;
-    unsigned int npair = 0;
-    auto forces = [&]() -> R {
+    // Verlet lists: atoms binned into the list cells, then each atom's
+    // neighbours within r_l (minimum image) from the distinct cells around
+    // it, kept in index order (the force sums then do not depend on when a
+    // list was built), written to the CTA's global scratch in cell order.
+    auto build_lists = [&]() {
+        for (int c = tid; c < ncm; c += T) cnt[c] = 0;
+        __syncthreads();
+        if (tid == 0) { m->rebuild = 0; m->n_build++; m->fxa = m->fza = m->ea = 1.f; }
+        for (int i = tid; i < N; i += T) {
+            const R4 p = pos_r(i);
+            const float q[3] = {(float)p.x, (float)p.y, (float)p.z};
+            int cc[3];
+            for (int k = 0; k < 3; k++) {
+                const int c = __float2int_rd(__fmul_rn(__fmaf_rn(0.5f, m->Lf[k], q[k]), m->sf[k]));
+                cc[k] = c < 0 ? 0 : (c >= m->nc[k] ? m->nc[k] - 1 : c);
+            }
+            const int c = (cc[2] * m->nc[1] + cc[1]) * m->nc[0] + cc[0];
+            cellof[i] = (unsigned short)c;
+            rank[i] = (unsigned short)atomicAdd(&cnt[c], 1);
+            ref4[i] = make_float4(q[0], q[1], q[2], 0.f);
+        }
+        __syncthreads();
         cta_exclusive_scan(cnt, start, m->ncell, warp_tmp);
         __syncthreads();
-        for (int i = tid; i < N; i += T) {
-            const R x = (R)shi(load_slot<S>(st + i)), y = (R)shi(load_slot<S>(st + N + i)),
-                    z = (R)shi(load_slot<S>(st + 2 * N + i));
-            cpos[start[cellof[i]] + rank[i]] = make_p4(x, y, z, i);
-        }
-        __syncthreads();
-        for (int c = tid; c < m->ncell; c += T) {   // each cell in index order
-            for (int u = start[c] + 1; u < start[c + 1]; u++) {
-                const P4 v = cpos[u];
-                int w = u;
-                while (w > start[c] && idx_of(cpos[w - 1]) > idx_of(v)) { cpos[w] = cpos[w - 1]; w--; }
-                cpos[w] = v;
-            }
-        }
+        for (int i = tid; i < N; i += T) catom[start[cellof[i]] + rank[i]] = (unsigned short)i;
         __syncthreads();
         const int nc0 = m->nc[0], nc1 = m->nc[1], nc2 = m->nc[2];
         const R Lx = (R)shi(m->Lg[0]), Ly = (R)shi(m->Lg[1]), Lz = (R)shi(m->Lg[2]);
-        R wd = (R)0;
+        const float ilx = m->invLf[0], ily = m->invLf[1], ilz = m->invLf[2];
+        const R rl2 = (R)m->rl2;
         for (int k = tid; k < N; k += T) {
-            const P4 pi = cpos[k];
-            const int i = idx_of(pi);
+            const int i = catom[k];
+            const R4 pi = pos_r(i);
             const int c = cellof[i];
             const int cx = c % nc0, cy = (c / nc0) % nc1, cz = c / (nc0 * nc1);
-            R fx = (R)0, fy = (R)0, fz = (R)0;
-            for (int oz = -1; oz <= 1; oz++) {
-                int zc = cz + oz;
-                const int kz = zc < 0 ? -1 : (zc >= nc2 ? 1 : 0);
-                zc -= kz * nc2;
-                const R uz = rfma(-(R)kz, Lz, pi.z);   // i against the image of the cell row
-                for (int oy = -1; oy <= 1; oy++) {
-                    int yc = cy + oy;
-                    const int ky = yc < 0 ? -1 : (yc >= nc1 ? 1 : 0);
-                    yc -= ky * nc1;
-                    const R uy = rfma(-(R)ky, Ly, pi.y);
-                    for (int ox = -1; ox <= 1; ox++) {
-                        int xc = cx + ox;
-                        const int kx = xc < 0 ? -1 : (xc >= nc0 ? 1 : 0);
-                        xc -= kx * nc0;
-                        const R ux = rfma(-(R)kx, Lx, pi.x);
-                        const int cc = (zc * nc1 + yc) * nc0 + xc;
-                        const int t1 = start[cc + 1];
-                        for (int t = start[cc]; t < t1; t++) {
-                            const P4 pj = cpos[t];
-                            const R dx = rsub(ux, pj.x), dy = rsub(uy, pj.y), dz = rsub(uz, pj.z);
-                            const R r2 = rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
-                            if (r2 < rc2 && idx_of(pj) != i) {
-                                const R s = (R)1 / r2;
-                                const R s3 = rmul(rmul(s, s), s);
-                                const R f = rmul(rmul(s, s3), rfma((R)48, s3, (R)-24));
-                                fx = rfma(f, dx, fx); fy = rfma(f, dy, fy); fz = rfma(f, dz, fz);
-                                wd = rfma(f, rsub(rmul(dx, dx), rmul(dz, dz)), wd);
-                                npair++;
+            // each distinct cell within one of the atom's: three per axis, or
+            // all of them where the axis has fewer than three
+            const int z0 = nc2 >= 3 ? cz + nc2 - 1 : 0, zn = nc2 >= 3 ? 3 : nc2;
+            const int y0 = nc1 >= 3 ? cy + nc1 - 1 : 0, yn = nc1 >= 3 ? 3 : nc1;
+            const int x0 = nc0 >= 3 ? cx + nc0 - 1 : 0, xn = nc0 >= 3 ? 3 : nc0;
+            unsigned short lst[ELONG_CAP];
+            int n = 0, over = 0;
+            for (int oz = 0; oz < zn; oz++) {
+                const int zc = (z0 + oz) % nc2;
+                for (int oy = 0; oy < yn; oy++) {
+                    const int yc = (y0 + oy) % nc1;
+                    for (int ox = 0; ox < xn; ox++) {
+                        const int cc = (zc * nc1 + yc) * nc0 + (x0 + ox) % nc0;
+                        for (int t = start[cc]; t < start[cc + 1]; t++) {
+                            const int j = catom[t];
+                            if (j == i) continue;
+                            const R4 pj = pos_r(j);
+                            const R dx = mimg(rsub(pi.x, pj.x), ilx, Lx);
+                            const R dy = mimg(rsub(pi.y, pj.y), ily, Ly);
+                            const R dz = mimg(rsub(pi.z, pj.z), ilz, Lz);
+                            if (rfma(dz, dz, rfma(dy, dy, rmul(dx, dx))) < rl2) {
+                                if (n == ELONG_CAP) { over = 1; continue; }
+                                int w = n++;
+                                while (w > 0 && lst[w - 1] > j) { lst[w] = lst[w - 1]; w--; }
+                                lst[w] = (unsigned short)j;
                             }
                         }
                     }
                 }
             }
-            F[i] = fx; F[N + i] = fy; F[2 * N + i] = fz;
+            for (int e = 0; e < n; e++) nb[(size_t)e * N + k] = lst[e];
+            cntl[k] = (unsigned char)n;
+            if (over) atomicOr(&m->stop, TTCF_D_NBR_OVERFLOW);
         }
         __syncthreads();
-        return wd;
+    };
+    // forces from the lists (atoms in the lists' cell order), into F4 with
+    // each atom's virial term sum_j f (dx^2 - dz^2); counts the interacting
+    // ordered pairs
+    const R rc2 = (R)1.2599210498948732;
+    unsigned int npair = 0;
+    auto force_pass = [&]() {
+        const R Lx = (R)shi(m->Lg[0]), Ly = (R)shi(m->Lg[1]), Lz = (R)shi(m->Lg[2]);
+        const float ilx = m->invLf[0], ily = m->invLf[1], ilz = m->invLf[2];
+        for (int k = tid; k < N; k += T) {
+            const int i = catom[k];
+            const R4 pi = pos_r(i);
+            const int n = cntl[k];
+            R fx = (R)0, fy = (R)0, fz = (R)0, wv = (R)0;
+            for (int e = 0; e < n; e++) {
+                const int j = nb[(size_t)e * N + k];
+                const R4 pj = pos_r(j);
+                const R dx = mimg(rsub(pi.x, pj.x), ilx, Lx);
+                const R dy = mimg(rsub(pi.y, pj.y), ily, Ly);
+                const R dz = mimg(rsub(pi.z, pj.z), ilz, Lz);
+                const R r2 = rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
+                if (r2 < rc2) {
+                    const R s = (R)1 / r2;
+                    const R s3 = rmul(rmul(s, s), s);
+                    const R f = rmul(rmul(s, s3), rfma((R)48, s3, (R)-24));
+                    fx = rfma(f, dx, fx); fy = rfma(f, dy, fy); fz = rfma(f, dz, fz);
+                    wv = rfma(f, rsub(rmul(dx, dx), rmul(dz, dz)), wv);
+                    npair++;
+                }
+            }
+            R4 o;
+            o.x = fx; o.y = fy; o.z = fz; o.w = wv;
+            F4[i] = o;
+        }
+        __syncthreads();
     };
     // thread 0: the box one step on, and its grid (the positions the next
     // drift makes live there)
@@ -382,6 +460,13 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
         m->hLx1 = xmulf(m->Lx1, (R)0.5);
         m->hLz1 = xmulf(m->Lz1, (R)0.5);
         set_grid(m->Lx1, m->Lz1);
+    };
+    // thread 0: the affine factors and the rebuild threshold of the next step
+    auto advance_lists = [&]() {
+        m->fxa *= m->exf; m->fza *= m->ezf; m->ea *= m->eaf;
+        const float thr = 0.5f * (m->ea * m->rl - (float)RC) - 2e-3f;
+        m->thr2 = thr > 0.f ? thr * thr : -1.f;
+        m->umax2 = 0u;
     };
     // thread 0: the opening E flow of a step (alpha at the end of the last
     // step and sum p^2 there) and its D factor
@@ -399,22 +484,20 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
         open_step(inc);
     };
 
-    // ---- forces and sum p^2 at the starting point ----
+    // ---- lists, forces and sum p^2 at the starting point ----
     __syncthreads();
-    for (int i = tid; i < N; i += T)
-        bin_atom(i, (R)shi(load_slot<S>(st + i)), (R)shi(load_slot<S>(st + N + i)),
-                 (R)shi(load_slot<S>(st + 2 * N + i)));
-    __syncthreads();
-    forces();
+    build_lists();
+    force_pass();
     npair = 0;   // counted over the steps only
     {
         R k2, bk;
-        kin_partial(k2, bk);
+        kin_partial(k2, bk, false);
         S sums[2];
         cta_sum2(k2, (R)0, sums);
         if (tid == 0) {
             open_step(e_increment(sums[0]));   // the first step's opening E flow
             advance_box();
+            advance_lists();
             if (m->flag_lost || !isfinite(sdbl(sums[0]))) m->stop |= TTCF_D_NONFINITE;
         }
     }
@@ -423,50 +506,59 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
     int steps_run = 0;
     for (int s = a.step0 + 1; s <= a.step1 && !m->stop; s++) {
         // ---- D, C', B half flows, A' drift into the box of step s (Lx1,
-        //      Lz1), binning on its grid ----
-        for (int c = tid; c < ncm; c += T) cnt[c] = 0;
-        __syncthreads();
+        //      Lz1), displacement beyond the affine flow since the lists ----
         {
             const S c = m->c, cxh = m->cxh, czh = m->czh, hh = m->hh;
             const S ex = m->ex, ez = m->ez, phx = m->phx, phz = m->phz, h = m->h;
             const S Lx = m->Lx1, Lz = m->Lz1, hLx = m->hLx1, hLz = m->hLz1, Ly = m->Ly, hLy = m->hLy;
+            const float fxa = m->fxa, fza = m->fza;
+            const float Lxf = m->Lf[0], Lyf = m->Lf[1], Lzf = m->Lf[2];
+            const float ilx = m->invLf[0], ily = m->invLf[1], ilz = m->invLf[2];
+            float umax = 0.f;
             for (int i = tid; i < N; i += T) {
-                S px = load_slot<S>(st + 3 * N + i), py = load_slot<S>(st + 4 * N + i),
-                  pz = load_slot<S>(st + 5 * N + i);
+                S px = load_slot<S>(mom + i), py = load_slot<S>(mom + N + i), pz = load_slot<S>(mom + 2 * N + i);
+                const R4 f = F4[i];
                 px = xmul(px, c); py = xmul(py, c); pz = xmul(pz, c);
                 px = xmul(px, cxh); pz = xmul(pz, czh);
-                px = xadd(px, xmulf(hh, F[i]));
-                py = xadd(py, xmulf(hh, F[N + i]));
-                pz = xadd(pz, xmulf(hh, F[2 * N + i]));
-                S x = load_slot<S>(st + i), y = load_slot<S>(st + N + i), z = load_slot<S>(st + 2 * N + i);
+                px = xadd(px, xmulf(hh, f.x));
+                py = xadd(py, xmulf(hh, f.y));
+                pz = xadd(pz, xmulf(hh, f.z));
+                S x, y, z;
+                ld_pos(i, x, y, z);
                 x = wrap_once(xadd(xmul(x, ex), xmul(px, phx)), Lx, hLx);
                 y = wrap_once(xadd(y, xmul(py, h)), Ly, hLy);
                 z = wrap_once(xadd(xmul(z, ez), xmul(pz, phz)), Lz, hLz);
-                store_slot(st + i, x); store_slot(st + N + i, y); store_slot(st + 2 * N + i, z);
-                store_slot(st + 3 * N + i, px); store_slot(st + 4 * N + i, py); store_slot(st + 5 * N + i, pz);
-                bin_atom(i, (R)shi(x), (R)shi(y), (R)shi(z));
+                st_pos(i, x, y, z);
+                store_slot(mom + i, px); store_slot(mom + N + i, py); store_slot(mom + 2 * N + i, pz);
+                const float4 r0 = ref4[i];
+                float ux = (float)shi(x) - fxa * r0.x, uy = (float)shi(y) - r0.y, uz = (float)shi(z) - fza * r0.z;
+                ux -= Lxf * rintf(ux * ilx); uy -= Lyf * rintf(uy * ily); uz -= Lzf * rintf(uz * ilz);
+                const float u2 = ux * ux + uy * uy + uz * uz;
+                if (!(u2 <= umax) && umax == umax) umax = u2;   // a NaN stays and forces a rebuild
             }
+            if (umax > 0.f || umax != umax) atomicMax(&m->umax2, __float_as_uint(umax));
         }
         __syncthreads();
-        const R wd = forces();
+        if (m->rebuild || __uint_as_float(m->umax2) >= m->thr2 || m->umax2 > 0x7f800000u) build_lists();
+        force_pass();
         // ---- B, C', D half flows with the new forces ----
         {
             const S c = m->c, cxh = m->cxh, czh = m->czh, hh = m->hh;
             for (int i = tid; i < N; i += T) {
-                S px = load_slot<S>(st + 3 * N + i), py = load_slot<S>(st + 4 * N + i),
-                  pz = load_slot<S>(st + 5 * N + i);
-                px = xadd(px, xmulf(hh, F[i]));
-                py = xadd(py, xmulf(hh, F[N + i]));
-                pz = xadd(pz, xmulf(hh, F[2 * N + i]));
+                S px = load_slot<S>(mom + i), py = load_slot<S>(mom + N + i), pz = load_slot<S>(mom + 2 * N + i);
+                const R4 f = F4[i];
+                px = xadd(px, xmulf(hh, f.x));
+                py = xadd(py, xmulf(hh, f.y));
+                pz = xadd(pz, xmulf(hh, f.z));
                 px = xmul(px, cxh); pz = xmul(pz, czh);
                 px = xmul(px, c); py = xmul(py, c); pz = xmul(pz, c);
-                store_slot(st + 3 * N + i, px); store_slot(st + 4 * N + i, py); store_slot(st + 5 * N + i, pz);
+                store_slot(mom + i, px); store_slot(mom + N + i, py); store_slot(mom + 2 * N + i, pz);
             }
         }
         R k2, bk;
-        kin_partial(k2, bk);
+        kin_partial(k2, bk, true);
         S sums[2];
-        cta_sum2(k2, bk + (R)0.5 * wd, sums);
+        cta_sum2(k2, bk, sums);
         steps_run++;
         if (tid == 0) {
             chain(sums[0]);
@@ -476,6 +568,7 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
             m->Lx = m->Lx1;
             m->Lz = m->Lz1;
             advance_box();
+            advance_lists();
             if (m->flag_lost || !isfinite(bv) || !isfinite(sdbl(sums[0]))) m->stop |= TTCF_D_NONFINITE;
             if (a.abort_flag && (s & 63) == 0 && *a.abort_flag) m->stop |= TTCF_D_ABORTED;
         }
@@ -487,7 +580,7 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
     __syncthreads();
     if (tid == 0) {
         b.pairs[d] += m->pairs;   // ordered pairs, as the other kernels count them
-        b.rebuilds[d] += (unsigned int)steps_run;
+        b.rebuilds[d] += (unsigned int)m->n_build;
         if (m->stop) b.status[d] |= m->stop;
         if (a.save_state) {
             unsigned long long *sc = reinterpret_cast<unsigned long long *>(b.scal) + 4 * (size_t)d;
@@ -498,7 +591,12 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
     }
     if (a.save_state) {
         unsigned long long *dst = b.state + (size_t)d * 6 * N;
-        for (int e = tid; e < 6 * N; e += T) dst[e] = st[e];
+        for (int i = tid; i < N; i += T) {
+            S x, y, z;
+            ld_pos(i, x, y, z);
+            store_slot(dst + i, x); store_slot(dst + N + i, y); store_slot(dst + 2 * N + i, z);
+            dst[3 * N + i] = mom[i]; dst[4 * N + i] = mom[N + i]; dst[5 * N + i] = mom[2 * N + i];
+        }
     }
 }
 
@@ -514,22 +612,23 @@ __global__ void __launch_bounds__(512, 2) elong_kernel(const ElongArgs a) {
 
 }  // namespace
 
-cudaError_t launch_elong(bool mixed, const ElongArgs &a, int nsm, cudaStream_t st, int *grid_out) {
+int elong_grid(bool mixed, int N, int ncellmax, int nsm, long long D) {
+    const size_t smem = elong_smem_bytes(mixed, N, ncellmax);
+    auto fn = mixed ? elong_kernel<true> : elong_kernel<false>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, elong_threads(N), smem) != cudaSuccess) return 0;
+    return (int)std::min<long long>(D, (long long)nsm * per_sm);
+}
+
+cudaError_t launch_elong(bool mixed, const ElongArgs &a, int grid, cudaStream_t st) {
     const int ncm = a.ncmax[0] * a.ncmax[1] * a.ncmax[2];
     const size_t smem = elong_smem_bytes(mixed, a.b.N, ncm);
-    const int T = elong_threads(a.b.N);
     auto fn = mixed ? elong_kernel<true> : elong_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const long long D = (long long)a.b.G * a.b.M;
-    const long long g = std::min<long long>(D, (long long)nsm * per_sm);
-    if (grid_out) *grid_out = (int)g;
-    if (g <= 0) return cudaSuccess;
-    fn<<<(unsigned)g, T, smem, st>>>(a);
+    if (grid <= 0) return cudaSuccess;
+    fn<<<(unsigned)grid, elong_threads(a.b.N), smem, st>>>(a);
     return cudaGetLastError();
 }
 

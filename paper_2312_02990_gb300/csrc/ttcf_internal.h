@@ -15,8 +15,11 @@ int daughter_occupancy(bool mixed, int variant, int threads, size_t smem);
 
 // daughters under planar elongational flow (ttcf_elong.cu): one CTA per
 // daughter of one batch (gamma holds the elongation rates), persistent over
-// the batch; the cell grid of each step has at most ncmax[k] cells along
-// axis k (the bound of the largest box the run reaches).
+// the batch; Verlet lists of radius r_c + skin, built on cell grids of at
+// most ncmax[k] cells along axis k (the bound of the largest box the run
+// reaches), ELONG_CAP entries per atom in a [grid][ELONG_CAP][N] scratch.
+constexpr int ELONG_CAP = 32;
+constexpr double ELONG_SKIN = 0.35;
 struct ElongArgs {
     BatchDev b;
     int step0, step1;              // run absolute steps step0+1 .. step1
@@ -25,12 +28,16 @@ struct ElongArgs {
     int save_state;                // write the loop state at step1
     int reset_alpha;
     int ncmax[3];
+    float skin;
     double dt;
+    unsigned short *nbr;           // Verlet list scratch [grid][ELONG_CAP][N]
     const volatile int *abort_flag;  // host-mapped, may be null
 };
 size_t elong_smem_bytes(bool mixed, int N, int ncellmax);
 int elong_threads(int N);
-cudaError_t launch_elong(bool mixed, const ElongArgs &a, int nsm, cudaStream_t st, int *grid_out);
+// CTAs of a launch over D daughters (0 if one does not fit)
+int elong_grid(bool mixed, int N, int ncellmax, int nsm, long long D);
+cudaError_t launch_elong(bool mixed, const ElongArgs &a, int grid, cudaStream_t st);
 
 // momentum kicks of copies of one phase point (ttcf_kick.cu)
 struct KickArgs {

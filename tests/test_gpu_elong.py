@@ -127,9 +127,9 @@ def test_affine_crystal_follows_the_closed_form(ttcf, precision, tol):
 
 def test_two_cells_along_the_compressed_axis(ttcf):
     """N = 108 at eps = 0.5 for 400 steps: the z edge shrinks from 5.04 to
-    3.06, below three cells of r_c, so the grid has two cells along z and
-    the force pass visits each under two shifts (FP64 against the oracle,
-    which takes every image there)."""
+    3.06, so the list cells (at least r_c + skin wide) number two along z
+    and the list build scans each of them once at the minimum image (FP64
+    against the oracle, which takes every image there)."""
     N, eps, n = 108, 0.5, 400
     b = oracle.Bulk(n=N, L=tuple(inputs.bulk_box(N)))
     ms, al = oracle.mother(b, inputs.initial_state(N, 3), 2000, 1, 10)
@@ -146,6 +146,27 @@ def test_two_cells_along_the_compressed_axis(ttcf):
         dx = states[d][0][:3] - fin[:3]
         dx -= Lt * np.rint(dx / Lt)
         assert np.abs(dx).max() < 1e-9, d
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_odd_atom_count(ttcf, precision):
+    """N = 255 (one atom taken out of a 256-atom state): with an odd N the
+    momentum slots end off a 16-byte boundary, which the shared-memory
+    layout pads for the float4 and double arrays behind them."""
+    N = 255
+    L = tuple(inputs.bulk_box(256))
+    b = oracle.Bulk(n=N, L=L)
+    st = np.ascontiguousarray(inputs.jittered_states(256, 1, seed=23, amp=0.1)[:, :, 1:])
+    eps, n = 0.1, 30
+    with ctx(ttcf, precision=precision, n_steps=n) as c:
+        bid = c.spawn_daughters(st, None, eps, box=b.L)
+        c.run()
+        B, _ = c.daughter_series(bid, 4)
+        stat = c.group_status(bid, 1)
+    assert np.all(stat == 0)
+    for d in range(4):
+        Bo = oracle.daughter_elong(b, st[0], 0.0, ELONG_SET[d], eps, n)[0]
+        assert np.abs(B[d] - Bo).max() < (1e-9 if precision == 0 else 1e-4) * np.abs(Bo).max(), d
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -177,6 +198,8 @@ def test_mixed_ensemble_within_two_standard_errors(ttcf, eq_mothers_256):
         c.run()
         r = c.response(bid)
         v = c.viscosity(bid)
+        st = c.get_stats()
+    assert st["rebuilds"] > 2 * 4 * len(ms)   # the lists were rebuilt along the way
     for k in ("dav", "ttcf"):
         for s in (100, 200, 300):
             se = np.hypot(r[k + "_se"][s], ro[k + "_se"][s])
