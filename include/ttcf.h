@@ -78,9 +78,11 @@ typedef enum {
  *                    {0, 1, 16, 17} (mapping_mask 0x30003) cancels
  *                    <Omega(0)> per group.  One CTA per daughter with the
  *                    whole daughter in shared memory (N up to about 2200
- *                    in MIXED, 1500 in FP64); use_graph, skin,
- *                    kernel_variant, block_threads and cell_frac do not
- *                    apply; the control variate is not available.  The
+ *                    in MIXED, 1900 in FP64) and its Verlet lists (skin
+ *                    0.35, less where the compressed edge needs it) in a
+ *                    global scratch; use_graph, skin, kernel_variant,
+ *                    block_threads and cell_frac do not apply; the
+ *                    control variate is not available.  The
  *                    equilibrium tools (ttcf_sample_mothers,
  *                    ttcf_mother_acf, ttcf_forces) work as in
  *                    TTCF_BULK_WCA.                                     */

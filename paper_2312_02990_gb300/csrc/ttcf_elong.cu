@@ -157,7 +157,8 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
     const int map = b.maps[d % b.M];
     const double eps = b.gamma[gl];
     const int ncm = a.ncmax[0] * a.ncmax[1] * a.ncmax[2];
-    unsigned short *nb = a.nbr + (size_t)blockIdx.x * ELONG_CAP * N;   // [ELONG_CAP][N] lists
+    // the CTA's lists: [ELONG_CAP / 8][N] groups of 8 uint16 entries
+    uint4 *nb4 = reinterpret_cast<uint4 *>(a.nbr + (size_t)blockIdx.x * ELONG_CAP * N);
 
     // shared-memory carve-up (elong_smem_bytes mirrors it)
     unsigned char *sp = smem;
@@ -411,7 +412,15 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
                     }
                 }
             }
-            for (int e = 0; e < n; e++) nb[(size_t)e * N + k] = lst[e];
+            for (int w = 0; w * 8 < n; w++) {   // 16-byte groups of 8 entries
+                unsigned int q[4];
+                for (int hw = 0; hw < 4; hw++) {
+                    const int e0 = w * 8 + 2 * hw;
+                    const unsigned int lo = e0 < n ? lst[e0] : 0u, hi = e0 + 1 < n ? lst[e0 + 1] : 0u;
+                    q[hw] = lo | (hi << 16);
+                }
+                nb4[(size_t)w * N + k] = make_uint4(q[0], q[1], q[2], q[3]);
+            }
             cntl[k] = (unsigned char)n;
             if (over) atomicOr(&m->stop, TTCF_D_NBR_OVERFLOW);
         }
@@ -430,8 +439,7 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
             const R4 pi = pos_r(i);
             const int n = cntl[k];
             R fx = (R)0, fy = (R)0, fz = (R)0, wv = (R)0;
-            for (int e = 0; e < n; e++) {
-                const int j = nb[(size_t)e * N + k];
+            auto pair = [&](int j) {
                 const R4 pj = pos_r(j);
                 const R dx = mimg(rsub(pi.x, pj.x), ilx, Lx);
                 const R dy = mimg(rsub(pi.y, pj.y), ily, Ly);
@@ -444,6 +452,19 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
                     fx = rfma(f, dx, fx); fy = rfma(f, dy, fy); fz = rfma(f, dz, fz);
                     wv = rfma(f, rsub(rmul(dx, dx), rmul(dz, dz)), wv);
                     npair++;
+                }
+            };
+            // one 16-byte group of 8 entries per load, the next one in
+            // flight while the current one is worked on
+            uint4 q = n > 0 ? nb4[k] : make_uint4(0u, 0u, 0u, 0u);
+            for (int w = 0; w * 8 < n; w++) {
+                const uint4 cur = q;
+                if ((w + 1) * 8 < n) q = nb4[(size_t)(w + 1) * N + k];
+                const int m8 = min(8, n - w * 8);
+                for (int hw = 0; 2 * hw < m8; hw++) {
+                    const unsigned int word = hw == 0 ? cur.x : hw == 1 ? cur.y : hw == 2 ? cur.z : cur.w;
+                    pair((int)(word & 0xFFFFu));
+                    if (2 * hw + 1 < m8) pair((int)(word >> 16));
                 }
             }
             R4 o;
@@ -484,94 +505,92 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
         open_step(inc);
     };
 
-    // ---- lists, forces and sum p^2 at the starting point ----
+    // ---- the steps.  Pass s = step0 only builds the lists and takes the
+    //      forces and sum p^2 at the starting point, so that every force,
+    //      list and sum is computed by one copy of the code (the same
+    //      roundings in a chunked run as in an uninterrupted one) ----
     __syncthreads();
-    build_lists();
-    force_pass();
-    npair = 0;   // counted over the steps only
-    {
+    int steps_run = 0;
+    for (int s = a.step0; s <= a.step1 && !m->stop; s++) {
+        const bool first = s == a.step0;
+        if (!first) {
+            // ---- D, C', B half flows, A' drift into the box of step s (Lx1,
+            //      Lz1), displacement beyond the affine flow since the lists ----
+            {
+                const S c = m->c, cxh = m->cxh, czh = m->czh, hh = m->hh;
+                const S ex = m->ex, ez = m->ez, phx = m->phx, phz = m->phz, h = m->h;
+                const S Lx = m->Lx1, Lz = m->Lz1, hLx = m->hLx1, hLz = m->hLz1, Ly = m->Ly, hLy = m->hLy;
+                const float fxa = m->fxa, fza = m->fza;
+                const float Lxf = m->Lf[0], Lyf = m->Lf[1], Lzf = m->Lf[2];
+                const float ilx = m->invLf[0], ily = m->invLf[1], ilz = m->invLf[2];
+                float umax = 0.f;
+                for (int i = tid; i < N; i += T) {
+                    S px = load_slot<S>(mom + i), py = load_slot<S>(mom + N + i), pz = load_slot<S>(mom + 2 * N + i);
+                    const R4 f = F4[i];
+                    px = xmul(px, c); py = xmul(py, c); pz = xmul(pz, c);
+                    px = xmul(px, cxh); pz = xmul(pz, czh);
+                    px = xadd(px, xmulf(hh, f.x));
+                    py = xadd(py, xmulf(hh, f.y));
+                    pz = xadd(pz, xmulf(hh, f.z));
+                    S x, y, z;
+                    ld_pos(i, x, y, z);
+                    x = wrap_once(xadd(xmul(x, ex), xmul(px, phx)), Lx, hLx);
+                    y = wrap_once(xadd(y, xmul(py, h)), Ly, hLy);
+                    z = wrap_once(xadd(xmul(z, ez), xmul(pz, phz)), Lz, hLz);
+                    st_pos(i, x, y, z);
+                    store_slot(mom + i, px); store_slot(mom + N + i, py); store_slot(mom + 2 * N + i, pz);
+                    const float4 r0 = ref4[i];
+                    float ux = (float)shi(x) - fxa * r0.x, uy = (float)shi(y) - r0.y, uz = (float)shi(z) - fza * r0.z;
+                    ux -= Lxf * rintf(ux * ilx); uy -= Lyf * rintf(uy * ily); uz -= Lzf * rintf(uz * ilz);
+                    const float u2 = ux * ux + uy * uy + uz * uz;
+                    if (!(u2 <= umax) && umax == umax) umax = u2;   // a NaN stays and forces a rebuild
+                }
+                if (umax > 0.f || umax != umax) atomicMax(&m->umax2, __float_as_uint(umax));
+            }
+        }
+        __syncthreads();
+        if (first || m->rebuild || __uint_as_float(m->umax2) >= m->thr2 || m->umax2 > 0x7f800000u)
+            build_lists();
+        force_pass();
+        if (first) npair = 0;   // counted over the steps only
+        else {
+            // ---- B, C', D half flows with the new forces ----
+            {
+                const S c = m->c, cxh = m->cxh, czh = m->czh, hh = m->hh;
+                for (int i = tid; i < N; i += T) {
+                    S px = load_slot<S>(mom + i), py = load_slot<S>(mom + N + i), pz = load_slot<S>(mom + 2 * N + i);
+                    const R4 f = F4[i];
+                    px = xadd(px, xmulf(hh, f.x));
+                    py = xadd(py, xmulf(hh, f.y));
+                    pz = xadd(pz, xmulf(hh, f.z));
+                    px = xmul(px, cxh); pz = xmul(pz, czh);
+                    px = xmul(px, c); py = xmul(py, c); pz = xmul(pz, c);
+                    store_slot(mom + i, px); store_slot(mom + N + i, py); store_slot(mom + 2 * N + i, pz);
+                }
+            }
+        }
         R k2, bk;
-        kin_partial(k2, bk, false);
+        kin_partial(k2, bk, !first);
         S sums[2];
-        cta_sum2(k2, (R)0, sums);
+        cta_sum2(k2, bk, sums);
         if (tid == 0) {
-            open_step(e_increment(sums[0]));   // the first step's opening E flow
+            if (first) {
+                open_step(e_increment(sums[0]));   // the first step's opening E flow
+            } else {
+                chain(sums[0]);
+                const double bv = sdbl(sums[1]) * m->invV;   // P_xx - P_zz
+                if (s % a.sample_every == 0) b.B[(size_t)d * b.S + s / a.sample_every] = bv;
+                if (!isfinite(bv)) m->stop |= TTCF_D_NONFINITE;
+                // the positions now live in the box of step s
+                m->Lx = m->Lx1;
+                m->Lz = m->Lz1;
+            }
             advance_box();
             advance_lists();
             if (m->flag_lost || !isfinite(sdbl(sums[0]))) m->stop |= TTCF_D_NONFINITE;
-        }
-    }
-    __syncthreads();
-
-    int steps_run = 0;
-    for (int s = a.step0 + 1; s <= a.step1 && !m->stop; s++) {
-        // ---- D, C', B half flows, A' drift into the box of step s (Lx1,
-        //      Lz1), displacement beyond the affine flow since the lists ----
-        {
-            const S c = m->c, cxh = m->cxh, czh = m->czh, hh = m->hh;
-            const S ex = m->ex, ez = m->ez, phx = m->phx, phz = m->phz, h = m->h;
-            const S Lx = m->Lx1, Lz = m->Lz1, hLx = m->hLx1, hLz = m->hLz1, Ly = m->Ly, hLy = m->hLy;
-            const float fxa = m->fxa, fza = m->fza;
-            const float Lxf = m->Lf[0], Lyf = m->Lf[1], Lzf = m->Lf[2];
-            const float ilx = m->invLf[0], ily = m->invLf[1], ilz = m->invLf[2];
-            float umax = 0.f;
-            for (int i = tid; i < N; i += T) {
-                S px = load_slot<S>(mom + i), py = load_slot<S>(mom + N + i), pz = load_slot<S>(mom + 2 * N + i);
-                const R4 f = F4[i];
-                px = xmul(px, c); py = xmul(py, c); pz = xmul(pz, c);
-                px = xmul(px, cxh); pz = xmul(pz, czh);
-                px = xadd(px, xmulf(hh, f.x));
-                py = xadd(py, xmulf(hh, f.y));
-                pz = xadd(pz, xmulf(hh, f.z));
-                S x, y, z;
-                ld_pos(i, x, y, z);
-                x = wrap_once(xadd(xmul(x, ex), xmul(px, phx)), Lx, hLx);
-                y = wrap_once(xadd(y, xmul(py, h)), Ly, hLy);
-                z = wrap_once(xadd(xmul(z, ez), xmul(pz, phz)), Lz, hLz);
-                st_pos(i, x, y, z);
-                store_slot(mom + i, px); store_slot(mom + N + i, py); store_slot(mom + 2 * N + i, pz);
-                const float4 r0 = ref4[i];
-                float ux = (float)shi(x) - fxa * r0.x, uy = (float)shi(y) - r0.y, uz = (float)shi(z) - fza * r0.z;
-                ux -= Lxf * rintf(ux * ilx); uy -= Lyf * rintf(uy * ily); uz -= Lzf * rintf(uz * ilz);
-                const float u2 = ux * ux + uy * uy + uz * uz;
-                if (!(u2 <= umax) && umax == umax) umax = u2;   // a NaN stays and forces a rebuild
-            }
-            if (umax > 0.f || umax != umax) atomicMax(&m->umax2, __float_as_uint(umax));
-        }
-        __syncthreads();
-        if (m->rebuild || __uint_as_float(m->umax2) >= m->thr2 || m->umax2 > 0x7f800000u) build_lists();
-        force_pass();
-        // ---- B, C', D half flows with the new forces ----
-        {
-            const S c = m->c, cxh = m->cxh, czh = m->czh, hh = m->hh;
-            for (int i = tid; i < N; i += T) {
-                S px = load_slot<S>(mom + i), py = load_slot<S>(mom + N + i), pz = load_slot<S>(mom + 2 * N + i);
-                const R4 f = F4[i];
-                px = xadd(px, xmulf(hh, f.x));
-                py = xadd(py, xmulf(hh, f.y));
-                pz = xadd(pz, xmulf(hh, f.z));
-                px = xmul(px, cxh); pz = xmul(pz, czh);
-                px = xmul(px, c); py = xmul(py, c); pz = xmul(pz, c);
-                store_slot(mom + i, px); store_slot(mom + N + i, py); store_slot(mom + 2 * N + i, pz);
-            }
-        }
-        R k2, bk;
-        kin_partial(k2, bk, true);
-        S sums[2];
-        cta_sum2(k2, bk, sums);
-        steps_run++;
-        if (tid == 0) {
-            chain(sums[0]);
-            const double bv = sdbl(sums[1]) * m->invV;   // P_xx - P_zz
-            if (s % a.sample_every == 0) b.B[(size_t)d * b.S + s / a.sample_every] = bv;
-            // the positions now live in the box of step s
-            m->Lx = m->Lx1;
-            m->Lz = m->Lz1;
-            advance_box();
-            advance_lists();
-            if (m->flag_lost || !isfinite(bv) || !isfinite(sdbl(sums[0]))) m->stop |= TTCF_D_NONFINITE;
             if (a.abort_flag && (s & 63) == 0 && *a.abort_flag) m->stop |= TTCF_D_ABORTED;
         }
+        if (!first) steps_run++;
         __syncthreads();
     }
 
