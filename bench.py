@@ -19,10 +19,10 @@ e2e    = the same through the C ABI with host buffers: mothers copied from
          region.
 
 The last stdout line is the compact result (one JSON object of < 2 KB).
-The long sections (confined channel, uneven batch, control variate,
-precision floor, Green-Kubo, momentum kicks, mapping study, plain GPU arm,
-oracle parity sample) are printed before it, one JSON line each, or written
-to the file given by --sections-out.
+The long sections (confined channel, uneven batch, planar elongational
+flow, control variate, precision floor, Green-Kubo, momentum kicks, mapping
+study, plain GPU arm, oracle parity sample) are printed before it, one JSON
+line each, or written to the file given by --sections-out.
 
 Launch:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs the same per-GPU workload on its own mothers
