@@ -218,3 +218,27 @@ def test_rejects_a_rate_that_would_collapse_the_box(ttcf):
             c.spawn_daughters(st, None, 1.0, box=inputs.bulk_box(N))
         with pytest.raises(ttcf.TTCFError):
             c.spawn_daughters(st, None, -1.0, box=inputs.bulk_box(N))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_continues_bitwise(ttcf, eq_mothers_256, tmp_path, precision):
+    """An elongational run written to disk after 30 of 80 steps and continued
+    in a new context (which recomputes the list bounds and skin from the
+    saved box and rates) gives bitwise the uninterrupted series."""
+    b, ms, al = eq_mothers_256
+    rates = np.array([0.1, -0.05])
+    kw = dict(precision=precision, n_steps=80)
+    with ctx(ttcf, **kw) as c:
+        bid = c.spawn_daughters(ms[:2], al[:2], rates, box=b.L)
+        c.run()
+        B_ref, Om_ref = c.daughter_series(bid, 8)
+    path = str(tmp_path / "elong.ckpt")
+    with ctx(ttcf, **kw) as c:
+        c.spawn_daughters(ms[:2], al[:2], rates, box=b.L)
+        c.run(30)
+        c.save(path)
+    with ctx(ttcf, **kw) as c:
+        c.load(path)
+        c.run()
+        B, Om = c.daughter_series(0, 8)
+    assert np.array_equal(B, B_ref) and np.array_equal(Om, Om_ref)
