@@ -480,7 +480,8 @@ ttcf_status ttcf_load(ttcf_ctx *ctx, const char *path);
  * GPU that loads the library holds that array until the process exits).
  * No cudaMalloc, cudaFree or other allocating routine is called.
  *
- *  cfg            as for ttcf_create; stream, precision, dt, T, tau_T,
+ *  cfg            as for ttcf_create, system TTCF_BULK_WCA only (the
+ *                 sheared bulk fluid); stream, precision, dt, T, tau_T,
  *                 dof_mode, n_steps, sample_every, mapping_mask,
  *                 reset_alpha, skin, kernel_variant, block_threads,
  *                 cell_frac are used (with the same defaults as a context
