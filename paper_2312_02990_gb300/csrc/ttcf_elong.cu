@@ -454,6 +454,31 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
                     npair++;
                 }
             };
+            // MIXED: the two entries of a list word side by side on packed
+            // FP32 pairs (each lane the same IEEE operations as the scalar
+            // pass), accumulated in index order
+            auto pair2 = [&](int j0, int j1, bool has1) {
+                const float4 p0 = pos4[j0], p1 = pos4[has1 ? j1 : j0];
+                float2 dx = sub2(f2((float)pi.x), make_float2(p0.x, p1.x));
+                float2 dy = sub2(f2((float)pi.y), make_float2(p0.y, p1.y));
+                float2 dz = sub2(f2((float)pi.z), make_float2(p0.z, p1.z));
+                dx = __ffma2_rn(neg2(rint2(dx, f2(ilx))), f2((float)Lx), dx);
+                dy = __ffma2_rn(neg2(rint2(dy, f2(ily))), f2((float)Ly), dy);
+                dz = __ffma2_rn(neg2(rint2(dz, f2(ilz))), f2((float)Lz), dz);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const bool in0 = r2.x < (float)rc2, in1 = has1 && r2.y < (float)rc2;
+                if (in0 || in1) {
+                    const float2 s = make_float2(in0 ? 1.f / r2.x : 0.f, in1 ? 1.f / r2.y : 0.f);
+                    const float2 s3 = __fmul2_rn(__fmul2_rn(s, s), s);
+                    const float2 f = __fmul2_rn(__fmul2_rn(s, s3), __ffma2_rn(f2(48.f), s3, f2(-24.f)));
+                    const float2 w2 = sub2(__fmul2_rn(dx, dx), __fmul2_rn(dz, dz));
+                    fx = rfma((R)f.x, (R)dx.x, fx); fy = rfma((R)f.x, (R)dy.x, fy);
+                    fz = rfma((R)f.x, (R)dz.x, fz); wv = rfma((R)f.x, (R)w2.x, wv);
+                    fx = rfma((R)f.y, (R)dx.y, fx); fy = rfma((R)f.y, (R)dy.y, fy);
+                    fz = rfma((R)f.y, (R)dz.y, fz); wv = rfma((R)f.y, (R)w2.y, wv);
+                    npair += (unsigned int)in0 + (unsigned int)in1;
+                }
+            };
             // one 16-byte group of 8 entries per load, the next one in
             // flight while the current one is worked on
             uint4 q = n > 0 ? nb4[k] : make_uint4(0u, 0u, 0u, 0u);
@@ -463,8 +488,12 @@ __device__ void elong_daughter(const ElongArgs &a, int d, unsigned char *smem) {
                 const int m8 = min(8, n - w * 8);
                 for (int hw = 0; 2 * hw < m8; hw++) {
                     const unsigned int word = hw == 0 ? cur.x : hw == 1 ? cur.y : hw == 2 ? cur.z : cur.w;
-                    pair((int)(word & 0xFFFFu));
-                    if (2 * hw + 1 < m8) pair((int)(word >> 16));
+                    if constexpr (MIXED) {
+                        pair2((int)(word & 0xFFFFu), (int)(word >> 16), 2 * hw + 1 < m8);
+                    } else {
+                        pair((int)(word & 0xFFFFu));
+                        if (2 * hw + 1 < m8) pair((int)(word >> 16));
+                    }
                 }
             }
             R4 o;
