@@ -106,8 +106,9 @@ def parse():
     p.add_argument("--no-mapstudy", action="store_true", help="skip the mapping-set / Eq. 4 study")
     p.add_argument("--no-probe", action="store_true", help="skip the FP32 throughput probe")
     p.add_argument("--no-elong", action="store_true", help="skip the planar elongational flow section")
-    p.add_argument("--elong-chains", type=int, default=256)
-    p.add_argument("--elong-states", type=int, default=16)
+    p.add_argument("--elong-chains", type=int, default=256,
+                   help="independent N=256 mother chains of the elongational section")
+    p.add_argument("--elong-states", type=int, default=16, help="mother states per chain")
     p.add_argument("--only", default=None,
                    help="run one section alone and print its JSON (confined, uneven, cv, floor, "
                         "gk, kick, mapstudy, probe, elong)")
