@@ -148,3 +148,20 @@ def test_ensemble_driver_matches_single_daughters():
         Bd, od, _, _ = oracle.daughter_elong(b, ms[g], a0, ELONG_SET[m], [0.05, -0.05][g], 20,
                                              sample_every=5)
         assert np.array_equal(B[d], Bd) and Om[d] == od
+
+
+def test_elongational_ttcf_reduces_to_green_kubo_at_weak_field(eq_mothers_256):
+    """At eps -> 0, Eq. 1 with Omega(0) = -eps V B(0)/T and the mapped set's
+    <B(0)> = 0 gives eta_1(t) = (V / 4T) int_0^t <B(0) B(s)> ds, the
+    Green-Kubo integral of B = P_xx - P_zz along the zero-field trajectories
+    of the same mapped states (a wrong sign or factor of Omega, or of the
+    1/(4 eps) of eta_1, fails it)."""
+    b, ms, al = eq_mothers_256
+    n, eps = 120, 1e-8
+    B, Om = oracle.daughters_elong(b, ms[:16], al[:16], eps, n)
+    eta1 = -oracle.responses(B, Om, 4, b.dt)["ttcf"] / (4.0 * eps)
+    B0, _ = oracle.daughters_elong(b, ms[:16], al[:16], 0.0, n)
+    acf = (B0[:, :1] * B0).mean(axis=0)
+    gk = b.V / (4.0 * b.T) * np.concatenate([[0.0], np.cumsum(0.5 * b.dt * (acf[1:] + acf[:-1]))])
+    assert np.abs(gk).max() > 0.1
+    assert np.allclose(eta1[1:], gk[1:], rtol=1e-5, atol=1e-7 * np.abs(gk).max())
